@@ -1,0 +1,69 @@
+/*
+ * oracle.h -- CPU oracle of the batched limit-order-book environment step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg may load this library.  It shares no
+ * code, header, table or helper with the CUDA engine; both read the same
+ * message bytes written by the input generator.
+ *
+ * What it computes (JaxMARL-HFT, Sec. 4 "Design", the five stages of one
+ * environment step): action conversion with carry-over cancels, a random
+ * shuffle of the agents' new orders, concatenation (agent cancels, agent
+ * orders, then the step's background messages), price-time-priority matching
+ * (the continuous double auction of Sec. 2.1) and the step outcomes
+ * (observations, portfolio-value rewards per Eq. 1, termination flags).
+ * Points the paper leaves open are fixed by the readings listed beside each
+ * function in oracle.cpp.
+ */
+#ifndef LOB_ORACLE_H
+#define LOB_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NCOUNTERS 16
+
+typedef struct orc_config {
+    int32_t n_envs;
+    int32_t n_agents;     /* 0 (pure replay) or 2 (agent 0 executes, agent 1 makes markets) */
+    int32_t cap;          /* book capacity per side when no per-env array is given */
+    int32_t top_levels;   /* L aggregated levels per side in the observation */
+    int32_t episode_len;  /* T */
+    int32_t mm_lot;
+    int32_t exec_target;
+    int32_t exec_dir;     /* -1 sell task, +1 buy task */
+    int32_t action_mode;  /* 0: actions given per step, 1: seeded uniform random policy */
+    int32_t trace;        /* bit0: keep the step's fill log; bit1: book snapshot of env 0 after every message */
+    int32_t start_px;     /* reference price before the first trade */
+    int32_t n_threads;
+} orc_config;
+
+void   *orc_create(const orc_config *cfg, const int32_t *caps /* [n_envs] or NULL */);
+void    orc_destroy(void *h);
+void    orc_reset(void *h, const uint64_t *env_seeds);
+/* One env step for every env.  Env e's background messages of this step are
+ * msgs[offsets[e*stride + k] .. offsets[e*stride + k + 1]).  Returns 0, or -6
+ * when some message was malformed (it is skipped and counted). */
+int     orc_step(void *h, const int32_t *actions, const void *msgs, const int64_t *offsets,
+                 int64_t stride, int32_t k);
+void    orc_observe(void *h, float *obs, int64_t *rewards, uint8_t *done);
+int32_t orc_obs_dim(void *h);
+void    orc_get_book(void *h, int64_t env, int32_t *n2, int32_t *px, int32_t *qty, int64_t *id, int64_t *ts);
+void    orc_get_counters(void *h, int64_t *out);
+void    orc_get_agents(void *h, int64_t *out);
+void    orc_get_env_misc(void *h, int64_t *out);
+void    orc_get_actions(void *h, int32_t *out);
+int64_t orc_get_fills(void *h, int64_t env, void *out, int64_t cap);
+int64_t orc_get_snapshots(void *h, void *out, int64_t cap);
+/* The random-policy action and shuffle draws, exposed so tests can pin them. */
+uint64_t orc_draw(uint64_t env_seed, int64_t t, uint64_t tag, int64_t i);
+uint32_t orc_lemire(uint64_t x, uint32_t n);
+/* i-th (0-based) output of SplitMix64 started from `state`. */
+uint64_t orc_splitmix(uint64_t state, int64_t i);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,79 @@
+"""Oracle vs. a brute-force sorted-list book on tiny random inputs.
+
+Capacities of 1-8 per side and a narrow price band make every branch of the
+matcher fire (evictions, drops, sweeps to empty, partial cancels to zero,
+misses), and both agents act every step.
+"""
+import numpy as np
+import pytest
+
+import brute_lob
+import oracle
+from paper_2511_02136_gb300 import mbogen
+
+
+def _compare(o, b, env, step_fills):
+    n2, px, qty, oid, ts = o.book(env)
+    got = [[(int(px[s, j]), int(qty[s, j]), int(oid[s, j]), int(ts[s, j])) for j in range(n2[s])]
+           for s in range(2)]
+    assert got == b.book_arrays()
+    if step_fills is not None:
+        assert [tuple(int(v) for v in f) for f in step_fills] == [tuple(f) for f in b.fills]
+    cnt = dict(zip(oracle.COUNTER_NAMES, o.counters()[env].tolist()))
+    for k, v in b.c.items():
+        assert cnt[k] == v, k
+    assert cnt["bg_cash"] == b.bg_cash and cnt["bg_inv"] == b.bg_inv
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_oracle_matches_brute(seed):
+    rng = np.random.default_rng(seed)
+    cap = int(rng.integers(1, 9))
+    T = 10
+    n_env = 3
+    model = mbogen.MessageModel(price_p=float(rng.uniform(0.4, 0.8)), size_p=0.3,
+                                msgs_per_step=int(rng.integers(5, 30)),
+                                mix_market=float(rng.uniform(0.05, 0.3)))
+    seeds = mbogen.env_seeds(1000 + seed, n_env)
+    st = mbogen.generate(model, seeds, T)
+    host = seed % 2 == 0
+    kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)),
+              exec_target=int(rng.integers(5, 60)), exec_dir=int(rng.choice([-1, 1])),
+              start_px=10_000)
+    o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
+    o.reset(seeds)
+    o.load_messages(st.msgs, st.offsets)
+    brutes = [brute_lob.BruteEnv(cap, n_agents=2, seed=int(seeds[e]), action_mode=0 if host else 1, **kw)
+              for e in range(n_env)]
+    for t in range(T):
+        acts = rng.integers(0, 12, size=(n_env, 2)).astype(np.int32) if host else None
+        o.step(acts)
+        obs, rew, done = o.observe()
+        for e in range(n_env):
+            b = brutes[e]
+            msgs = st.msgs[st.offsets[e, t]:st.offsets[e, t + 1]]
+            b.step(msgs, None if acts is None else acts[e].tolist())
+            fl = o.fills(e)
+            _compare(o, b, e, [(f["maker_id"], f["taker_id"], f["px"], f["qty"], f["msg_idx"], f["taker_side"])
+                               for f in fl])
+            np.testing.assert_array_equal(obs[e], np.array(b.obs, np.float32))
+            assert rew[e].tolist() == b.rew
+            assert int(done[e]) == b.done
+            assert o.actions()[e].tolist() == b.acts
+
+
+def test_oracle_matches_brute_replay_only():
+    """No agents: the plain replay configuration."""
+    st = mbogen.generate(mbogen.MessageModel(price_p=0.6, size_p=0.2, msgs_per_step=200),
+                         mbogen.env_seeds(77, 1), 3)
+    for cap in (1, 4, 100):
+        o = oracle.Oracle(1, n_agents=0, cap=cap, episode_len=3, trace=1)
+        o.reset(st.seeds)
+        o.load_messages(st.msgs, st.offsets)
+        b = brute_lob.BruteEnv(cap, n_agents=0, episode_len=3)
+        for t in range(3):
+            o.step()
+            b.step(st.msgs[st.offsets[0, t]:st.offsets[0, t + 1]])
+            fl = o.fills(0)
+            _compare(o, b, 0, [(f["maker_id"], f["taker_id"], f["px"], f["qty"], f["msg_idx"], f["taker_side"])
+                               for f in fl])
