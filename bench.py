@@ -1,0 +1,365 @@
+"""Benchmark of the batched limit-order-book environment step on GB300.
+
+Workload (the 1,024-env configuration): 1,024 independent envs, book capacity
+100 per side, 100 synthetic market-by-order messages per env-step, 1,000-step
+episodes, two agents per env (execution + market making) acting from the
+seeded uniform random policy, top-10-level observations.  One bench step is
+one lob_step over all envs: load the books, convert actions (with carry-over
+cancels), shuffle, match the agents' and the background messages, compute
+observations / rewards / done, write the books back.
+
+Timing: every timed step is bracketed by CUDA events on the launching stream;
+a 256 MiB buffer is written between timed steps so the books and messages
+come from HBM, not L2 (the flush is outside the events).  The metric is MBO
+messages processed per second (background plus agent messages) and
+env-steps per second on one GPU.  ``--impl reference`` times the CPU oracle
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ENVS, CAP, M, T, L = 1024, 100, 100, 1000, 10
+EXEC_TARGET = 500
+METRIC = "MBO messages/sec and env-steps/sec on 1 GB300 (bit-exact vs oracle); % HBM roofline"
+WORKLOAD = "1024 envs x cap 100/side x 100 msgs/step, 1000-step episodes, 2 agents (exec 500-lot sell + MM), random policy, top-10 obs"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_record():
+    """ncu DRAM bytes per launch of the step kernel, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "k_env_steps_1024env_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    from paper_2511_02136_gb300 import lob
+    import hashlib
+    h = hashlib.sha256()
+    for src in lob._DEPS:
+        with open(src, "rb") as g:
+            h.update(g.read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def make_inputs(seed):
+    from paper_2511_02136_gb300 import mbogen
+    seeds = mbogen.env_seeds(seed, N_ENVS)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=M), seeds, T)
+    return seeds, st
+
+
+def run_gpu(args):
+    import torch
+    from paper_2511_02136_gb300 import lob
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lob.build()
+    seeds, st = make_inputs(1 + rank)
+    dev = torch.device("cuda", local)
+    msgs_d = torch.from_numpy(st.msgs.view(np.uint8)).to(dev)
+    off_d = torch.from_numpy(st.offsets).to(dev)
+    seeds_d = torch.from_numpy(seeds.view(np.int64).copy()).to(dev)
+    env = lob.LobEnv(N_ENVS, cap=CAP, top_levels=L, episode_len=T, exec_target=EXEC_TARGET,
+                     action_mode=lob.LOB_ACT_RANDOM, warps_per_block=args.wpb)
+    env.load_messages(msgs_d, off_d)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    state = {"t": T}
+
+    def next_step():
+        if state["t"] >= T:                       # new episode: reset + rebind (untimed)
+            env.reset(seeds_d)
+            env.load_messages(msgs_d, off_d)
+            state["t"] = 0
+        env.step()
+        state["t"] += 1
+
+    for _ in range(args.warmup):
+        next_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
+    def msgs_so_far():
+        return int(env.counters()[:, 0].sum().item())
+
+    msgs_total = -msgs_so_far()           # counters restart at every reset
+    launches0 = lob.lob_kernel_launches(env.h)
+    live_slots = []
+    clk = Clocks(local)
+    t_wall0 = time.perf_counter()
+    for i in range(K):
+        if state["t"] >= T:               # episode boundary: bank its messages, reset (untimed)
+            msgs_total += msgs_so_far()
+            env.reset(seeds_d)
+            env.load_messages(msgs_d, off_d)
+            state["t"] = 0
+        flush.fill_(i)
+        ev[i][0].record(stream)
+        env.step()
+        ev[i][1].record(stream)
+        state["t"] += 1
+        if i % 97 == 0:
+            live_slots.append(env.books_live())
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    msgs_total += msgs_so_far()
+    launches = lob.lob_kernel_launches(env.h) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    rc = env.sync()
+    if rc != 0:
+        raise RuntimeError(f"device status {lob.lob_strerror(rc)}")
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = tt.item()
+        mt = torch.tensor([float(msgs_total)], device=dev)
+        dist.all_reduce(mt, op=dist.ReduceOp.SUM)
+        msgs_total = mt.item()
+    env_steps = K * N_ENVS * world
+    value = msgs_total / total_s
+    # algorithmic bytes per launch (one launch per step): messages, book
+    # load + store of the live slots, per-env scalars, counters, seed,
+    # offsets, observations, rewards, done
+    live = float(np.mean(live_slots))
+    D = env.D
+    per_env = (M * 32 + 2 * 24 * live + 2 * 128 + 2 * 16 * 8 + 8 + 16 + 2 * (4 * D + 8) + 1)
+    alg_bytes = per_env * N_ENVS
+    peak, peak_kind = _peaks()
+    mean_step_s = total_s / K
+    achieved = alg_bytes / mean_step_s / 1e9
+    traffic = _traffic_record()
+
+    e2e = run_e2e(args, env, st, seeds_d) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(seeds, st, budget_s=args.cpu_seconds)
+    env.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * mean_step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "env_steps_per_s": env_steps / total_s,
+            "config": {"workload": WORKLOAD, "n_envs": N_ENVS, "cap_per_side": CAP, "msgs_per_step": M,
+                       "episode_len": T, "top_levels": L, "global_batch": N_ENVS * world,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "timing": "CUDA events per step on the launching stream, summed"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                         "kernel": "k_env_steps<4>", "alg_bytes_per_launch": alg_bytes,
+                         "mean_live_slots_per_env": live},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
+            "wall_s": t_wall,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, env, st, seeds_d):
+    """Same metric through lob_step_host: pinned host messages in, obs/rewards/done out, every step."""
+    import torch
+    from paper_2511_02136_gb300 import lob
+    K = min(args.e2e_steps, T)
+    env.reset(seeds_d)
+    # per-step host slices: messages of every env for step t, packed, plus offsets
+    packs = []
+    for t in range(K):
+        lo = st.offsets[:, t]
+        hi = st.offsets[:, t + 1]
+        idx = np.concatenate([np.arange(a, b) for a, b in zip(lo, hi)])
+        pm = torch.from_numpy(st.msgs[idx].view(np.uint8)).pin_memory()
+        off = np.zeros(N_ENVS + 1, np.int64)
+        off[1:] = np.cumsum(hi - lo)
+        packs.append((pm, off))
+    D = env.D
+    obs = torch.zeros((N_ENVS, 2, D), dtype=torch.float32).pin_memory()
+    rew = torch.zeros((N_ENVS, 2), dtype=torch.int64).pin_memory()
+    done = torch.zeros(N_ENVS, dtype=torch.uint8).pin_memory()
+    h = env.h
+    lib = lob._load()
+    s = torch.cuda.current_stream().cuda_stream
+    msgs_before = int(env.counters()[:, 0].sum().item())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(K):
+        pm, off = packs[t]
+        rc = lib.lob_step_host(h, pm.data_ptr(), off.ctypes.data, None, obs.data_ptr(), rew.data_ptr(),
+                               done.data_ptr(), s)
+        if rc:
+            raise RuntimeError(lob.lob_strerror(rc))
+    el = time.perf_counter() - t0
+    msgs = env.counters()[:, 0].sum().item() - msgs_before
+    bi = int(np.mean([p[0].numel() + p[1].nbytes for p in packs]))
+    bo = obs.numel() * 4 + rew.numel() * 8 + done.numel()
+    return {"value": msgs / el, "unit": "msgs/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "steps": K, "env_steps_per_s": K * N_ENVS / el}
+
+
+def cpu_baseline(seeds, st, budget_s=15.0, n_threads=None):
+    """The oracle as it stands on the host cores: whole env steps of all envs until ~budget_s."""
+    import oracle
+    n_threads = n_threads or os.cpu_count() or 1
+    o = oracle.Oracle(N_ENVS, cap=CAP, top_levels=L, episode_len=T, exec_target=EXEC_TARGET,
+                      action_mode=1, n_threads=n_threads)
+    o.reset(seeds)
+    o.load_messages(st.msgs, st.offsets)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < T and time.perf_counter() - t0 < budget_s:
+        o.step()
+        steps += 1
+    el = time.perf_counter() - t0
+    msgs = int(o.counters()[:, 0].sum())
+    return {"value": msgs / el, "unit": "msgs/s", "cores": n_threads, "kind": "oracle",
+            "sample": f"all {N_ENVS} envs, first {steps} of {T} steps of the same episode",
+            "env_steps_per_s": steps * N_ENVS / el}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm, on the same workload and metric."""
+    rank, world = _dist()
+    if rank != 0:
+        return
+    seeds, st = make_inputs(1)
+    import oracle
+    n_threads = os.cpu_count() or 1
+    o = oracle.Oracle(N_ENVS, cap=CAP, top_levels=L, episode_len=T, exec_target=EXEC_TARGET,
+                      action_mode=1, n_threads=n_threads)
+    o.reset(seeds)
+    o.load_messages(st.msgs, st.offsets)
+    t = 0
+    for _ in range(args.warmup):
+        o.step()
+        t += 1
+    before = int(o.counters()[:, 0].sum())
+    K = min(args.steps, T - t)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        o.step()
+    el = time.perf_counter() - t0
+    msgs = int(o.counters()[:, 0].sum()) - before
+    value = msgs / el
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": world,
+           "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "env_steps_per_s": K * N_ENVS / el,
+           "config": {"workload": WORKLOAD, "n_envs": N_ENVS, "cap_per_side": CAP, "msgs_per_step": M},
+           "cpu_baseline": {"value": value, "unit": "msgs/s", "cores": n_threads, "kind": "oracle",
+                            "sample": f"all {N_ENVS} envs, steps {t}..{t + K - 1} of one episode"},
+           "e2e": {"value": value, "unit": "msgs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--wpb", type=int, default=0, help="warps per block (0 = library default)")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * lob.h -- C ABI of the GB300 batched limit-order-book environment (liblob.so).
+ *
+ * The library steps thousands of independent market environments at once, the
+ * environment step of JaxMARL-HFT Sec. 4 ("Design"):
+ *   1. action conversion: each agent's action becomes limit orders; the
+ *      agent's unmatched orders from the previous step are cancelled unless a
+ *      new order sits at the same price level (Sec. 4, "Action Conversion");
+ *   2. the agents' new orders are randomly shuffled (Sec. 4, "Random shuffling");
+ *   3. cancels, then the agents' orders, then the step's market-replay
+ *      messages are concatenated in that order (Sec. 4, "Augment with
+ *      market-replay messages");
+ *   4. a price-time-priority matching engine (Sec. 2.1) processes them and
+ *      records the trades (Sec. 4, "Processing by JAX-LOB");
+ *   5. rewards, termination flags and observations are computed (Sec. 4,
+ *      "Calculate step outcomes"; portfolio value per Eq. 1).
+ * Agent 0 is the order-execution agent (Sec. 4.1.2, 12 discrete actions:
+ * four reference prices x {1, 2, 5} lots); agent 1 is the market maker
+ * (Sec. 4.1.1, 12 discrete actions: one lot at the best bid/ask -/+ {0,1,2}
+ * ticks, or one tick into the spread on either side).  With n_agents = 0 the
+ * library is a plain market-replay engine.
+ *
+ * Conventions (every entry point):
+ *   - returns LOB_OK (0) or a negative LOB_E* code; lob_strerror() names it;
+ *   - pointers prefixed d_ are device pointers (any CUDA allocation on the
+ *     handle's device), h_ are host pointers; the caller owns every buffer it
+ *     passes and keeps it alive while work using it may run;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     device work is enqueued on it and the call returns without waiting,
+ *     except where a function says it synchronises;
+ *   - errors found on the device (a malformed message, an invalid action, a
+ *     bounded wait that expired) are recorded in the handle's status word and
+ *     returned by the next lob_sync() or lob_get_status();
+ *   - a handle is not thread-safe; handles are independent of each other.
+ */
+#ifndef LOB_H
+#define LOB_H
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LOB_OK          0
+#define LOB_EINVAL     (-1)  /* bad argument, or an action outside [0, 12) */
+#define LOB_ENOMEM     (-2)  /* device allocation failed */
+#define LOB_ECUDA      (-3)  /* a CUDA call failed */
+#define LOB_ETIMEOUT   (-4)  /* a bounded device wait expired */
+#define LOB_ECAPACITY  (-5)  /* a size exceeds what the handle or build supports */
+#define LOB_EBADMSG    (-6)  /* a message with unknown type/side or non-positive size (skipped) */
+#define LOB_ESTATE     (-7)  /* call out of order (no messages bound, window exhausted) */
+
+/* message types and sides (LOBSTER-style event codes) */
+#define LOB_ADD     1
+#define LOB_PARTIAL 2
+#define LOB_DELETE  3
+#define LOB_MARKET  4
+#define LOB_BUY     1
+#define LOB_SELL   (-1)
+
+/* action sources */
+#define LOB_ACT_HOST   0  /* actions passed to lob_step per step */
+#define LOB_ACT_RANDOM 1  /* seeded uniform random policy drawn on the device */
+
+#define LOB_NCOUNTERS 16
+/* per-env cumulative counters, in this order (int64 each):
+ * msgs, agent_msgs, fills, fill_vol, add_vol, mkt_vol, mkt_discard_vol,
+ * cancel_vol, cancel_miss, drop_vol, drop_cnt, evict_vol, evict_cnt,
+ * bad_msgs, bg_cash, bg_inv */
+
+/* 32-byte market-by-order message record (little endian). */
+typedef struct lob_msg {
+    int64_t ts;    /* source timestamp (not used by matching) */
+    int64_t oid;   /* order id; background ids are >= 0 */
+    int32_t px;    /* limit price in ticks (ignored for market orders) */
+    int32_t qty;   /* size; cancelled amount for LOB_PARTIAL; ignored for LOB_DELETE */
+    int16_t type;  /* LOB_ADD .. LOB_MARKET */
+    int16_t side;  /* LOB_BUY or LOB_SELL */
+    int32_t pad;
+} lob_msg;
+
+/* 32-byte trade record of the fill log. */
+typedef struct lob_fill {
+    int64_t maker_id;   /* resting order */
+    int64_t taker_id;   /* incoming order */
+    int32_t px;         /* trade price = resting order's price */
+    int32_t qty;
+    int32_t msg_idx;    /* index of the incoming message within the step's processing order */
+    int32_t taker_side; /* LOB_BUY / LOB_SELL */
+} lob_fill;
+
+typedef struct lob_config {
+    int32_t n_envs;        /* >= 1 */
+    int32_t n_agents;      /* 0 (replay only) or 2 (execution agent 0, market maker 1) */
+    int32_t cap_per_side;  /* book capacity per side, 1..LOB_MAX_CAP (Table 2: 100) */
+    int32_t top_levels;    /* L aggregated levels per side in the observation, 1..64 */
+    int32_t episode_len;   /* T steps per episode, >= 1 */
+    int32_t mm_lot;        /* market maker's quote size, >= 1 */
+    int32_t exec_target;   /* execution task size, >= 0 */
+    int32_t exec_dir;      /* LOB_SELL or LOB_BUY: side of the execution task */
+    int32_t action_mode;   /* LOB_ACT_HOST or LOB_ACT_RANDOM */
+    int32_t trace;         /* bit0: fill log; bit1: env 0 book snapshot after every message */
+    int32_t start_px;      /* reference price before the first trade (e.g. 10000) */
+    int32_t warps_per_block; /* launch shape hint; 0 = library default */
+    int32_t reserved[4];   /* must be zero */
+} lob_config;
+
+#define LOB_MAX_CAP 256    /* per-side capacity supported by this build */
+
+typedef struct lob_handle lob_handle;
+
+/* Observation length per agent: 4 * top_levels + 5 (0 when n_agents == 0).
+ * Layout per agent: [bid (px - anchor, qty) x L][ask (px - anchor, qty) x L],
+ * inventory, cash, time left (T - t) / T, remaining execution target (agent 0)
+ * or 0, the agent's own resting quantity.  anchor = floor((best bid + best
+ * ask) / 2); an empty side's touch is the last trade price; missing levels
+ * are (0, 0). */
+int32_t lob_obs_dim(const lob_config *cfg);
+
+/* Create a handle on the current CUDA device and allocate its state (books,
+ * agent state, counters).  h_caps: optional host array [n_envs] of per-env
+ * capacities (each 1..LOB_MAX_CAP) overriding cap_per_side.  The handle starts
+ * unusable until lob_reset(). */
+int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out);
+int lob_destroy(lob_handle *h);   /* frees device state; synchronises the device */
+
+/* Bind a window of background messages (the contiguous store with start
+ * indices of Sec. 4): env e's messages of window step k are
+ * d_msgs[d_offsets[e * stride + k] .. d_offsets[e * stride + k + 1]).
+ * Offsets are message indices; stride >= n_steps + 1.  The buffers are
+ * borrowed and must stay alive while steps using them run.  Rebinding resets
+ * the window cursor to 0 without touching env state. */
+int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets,
+                      int32_t n_steps, int64_t stride);
+
+/* Start a new episode in every env: empty books, zero agent state and
+ * counters, step t = 0.  d_env_seeds: device [n_envs] uint64 keys for the
+ * shuffle and the random policy. */
+int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream);
+
+/* One environment step for every env (stages 1-5 above), consuming the next
+ * window step of bound messages.  d_actions: device int32 [n_envs][2] in
+ * LOB_ACT_HOST mode, ignored (may be NULL) otherwise.  Fails with LOB_ESTATE
+ * when the episode is over (t == T) or the window is exhausted. */
+int lob_step(lob_handle *h, const int32_t *d_actions, void *stream);
+
+/* Outputs of the last step: d_obs float [n_envs][n_agents][obs_dim],
+ * d_rewards int64 [n_envs][n_agents] (change of portfolio value, Eq. 1, in
+ * tick * qty), d_done uint8 [n_envs].  Any pointer may be NULL. */
+int lob_observe(lob_handle *h, float *d_obs, int64_t *d_rewards, uint8_t *d_done, void *stream);
+
+/* Several steps in one persistent launch, the book kept on chip between
+ * steps.  Outputs of step i go to d_obs + i * n_envs * n_agents * obs_dim etc.
+ * (any may be NULL).  Actions: LOB_ACT_RANDOM, or LOB_ACT_HOST with
+ * d_actions [n_steps][n_envs][2]. */
+int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float *d_obs,
+                int64_t *d_rewards, uint8_t *d_done, void *stream);
+
+/* Host-buffer convenience step: copies this step's background messages
+ * (h_msgs[h_offsets[e] .. h_offsets[e + 1]], h_offsets [n_envs + 1]) and
+ * actions to the device, steps, and copies obs / rewards / done back to host
+ * buffers (any output may be NULL).  Synchronises the stream. */
+int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets,
+                  const int32_t *h_actions, float *h_obs, int64_t *h_rewards,
+                  uint8_t *h_done, void *stream);
+
+/* Book of every env in the canonical layout, per env a record of
+ * 8 + 48 * C bytes (C = that env's capacity): int32 n[2]; int32 px[2][C];
+ * int32 qty[2][C]; int64 id[2][C]; int64 ts[2][C]; side 0 = bids, 1 = asks,
+ * each in priority order, unused slots zero.  Records are packed back to
+ * back in env order.  d_out must hold lob_book_bytes() bytes. */
+int64_t lob_book_bytes(const lob_handle *h);
+int lob_get_book(lob_handle *h, void *d_out, void *stream);
+
+/* d_out int64 [n_envs][LOB_NCOUNTERS]. */
+int lob_get_counters(lob_handle *h, int64_t *d_out, void *stream);
+/* d_out int64 [n_envs][n_agents][4]: inventory, cash, last portfolio value, executed volume. */
+int lob_get_agents(lob_handle *h, int64_t *d_out, void *stream);
+/* d_out int64 [n_envs][4]: next arrival stamp, next agent order sequence, last trade price, step t. */
+int lob_get_env_misc(lob_handle *h, int64_t *d_out, void *stream);
+/* d_out int32 [n_envs][n_agents]: the actions used in the last step. */
+int lob_get_actions(lob_handle *h, int32_t *d_out, void *stream);
+
+/* Trace buffers (caller-owned, device): fill log of the last step for every
+ * env, d_fills [n_envs][fill_cap] with d_fill_counts int32 [n_envs] (counts
+ * beyond fill_cap are still counted); env 0's book after every message of
+ * the last step, d_snaps [snap_cap] canonical records (see lob_get_book) with
+ * d_snap_count int64.  Pass NULL to disable either. */
+int lob_set_trace(lob_handle *h, lob_fill *d_fills, int32_t fill_cap, int32_t *d_fill_counts,
+                  void *d_snaps, int64_t snap_cap, int64_t *d_snap_count);
+
+/* Wait for the handle's work on `stream`, then return and clear the device
+ * status (first error seen: LOB_EBADMSG, LOB_EINVAL or LOB_ETIMEOUT). */
+int lob_sync(lob_handle *h, void *stream);
+/* Launch-shape control used by the autotuner: warps per block for the step
+ * kernels (1..32) and whether they take envs from a work queue. */
+int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
+/* Number of kernels the library launched since creation (for accounting). */
+int64_t lob_kernel_launches(const lob_handle *h);
+
+const char *lob_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOB_H */

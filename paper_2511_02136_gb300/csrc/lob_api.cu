@@ -1,0 +1,525 @@
+// lob_api.cu -- host side of the C ABI declared in include/lob.h.
+//
+// Owns the device state of a handle (books, per-env scalars, counters, the
+// last step's outputs), validates every argument on the host, groups envs by
+// book-capacity class (32, 64, 128 or 256 slots per side) and launches the
+// warp-per-env step kernels of lob_device.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lob.h"
+#include "lob_device.cuh"
+
+using namespace lobk;
+
+namespace {
+
+constexpr int NCLASS = 4;                 // K = 1, 2, 4, 8
+constexpr int CLASS_K[NCLASS] = {1, 2, 4, 8};
+constexpr long long DEFAULT_WAIT_BUDGET = 2000000000LL;  // ~1 s of SM cycles
+
+int class_of(int cap) {
+    for (int i = 0; i < NCLASS; i++)
+        if (cap <= 32 * CLASS_K[i]) return i;
+    return -1;
+}
+
+}  // namespace
+
+struct lob_handle {
+    lob_config cfg;
+    int dev = 0;
+    int D = 0;
+    std::vector<int> caps;
+    // device state
+    unsigned char *d_books = nullptr;
+    long long *d_book_off = nullptr;
+    long long *d_canon_off = nullptr;
+    int *d_caps = nullptr;
+    EnvState *d_state = nullptr;
+    long long *d_counters = nullptr;
+    unsigned long long *d_seeds = nullptr;
+    int *d_status = nullptr;
+    float *d_obs = nullptr;
+    long long *d_rew = nullptr;
+    unsigned char *d_done = nullptr;
+    int *d_act = nullptr;
+    int *d_env_list = nullptr;
+    int *d_queue = nullptr;
+    int class_begin[NCLASS] = {0, 0, 0, 0};
+    int class_count[NCLASS] = {0, 0, 0, 0};
+    long long book_bytes = 0, canon_bytes = 0;
+    // bound messages
+    const lob_msg *msgs = nullptr;
+    const int64_t *offsets = nullptr;
+    int32_t win_steps = 0;
+    int64_t stride = 0;
+    int32_t cursor = 0;
+    int32_t t = 0;
+    bool reset_done = false;
+    // trace
+    lob_fill *d_fills = nullptr;
+    int32_t fill_cap = 0;
+    int32_t *d_fill_counts = nullptr;
+    unsigned char *d_snaps = nullptr;
+    int64_t snap_cap = 0;
+    int64_t *d_snap_count = nullptr;
+    // launch shape
+    int wpb = 4;
+    int persistent = 0;
+    int n_sm = 0;
+    int64_t launches = 0;
+    // host-step staging
+    lob_msg *d_stage_msgs = nullptr;
+    size_t stage_cap = 0;
+    int64_t *d_stage_off = nullptr;
+    int32_t *d_stage_act = nullptr;
+};
+
+static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LOB_OK : LOB_ECUDA; }
+
+static void free_all(lob_handle *h) {
+    void *ptrs[] = {h->d_books, h->d_book_off, h->d_canon_off, h->d_caps, h->d_state, h->d_counters,
+                    h->d_seeds, h->d_status, h->d_obs, h->d_rew, h->d_done, h->d_act, h->d_env_list,
+                    h->d_queue, h->d_stage_msgs, h->d_stage_off, h->d_stage_act};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" {
+
+int32_t lob_obs_dim(const lob_config *cfg) {
+    if (!cfg) return 0;
+    return cfg->n_agents > 0 ? 4 * cfg->top_levels + 5 : 0;
+}
+
+const char *lob_strerror(int code) {
+    switch (code) {
+        case LOB_OK: return "ok";
+        case LOB_EINVAL: return "invalid argument or action";
+        case LOB_ENOMEM: return "device allocation failed";
+        case LOB_ECUDA: return "CUDA call failed";
+        case LOB_ETIMEOUT: return "bounded device wait expired";
+        case LOB_ECAPACITY: return "size exceeds supported capacity";
+        case LOB_EBADMSG: return "malformed message (skipped)";
+        case LOB_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
+    if (!cfg || !out) return LOB_EINVAL;
+    *out = nullptr;
+    const lob_config &c = *cfg;
+    if (c.n_envs < 1 || (c.n_agents != 0 && c.n_agents != 2) || c.top_levels < 1 || c.top_levels > LMAX ||
+        c.episode_len < 1 || c.mm_lot < 1 || c.exec_target < 0 ||
+        (c.exec_dir != LOB_SELL && c.exec_dir != LOB_BUY) ||
+        (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace < 0 || c.trace > 3 ||
+        c.warps_per_block < 0 || c.warps_per_block > 8)
+        return LOB_EINVAL;
+    for (int i = 0; i < 4; i++)
+        if (c.reserved[i] != 0) return LOB_EINVAL;
+    std::vector<int> caps((size_t)c.n_envs);
+    for (int e = 0; e < c.n_envs; e++) {
+        const int cp = h_caps ? h_caps[e] : c.cap_per_side;
+        if (cp < 1) return LOB_EINVAL;
+        if (cp > LOB_MAX_CAP) return LOB_ECAPACITY;
+        caps[(size_t)e] = cp;
+    }
+    lob_handle *h = new (std::nothrow) lob_handle();
+    if (!h) return LOB_ENOMEM;
+    h->cfg = c;
+    h->caps = caps;
+    h->D = lob_obs_dim(cfg);
+    if (c.warps_per_block > 0) h->wpb = c.warps_per_block;
+    if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return LOB_ECUDA; }
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
+
+    // group envs by capacity class; book blocks are 256-byte aligned
+    std::vector<int> list;
+    std::vector<long long> off((size_t)c.n_envs), coff((size_t)c.n_envs);
+    long long acc = 0, cacc = 0;
+    for (int k = 0; k < NCLASS; k++) {
+        h->class_begin[k] = (int)list.size();
+        for (int e = 0; e < c.n_envs; e++)
+            if (class_of(caps[(size_t)e]) == k) list.push_back(e);
+        h->class_count[k] = (int)list.size() - h->class_begin[k];
+    }
+    for (int e = 0; e < c.n_envs; e++) {
+        const int slots = 32 * CLASS_K[class_of(caps[(size_t)e])];
+        off[(size_t)e] = acc;
+        acc += ((48LL * slots + 255) / 256) * 256;
+        coff[(size_t)e] = cacc;
+        cacc += 8 + 48LL * caps[(size_t)e];
+    }
+    h->book_bytes = acc;
+    h->canon_bytes = cacc;
+    const size_t n = (size_t)c.n_envs;
+    const int A = c.n_agents;
+    bool fail = false;
+    auto alloc = [&](void **p, size_t b) {
+        if (fail) return;
+        if (cudaMalloc(p, b ? b : 1) != cudaSuccess) fail = true;
+    };
+    alloc((void **)&h->d_books, (size_t)acc);
+    alloc((void **)&h->d_book_off, n * 8);
+    alloc((void **)&h->d_canon_off, n * 8);
+    alloc((void **)&h->d_caps, n * 4);
+    alloc((void **)&h->d_state, n * sizeof(EnvState));
+    alloc((void **)&h->d_counters, n * 8 * LOB_NCOUNTERS);
+    alloc((void **)&h->d_seeds, n * 8);
+    alloc((void **)&h->d_status, 4);
+    alloc((void **)&h->d_obs, n * (size_t)(A * h->D) * 4);
+    alloc((void **)&h->d_rew, n * (size_t)A * 8);
+    alloc((void **)&h->d_done, n);
+    alloc((void **)&h->d_act, n * 2 * 4);
+    alloc((void **)&h->d_env_list, n * 4);
+    alloc((void **)&h->d_queue, NCLASS * 4);
+    if (fail) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return LOB_ENOMEM;
+    }
+    int rc = LOB_OK;
+    rc |= cuda_ok(cudaMemcpy(h->d_book_off, off.data(), n * 8, cudaMemcpyHostToDevice));
+    rc |= cuda_ok(cudaMemcpy(h->d_canon_off, coff.data(), n * 8, cudaMemcpyHostToDevice));
+    rc |= cuda_ok(cudaMemcpy(h->d_caps, caps.data(), n * 4, cudaMemcpyHostToDevice));
+    rc |= cuda_ok(cudaMemcpy(h->d_env_list, list.data(), n * 4, cudaMemcpyHostToDevice));
+    rc |= cuda_ok(cudaMemset(h->d_status, 0, 4));
+    rc |= cuda_ok(cudaMemset(h->d_obs, 0, n * (size_t)(A * h->D) * 4 + 0));
+    if (rc != LOB_OK) {
+        free_all(h);
+        delete h;
+        return LOB_ECUDA;
+    }
+    *out = h;
+    return LOB_OK;
+}
+
+int lob_destroy(lob_handle *h) {
+    if (!h) return LOB_EINVAL;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return LOB_OK;
+}
+
+int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets, int32_t n_steps,
+                      int64_t stride) {
+    if (!h || !d_offsets || n_steps < 0 || stride < (int64_t)n_steps + 1) return LOB_EINVAL;
+    if (!d_msgs && n_steps > 0) {
+        // an all-empty window may pass a NULL message pointer; offsets still needed
+    }
+    h->msgs = d_msgs;
+    h->offsets = d_offsets;
+    h->win_steps = n_steps;
+    h->stride = stride;
+    h->cursor = 0;
+    return LOB_OK;
+}
+
+}  // extern "C"
+
+// zero the state of every env
+__global__ void k_reset(EnvState *st, long long *cnt, unsigned long long *seeds_dst,
+                        const unsigned long long *seeds_src, int n, int start_px) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    EnvState z;
+    memset(&z, 0, sizeof(z));
+    z.last_px = start_px;
+    st[e] = z;
+    for (int i = 0; i < LOB_NCOUNTERS; i++) cnt[(long long)e * LOB_NCOUNTERS + i] = 0;
+    seeds_dst[e] = seeds_src[e];
+}
+
+// internal blocked layout -> canonical priority-ordered record per env
+__global__ void k_get_book(const unsigned char *books, const long long *book_off, const long long *canon_off,
+                           const int *caps, const EnvState *st, unsigned char *out, int n) {
+    const int e = blockIdx.x;
+    if (e >= n) return;
+    const int C = caps[e];
+    int slots = 32;
+    while (slots < C) slots *= 2;
+    const unsigned char *blk = books + book_off[e];
+    unsigned char *rec = out + canon_off[e];
+    int *n2 = reinterpret_cast<int *>(rec);
+    int *px = n2 + 2;
+    int *qt = px + 2 * C;
+    long long *id = reinterpret_cast<long long *>(rec + 8 + 16LL * C);
+    long long *ts = id + 2 * C;
+    const int *ipx = reinterpret_cast<const int *>(blk);
+    const int *iqt = ipx + 2 * slots;
+    const long long *iid = reinterpret_cast<const long long *>(blk + 16LL * slots);
+    const long long *its = reinterpret_cast<const long long *>(blk + 32LL * slots);
+    if (threadIdx.x == 0) { n2[0] = st[e].n[0]; n2[1] = st[e].n[1]; }
+    for (int i = threadIdx.x; i < 2 * C; i += blockDim.x) {
+        const int s = i / C, j = i % C;
+        const bool live = j < st[e].n[s];
+        px[i] = live ? ipx[s * slots + j] : 0;
+        qt[i] = live ? iqt[s * slots + j] : 0;
+        id[i] = live ? iid[s * slots + j] : 0;
+        ts[i] = live ? its[s * slots + j] : 0;
+    }
+}
+
+__global__ void k_get_agents(const EnvState *st, long long *out, int n, int A, int misc) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const EnvState &s = st[e];
+    if (misc) {
+        out[e * 4 + 0] = s.ts_next; out[e * 4 + 1] = s.seq_next;
+        out[e * 4 + 2] = s.last_px; out[e * 4 + 3] = s.t;
+        return;
+    }
+    for (int a = 0; a < A; a++) {
+        long long *o = out + ((long long)e * A + a) * 4;
+        o[0] = s.inv[a]; o[1] = s.cash[a]; o[2] = s.pv_prev[a]; o[3] = a == 0 ? s.exec_done : 0;
+    }
+}
+
+static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
+                        int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
+                        long long *rew, unsigned char *done, cudaStream_t s) {
+    const lob_config &c = h->cfg;
+    KParams p;
+    memset(&p, 0, sizeof(p));
+    p.books = h->d_books; p.book_off = h->d_book_off; p.caps = h->d_caps; p.st = h->d_state;
+    p.counters = h->d_counters; p.seeds = h->d_seeds; p.status = h->d_status;
+    p.msgs = reinterpret_cast<const DevMsg *>(msgs); p.offsets = reinterpret_cast<const long long *>(offsets);
+    p.off_stride = stride; p.k0 = k0;
+    p.actions = d_actions; p.act_step_stride = act_step_stride; p.action_mode = c.action_mode;
+    p.obs = obs; p.rew = rew; p.done = done; p.act_out = nullptr;
+    p.n_envs = c.n_envs; p.n_agents = c.n_agents; p.L = c.top_levels; p.T = c.episode_len;
+    p.mm_lot = c.mm_lot; p.exec_target = c.exec_target; p.exec_dir = c.exec_dir; p.D = h->D;
+    p.t0 = h->t; p.n_steps = n_steps;
+    p.fills = (c.trace & 1) ? h->d_fills : nullptr; p.fill_cap = h->fill_cap;
+    p.fill_counts = (c.trace & 1) ? h->d_fill_counts : nullptr;
+    p.snaps = (c.trace & 2) ? h->d_snaps : nullptr; p.snap_cap = h->snap_cap;
+    p.snap_count = (c.trace & 2) ? reinterpret_cast<long long *>(h->d_snap_count) : nullptr;
+    p.wait_budget = DEFAULT_WAIT_BUDGET;
+    const int wpb = h->wpb;
+    const size_t smem = (size_t)wpb * sizeof(WarpSmem);
+    if (h->persistent) {
+        if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
+    }
+    for (int k = 0; k < NCLASS; k++) {
+        const int cnt = h->class_count[k];
+        if (cnt == 0) continue;
+        p.env_list = h->d_env_list + h->class_begin[k];
+        p.n_list = cnt;
+        p.queue = h->persistent ? h->d_queue + k : nullptr;
+        int blocks = (cnt + wpb - 1) / wpb;
+        if (h->persistent) blocks = std::min(blocks, h->n_sm * std::max(1, 32 / wpb));
+        switch (CLASS_K[k]) {
+            case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
+            case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
+            case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
+            case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        }
+        h->launches++;
+        if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+    }
+    return LOB_OK;
+}
+
+extern "C" {
+
+int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
+    if (!h || !d_env_seeds) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->cfg.n_envs;
+    k_reset<<<(n + 127) / 128, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
+                                             reinterpret_cast<const unsigned long long *>(d_env_seeds), n,
+                                             h->cfg.start_px);
+    h->launches++;
+    if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+    h->t = 0;
+    h->reset_done = true;
+    return LOB_OK;
+}
+
+int lob_step(lob_handle *h, const int32_t *d_actions, void *stream) {
+    if (!h) return LOB_EINVAL;
+    if (!h->reset_done || !h->offsets || h->cursor >= h->win_steps || h->t >= h->cfg.episode_len)
+        return LOB_ESTATE;
+    if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
+    int rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, 1, d_actions, 0, h->d_obs, h->d_rew,
+                          h->d_done, (cudaStream_t)stream);
+    if (rc != LOB_OK) return rc;
+    h->cursor++;
+    h->t++;
+    return LOB_OK;
+}
+
+int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float *d_obs, int64_t *d_rewards,
+                uint8_t *d_done, void *stream) {
+    if (!h || n_steps < 1) return LOB_EINVAL;
+    if (!h->reset_done || !h->offsets || h->cursor + n_steps > h->win_steps ||
+        h->t + n_steps > h->cfg.episode_len)
+        return LOB_ESTATE;
+    if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, n_steps, d_actions,
+                          2LL * h->cfg.n_envs, d_obs, reinterpret_cast<long long *>(d_rewards), d_done, s);
+    if (rc != LOB_OK) return rc;
+    // keep the last step's outputs for lob_observe
+    const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
+    const size_t last = (size_t)(n_steps - 1);
+    if (d_obs && A) cudaMemcpyAsync(h->d_obs, d_obs + last * n * A * D, n * A * D * 4, cudaMemcpyDeviceToDevice, s);
+    if (d_rewards && A) cudaMemcpyAsync(h->d_rew, d_rewards + last * n * A, n * A * 8, cudaMemcpyDeviceToDevice, s);
+    if (d_done) cudaMemcpyAsync(h->d_done, d_done + last * n, n, cudaMemcpyDeviceToDevice, s);
+    h->cursor += n_steps;
+    h->t += n_steps;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+int lob_observe(lob_handle *h, float *d_obs, int64_t *d_rewards, uint8_t *d_done, void *stream) {
+    if (!h) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
+    int rc = LOB_OK;
+    if (d_obs && A) rc |= cuda_ok(cudaMemcpyAsync(d_obs, h->d_obs, n * A * D * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_rewards && A) rc |= cuda_ok(cudaMemcpyAsync(d_rewards, h->d_rew, n * A * 8, cudaMemcpyDeviceToDevice, s));
+    if (d_done) rc |= cuda_ok(cudaMemcpyAsync(d_done, h->d_done, n, cudaMemcpyDeviceToDevice, s));
+    return rc ? LOB_ECUDA : LOB_OK;
+}
+
+int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets, const int32_t *h_actions,
+                  float *h_obs, int64_t *h_rewards, uint8_t *h_done, void *stream) {
+    if (!h || !h_offsets) return LOB_EINVAL;
+    if (!h->reset_done || h->t >= h->cfg.episode_len) return LOB_ESTATE;
+    const lob_config &c = h->cfg;
+    if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST && !h_actions) return LOB_EINVAL;
+    const int n = c.n_envs;
+    const int64_t base = h_offsets[0], total = h_offsets[n] - base;
+    if (total < 0) return LOB_EINVAL;
+    for (int e = 0; e < n; e++)
+        if (h_offsets[e + 1] < h_offsets[e]) return LOB_EINVAL;
+    if (total > 0 && !h_msgs) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((size_t)total > h->stage_cap) {
+        if (h->d_stage_msgs) cudaFree(h->d_stage_msgs);
+        h->d_stage_msgs = nullptr;
+        size_t want = std::max((size_t)total, h->stage_cap * 2);
+        if (cudaMalloc(&h->d_stage_msgs, want * sizeof(lob_msg)) != cudaSuccess) {
+            h->stage_cap = 0;
+            return LOB_ENOMEM;
+        }
+        h->stage_cap = want;
+    }
+    if (!h->d_stage_off) {
+        if (cudaMalloc(&h->d_stage_off, ((size_t)n + 1) * 8) != cudaSuccess) return LOB_ENOMEM;
+        if (cudaMalloc(&h->d_stage_act, (size_t)n * 2 * 4) != cudaSuccess) return LOB_ENOMEM;
+    }
+    int rc = LOB_OK;
+    if (total > 0)
+        rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_msgs, h_msgs + base, (size_t)total * sizeof(lob_msg),
+                                      cudaMemcpyHostToDevice, s));
+    // offsets relative to the staged slice
+    std::vector<int64_t> rel((size_t)n + 1);
+    for (int e = 0; e <= n; e++) rel[(size_t)e] = h_offsets[e] - base;
+    rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_off, rel.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST)
+        rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_act, h_actions, (size_t)n * 2 * 4, cudaMemcpyHostToDevice, s));
+    if (rc != LOB_OK) return LOB_ECUDA;
+    rc = launch_steps(h, h->d_stage_msgs, h->d_stage_off, 1, 0, 1, h->d_stage_act, 0, h->d_obs, h->d_rew,
+                      h->d_done, s);
+    if (rc != LOB_OK) return rc;
+    h->t++;
+    const size_t A = (size_t)c.n_agents, D = (size_t)h->D;
+    if (h_obs && A) rc |= cuda_ok(cudaMemcpyAsync(h_obs, h->d_obs, (size_t)n * A * D * 4, cudaMemcpyDeviceToHost, s));
+    if (h_rewards && A) rc |= cuda_ok(cudaMemcpyAsync(h_rewards, h->d_rew, (size_t)n * A * 8, cudaMemcpyDeviceToHost, s));
+    if (h_done) rc |= cuda_ok(cudaMemcpyAsync(h_done, h->d_done, (size_t)n, cudaMemcpyDeviceToHost, s));
+    rc |= cuda_ok(cudaStreamSynchronize(s));
+    if (rc != LOB_OK) return LOB_ECUDA;
+    return LOB_OK;
+}
+
+int64_t lob_book_bytes(const lob_handle *h) { return h ? h->canon_bytes : 0; }
+
+int lob_get_book(lob_handle *h, void *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    k_get_book<<<h->cfg.n_envs, 128, 0, (cudaStream_t)stream>>>(h->d_books, h->d_book_off, h->d_canon_off, h->d_caps,
+                                                                 h->d_state, (unsigned char *)d_out, h->cfg.n_envs);
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+int lob_get_counters(lob_handle *h, int64_t *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    return cuda_ok(cudaMemcpyAsync(d_out, h->d_counters, (size_t)h->cfg.n_envs * 8 * LOB_NCOUNTERS,
+                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+int lob_get_agents(lob_handle *h, int64_t *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    if (h->cfg.n_agents == 0) return LOB_OK;
+    const int n = h->cfg.n_envs;
+    k_get_agents<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->d_state, reinterpret_cast<long long *>(d_out),
+                                                                     n, h->cfg.n_agents, 0);
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+int lob_get_env_misc(lob_handle *h, int64_t *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    const int n = h->cfg.n_envs;
+    k_get_agents<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->d_state, reinterpret_cast<long long *>(d_out),
+                                                                     n, 0, 1);
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+int lob_get_actions(lob_handle *h, int32_t *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    if (h->cfg.n_agents == 0) return LOB_OK;
+    return cuda_ok(cudaMemcpy2DAsync(d_out, 8, reinterpret_cast<const char *>(h->d_state) + offsetof(EnvState, act),
+                                     sizeof(EnvState), 8, (size_t)h->cfg.n_envs, cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream));
+}
+
+int lob_set_trace(lob_handle *h, lob_fill *d_fills, int32_t fill_cap, int32_t *d_fill_counts, void *d_snaps,
+                  int64_t snap_cap, int64_t *d_snap_count) {
+    if (!h || fill_cap < 0 || snap_cap < 0) return LOB_EINVAL;
+    if ((d_fills == nullptr) != (d_fill_counts == nullptr)) return LOB_EINVAL;
+    if ((d_snaps == nullptr) != (d_snap_count == nullptr)) return LOB_EINVAL;
+    h->d_fills = d_fills;
+    h->fill_cap = d_fills ? fill_cap : 0;
+    h->d_fill_counts = d_fill_counts;
+    h->d_snaps = (unsigned char *)d_snaps;
+    h->snap_cap = d_snaps ? snap_cap : 0;
+    h->d_snap_count = d_snap_count;
+    h->cfg.trace = (d_fills ? 1 : 0) | (d_snaps ? 2 : 0);
+    return LOB_OK;
+}
+
+int lob_sync(lob_handle *h, void *stream) {
+    if (!h) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LOB_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, h->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LOB_ECUDA;
+    if (st) cudaMemset(h->d_status, 0, 4);
+    if (st & ST_TIMEOUT) return LOB_ETIMEOUT;
+    if (st & ST_BADACT) return LOB_EINVAL;
+    if (st & ST_BADMSG) return LOB_EBADMSG;
+    return LOB_OK;
+}
+
+int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
+    if (!h || warps_per_block < 1 || warps_per_block > 8 || (persistent != 0 && persistent != 1)) return LOB_EINVAL;
+    h->wpb = warps_per_block;
+    h->persistent = persistent;
+    return LOB_OK;
+}
+
+int64_t lob_kernel_launches(const lob_handle *h) { return h ? h->launches : 0; }
+
+}  // extern "C"

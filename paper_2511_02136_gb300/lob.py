@@ -1,0 +1,344 @@
+"""Thin Python binding of liblob.so (the C ABI in include/lob.h).
+
+Argument marshalling only: every stage of the environment step runs in the
+CUDA kernels of the library.  PyTorch supplies device memory and streams.
+Importing works without a GPU; loading the library requires it to be built
+(``build()``), and every call that touches the device requires CUDA.  There is
+no CPU fallback: if the library is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INC = os.path.join(_ROOT, "include")
+LIB_PATH = os.path.join(_PKG, "liblob.so")
+_SOURCES = [os.path.join(_CSRC, "lob_api.cu")]
+_DEPS = _SOURCES + [os.path.join(_CSRC, "lob_device.cuh"), os.path.join(_INC, "lob.h")]
+_lock = threading.Lock()
+_lib = None
+
+ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+LOB_OK, LOB_EINVAL, LOB_ENOMEM, LOB_ECUDA, LOB_ETIMEOUT, LOB_ECAPACITY, LOB_EBADMSG, LOB_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+LOB_ACT_HOST, LOB_ACT_RANDOM = 0, 1
+LOB_NCOUNTERS = 16
+LOB_MAX_CAP = 256
+FILL_BYTES = 32
+
+# Every entry point include/lob.h declares (checked by the test suite).
+EXPORTS = [
+    "lob_obs_dim", "lob_create", "lob_destroy", "lob_load_messages", "lob_reset", "lob_step",
+    "lob_observe", "lob_rollout", "lob_step_host", "lob_book_bytes", "lob_get_book",
+    "lob_get_counters", "lob_get_agents", "lob_get_env_misc", "lob_get_actions", "lob_set_trace",
+    "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror",
+]
+
+
+class LobError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = _load().lob_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class lob_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_envs", "n_agents", "cap_per_side", "top_levels", "episode_len", "mm_lot",
+        "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block")] + \
+        [("reserved", ctypes.c_int32 * 4)]
+
+
+def _stale(target, deps):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def nvcc_cmd(out_path, extra=()):
+    return (["nvcc", "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+             "-I", _INC, "-o", out_path] + list(extra) + _SOURCES)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile liblob.so in-tree for sm_103a (nvcc cross-compiles without a GPU)."""
+    with _lock:
+        if not force and not _stale(LIB_PATH, _DEPS):
+            return LIB_PATH
+        tmp = LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = nvcc_cmd(tmp, ["-Xptxas", "-v"] if verbose else [])
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB_PATH)
+        return LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblob.so is not built ({LIB_PATH}); call paper_2511_02136_gb300.lob.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "lob_obs_dim": (I32, [ctypes.POINTER(lob_config)]),
+        "lob_create": (ctypes.c_int, [ctypes.POINTER(lob_config), P, ctypes.POINTER(P)]),
+        "lob_destroy": (ctypes.c_int, [P]),
+        "lob_load_messages": (ctypes.c_int, [P, P, P, I32, I64]),
+        "lob_reset": (ctypes.c_int, [P, P, P]),
+        "lob_step": (ctypes.c_int, [P, P, P]),
+        "lob_observe": (ctypes.c_int, [P, P, P, P, P]),
+        "lob_rollout": (ctypes.c_int, [P, I32, P, P, P, P, P]),
+        "lob_step_host": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
+        "lob_book_bytes": (I64, [P]),
+        "lob_get_book": (ctypes.c_int, [P, P, P]),
+        "lob_get_counters": (ctypes.c_int, [P, P, P]),
+        "lob_get_agents": (ctypes.c_int, [P, P, P]),
+        "lob_get_env_misc": (ctypes.c_int, [P, P, P]),
+        "lob_get_actions": (ctypes.c_int, [P, P, P]),
+        "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
+        "lob_sync": (ctypes.c_int, [P, P]),
+        "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
+        "lob_kernel_launches": (I64, [P]),
+        "lob_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != LOB_OK:
+        raise LobError(rc, what)
+    return rc
+
+
+def _dp(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------- same-name wrappers
+def lob_obs_dim(cfg: lob_config) -> int:
+    return _load().lob_obs_dim(ctypes.byref(cfg))
+
+
+def lob_create(cfg: lob_config, caps=None):
+    h = ctypes.c_void_p()
+    c = None if caps is None else np.ascontiguousarray(caps, dtype=np.int32)
+    _check(_load().lob_create(ctypes.byref(cfg), None if c is None else c.ctypes.data, ctypes.byref(h)),
+           "lob_create")
+    return h
+
+
+def lob_destroy(h):
+    return _check(_load().lob_destroy(h), "lob_destroy")
+
+
+def lob_load_messages(h, msgs, offsets, n_steps, stride):
+    return _check(_load().lob_load_messages(h, _dp(msgs), _dp(offsets), n_steps, stride), "lob_load_messages")
+
+
+def lob_reset(h, seeds, stream=None):
+    return _check(_load().lob_reset(h, _dp(seeds), _stream(stream)), "lob_reset")
+
+
+def lob_step(h, actions=None, stream=None):
+    return _check(_load().lob_step(h, _dp(actions), _stream(stream)), "lob_step")
+
+
+def lob_observe(h, obs=None, rewards=None, done=None, stream=None):
+    return _check(_load().lob_observe(h, _dp(obs), _dp(rewards), _dp(done), _stream(stream)), "lob_observe")
+
+
+def lob_rollout(h, n_steps, actions=None, obs=None, rewards=None, done=None, stream=None):
+    return _check(_load().lob_rollout(h, n_steps, _dp(actions), _dp(obs), _dp(rewards), _dp(done),
+                                      _stream(stream)), "lob_rollout")
+
+
+def lob_step_host(h, msgs, offsets, actions, obs, rewards, done, stream=None):
+    """Host numpy (ideally pinned) buffers in and out; synchronises."""
+    def hp(a):
+        return None if a is None else a.ctypes.data
+    return _check(_load().lob_step_host(h, hp(msgs), hp(offsets), hp(actions), hp(obs), hp(rewards), hp(done),
+                                        _stream(stream)), "lob_step_host")
+
+
+def lob_book_bytes(h) -> int:
+    return _load().lob_book_bytes(h)
+
+
+def lob_get_book(h, out, stream=None):
+    return _check(_load().lob_get_book(h, _dp(out), _stream(stream)), "lob_get_book")
+
+
+def lob_get_counters(h, out, stream=None):
+    return _check(_load().lob_get_counters(h, _dp(out), _stream(stream)), "lob_get_counters")
+
+
+def lob_get_agents(h, out, stream=None):
+    return _check(_load().lob_get_agents(h, _dp(out), _stream(stream)), "lob_get_agents")
+
+
+def lob_get_env_misc(h, out, stream=None):
+    return _check(_load().lob_get_env_misc(h, _dp(out), _stream(stream)), "lob_get_env_misc")
+
+
+def lob_get_actions(h, out, stream=None):
+    return _check(_load().lob_get_actions(h, _dp(out), _stream(stream)), "lob_get_actions")
+
+
+def lob_set_trace(h, fills=None, fill_cap=0, fill_counts=None, snaps=None, snap_cap=0, snap_count=None):
+    return _check(_load().lob_set_trace(h, _dp(fills), fill_cap, _dp(fill_counts), _dp(snaps), snap_cap,
+                                        _dp(snap_count)), "lob_set_trace")
+
+
+def lob_sync(h, stream=None):
+    """Returns the device status code (0, or LOB_EBADMSG / LOB_EINVAL / LOB_ETIMEOUT)."""
+    return _load().lob_sync(h, _stream(stream))
+
+
+def lob_set_launch(h, warps_per_block, persistent):
+    return _check(_load().lob_set_launch(h, warps_per_block, persistent), "lob_set_launch")
+
+
+def lob_kernel_launches(h) -> int:
+    return _load().lob_kernel_launches(h)
+
+
+def lob_strerror(code) -> str:
+    return _load().lob_strerror(code).decode()
+
+
+def book_dtype(C):
+    return np.dtype([("n", "<i4", (2,)), ("px", "<i4", (2, C)), ("qty", "<i4", (2, C)),
+                     ("id", "<i8", (2, C)), ("ts", "<i8", (2, C))])
+
+
+FILL_DTYPE = np.dtype([("maker_id", "<i8"), ("taker_id", "<i8"), ("px", "<i4"), ("qty", "<i4"),
+                       ("msg_idx", "<i4"), ("taker_side", "<i4")])
+
+
+class LobEnv:
+    """Convenience owner of a handle plus torch output buffers (all on the current CUDA device)."""
+
+    def __init__(self, n_envs, n_agents=2, cap=100, top_levels=10, episode_len=1000, mm_lot=1,
+                 exec_target=500, exec_dir=-1, action_mode=LOB_ACT_RANDOM, start_px=10_000,
+                 warps_per_block=0, caps=None):
+        import torch
+        self.torch = torch
+        self.cfg = lob_config(n_envs, n_agents, cap, top_levels, episode_len, mm_lot, exec_target,
+                              exec_dir, action_mode, 0, start_px, warps_per_block)
+        self.caps = caps
+        self.h = lob_create(self.cfg, caps)
+        self.n_envs, self.n_agents = n_envs, n_agents
+        self.D = lob_obs_dim(self.cfg)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+        self.obs = torch.zeros((n_envs, n_agents, self.D), dtype=torch.float32, device=dev)
+        self.rew = torch.zeros((n_envs, max(n_agents, 1)), dtype=torch.int64, device=dev)
+        self.done = torch.zeros(n_envs, dtype=torch.uint8, device=dev)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            lob_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_messages(self, msgs_dev, offsets_dev):
+        """msgs_dev: uint8/int64 tensor of 32-byte records; offsets_dev int64 [n_envs, n_steps+1]."""
+        self._keep = [msgs_dev, offsets_dev]
+        lob_load_messages(self.h, msgs_dev, offsets_dev, offsets_dev.shape[1] - 1, offsets_dev.shape[1])
+
+    def reset(self, seeds_dev, stream=None):
+        self._seeds = seeds_dev
+        lob_reset(self.h, seeds_dev, stream)
+
+    def step(self, actions=None, stream=None):
+        lob_step(self.h, actions, stream)
+
+    def observe(self, stream=None):
+        lob_observe(self.h, self.obs, self.rew if self.n_agents else None, self.done, stream)
+        return self.obs, self.rew, self.done
+
+    def counters(self):
+        out = self.torch.zeros((self.n_envs, LOB_NCOUNTERS), dtype=self.torch.int64, device=self.dev)
+        lob_get_counters(self.h, out)
+        return out
+
+    def agents(self):
+        out = self.torch.zeros((self.n_envs, max(self.n_agents, 1), 4), dtype=self.torch.int64, device=self.dev)
+        lob_get_agents(self.h, out)
+        return out[:, :self.n_agents]
+
+    def env_misc(self):
+        out = self.torch.zeros((self.n_envs, 4), dtype=self.torch.int64, device=self.dev)
+        lob_get_env_misc(self.h, out)
+        return out
+
+    def actions(self):
+        out = self.torch.zeros((self.n_envs, 2), dtype=self.torch.int32, device=self.dev)
+        lob_get_actions(self.h, out)
+        return out[:, :self.n_agents]
+
+    def books(self):
+        """List of per-env canonical book records (numpy) in env order."""
+        nb = lob_book_bytes(self.h)
+        out = self.torch.zeros(nb, dtype=self.torch.uint8, device=self.dev)
+        lob_get_book(self.h, out)
+        raw = out.cpu().numpy()
+        caps = (np.full(self.n_envs, self.cfg.cap_per_side, np.int32) if self.caps is None
+                else np.asarray(self.caps, np.int32))
+        recs, off = [], 0
+        for e in range(self.n_envs):
+            dt = book_dtype(int(caps[e]))
+            recs.append(np.frombuffer(raw[off:off + dt.itemsize].tobytes(), dtype=dt)[0])
+            off += dt.itemsize
+        return recs
+
+    def books_live(self):
+        """Mean number of live orders per env (bids + asks), read on the device."""
+        nb = lob_book_bytes(self.h)
+        if getattr(self, "_bookbuf", None) is None or self._bookbuf.numel() != nb:
+            self._bookbuf = self.torch.zeros(nb, dtype=self.torch.uint8, device=self.dev)
+            caps = (np.full(self.n_envs, self.cfg.cap_per_side, np.int64) if self.caps is None
+                    else np.asarray(self.caps, np.int64))
+            rec = 8 + 48 * caps
+            off = np.concatenate([[0], np.cumsum(rec)[:-1]]) // 4
+            self._nidx = self.torch.from_numpy(np.stack([off, off + 1], 1).reshape(-1)).to(self.dev)
+        lob_get_book(self.h, self._bookbuf)
+        n = self._bookbuf.view(self.torch.int32)[self._nidx]
+        return n.double().sum().item() / self.n_envs
+
+    def sync(self):
+        return lob_sync(self.h)

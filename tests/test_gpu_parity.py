@@ -1,0 +1,219 @@
+"""GPU (liblob.so, sm_103a) vs. the CPU oracle, element by element, through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+from harness import Pair
+from paper_2511_02136_gb300 import lob, mbogen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lob.build()
+    import torch
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+
+
+def test_plain_replay_one_env_trace_every_message():
+    """1 env, 10,000 messages from seed 0, capacity 100, no agents: book after
+    every message and every fill identical to the oracle."""
+    T, M = 100, 100
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=M), mbogen.env_seeds(0, 1), T)
+    pr = Pair(1, st, n_agents=0, cap=100, fill_cap=4 * M, snap_cap=M)
+    for _ in range(T):
+        pr.step()
+        pr.check_fills()
+        pr.check_snapshots()
+    pr.check_outputs()
+    pr.check_state()
+    pr.close()
+
+
+@pytest.mark.parametrize("wpb,persistent", [(4, 0), (1, 0), (8, 0), (2, 1), (4, 1)])
+def test_two_agents_random_policy_ragged(wpb, persistent):
+    """37 envs (ragged against every warps-per-block), 45 messages per step
+    (one full 32-message tile plus a ragged tail), 25 steps."""
+    n, T = 37, 25
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=45), mbogen.env_seeds(11, n), T)
+    pr = Pair(n, st, cap=100, exec_target=60, fill_cap=256, warps_per_block=wpb, persistent=persistent)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
+
+
+def test_host_actions_and_buy_task():
+    n, T = 29, 30
+    rng = np.random.default_rng(5)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=70), mbogen.env_seeds(12, n), T)
+    pr = Pair(n, st, cap=100, exec_target=200, exec_dir=1, mm_lot=3, top_levels=20,
+              action_mode=lob.LOB_ACT_HOST, fill_cap=512)
+    for _ in range(T):
+        pr.step(rng.integers(0, 12, size=(n, 2)).astype(np.int32))
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    pr.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_capacities_every_branch(seed):
+    """Capacities 1..8 and a narrow price band: evictions, drops, sweeps to an
+    empty side, partial cancels to zero and misses all fire."""
+    n, T = 40, 20
+    rng = np.random.default_rng(seed)
+    caps = rng.integers(1, 9, size=n).astype(np.int32)
+    model = mbogen.MessageModel(price_p=0.6, size_p=0.3, msgs_per_step=int(rng.integers(20, 70)),
+                                mix_market=0.2)
+    st = mbogen.generate(model, mbogen.env_seeds(100 + seed, n), T)
+    pr = Pair(n, st, caps=caps, cap=8, exec_target=30, top_levels=3,
+              action_mode=lob.LOB_ACT_HOST if seed % 2 else lob.LOB_ACT_RANDOM, fill_cap=512)
+    for _ in range(T):
+        pr.step(rng.integers(0, 12, size=(n, 2)).astype(np.int32) if seed % 2 else None)
+        pr.check_outputs()
+        pr.check_fills()
+        pr.check_state()
+    pr.close()
+
+
+def test_uneven_caps_and_poisson_counts():
+    """Capacities from {50, 100, 200, 256} (all register classes) and
+    M_t ~ Poisson(lambda_env), including empty steps."""
+    n, T = 96, 15
+    caps = mbogen.env_caps(3, n, choices=(20, 50, 100, 200, 256))
+    st = mbogen.generate(mbogen.MessageModel(poisson=True, lam_lo=0.5, lam_hi=300.0), mbogen.env_seeds(13, n), T)
+    assert (st.counts == 0).any()
+    pr = Pair(n, st, caps=caps, cap=256, exec_target=100, fill_cap=1024)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    pr.close()
+
+
+def test_rollout_matches_stepwise_oracle():
+    """Several steps in one persistent launch with the book kept on chip."""
+    import torch
+    n, T = 50, 12
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=60), mbogen.env_seeds(21, n), T)
+    for mode in (lob.LOB_ACT_RANDOM, lob.LOB_ACT_HOST):
+        pr = Pair(n, st, cap=100, exec_target=40, action_mode=mode)
+        rng = np.random.default_rng(1)
+        acts = rng.integers(0, 12, size=(T, n, 2)).astype(np.int32)
+        D = pr.env.D
+        obs = torch.zeros((T, n, 2, D), dtype=torch.float32, device="cuda")
+        rew = torch.zeros((T, n, 2), dtype=torch.int64, device="cuda")
+        done = torch.zeros((T, n), dtype=torch.uint8, device="cuda")
+        a_d = torch.from_numpy(acts).cuda() if mode == lob.LOB_ACT_HOST else None
+        # first 5 steps as one rollout, then the remaining 7 as another
+        lob.lob_rollout(pr.env.h, 5, a_d[:5].contiguous() if a_d is not None else None, obs[:5], rew[:5], done[:5])
+        lob.lob_rollout(pr.env.h, 7, a_d[5:].contiguous() if a_d is not None else None, obs[5:], rew[5:], done[5:])
+        for t in range(T):
+            pr.orc.step(acts[t] if mode == lob.LOB_ACT_HOST else None)
+            o_obs, o_rew, o_done = pr.orc.observe()
+            np.testing.assert_allclose(obs[t].cpu().numpy(), o_obs, rtol=1e-6, atol=0)
+            np.testing.assert_array_equal(rew[t].cpu().numpy(), o_rew)
+            np.testing.assert_array_equal(done[t].cpu().numpy(), o_done)
+        pr.check_state()
+        pr.check_outputs()
+        pr.close()
+
+
+def test_step_host_buffers():
+    n, T = 33, 6
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=50), mbogen.env_seeds(31, n), T)
+    pr = Pair(n, st, cap=100, exec_target=30, action_mode=lob.LOB_ACT_HOST)
+    rng = np.random.default_rng(2)
+    D = pr.env.D
+    for t in range(T):
+        acts = rng.integers(0, 12, size=(n, 2)).astype(np.int32)
+        lo = st.offsets[:, t]
+        hi = st.offsets[:, t + 1]
+        chunk = np.concatenate([st.msgs[lo[e]:hi[e]] for e in range(n)])
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = np.cumsum(hi - lo)
+        obs = np.zeros((n, 2, D), np.float32)
+        rew = np.zeros((n, 2), np.int64)
+        done = np.zeros(n, np.uint8)
+        lob.lob_step_host(pr.env.h, chunk, off, acts, obs, rew, done)
+        pr.orc.step(acts)
+        o_obs, o_rew, o_done = pr.orc.observe()
+        np.testing.assert_allclose(obs, o_obs, rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(rew, o_rew)
+        np.testing.assert_array_equal(done, o_done)
+    pr.check_state()
+    pr.close()
+
+
+def test_full_size_1024_envs_1000_steps():
+    """The benchmark workload in the benchmark's launch configuration: 1,024
+    envs x capacity 100 x 100 messages x 1,000 steps, random policy.  Every
+    env's rewards are summed over all steps on both sides; observations of all
+    envs are compared every 100 steps; books, counters and agents at the end."""
+    import torch
+    n, T = 1024, 1000
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(1, n), T)
+    pr = Pair(n, st, cap=100, exec_target=500, n_threads=os.cpu_count() or 1)
+    rsum_g = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    rsum_o = np.zeros((n, 2), np.int64)
+    for t in range(T):
+        pr.env.step()
+        pr.orc.step()
+        _, rew, _ = pr.env.observe()
+        rsum_g += rew
+        _, o_rew, _ = pr.orc.observe()
+        rsum_o += o_rew
+        if t % 100 == 99:
+            pr.check_outputs()
+    np.testing.assert_array_equal(rsum_g.cpu().numpy(), rsum_o)
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
+
+
+def test_error_status_paths():
+    import torch
+    n = 4
+    bad = mbogen.generate(mbogen.MessageModel(msgs_per_step=10), mbogen.env_seeds(41, n), 2)
+    msgs = bad.msgs.copy()
+    msgs["type"][3] = 9                   # unknown type
+    msgs["qty"][5] = 0 if msgs["type"][5] != 3 else msgs["qty"][5]
+    bad.msgs = msgs
+    pr = Pair(n, bad, cap=50, action_mode=lob.LOB_ACT_HOST)
+    assert lob.lob_sync(pr.env.h) == 0
+    pr.step(np.zeros((n, 2), np.int32))
+    assert lob.lob_sync(pr.env.h) == lob.LOB_EBADMSG
+    assert lob.lob_sync(pr.env.h) == 0                      # cleared after reporting
+    pr.check_state()                                        # skipped messages counted like the oracle
+    acts = torch.full((n, 2), 12, dtype=torch.int32, device="cuda")
+    lob.lob_step(pr.env.h, acts)
+    assert lob.lob_sync(pr.env.h) == lob.LOB_EINVAL
+    with pytest.raises(lob.LobError) as ei:                 # window of 2 steps exhausted
+        lob.lob_step(pr.env.h, acts)
+    assert ei.value.code == lob.LOB_ESTATE
+    pr.close()
+
+
+def test_create_rejects_bad_configs():
+    cfg = lob.lob_config(4, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
+    h = lob.lob_create(cfg)
+    with pytest.raises(lob.LobError) as ei:                 # step before reset
+        lob.lob_step(h)
+    assert ei.value.code == lob.LOB_ESTATE
+    lob.lob_destroy(h)
+    for field, val, code in (("n_envs", 0, lob.LOB_EINVAL), ("n_agents", 1, lob.LOB_EINVAL),
+                             ("cap_per_side", lob.LOB_MAX_CAP + 1, lob.LOB_ECAPACITY),
+                             ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 0, lob.LOB_EINVAL),
+                             ("action_mode", 7, lob.LOB_EINVAL)):
+        c = lob.lob_config(4, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
+        setattr(c, field, val)
+        with pytest.raises(lob.LobError) as ei:
+            lob.lob_create(c)
+        assert ei.value.code == code, field
