@@ -116,10 +116,10 @@ def _traffic_record():
     return float(rec["dram_bytes_per_launch"])
 
 
-def make_inputs(seed):
+def make_inputs(seed, gen_steps=T):
     from paper_2511_02136_gb300 import mbogen
     seeds = mbogen.env_seeds(seed, N_ENVS)
-    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=M), seeds, T)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=M), seeds, gen_steps)
     return seeds, st
 
 
@@ -134,7 +134,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     lob.build()
-    seeds, st = make_inputs(1 + rank)
+    gen = min(T, args.gen_steps)
+    seeds, st = make_inputs(1 + rank, gen)
     dev = torch.device("cuda", local)
     msgs_d = torch.from_numpy(st.msgs.view(np.uint8)).to(dev)
     off_d = torch.from_numpy(st.offsets).to(dev)
@@ -145,10 +146,10 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
-    state = {"t": T}
+    state = {"t": gen}
 
     def next_step():
-        if state["t"] >= T:                       # new episode: reset + rebind (untimed)
+        if state["t"] >= gen:                       # new episode: reset + rebind (untimed)
             env.reset(seeds_d)
             env.load_messages(msgs_d, off_d)
             state["t"] = 0
@@ -173,7 +174,7 @@ def run_gpu(args):
     clk = Clocks(local)
     t_wall0 = time.perf_counter()
     for i in range(K):
-        if state["t"] >= T:               # episode boundary: bank its messages, reset (untimed)
+        if state["t"] >= gen:             # end of the generated window: bank its messages, reset (untimed)
             msgs_total += msgs_so_far()
             env.reset(seeds_d)
             env.load_messages(msgs_d, off_d)
@@ -251,7 +252,7 @@ def run_e2e(args, env, st, seeds_d):
     """Same metric through lob_step_host: pinned host messages in, obs/rewards/done out, every step."""
     import torch
     from paper_2511_02136_gb300 import lob
-    K = min(args.e2e_steps, T)
+    K = min(args.e2e_steps, st.offsets.shape[1] - 1)
     env.reset(seeds_d)
     # per-step host slices: messages of every env for step t, packed, plus offsets
     packs = []
@@ -297,13 +298,13 @@ def cpu_baseline(seeds, st, budget_s=15.0, n_threads=None):
     o.load_messages(st.msgs, st.offsets)
     t0 = time.perf_counter()
     steps = 0
-    while steps < T and time.perf_counter() - t0 < budget_s:
+    while steps < st.offsets.shape[1] - 1 and time.perf_counter() - t0 < budget_s:
         o.step()
         steps += 1
     el = time.perf_counter() - t0
     msgs = int(o.counters()[:, 0].sum())
     return {"value": msgs / el, "unit": "msgs/s", "cores": n_threads, "kind": "oracle",
-            "sample": f"all {N_ENVS} envs, first {steps} of {T} steps of the same episode",
+            "sample": f"all {N_ENVS} envs, first {steps} steps of the same episode",
             "env_steps_per_s": steps * N_ENVS / el}
 
 
@@ -352,6 +353,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gen-steps", type=int, default=T,
+                    help="steps of messages generated (the episode wraps there; default: the full episode)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
