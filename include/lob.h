@@ -200,6 +200,63 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
 /* Number of kernels the library launched since creation (for accounting). */
 int64_t lob_kernel_launches(const lob_handle *h);
 
+/* ---- Allocation-free step (the paper has no counterpart) ------------------
+ * For callers that cannot call cudaMalloc: code embedded in a host program
+ * whose device memory is all reserved up front by its own allocator or a fixed
+ * memory budget, and loops that must not pay cudaMalloc's implicit device-wide
+ * synchronisation.  No handle is used: the caller passes every input and
+ * output buffer, and the work queue plus the env tables the step kernel
+ * needs live in one file-scope static device array of this library
+ * (LOB_NOALLOC_MAX_ENVS entries, about 256 KB, held by every GPU that loads
+ * the library until the process exits).  The function calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call shares the array and overwrites it (the
+ * queue counter is cleared at the start of each call), so calls that overlap
+ * on the GPU -- on two streams, or on two host threads -- race: serialise
+ * them.
+ *
+ * It runs one env step for every env (the same stages, kernel and results as
+ * lob_step in persistent mode) on caller-owned state:
+ *   cfg           uniform capacity cap_per_side, trace must be 0,
+ *                 warps_per_block 0..8 (0 = 4); n_envs <= LOB_NOALLOC_MAX_ENVS
+ *   d_books       n_envs book blocks, each 48*S bytes rounded up to a multiple
+ *                 of 256, S = the smallest of 32, 64, 128, 256 that is >= cap
+ *   d_env_state   n_envs * 128 bytes of per-env scalars (opaque)
+ *   d_counters    int64 [n_envs][LOB_NCOUNTERS]
+ *   d_env_seeds   uint64 [n_envs]
+ *   d_msgs, d_offsets, stride, k   as lob_load_messages: this step uses
+ *                 window step k
+ *   t             episode step; t == 0 first resets every env (empty books,
+ *                 zero agents and counters), as lob_reset does
+ *   d_actions     int32 [n_envs][2] in LOB_ACT_HOST mode, else ignored
+ *   d_obs, d_rewards, d_done   outputs as lob_observe (any may be NULL)
+ *   d_status      int32, OR-ed with 1 (malformed message), 2 (invalid action),
+ *                 4 (bounded wait expired); the caller clears it
+ * Returns LOB_EINVAL for a bad argument, LOB_ECAPACITY when n_envs or the
+ * capacity exceeds the limits above, LOB_ECUDA if a CUDA call fails. */
+#define LOB_NOALLOC_MAX_ENVS 16384
+typedef struct lob_noalloc_args {
+    const lob_config *cfg;
+    void *d_books;
+    void *d_env_state;
+    int64_t *d_counters;
+    const uint64_t *d_env_seeds;
+    const lob_msg *d_msgs;
+    const int64_t *d_offsets;
+    int64_t stride;
+    int32_t k;
+    int32_t t;
+    const int32_t *d_actions;
+    float *d_obs;
+    int64_t *d_rewards;
+    uint8_t *d_done;
+    int32_t *d_status;
+} lob_noalloc_args;
+int lob_step_noalloc(const lob_noalloc_args *args, void *stream);
+
 const char *lob_strerror(int code);
 
 #ifdef __cplusplus

@@ -523,3 +523,119 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
 int64_t lob_kernel_launches(const lob_handle *h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free step.  Callers that cannot call cudaMalloc (a host program
+// that reserves all device memory through its own allocator or a fixed
+// budget, or a loop that must not take cudaMalloc's device-wide sync) pass
+// every input and output; the scratch the persistent step kernel needs -- its
+// work-queue counter and the env list / book offset / capacity tables --
+// lives in this file-scope device array instead of a cudaMalloc'd buffer.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t NOALLOC_QUEUE_BYTES = 256;
+constexpr size_t NOALLOC_LIST_OFF = NOALLOC_QUEUE_BYTES;
+constexpr size_t NOALLOC_BOOKOFF_OFF = NOALLOC_LIST_OFF + 4 * (size_t)LOB_NOALLOC_MAX_ENVS;
+constexpr size_t NOALLOC_CAPS_OFF = NOALLOC_BOOKOFF_OFF + 8 * (size_t)LOB_NOALLOC_MAX_ENVS;
+constexpr size_t NOALLOC_BYTES = NOALLOC_CAPS_OFF + 4 * (size_t)LOB_NOALLOC_MAX_ENVS;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+}  // namespace
+
+// In host code this name is only a host-side stand-in for the symbol, not a
+// device address: kernels receive the address cudaGetSymbolAddress returns.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static unsigned char *g_noalloc_dev_ptr[NOALLOC_MAX_DEVICES];
+static int g_noalloc_n_sm[NOALLOC_MAX_DEVICES];
+
+// Per-call preparation of the scratch tables (and the episode reset at t = 0).
+__global__ void k_noalloc_prepare(unsigned char *scratch, int n, int cap, long long block_bytes, int reset,
+                                  EnvState *st, long long *cnt, int start_px) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) *reinterpret_cast<int *>(scratch) = 0;   // the work queue starts at zero every call
+    if (e >= n) return;
+    reinterpret_cast<int *>(scratch + NOALLOC_LIST_OFF)[e] = e;
+    reinterpret_cast<long long *>(scratch + NOALLOC_BOOKOFF_OFF)[e] = (long long)e * block_bytes;
+    reinterpret_cast<int *>(scratch + NOALLOC_CAPS_OFF)[e] = cap;
+    if (reset) {
+        EnvState z;
+        memset(&z, 0, sizeof(z));
+        z.last_px = start_px;
+        st[e] = z;
+        for (int i = 0; i < LOB_NCOUNTERS; i++) cnt[(long long)e * LOB_NCOUNTERS + i] = 0;
+    }
+}
+
+extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
+    if (!a || !a->cfg) return LOB_EINVAL;
+    const lob_config &c = *a->cfg;
+    if (c.n_envs < 1 || (c.n_agents != 0 && c.n_agents != 2) || c.top_levels < 1 || c.top_levels > LMAX ||
+        c.episode_len < 1 || c.mm_lot < 1 || c.exec_target < 0 ||
+        (c.exec_dir != LOB_SELL && c.exec_dir != LOB_BUY) ||
+        (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace != 0 ||
+        c.warps_per_block < 0 || c.warps_per_block > 8 || c.cap_per_side < 1)
+        return LOB_EINVAL;
+    if (c.n_envs > LOB_NOALLOC_MAX_ENVS || c.cap_per_side > LOB_MAX_CAP) return LOB_ECAPACITY;
+    if (!a->d_books || !a->d_env_state || !a->d_counters || !a->d_env_seeds || !a->d_offsets || !a->d_status ||
+        a->k < 0 || a->stride < (int64_t)a->k + 2 || a->t < 0 || a->t >= c.episode_len)
+        return LOB_EINVAL;
+    if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST && !a->d_actions) return LOB_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LOB_ECUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LOB_ECAPACITY;
+    if (g_noalloc_dev_ptr[dev] == nullptr) {   // once per device, with that device current
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return LOB_ECUDA;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LOB_ECUDA;
+        g_noalloc_n_sm[dev] = nsm;
+        g_noalloc_dev_ptr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    unsigned char *scratch = g_noalloc_dev_ptr[dev];
+    const int cls = class_of(c.cap_per_side);
+    const int K = CLASS_K[cls];
+    const long long block_bytes = ((48LL * 32 * K + 255) / 256) * 256;
+    const int n = c.n_envs;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_noalloc_prepare<<<(n + 127) / 128, 128, 0, s>>>(scratch, n, c.cap_per_side, block_bytes, a->t == 0 ? 1 : 0,
+                                                       reinterpret_cast<EnvState *>(a->d_env_state),
+                                                       reinterpret_cast<long long *>(a->d_counters), c.start_px);
+    if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+
+    KParams p;
+    memset(&p, 0, sizeof(p));
+    p.books = static_cast<unsigned char *>(a->d_books);
+    p.book_off = reinterpret_cast<const long long *>(scratch + NOALLOC_BOOKOFF_OFF);
+    p.caps = reinterpret_cast<const int *>(scratch + NOALLOC_CAPS_OFF);
+    p.st = reinterpret_cast<EnvState *>(a->d_env_state);
+    p.counters = reinterpret_cast<long long *>(a->d_counters);
+    p.seeds = reinterpret_cast<const unsigned long long *>(a->d_env_seeds);
+    p.status = a->d_status;
+    p.msgs = reinterpret_cast<const DevMsg *>(a->d_msgs);
+    p.offsets = reinterpret_cast<const long long *>(a->d_offsets);
+    p.off_stride = a->stride;
+    p.k0 = a->k;
+    p.actions = a->d_actions;
+    p.act_step_stride = 0;
+    p.action_mode = c.action_mode;
+    p.obs = a->d_obs;
+    p.rew = reinterpret_cast<long long *>(a->d_rewards);
+    p.done = a->d_done;
+    p.n_envs = n; p.n_agents = c.n_agents; p.L = c.top_levels; p.T = c.episode_len;
+    p.mm_lot = c.mm_lot; p.exec_target = c.exec_target; p.exec_dir = c.exec_dir; p.D = lob_obs_dim(&c);
+    p.t0 = a->t; p.n_steps = 1;
+    p.env_list = reinterpret_cast<const int *>(scratch + NOALLOC_LIST_OFF);
+    p.n_list = n;
+    p.queue = reinterpret_cast<int *>(scratch);
+    p.wait_budget = DEFAULT_WAIT_BUDGET;
+    const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;
+    const size_t smem = (size_t)wpb * sizeof(WarpSmem);
+    const int blocks = std::min((n + wpb - 1) / wpb, g_noalloc_n_sm[dev] * std::max(1, 32 / wpb));
+    switch (K) {
+        case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}

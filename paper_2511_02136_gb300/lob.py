@@ -39,8 +39,9 @@ EXPORTS = [
     "lob_obs_dim", "lob_create", "lob_destroy", "lob_load_messages", "lob_reset", "lob_step",
     "lob_observe", "lob_rollout", "lob_step_host", "lob_book_bytes", "lob_get_book",
     "lob_get_counters", "lob_get_agents", "lob_get_env_misc", "lob_get_actions", "lob_set_trace",
-    "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror",
+    "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
 ]
+LOB_NOALLOC_MAX_ENVS = 16384
 
 
 class LobError(RuntimeError):
@@ -55,6 +56,16 @@ class lob_config(ctypes.Structure):
         "n_envs", "n_agents", "cap_per_side", "top_levels", "episode_len", "mm_lot",
         "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block")] + \
         [("reserved", ctypes.c_int32 * 4)]
+
+
+class lob_noalloc_args(ctypes.Structure):
+    """Arguments of lob_step_noalloc (see include/lob.h): every buffer is the caller's."""
+    _fields_ = [("cfg", ctypes.POINTER(lob_config)), ("d_books", ctypes.c_void_p),
+                ("d_env_state", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
+                ("d_env_seeds", ctypes.c_void_p), ("d_msgs", ctypes.c_void_p),
+                ("d_offsets", ctypes.c_void_p), ("stride", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("t", ctypes.c_int32), ("d_actions", ctypes.c_void_p), ("d_obs", ctypes.c_void_p),
+                ("d_rewards", ctypes.c_void_p), ("d_done", ctypes.c_void_p), ("d_status", ctypes.c_void_p)]
 
 
 def _stale(target, deps):
@@ -110,6 +121,7 @@ def _load():
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
         "lob_kernel_launches": (I64, [P]),
         "lob_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lob_step_noalloc": (ctypes.c_int, [ctypes.POINTER(lob_noalloc_args), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +240,19 @@ def lob_set_launch(h, warps_per_block, persistent):
 
 def lob_kernel_launches(h) -> int:
     return _load().lob_kernel_launches(h)
+
+
+def lob_step_noalloc(args: lob_noalloc_args, stream=None):
+    """One env step on caller-owned buffers; allocates nothing (see include/lob.h)."""
+    return _check(_load().lob_step_noalloc(ctypes.byref(args), _stream(stream)), "lob_step_noalloc")
+
+
+def noalloc_book_block_bytes(cap: int) -> int:
+    """Bytes of one env's book block for lob_step_noalloc (48*S rounded up to 256)."""
+    S = 32
+    while S < cap:
+        S *= 2
+    return ((48 * S + 255) // 256) * 256
 
 
 def lob_strerror(code) -> str:
