@@ -29,6 +29,49 @@ int class_of(int cap) {
     return -1;
 }
 
+// Execution agent's base lot q0 = max(1, ceil(target / T)) (Sec. 4.1.2).
+long long exec_lot(const lob_config &c) {
+    const long long q0 = ((long long)c.exec_target + c.episode_len - 1) / c.episode_len;
+    return q0 < 1 ? 1 : q0;
+}
+
+size_t warp_smem_bytes(int K) {
+    switch (K) {
+        case 1: return sizeof(WarpSmem<1>);
+        case 2: return sizeof(WarpSmem<2>);
+        case 4: return sizeof(WarpSmem<4>);
+        default: return sizeof(WarpSmem<8>);
+    }
+}
+
+// Launch the step kernel of class K; opts into the dynamic shared memory the
+// launch shape needs (once per K and size).
+cudaError_t launch_k(int K, int blocks, int wpb, cudaStream_t s, const KParams &p) {
+    const size_t smem = (size_t)wpb * warp_smem_bytes(K);
+    static size_t opted[64][9];   // per device, per K: largest size opted into so far
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem > opted[dev][K]) {
+        switch (K) {
+            case 1: e = cudaFuncSetAttribute(k_env_steps<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+            case 2: e = cudaFuncSetAttribute(k_env_steps<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+            case 4: e = cudaFuncSetAttribute(k_env_steps<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+            default: e = cudaFuncSetAttribute(k_env_steps<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+        }
+        if (e != cudaSuccess) return e;
+        opted[dev][K] = smem;
+    }
+    switch (K) {
+        case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        default: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 struct lob_handle {
@@ -51,6 +94,8 @@ struct lob_handle {
     int *d_act = nullptr;
     int *d_env_list = nullptr;
     int *d_queue = nullptr;
+    bool uniform_cap = false;
+    long long uni_block = 0;
     int class_begin[NCLASS] = {0, 0, 0, 0};
     int class_count[NCLASS] = {0, 0, 0, 0};
     long long book_bytes = 0, canon_bytes = 0;
@@ -159,6 +204,8 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     }
     h->book_bytes = acc;
     h->canon_bytes = cacc;
+    h->uniform_cap = !h_caps;
+    h->uni_block = ((48LL * 32 * CLASS_K[class_of(c.cap_per_side < 1 ? 1 : (c.cap_per_side > LOB_MAX_CAP ? LOB_MAX_CAP : c.cap_per_side))] + 255) / 256) * 256;
     const size_t n = (size_t)c.n_envs;
     const int A = c.n_agents;
     bool fail = false;
@@ -304,27 +351,24 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.snaps = (c.trace & 2) ? h->d_snaps : nullptr; p.snap_cap = h->snap_cap;
     p.snap_count = (c.trace & 2) ? reinterpret_cast<long long *>(h->d_snap_count) : nullptr;
     p.wait_budget = DEFAULT_WAIT_BUDGET;
+    p.exec_q0 = exec_lot(c);
     const int wpb = h->wpb;
-    const size_t smem = (size_t)wpb * sizeof(WarpSmem);
     if (h->persistent) {
         if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
     }
     for (int k = 0; k < NCLASS; k++) {
         const int cnt = h->class_count[k];
         if (cnt == 0) continue;
-        p.env_list = h->d_env_list + h->class_begin[k];
+        const bool uniform = cnt == c.n_envs && h->uniform_cap;
+        p.env_list = uniform ? nullptr : h->d_env_list + h->class_begin[k];
+        p.uni_cap = uniform ? c.cap_per_side : 0;
+        p.uni_block = uniform ? h->uni_block : 0;
         p.n_list = cnt;
         p.queue = h->persistent ? h->d_queue + k : nullptr;
         int blocks = (cnt + wpb - 1) / wpb;
         if (h->persistent) blocks = std::min(blocks, h->n_sm * std::max(1, 32 / wpb));
-        switch (CLASS_K[k]) {
-            case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
-            case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
-            case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
-            case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        }
         h->launches++;
-        if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+        if (launch_k(CLASS_K[k], blocks, wpb, s, p) != cudaSuccess) return LOB_ECUDA;
     }
     return LOB_OK;
 }
@@ -628,14 +672,9 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     p.n_list = n;
     p.queue = reinterpret_cast<int *>(scratch);
     p.wait_budget = DEFAULT_WAIT_BUDGET;
+    p.exec_q0 = exec_lot(c);
     const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;
-    const size_t smem = (size_t)wpb * sizeof(WarpSmem);
     const int blocks = std::min((n + wpb - 1) / wpb, g_noalloc_n_sm[dev] * std::max(1, 32 / wpb));
-    switch (K) {
-        case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
-    }
+    if (launch_k(K, blocks, wpb, s, p) != cudaSuccess) return LOB_ECUDA;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }

@@ -1,13 +1,22 @@
 // lob_device.cuh -- sm_103a kernels of the batched limit-order-book env step.
 //
-// One warp runs one environment.  Each side of the book is a priority-sorted
-// array (best price first, then arrival) held in REGISTERS in a blocked
-// layout: lane l owns slots l*K .. l*K+K-1 of a side (capacity 32*K).  An
-// insert or a removal is then one neighbour-lane shuffle plus per-lane
-// selects; a lookup is a compare plus a ballot.  Messages are staged into
-// shared memory tile by tile with cp.async.bulk (TMA bulk copy) completing on
-// an mbarrier, and broadcast to the warp from there.  Agents, counters and
-// all other per-env scalars are warp-uniform registers.
+// One warp runs one environment.  Each side of the book is a POOL of S = 32*K
+// order slots plus a priority INDEX:
+//   * pool slot s belongs to lane s / K (register r = s % K); that lane keeps
+//     the slot's price and id in registers so that "how many resting orders
+//     rank ahead of price p" and "which slot holds (price, id)" are one
+//     compare per register plus one warp reduction / ballot;
+//   * every slot's price, size, id and arrival stamp are also in shared memory
+//     (written once when the order comes to rest);
+//   * the index lists slot numbers in priority order (best price first, then
+//     arrival), one byte per position, positions lane*K .. lane*K+K-1 packed
+//     four to a 32-bit register of that lane.  Resting an order or removing
+//     one shifts only these bytes: one neighbour-lane shuffle and a few
+//     byte-mask operations, whatever the number of fields per order;
+//   * the front order (position 0) is cached in warp-uniform registers.
+// Messages are staged into shared memory 32 records at a time by
+// cp.async.bulk (TMA bulk copy) completing on an mbarrier, and the next record
+// is always read one message ahead.
 //
 // The stages follow the environment step of JaxMARL-HFT Sec. 4: action
 // conversion with carry-over cancels, random shuffle of the agents' orders,
@@ -23,6 +32,7 @@ namespace lobk {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TILE = 32;        // messages per staged tile
 constexpr int LMAX = 64;        // max observation levels per side
+constexpr int SMAX = 256;       // max pool slots per side (byte-wide index)
 constexpr int ST_BADMSG = 1, ST_BADACT = 2, ST_TIMEOUT = 4;
 
 struct DevMsg {
@@ -73,10 +83,15 @@ struct KParams {
     unsigned char *snaps;
     long long snap_cap;
     long long *snap_count;
-    const int *env_list;
+    const int *env_list;   // NULL: env = list position (identity)
     int n_list;
     int *queue;
     long long wait_budget;
+    // uniform layout: when uni_cap > 0 every env has capacity uni_cap and its
+    // book block at env * uni_block; book_off / caps are not read
+    int uni_cap;
+    long long uni_block;
+    long long exec_q0;     // max(1, ceil(exec_target / T)), computed on the host
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -139,170 +154,141 @@ __device__ __forceinline__ unsigned bounded(unsigned long long x, unsigned n) {
     return (unsigned)(((unsigned long long)(unsigned)(x >> 32) * n) >> 32);
 }
 
-// ---------------------------------------------------------------- book
+// ---------------------------------------------------------------- shared memory
+// Pool copies of one side (slot-indexed), S = 32*K slots.
 template <int K>
-struct Book {
-    int px[K], qty[K];
-    long long id[K], ts[K];
-    int n;     // live orders (warp-uniform)
-    int best;  // price of slot 0 when n > 0 (warp-uniform)
+struct PoolSmem {
+    long long id[32 * K];
+    long long ts[32 * K];
+    int px[32 * K];
+    int qty[32 * K];
 };
 
-// "a has priority over (or ties with) a new order at p" on a side
+// Per-warp shared memory.
+template <int K>
+struct WarpSmem {
+    DevMsg tile[2][TILE];
+    DevMsg amsg[4];                // the step's agent orders, after the shuffle
+    unsigned long long bar[2];
+    PoolSmem<K> pool[2];           // 0 = bids, 1 = asks
+    long long lvl_q[2][LMAX];
+    int lvl_px[2][LMAX];
+    unsigned char cand[2][32 * K]; // carry-over cancel flags per slot
+};
+
+// ---------------------------------------------------------------- book side
+template <int K>
+struct Side {
+    static constexpr int NW = (K + 3) / 4;           // index words per lane
+    static constexpr int BPW = K < 4 ? K : 4;        // index bytes used per word
+    static constexpr unsigned ALLB = BPW == 4 ? 0xffffffffu : ((1u << (8 * BPW)) - 1u);
+    static constexpr unsigned KMASK = K == 32 ? 0xffffffffu : ((1u << K) - 1u);
+    int px[K];          // price of pool slot lane*K + r
+    long long id[K];    // id of pool slot lane*K + r
+    unsigned occ;       // occupied pool slots of this lane (bit r)
+    unsigned ix[NW];    // index bytes for positions lane*K .. lane*K+K-1
+    int n;              // live orders (warp-uniform)
+    int fpx, fqty, fslot;  // front order (position 0), valid when n > 0
+    long long fid;
+};
+
 template <bool BID>
 __device__ __forceinline__ bool at_least(int a, int p) { return BID ? a >= p : a <= p; }
 
-template <int K, bool BID>
-__device__ __forceinline__ void book_load(Book<K> &S, const unsigned char *blk, int cap_slots, int lane, int n) {
-    const int s = BID ? 0 : 1;
-    const int *px = reinterpret_cast<const int *>(blk) + s * cap_slots + lane * K;
-    const int *qt = reinterpret_cast<const int *>(blk) + 2 * cap_slots + s * cap_slots + lane * K;
-    const long long *id = reinterpret_cast<const long long *>(blk + 16 * cap_slots) + s * cap_slots + lane * K;
-    const long long *ts = reinterpret_cast<const long long *>(blk + 32 * cap_slots) + s * cap_slots + lane * K;
-    S.n = n;
-    if (lane * K < n) {
-        if constexpr (K % 4 == 0) {
-#pragma unroll
-            for (int v = 0; v < K / 4; v++) {
-                int4 a = reinterpret_cast<const int4 *>(px)[v];
-                int4 b = reinterpret_cast<const int4 *>(qt)[v];
-                S.px[4 * v] = a.x; S.px[4 * v + 1] = a.y; S.px[4 * v + 2] = a.z; S.px[4 * v + 3] = a.w;
-                S.qty[4 * v] = b.x; S.qty[4 * v + 1] = b.y; S.qty[4 * v + 2] = b.z; S.qty[4 * v + 3] = b.w;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < K; r++) { S.px[r] = px[r]; S.qty[r] = qt[r]; }
-        }
-        if constexpr (K % 2 == 0) {
-#pragma unroll
-            for (int v = 0; v < K / 2; v++) {
-                longlong2 a = reinterpret_cast<const longlong2 *>(id)[v];
-                longlong2 b = reinterpret_cast<const longlong2 *>(ts)[v];
-                S.id[2 * v] = a.x; S.id[2 * v + 1] = a.y;
-                S.ts[2 * v] = b.x; S.ts[2 * v + 1] = b.y;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < K; r++) { S.id[r] = id[r]; S.ts[r] = ts[r]; }
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < K; r++) { S.px[r] = 0; S.qty[r] = 0; S.id[r] = 0; S.ts[r] = 0; }
-    }
-    S.best = __shfl_sync(FULL, S.px[0], 0);
-}
-
-template <int K, bool BID>
-__device__ __forceinline__ void book_store(const Book<K> &S, unsigned char *blk, int cap_slots, int lane) {
-    const int s = BID ? 0 : 1;
-    int *px = reinterpret_cast<int *>(blk) + s * cap_slots + lane * K;
-    int *qt = reinterpret_cast<int *>(blk) + 2 * cap_slots + s * cap_slots + lane * K;
-    long long *id = reinterpret_cast<long long *>(blk + 16 * cap_slots) + s * cap_slots + lane * K;
-    long long *ts = reinterpret_cast<long long *>(blk + 32 * cap_slots) + s * cap_slots + lane * K;
-    if (lane * K >= S.n) return;
-    if constexpr (K % 4 == 0) {
-#pragma unroll
-        for (int v = 0; v < K / 4; v++) {
-            reinterpret_cast<int4 *>(px)[v] = make_int4(S.px[4 * v], S.px[4 * v + 1], S.px[4 * v + 2], S.px[4 * v + 3]);
-            reinterpret_cast<int4 *>(qt)[v] = make_int4(S.qty[4 * v], S.qty[4 * v + 1], S.qty[4 * v + 2], S.qty[4 * v + 3]);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < K; r++) { px[r] = S.px[r]; qt[r] = S.qty[r]; }
-    }
-    if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < K / 2; v++) {
-            reinterpret_cast<longlong2 *>(id)[v] = make_longlong2(S.id[2 * v], S.id[2 * v + 1]);
-            reinterpret_cast<longlong2 *>(ts)[v] = make_longlong2(S.ts[2 * v], S.ts[2 * v + 1]);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < K; r++) { id[r] = S.id[r]; ts[r] = S.ts[r]; }
-    }
-}
-
-// Rest an order.  Returns 0 inserted, 1 inserted after evicting the last
-// (worst price, latest arrival) order of a full side, 2 dropped (full and not
-// strictly better than the worst resting price).
-template <int K, bool BID>
-__device__ __forceinline__ int book_insert(Book<K> &S, int cap, int p, int q, long long oid, long long tsn,
-                                           int lane, long long &evict_vol) {
-    bool pre[K];
-    bool any_after = false;
-#pragma unroll
-    for (int r = 0; r < K; r++) {
-        const bool v = lane * K + r < S.n;
-        pre[r] = v && at_least<BID>(S.px[r], p);
-        any_after |= v && !pre[r];
-    }
-    const int ppx = __shfl_up_sync(FULL, S.px[K - 1], 1);
-    const int pq = __shfl_up_sync(FULL, S.qty[K - 1], 1);
-    const long long pid = __shfl_up_sync(FULL, S.id[K - 1], 1);
-    const long long pts = __shfl_up_sync(FULL, S.ts[K - 1], 1);
-    const bool ppre = lane == 0 || (lane * K - 1 < S.n && at_least<BID>(ppx, p));
-    int ret = 0;
-    if (S.n >= cap) {
-        if (__ballot_sync(FULL, any_after) == 0) return 2;
-#pragma unroll
-        for (int r = 0; r < K; r++)
-            if (lane * K + r == S.n - 1) evict_vol += S.qty[r];
-        ret = 1;
-    }
-#pragma unroll
-    for (int r = K - 1; r >= 0; r--) {
-        const bool pp = r == 0 ? ppre : pre[r - 1];
-        if (!pre[r]) {
-            if (pp) {
-                S.px[r] = p; S.qty[r] = q; S.id[r] = oid; S.ts[r] = tsn;
-            } else if (r == 0) {
-                S.px[0] = ppx; S.qty[0] = pq; S.id[0] = pid; S.ts[0] = pts;
-            } else {
-                S.px[r] = S.px[r - 1]; S.qty[r] = S.qty[r - 1]; S.id[r] = S.id[r - 1]; S.ts[r] = S.ts[r - 1];
-            }
-        }
-    }
-    S.best = S.n == 0 ? p : (BID ? max(S.best, p) : min(S.best, p));
-    if (ret == 0) S.n++;
-    return ret;
-}
-
-// Remove the single slot marked in `hit` (bits r) of lane `first`.
+// Byte (slot number) at local position j of this lane.
 template <int K>
-__device__ __forceinline__ void book_remove(Book<K> &S, unsigned hit, int first, int lane) {
-    const int nx = __shfl_down_sync(FULL, S.px[0], 1);
-    const int nq = __shfl_down_sync(FULL, S.qty[0], 1);
-    const long long nid = __shfl_down_sync(FULL, S.id[0], 1);
-    const long long nts = __shfl_down_sync(FULL, S.ts[0], 1);
-    bool after = lane > first;
-#pragma unroll
-    for (int r = 0; r < K; r++) {
-        after = after || ((hit >> r) & 1u);
-        if (after) {
-            if (r == K - 1) {
-                S.px[r] = nx; S.qty[r] = nq; S.id[r] = nid; S.ts[r] = nts;
-            } else {
-                S.px[r] = S.px[r + 1]; S.qty[r] = S.qty[r + 1]; S.id[r] = S.id[r + 1]; S.ts[r] = S.ts[r + 1];
-            }
-        }
-    }
-    S.n--;
-    S.best = __shfl_sync(FULL, S.px[0], 0);
+__device__ __forceinline__ int ix_byte(const Side<K> &S, int j) {
+    return (S.ix[j >> 2] >> (8 * (j & 3))) & 0xff;
 }
 
-// First slot (priority order) with this (price, id); returns the lane holding
-// it (or -1) and that lane's one-bit mask in `hit`.
+// Slot number at uniform position q (q < 32*K).
 template <int K>
-__device__ __forceinline__ int book_find(const Book<K> &S, int p, long long oid, int lane, unsigned &hit) {
-    unsigned h = 0;
+__device__ __forceinline__ int slot_at(const Side<K> &S, int q) {
+    const int j = q % K;
+    unsigned w = S.ix[0];
 #pragma unroll
-    for (int r = 0; r < K; r++)
-        if (lane * K + r < S.n && S.id[r] == oid && S.px[r] == p) h |= 1u << r;
-    const unsigned lanes = __ballot_sync(FULL, h != 0);
-    if (lanes == 0) { hit = 0; return -1; }
-    const int first = __ffs(lanes) - 1;
-    hit = lane == first ? (h & (0u - h)) : 0u;
-    return first;
+    for (int i = 1; i < Side<K>::NW; i++)
+        if ((j >> 2) == i) w = S.ix[i];
+    w = __shfl_sync(FULL, w, q / K);
+    return (w >> (8 * (j & 3))) & 0xff;
+}
+
+// Insert slot f at position pos; positions >= pos move up by one.
+template <int K>
+__device__ __forceinline__ void ix_insert(Side<K> &S, int pos, int f, int lane) {
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
+    constexpr unsigned ALLB = Side<K>::ALLB;
+    const unsigned top = (S.ix[NW - 1] >> (8 * (BPW - 1))) & 0xffu;
+    const unsigned carry = __shfl_up_sync(FULL, top, 1);
+    unsigned shifted[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const unsigned in = w == 0 ? carry : (S.ix[w - 1] >> 24);
+        shifted[w] = ((S.ix[w] << 8) | in) & ALLB;
+    }
+    const unsigned fb = (unsigned)f * 0x01010101u;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const int d = pos - (lane * K + 4 * w);
+        const unsigned keep = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
+        const unsigned fm = (d >= 0 && d < BPW) ? (0xffu << (8 * d)) : 0u;
+        S.ix[w] = (S.ix[w] & keep) | (fb & fm) | (shifted[w] & ~(keep | fm));
+    }
+}
+
+// Remove position q; positions > q move down by one.
+template <int K>
+__device__ __forceinline__ void ix_remove(Side<K> &S, int q, int lane) {
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
+    constexpr unsigned ALLB = Side<K>::ALLB;
+    const unsigned nxt = __shfl_down_sync(FULL, S.ix[0] & 0xffu, 1);
+    unsigned shifted[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const unsigned in = w + 1 < NW ? (S.ix[w + 1] & 0xffu) : nxt;
+        shifted[w] = ((S.ix[w] >> 8) | (in << (8 * (BPW - 1)))) & ALLB;
+    }
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const int d = q - (lane * K + 4 * w);
+        const unsigned keep = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
+        S.ix[w] = (S.ix[w] & keep) | (shifted[w] & ~keep);
+    }
+}
+
+// Position of slot s among the n live positions.
+template <int K>
+__device__ __forceinline__ int ix_find(const Side<K> &S, int s, int lane) {
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
+    constexpr unsigned ALLB = Side<K>::ALLB;
+    int local = -1;
+#pragma unroll
+    for (int w = NW - 1; w >= 0; w--) {
+        const int d = S.n - (lane * K + 4 * w);
+        const unsigned valid = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
+        const unsigned m = __vcmpeq4(S.ix[w], (unsigned)s * 0x01010101u) & valid;
+        if (m) local = 4 * w + ((__ffs(m) - 1) >> 3);
+    }
+    const unsigned lanes = __ballot_sync(FULL, local >= 0);
+    const int L = __ffs(lanes) - 1;
+    return __shfl_sync(FULL, lane * K + local, L);
+}
+
+template <int K>
+__device__ __forceinline__ void slot_clear(Side<K> &S, int s, int lane) {
+    if (lane == s / K) S.occ &= ~(1u << (s % K));
+}
+
+// Refresh the cached front order from position 0.
+template <int K>
+__device__ __forceinline__ void front_refresh(Side<K> &S, const PoolSmem<K> &P) {
+    if (S.n > 0) {
+        const int s = slot_at<K>(S, 0);
+        S.fslot = s;
+        S.fpx = P.px[s];
+        S.fqty = P.qty[s];
+        S.fid = P.id[s];
+    }
 }
 
 // ---------------------------------------------------------------- env context
@@ -313,10 +299,8 @@ struct Ctx {
     long long bg_cash, bg_inv;
     int last_px;
     int A, exec_dir;
-    // cumulative counters (uniform), plus per-lane partial sums
-    long long c_msgs, c_agent, c_fills, c_fill_vol, c_add_vol, c_mkt_vol, c_mkt_disc;
-    long long c_cancel_miss, c_drop_vol, c_drop_cnt, c_evict_cnt, c_bad;
-    long long l_cancel_vol, l_evict_vol;  // per lane
+    long long c_msgs, c_agent, c_fills, c_fill_vol, c_add_vol, c_mkt_vol, c_mkt_disc, c_cancel_vol;
+    long long c_cancel_miss, c_drop_vol, c_drop_cnt, c_evict_vol, c_evict_cnt, c_bad;
     int msg_idx;
     int fill_n;
     int status;
@@ -331,145 +315,282 @@ struct Ctx {
     __device__ __forceinline__ int owner(long long id) const {
         return (id >= 0 || A == 0) ? 2 : (int)((~id) & 1);
     }
-    // A trade at the resting order's price; cash and inventory move between
-    // the owners of the two orders.
-    __device__ __forceinline__ void fill(int px, int f, long long maker_id, long long taker_id, int taker_side,
-                                         int lane) {
-        const int om = owner(maker_id), ot = owner(taker_id);
-        const int buyer = taker_side == LOB_BUY ? ot : om;
-        const int seller = taker_side == LOB_BUY ? om : ot;
-        const long long notional = (long long)((unsigned long long)(long long)px * (unsigned long long)(long long)f);
-        credit(buyer, -notional, f);
-        credit(seller, notional, -(long long)f);
-        if (A > 0 && (exec_dir == LOB_SELL ? seller : buyer) == 0) exec_done += f;
-        last_px = px;
-        c_fills += 1;
-        c_fill_vol += f;
-        if (fill_log != nullptr && lane == 0 && fill_n < fill_cap) {
-            lob_fill r;
-            r.maker_id = maker_id; r.taker_id = taker_id; r.px = px; r.qty = f;
-            r.msg_idx = msg_idx; r.taker_side = taker_side;
-            fill_log[fill_n] = r;
-        }
-        fill_n++;
-    }
 };
+
+__device__ __noinline__ void log_fill(lob_fill *log, int idx, long long maker, long long taker, int px, int f,
+                                      int msg_idx, int side) {
+    lob_fill r;
+    r.maker_id = maker; r.taker_id = taker; r.px = px; r.qty = f; r.msg_idx = msg_idx; r.taker_side = side;
+    log[idx] = r;
+}
+
+// A trade at the resting order's price; cash and inventory move between the
+// owners of the two orders (0, 1 = agents, 2 = background).
+__device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_id, long long taker_id,
+                                        int taker_side, int lane) {
+    const int om = c.owner(maker_id), ot = c.owner(taker_id);
+    const int buyer = taker_side == LOB_BUY ? ot : om;
+    const int seller = taker_side == LOB_BUY ? om : ot;
+    const long long notional = (long long)((unsigned long long)(long long)px * (unsigned long long)(long long)f);
+    const long long ff = f;
+    c.cash0 += (buyer == 0 ? -notional : 0) + (seller == 0 ? notional : 0);
+    c.inv0 += (buyer == 0 ? ff : 0) - (seller == 0 ? ff : 0);
+    c.cash1 += (buyer == 1 ? -notional : 0) + (seller == 1 ? notional : 0);
+    c.inv1 += (buyer == 1 ? ff : 0) - (seller == 1 ? ff : 0);
+    c.bg_cash += (buyer == 2 ? -notional : 0) + (seller == 2 ? notional : 0);
+    c.bg_inv += (buyer == 2 ? ff : 0) - (seller == 2 ? ff : 0);
+    c.exec_done += (c.A > 0 && (c.exec_dir == LOB_SELL ? seller : buyer) == 0) ? ff : 0;
+    c.last_px = px;
+    c.c_fills += 1;
+    c.c_fill_vol += f;
+    if (c.fill_log != nullptr) {
+        if (lane == 0 && c.fill_n < c.fill_cap)
+            log_fill(c.fill_log, c.fill_n, maker_id, taker_id, px, f, c.msg_idx, taker_side);
+        c.fill_n++;
+    }
+}
 
 // Take liquidity from resting side O (RBID: O holds bids), price first then
 // time, up to the limit (if any).  Returns the unfilled quantity.
 template <int K, bool RBID>
-__device__ __forceinline__ int book_take(Book<K> &O, bool has_limit, int limit, int q, long long taker_id,
-                                         int taker_side, Ctx &c, int lane) {
-    if (O.n == 0 || (has_limit && !at_least<RBID>(O.best, limit))) return q;
-    while (q > 0 && O.n > 0) {
-        const int fpx = __shfl_sync(FULL, O.px[0], 0);
-        const int fq = __shfl_sync(FULL, O.qty[0], 0);
-        const long long fid = __shfl_sync(FULL, O.id[0], 0);
-        if (has_limit && !at_least<RBID>(fpx, limit)) break;
-        const int f = min(q, fq);
-        c.fill(fpx, f, fid, taker_id, taker_side, lane);
+__device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_limit, int limit, int q,
+                                         long long taker_id, int taker_side, Ctx &c, int lane) {
+    while (q > 0 && O.n > 0 && (!has_limit || at_least<RBID>(O.fpx, limit))) {
+        // the order behind the front, fetched before we know whether it is needed
+        const int s1 = slot_at<K>(O, 1);
+        const int npx = P.px[s1], nqt = P.qty[s1];
+        const long long nid = P.id[s1];
+        const int f = min(q, O.fqty);
+        do_fill(c, O.fpx, f, O.fid, taker_id, taker_side, lane);
         q -= f;
-        if (f == fq) {
-            const int nx = __shfl_down_sync(FULL, O.px[0], 1);
-            const int nq = __shfl_down_sync(FULL, O.qty[0], 1);
-            const long long nid = __shfl_down_sync(FULL, O.id[0], 1);
-            const long long nts = __shfl_down_sync(FULL, O.ts[0], 1);
-#pragma unroll
-            for (int r = 0; r < K - 1; r++) {
-                O.px[r] = O.px[r + 1]; O.qty[r] = O.qty[r + 1]; O.id[r] = O.id[r + 1]; O.ts[r] = O.ts[r + 1];
-            }
-            O.px[K - 1] = nx; O.qty[K - 1] = nq; O.id[K - 1] = nid; O.ts[K - 1] = nts;
+        if (f == O.fqty) {
+            slot_clear<K>(O, O.fslot, lane);
+            ix_remove<K>(O, 0, lane);
             O.n--;
-        } else if (lane == 0) {
-            O.qty[0] -= f;
+            O.fpx = npx; O.fqty = nqt; O.fid = nid; O.fslot = s1;
+        } else {
+            O.fqty -= f;
+            P.qty[O.fslot] = O.fqty;   // every lane stores the same value
         }
     }
-    O.best = __shfl_sync(FULL, O.px[0], 0);
     return q;
 }
 
-// Book of env 0 after a message, canonical layout (trace mode).
+// Rest an order on its own side, applying the capacity rule.
+template <int K, bool BID>
+__device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, int p, int q, long long oid,
+                                          Ctx &c, int lane) {
+    // independent of p: the worst order (evicted if the side is full) and a free slot
+    const int vic = slot_at<K>(S, S.n > 0 ? S.n - 1 : 0);
+    const int vic_q = P.qty[vic];
+    const unsigned fr = ~S.occ & Side<K>::KMASK;
+    const unsigned flanes = __ballot_sync(FULL, fr != 0);
+    const int free_slot = __shfl_sync(FULL, lane * K + __ffs(fr) - 1, __ffs(flanes) - 1);
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p));
+    const int pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
+    const bool full = S.n >= cap;
+    if (full && pos >= S.n) {  // not strictly better than the worst resting price
+        c.c_drop_vol += q;
+        c.c_drop_cnt += 1;
+        return;
+    }
+    const int f = full ? vic : free_slot;
+    if (full) {
+        c.c_evict_vol += vic_q;
+        c.c_evict_cnt += 1;
+        S.n--;
+    }
+    const int fl = f / K, fr_ = f % K;
+    if (lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
+#pragma unroll
+    for (int r = 0; r < K; r++)
+        if (lane == fl && r == fr_) { S.px[r] = p; S.id[r] = oid; }
+    P.px[f] = p; P.qty[f] = q; P.id[f] = oid; P.ts[f] = c.ts_next;   // same value from every lane
+    c.ts_next++;
+    ix_insert<K>(S, pos, f, lane);
+    S.n++;
+    if (pos == 0) { S.fpx = p; S.fqty = q; S.fid = oid; S.fslot = f; }
+}
+
+// Remove slot s (any position) and fix the front if it was there.
 template <int K>
-__device__ void write_snapshot(const Book<K> &B, const Book<K> &S, int C, unsigned char *rec, int lane) {
+__device__ __forceinline__ void side_remove_slot(Side<K> &S, PoolSmem<K> &P, int s, int lane) {
+    const int q = ix_find<K>(S, s, lane);
+    slot_clear<K>(S, s, lane);
+    ix_remove<K>(S, q, lane);
+    S.n--;
+    if (q == 0) front_refresh<K>(S, P);
+}
+
+// First slot in priority order holding (price, id), when several do.
+template <int K>
+__device__ __forceinline__ int first_dup_slot(const Side<K> &S, const PoolSmem<K> &P, int p, long long oid, int lane) {
+    int best = -1;
+#pragma unroll
+    for (int j = K - 1; j >= 0; j--) {
+        const int q = lane * K + j;
+        if (q < S.n) {
+            const int s = ix_byte<K>(S, j);
+            if (P.px[s] == p && P.id[s] == oid) best = j;
+        }
+    }
+    const unsigned lanes = __ballot_sync(FULL, best >= 0);
+    const int L = __ffs(lanes) - 1;
+    const int j = __shfl_sync(FULL, best, L);
+    return slot_at<K>(S, L * K + j);
+}
+
+// Partial cancel or delete: lookup by (price, id); a miss is a no-op.
+template <int K>
+__device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type, int p, int qty, long long oid,
+                                            Ctx &c, int lane) {
+    unsigned m = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++)
+        if (((S.occ >> r) & 1u) && S.px[r] == p && S.id[r] == oid) m |= 1u << r;
+    const unsigned lanes = __ballot_sync(FULL, m != 0);
+    if (lanes == 0) {
+        c.c_cancel_miss += 1;
+        return;
+    }
+    const bool dup = __popc(lanes) > 1 || __ballot_sync(FULL, __popc(m) > 1) != 0;
+    int s;
+    if (!dup) {
+        const int L = __ffs(lanes) - 1;
+        s = __shfl_sync(FULL, lane * K + __ffs(m) - 1, L);
+    } else {
+        s = first_dup_slot<K>(S, P, p, oid, lane);
+    }
+    const int q0 = P.qty[s];
+    const int cut = type == LOB_PARTIAL ? min(qty, q0) : q0;
+    c.c_cancel_vol += cut;
+    if (q0 - cut == 0) {
+        side_remove_slot<K>(S, P, s, lane);
+    } else {
+        P.qty[s] = q0 - cut;   // same value from every lane
+        if (s == S.fslot) S.fqty = q0 - cut;
+    }
+}
+
+// ---------------------------------------------------------------- load / store / gather
+template <int K, bool BID>
+__device__ __forceinline__ void side_load(Side<K> &S, PoolSmem<K> &P, const unsigned char *blk, int n, int lane) {
+    constexpr int SL = 32 * K;
+    const int s = BID ? 0 : 1;
+    const int *gpx = reinterpret_cast<const int *>(blk) + s * SL + lane * K;
+    const int *gqt = reinterpret_cast<const int *>(blk) + 2 * SL + s * SL + lane * K;
+    const long long *gid = reinterpret_cast<const long long *>(blk + 16 * SL) + s * SL + lane * K;
+    const long long *gts = reinterpret_cast<const long long *>(blk + 32 * SL) + s * SL + lane * K;
+    int qt[K];
+    long long ts[K];
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < K / 4; v++) {
+            const int4 a = reinterpret_cast<const int4 *>(gpx)[v];
+            const int4 b = reinterpret_cast<const int4 *>(gqt)[v];
+            S.px[4 * v] = a.x; S.px[4 * v + 1] = a.y; S.px[4 * v + 2] = a.z; S.px[4 * v + 3] = a.w;
+            qt[4 * v] = b.x; qt[4 * v + 1] = b.y; qt[4 * v + 2] = b.z; qt[4 * v + 3] = b.w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < K; r++) { S.px[r] = gpx[r]; qt[r] = gqt[r]; }
+    }
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < K / 2; v++) {
+            const longlong2 a = reinterpret_cast<const longlong2 *>(gid)[v];
+            const longlong2 b = reinterpret_cast<const longlong2 *>(gts)[v];
+            S.id[2 * v] = a.x; S.id[2 * v + 1] = a.y; ts[2 * v] = b.x; ts[2 * v + 1] = b.y;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < K; r++) { S.id[r] = gid[r]; ts[r] = gts[r]; }
+    }
+    // slot = position after a load; index bytes are the identity
+    S.n = n;
+    S.occ = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int slot = lane * K + r;
+        if (slot < n) S.occ |= 1u << r;
+        P.px[slot] = S.px[r]; P.qty[slot] = qt[r]; P.id[slot] = S.id[r]; P.ts[slot] = ts[r];
+    }
+#pragma unroll
+    for (int w = 0; w < Side<K>::NW; w++) {
+        unsigned v = 0;
+#pragma unroll
+        for (int b = 0; b < Side<K>::BPW; b++) v |= (unsigned)(lane * K + 4 * w + b) << (8 * b);
+        S.ix[w] = v;
+    }
+}
+
+// Position-ordered copies of this lane's K positions (priority order).
+template <int K>
+__device__ __forceinline__ void side_gather(const Side<K> &S, const PoolSmem<K> &P, int (&px)[K], int (&qt)[K],
+                                            long long (&id)[K], long long (&ts)[K]) {
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        const int s = ix_byte<K>(S, j);
+        px[j] = P.px[s]; qt[j] = P.qty[s]; id[j] = P.id[s]; ts[j] = P.ts[s];
+    }
+}
+
+template <int K, bool BID>
+__device__ __forceinline__ void side_store(const Side<K> &S, const int (&px)[K], const int (&qt)[K],
+                                           const long long (&id)[K], const long long (&ts)[K],
+                                           unsigned char *blk, int lane) {
+    constexpr int SL = 32 * K;
+    const int s = BID ? 0 : 1;
+    int *gpx = reinterpret_cast<int *>(blk) + s * SL + lane * K;
+    int *gqt = reinterpret_cast<int *>(blk) + 2 * SL + s * SL + lane * K;
+    long long *gid = reinterpret_cast<long long *>(blk + 16 * SL) + s * SL + lane * K;
+    long long *gts = reinterpret_cast<long long *>(blk + 32 * SL) + s * SL + lane * K;
+    if (lane * K >= S.n) return;
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < K / 4; v++) {
+            reinterpret_cast<int4 *>(gpx)[v] = make_int4(px[4 * v], px[4 * v + 1], px[4 * v + 2], px[4 * v + 3]);
+            reinterpret_cast<int4 *>(gqt)[v] = make_int4(qt[4 * v], qt[4 * v + 1], qt[4 * v + 2], qt[4 * v + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < K; r++) { gpx[r] = px[r]; gqt[r] = qt[r]; }
+    }
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < K / 2; v++) {
+            reinterpret_cast<longlong2 *>(gid)[v] = make_longlong2(id[2 * v], id[2 * v + 1]);
+            reinterpret_cast<longlong2 *>(gts)[v] = make_longlong2(ts[2 * v], ts[2 * v + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < K; r++) { gid[r] = id[r]; gts[r] = ts[r]; }
+    }
+}
+
+// Book of env 0 after a message, canonical layout (trace mode only).
+template <int K>
+__device__ __forceinline__ void write_snapshot(const Side<K> &B, const Side<K> &A, const WarpSmem<K> &sm, int C,
+                                            unsigned char *rec, int lane) {
     int *n2 = reinterpret_cast<int *>(rec);
     int *px = n2 + 2;
     int *qt = px + 2 * C;
     long long *id = reinterpret_cast<long long *>(rec + 8 + 16 * (long long)C);
     long long *ts = id + 2 * C;
-    if (lane == 0) { n2[0] = B.n; n2[1] = S.n; }
+    if (lane == 0) { n2[0] = B.n; n2[1] = A.n; }
 #pragma unroll
-    for (int r = 0; r < K; r++) {
-        const int j = lane * K + r;
-        if (j < C) {
-            const bool vb = j < B.n, va = j < S.n;
-            px[j] = vb ? B.px[r] : 0; qt[j] = vb ? B.qty[r] : 0; id[j] = vb ? B.id[r] : 0; ts[j] = vb ? B.ts[r] : 0;
-            px[C + j] = va ? S.px[r] : 0; qt[C + j] = va ? S.qty[r] : 0;
-            id[C + j] = va ? S.id[r] : 0; ts[C + j] = va ? S.ts[r] : 0;
+    for (int j = 0; j < K; j++) {
+        const int q = lane * K + j;
+        if (q < C) {
+            const bool vb = q < B.n, va = q < A.n;
+            const int sb = ix_byte<K>(B, j), sa = ix_byte<K>(A, j);
+            px[q] = vb ? sm.pool[0].px[sb] : 0; qt[q] = vb ? sm.pool[0].qty[sb] : 0;
+            id[q] = vb ? sm.pool[0].id[sb] : 0; ts[q] = vb ? sm.pool[0].ts[sb] : 0;
+            px[C + q] = va ? sm.pool[1].px[sa] : 0; qt[C + q] = va ? sm.pool[1].qty[sa] : 0;
+            id[C + q] = va ? sm.pool[1].id[sa] : 0; ts[C + q] = va ? sm.pool[1].ts[sa] : 0;
         }
-    }
-}
-
-// Partial cancel or delete on one side: lookup by (price, id); a miss is a no-op.
-template <int K>
-__device__ __forceinline__ void cancel_on(Book<K> &S, int type, int px, int qty, long long oid, Ctx &c, int lane) {
-    unsigned hit;
-    const int first = book_find<K>(S, px, oid, lane, hit);
-    if (first < 0) {
-        c.c_cancel_miss += 1;
-        return;
-    }
-    bool zero = false;
-#pragma unroll
-    for (int r = 0; r < K; r++) {
-        if ((hit >> r) & 1u) {
-            const int cut = type == LOB_PARTIAL ? min(qty, S.qty[r]) : S.qty[r];
-            c.l_cancel_vol += cut;
-            S.qty[r] -= cut;
-            zero = S.qty[r] == 0;
-        }
-    }
-    zero = __shfl_sync(FULL, zero, first);
-    if (zero) book_remove<K>(S, hit, first, lane);
-}
-
-// One message through the matching engine.
-template <int K>
-__device__ __forceinline__ void process_msg(Book<K> &bid, Book<K> &ask, int cap, int type, int side, int px,
-                                            int qty, long long oid, bool agent, Ctx &c, int lane) {
-    c.c_msgs += 1;
-    if (agent) c.c_agent += 1;
-    const bool ok = type >= LOB_ADD && type <= LOB_MARKET && (side == LOB_BUY || side == LOB_SELL) &&
-                    (type == LOB_DELETE || qty > 0);
-    if (!ok) {
-        c.c_bad += 1;
-        c.status |= ST_BADMSG;
-    } else if (type == LOB_ADD) {
-        c.c_add_vol += qty;
-        int left;
-        if (side == LOB_BUY) {
-            left = book_take<K, false>(ask, true, px, qty, oid, side, c, lane);
-            if (left > 0) {
-                const int r = book_insert<K, true>(bid, cap, px, left, oid, c.ts_next, lane, c.l_evict_vol);
-                if (r == 2) { c.c_drop_vol += left; c.c_drop_cnt += 1; }
-                else { c.ts_next++; if (r == 1) c.c_evict_cnt += 1; }
-            }
-        } else {
-            left = book_take<K, true>(bid, true, px, qty, oid, side, c, lane);
-            if (left > 0) {
-                const int r = book_insert<K, false>(ask, cap, px, left, oid, c.ts_next, lane, c.l_evict_vol);
-                if (r == 2) { c.c_drop_vol += left; c.c_drop_cnt += 1; }
-                else { c.ts_next++; if (r == 1) c.c_evict_cnt += 1; }
-            }
-        }
-    } else if (type == LOB_MARKET) {
-        c.c_mkt_vol += qty;
-        const int left = side == LOB_BUY ? book_take<K, false>(ask, false, 0, qty, oid, side, c, lane)
-                                         : book_take<K, true>(bid, false, 0, qty, oid, side, c, lane);
-        c.c_mkt_disc += left;
-    } else if (side == LOB_BUY) {
-        cancel_on<K>(bid, type, px, qty, oid, c, lane);
-    } else {
-        cancel_on<K>(ask, type, px, qty, oid, c, lane);
     }
 }
 
@@ -480,17 +601,20 @@ __device__ __forceinline__ long long warp_sum(long long v) {
     return v;
 }
 
-// Aggregated top-L levels of one side into shared memory; returns level count.
-template <int K, bool BID>
-__device__ __forceinline__ int side_levels(const Book<K> &S, int L, int *lvl_px, long long *lvl_q, int lane) {
-    const int ppx = __shfl_up_sync(FULL, S.px[K - 1], 1);
+// Aggregated top-L levels of one side (positions in priority order, this
+// lane's K positions in px/qt); sums runs within the lane before the
+// shared-memory atomics.  Returns the number of levels.
+template <int K>
+__device__ __forceinline__ int side_levels(const int (&px)[K], const int (&qt)[K], int n, int L, int *lvl_px,
+                                           long long *lvl_q, int lane) {
+    const int ppx = __shfl_up_sync(FULL, px[K - 1], 1);
     bool start[K];
     int cnt = 0;
 #pragma unroll
     for (int r = 0; r < K; r++) {
-        const int j = lane * K + r;
-        const int prev = r == 0 ? ppx : S.px[r - 1];
-        start[r] = j < S.n && (j == 0 || S.px[r] != prev);
+        const int q = lane * K + r;
+        const int prev = r == 0 ? ppx : px[r - 1];
+        start[r] = q < n && (q == 0 || px[r] != prev);
         cnt += start[r];
     }
     int incl = cnt;
@@ -500,77 +624,136 @@ __device__ __forceinline__ int side_levels(const Book<K> &S, int L, int *lvl_px,
         if (lane >= d) incl += y;
     }
     int lv = incl - cnt - 1;
+    long long run = 0;
+    int run_lv = -1;
 #pragma unroll
     for (int r = 0; r < K; r++) {
-        const int j = lane * K + r;
-        if (start[r]) lv++;
-        if (j < S.n && lv < L) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[lv]), (unsigned long long)(long long)S.qty[r]);
-            if (start[r]) lvl_px[lv] = S.px[r];
+        const int q = lane * K + r;
+        if (start[r]) {
+            if (run_lv >= 0 && run_lv < L) atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[run_lv]), (unsigned long long)run);
+            lv++;
+            run = 0;
+            if (lv < L) lvl_px[lv] = px[r];
         }
+        if (q < n) { run += qt[r]; run_lv = lv; }
     }
+    if (run_lv >= 0 && run_lv < L && run != 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[run_lv]), (unsigned long long)run);
     return __shfl_sync(FULL, incl, 31);
 }
 
-// Carry-over cancels of agent `a` on one side (Sec. 4, Action Conversion):
-// every resting order of the agent not at a wanted (side, price) is deleted,
-// in book order, each as one agent message.
-template <int K, bool BID>
-__device__ __forceinline__ void agent_cancels(Book<K> &S, const Book<K> &bid, const Book<K> &ask, int a,
-                                              const int (&wa)[3], const int (&ws)[3], const int (&wp)[3], int nw,
-                                              Ctx &c, int lane, bool snap_env, const KParams &p, int cap,
-                                              long long &snap_n, long long snap_bytes) {
-    const int side = BID ? LOB_BUY : LOB_SELL;
-    for (;;) {
-        unsigned h = 0;
+// Carry-over of one side (Sec. 4, Action Conversion): a resting order of an
+// agent at one of that agent's wanted (side, price) is kept (its quantity
+// added to `kept`); every other resting agent order is flagged for
+// cancellation -- per slot in `cand` (1 + agent) and as this lane's bit mask.
+template <int K>
+__device__ __forceinline__ unsigned side_carry(const Side<K> &S, const PoolSmem<K> &P, unsigned char *cand, int side,
+                                               const int (&wa)[3], const int (&ws)[3], const int (&wp)[3], int nw,
+                                               unsigned (&kept)[3], int lane) {
+    unsigned cmask = 0;
 #pragma unroll
-        for (int r = 0; r < K; r++) {
-            const int j = lane * K + r;
-            if (j < S.n && S.id[r] < 0 && (int)((~S.id[r]) & 1) == a) {
-                bool keep = false;
+    for (int r = 0; r < K; r++) {
+        const int slot = lane * K + r;
+        unsigned char flag = 0;
+        if (((S.occ >> r) & 1u) && S.id[r] < 0) {
+            const int a = (int)((~S.id[r]) & 1);
+            int m = -1;
 #pragma unroll
-                for (int i = 0; i < 3; i++) keep |= i < nw && wa[i] == a && ws[i] == side && wp[i] == S.px[r];
-                if (!keep) h |= 1u << r;
+            for (int i = 0; i < 3; i++)
+                if (i < nw && wa[i] == a && ws[i] == side && wp[i] == S.px[r]) m = i;
+            if (m < 0) {
+                flag = (unsigned char)(1 + a);
+                cmask |= 1u << r;
+            } else {
+                const unsigned q = (unsigned)P.qty[slot];
+#pragma unroll
+                for (int i = 0; i < 3; i++) if (m == i) kept[i] += q;
             }
         }
-        const unsigned lanes = __ballot_sync(FULL, h != 0);
+        cand[slot] = flag;
+    }
+    return cmask;
+}
+
+// Delete the flagged agent orders of one side in any order (the final book
+// does not depend on it); counts one agent message per cancel.
+template <int K>
+__device__ __forceinline__ void side_cancel_set(Side<K> &S, PoolSmem<K> &P, unsigned cmask, Ctx &c, int lane) {
+    unsigned vol = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++)
+        if ((cmask >> r) & 1u) vol += (unsigned)P.qty[lane * K + r];
+    const int ncan = (int)__reduce_add_sync(FULL, (unsigned)__popc(cmask));
+    if (ncan == 0) return;
+    c.c_cancel_vol += (long long)__reduce_add_sync(FULL, vol);
+    c.c_msgs += ncan;
+    c.c_agent += ncan;
+    c.msg_idx += ncan;
+    for (;;) {
+        const unsigned lanes = __ballot_sync(FULL, cmask != 0);
         if (lanes == 0) break;
-        const int first = __ffs(lanes) - 1;
-        h = lane == first ? (h & (0u - h)) : 0u;
+        const int L = __ffs(lanes) - 1;
+        const int s = __shfl_sync(FULL, lane * K + __ffs(cmask) - 1, L);
+        if (lane == L) cmask &= cmask - 1;
+        side_remove_slot<K>(S, P, s, lane);
+    }
+}
+
+// Delete, in priority order, agent a's flagged orders on one side.
+template <int K>
+__device__ __forceinline__ void side_agent_cancels(Side<K> &S, PoolSmem<K> &P, unsigned char *cand, int a, Ctx &c,
+                                                   int lane, const Side<K> &B, const Side<K> &A2,
+                                                   const WarpSmem<K> &sm, bool snap_env, const KParams &p, int cap,
+                                                   long long &snap_n, long long snap_bytes) {
+    for (;;) {
+        __syncwarp();
+        int first = -1;
+#pragma unroll
+        for (int j = K - 1; j >= 0; j--)
+            if (lane * K + j < S.n && cand[ix_byte<K>(S, j)] == 1 + a) first = j;
+        const unsigned lanes = __ballot_sync(FULL, first >= 0);
+        if (lanes == 0) break;
+        const int L = __ffs(lanes) - 1;
+        const int q = L * K + __shfl_sync(FULL, first, L);
+        const int s = slot_at<K>(S, q);
         c.c_msgs += 1;
         c.c_agent += 1;
-#pragma unroll
-        for (int r = 0; r < K; r++)
-            if ((h >> r) & 1u) c.l_cancel_vol += S.qty[r];
-        book_remove<K>(S, h, first, lane);
-        if (snap_env && snap_n < p.snap_cap) write_snapshot<K>(bid, ask, cap, p.snaps + snap_n * snap_bytes, lane);
+        c.c_cancel_vol += P.qty[s];
+        __syncwarp();
+        if (lane == 0) cand[s] = 0;
+        slot_clear<K>(S, s, lane);
+        ix_remove<K>(S, q, lane);
+        S.n--;
+        if (q == 0) front_refresh<K>(S, P);
+        if (snap_env && snap_n < p.snap_cap) write_snapshot<K>(B, A2, sm, cap, p.snaps + snap_n * snap_bytes, lane);
         snap_n++;
         c.msg_idx++;
     }
 }
 
-// Per-warp shared memory.
-struct WarpSmem {
-    DevMsg tile[2][TILE];
-    unsigned long long bar[2];
-    long long lvl_q[2][LMAX];
-    int lvl_px[2][LMAX];
-};
-
-// Message tile pipeline state of one warp.
+// Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
-    unsigned tiles;  // tiles issued so far by this warp (buffer = tiles & 1)
-    unsigned waited; // tiles waited for
+    unsigned tiles;
 };
 
-// Run n_steps env steps of env e with the book resident in registers.
+// Run n_steps env steps of env e with the book resident on chip.
 template <int K>
-__device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, int lane) {
+__device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe, int lane) {
     EnvState *st = p.st + e;
-    const int cap = p.caps[e];
-    const int CAPS = 32 * K;
-    unsigned char *blk = p.books + p.book_off[e];
+    const bool uni = p.uni_cap > 0;
+    const int cap = uni ? p.uni_cap : p.caps[e];
+    unsigned char *blk = p.books + (uni ? (long long)e * p.uni_block : p.book_off[e]);
     const int A = p.n_agents;
+    const unsigned long long seed = p.seeds[e];
+    long long *cnt = p.counters + (long long)e * LOB_NCOUNTERS;
+
+    // first message window, issued before anything waits on memory
+    long long mb = p.offsets[(long long)e * p.off_stride + p.k0];
+    long long me = p.offsets[(long long)e * p.off_stride + p.k0 + 1];
+
+    Side<K> bid, ask;
+    side_load<K, true>(bid, sm.pool[0], blk, 0, lane);
+    side_load<K, false>(ask, sm.pool[1], blk, 0, lane);
 
     Ctx c;
     c.ts_next = st->ts_next; c.seq_next = st->seq_next;
@@ -579,22 +762,28 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
     c.pv0 = st->pv_prev[0]; c.pv1 = st->pv_prev[1];
     c.exec_done = st->exec_done;
     c.last_px = st->last_px;
+    const int nb0 = st->n[0], na0 = st->n[1];
     c.A = A; c.exec_dir = p.exec_dir;
-    long long *cnt = p.counters + (long long)e * LOB_NCOUNTERS;
     c.c_msgs = cnt[0]; c.c_agent = cnt[1]; c.c_fills = cnt[2]; c.c_fill_vol = cnt[3];
-    c.c_add_vol = cnt[4]; c.c_mkt_vol = cnt[5]; c.c_mkt_disc = cnt[6];
-    c.c_cancel_miss = cnt[8]; c.c_drop_vol = cnt[9]; c.c_drop_cnt = cnt[10]; c.c_evict_cnt = cnt[12];
-    c.c_bad = cnt[13]; c.bg_cash = cnt[14]; c.bg_inv = cnt[15];
-    c.l_cancel_vol = 0; c.l_evict_vol = 0;
+    c.c_add_vol = cnt[4]; c.c_mkt_vol = cnt[5]; c.c_mkt_disc = cnt[6]; c.c_cancel_vol = cnt[7];
+    c.c_cancel_miss = cnt[8]; c.c_drop_vol = cnt[9]; c.c_drop_cnt = cnt[10]; c.c_evict_vol = cnt[11];
+    c.c_evict_cnt = cnt[12]; c.c_bad = cnt[13]; c.bg_cash = cnt[14]; c.bg_inv = cnt[15];
     c.status = 0;
     c.fill_log = p.fills ? p.fills + (long long)e * p.fill_cap : nullptr;
     c.fill_cap = p.fill_cap;
-    const unsigned long long seed = p.seeds[e];
-
-    Book<K> bid, ask;
-    const int nb0 = st->n[0], na0 = st->n[1];
-    book_load<K, true>(bid, blk, CAPS, lane, nb0);
-    book_load<K, false>(ask, blk, CAPS, lane, na0);
+    // live counts arrive with the state: mark occupancy now
+    bid.occ = 0;
+    ask.occ = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        if (lane * K + r < nb0) bid.occ |= 1u << r;
+        if (lane * K + r < na0) ask.occ |= 1u << r;
+    }
+    bid.n = nb0;
+    ask.n = na0;
+    __syncwarp();
+    front_refresh<K>(bid, sm.pool[0]);
+    front_refresh<K>(ask, sm.pool[1]);
 
     const bool snap_env = p.snaps != nullptr && e == 0;
     long long snap_n = 0;
@@ -603,9 +792,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
 
     for (int step = 0; step < p.n_steps && !timed_out; step++) {
         const int t = p.t0 + step;
-        const int k = p.k0 + step;
-        const long long mb = p.offsets[(long long)e * p.off_stride + k];
-        const long long me = p.offsets[(long long)e * p.off_stride + k + 1];
+        if (step > 0) {
+            mb = p.offsets[(long long)e * p.off_stride + p.k0 + step];
+            me = p.offsets[(long long)e * p.off_stride + p.k0 + step + 1];
+        }
         const int nmsg = (int)(me - mb);
         const int ntiles = (nmsg + TILE - 1) / TILE;
         const unsigned tile0 = pipe.tiles;
@@ -613,8 +803,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_smem();
-                const int cntm = min(TILE, nmsg);
-                tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb, (unsigned)cntm * 32u, &sm.bar[pipe.tiles & 1]);
+                tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb, (unsigned)min(TILE, nmsg) * 32u,
+                             &sm.bar[pipe.tiles & 1]);
             }
             pipe.tiles++;
         }
@@ -622,8 +812,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
         c.fill_n = 0;
         snap_n = 0;
 
-        // ---- 1-3. action conversion, carry-over cancels, shuffle, agent orders
-        int act0 = 0, act1 = 0;
+        // ---- 1-3. action conversion, carry-over cancels, shuffle
+        int act0 = 0, act1 = 0, ns = 0;
         if (A == 2) {
             if (p.action_mode == LOB_ACT_RANDOM) {
                 const unsigned long long key = step_key(seed, t, TAG_POLICY);
@@ -635,9 +825,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
                 act1 = ap[1];
                 if (act0 < 0 || act0 >= 12 || act1 < 0 || act1 >= 12) c.status |= ST_BADACT;
             }
-            const long long bb = bid.n ? bid.best : c.last_px;
-            const long long ba = ask.n ? ask.best : c.last_px;
-            // wanted orders: (agent, side, px, qty); at most 3
+            const long long bb = bid.n ? bid.fpx : c.last_px;
+            const long long ba = ask.n ? ask.fpx : c.last_px;
             int wa[3] = {0, 0, 0}, ws[3] = {0, 0, 0}, wp[3] = {0, 0, 0};
             long long wq[3] = {0, 0, 0};
             int nw = 0;
@@ -645,13 +834,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
             if (remaining > 0 && act0 >= 0 && act0 < 12) {
                 const int pi = act0 / 3, mi = act0 % 3;
                 const long long mult = mi == 0 ? 1 : (mi == 1 ? 2 : 5);
-                long long q0 = ((long long)p.exec_target + p.T - 1) / p.T;
-                q0 = q0 < 1 ? 1 : q0;
-                long long qty = mult * q0;
+                long long qty = mult * p.exec_q0;
                 qty = qty < remaining ? qty : remaining;
                 const long long s2 = bb + ba;
                 const long long fl = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
-                const long long ce = -((s2 <= 0) ? (-s2) / 2 : -((s2 + 1) / 2));
+                const long long ce = s2 <= 0 ? -((-s2) / 2) : (s2 + 1) / 2;
                 long long wpx;
                 if (p.exec_dir == LOB_SELL) wpx = pi == 0 ? bb : pi == 1 ? ce : pi == 2 ? ba : ba + 2;
                 else wpx = pi == 0 ? ba : pi == 1 ? fl : pi == 2 ? bb : bb - 2;
@@ -672,41 +859,28 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
                 }
                 nw += 2;
             }
-            // carry-over: resting agent orders at a wanted (agent, side, price) are kept
-            long long kept[3] = {0, 0, 0};
+            // carry-over: keep resting orders at a wanted (agent, side, price)
+            unsigned kept_u[3] = {0u, 0u, 0u};
+            const unsigned cm_b = side_carry<K>(bid, sm.pool[0], sm.cand[0], LOB_BUY, wa, ws, wp, nw, kept_u, lane);
+            const unsigned cm_a = side_carry<K>(ask, sm.pool[1], sm.cand[1], LOB_SELL, wa, ws, wp, nw, kept_u, lane);
+            long long kept[3];
 #pragma unroll
-            for (int r = 0; r < K; r++) {
-                const int j = lane * K + r;
-                if (j < bid.n && bid.id[r] < 0) {
-                    const int a = (int)((~bid.id[r]) & 1);
-                    int m = -1;
+            for (int i = 0; i < 3; i++) kept[i] = (long long)__reduce_add_sync(FULL, kept_u[i]);
+            if (snap_env) {
+                // trace mode: cancels one by one in the paper's order, a snapshot after each
 #pragma unroll
-                    for (int i = 0; i < 3; i++)
-                        if (i < nw && wa[i] == a && ws[i] == LOB_BUY && wp[i] == bid.px[r]) m = i;
-#pragma unroll
-                    for (int i = 0; i < 3; i++) if (m == i) kept[i] += bid.qty[r];
+                for (int a = 0; a < 2; a++) {
+                    side_agent_cancels<K>(bid, sm.pool[0], sm.cand[0], a, c, lane, bid, ask, sm, snap_env, p, cap,
+                                          snap_n, snap_bytes);
+                    side_agent_cancels<K>(ask, sm.pool[1], sm.cand[1], a, c, lane, bid, ask, sm, snap_env, p, cap,
+                                          snap_n, snap_bytes);
                 }
-                if (j < ask.n && ask.id[r] < 0) {
-                    const int a = (int)((~ask.id[r]) & 1);
-                    int m = -1;
-#pragma unroll
-                    for (int i = 0; i < 3; i++)
-                        if (i < nw && wa[i] == a && ws[i] == LOB_SELL && wp[i] == ask.px[r]) m = i;
-#pragma unroll
-                    for (int i = 0; i < 3; i++) if (m == i) kept[i] += ask.qty[r];
-                }
+            } else {
+                side_cancel_set<K>(bid, sm.pool[0], cm_b, c, lane);
+                side_cancel_set<K>(ask, sm.pool[1], cm_a, c, lane);
             }
-#pragma unroll
-            for (int i = 0; i < 3; i++) kept[i] = warp_sum(kept[i]);
-            // cancels: agent 0 then 1, bids then asks, each in book order
-            const bool snap_on = snap_env;
-            agent_cancels<K, true>(bid, bid, ask, 0, wa, ws, wp, nw, c, lane, snap_on, p, cap, snap_n, snap_bytes);
-            agent_cancels<K, false>(ask, bid, ask, 0, wa, ws, wp, nw, c, lane, snap_on, p, cap, snap_n, snap_bytes);
-            agent_cancels<K, true>(bid, bid, ask, 1, wa, ws, wp, nw, c, lane, snap_on, p, cap, snap_n, snap_bytes);
-            agent_cancels<K, false>(ask, bid, ask, 1, wa, ws, wp, nw, c, lane, snap_on, p, cap, snap_n, snap_bytes);
-            // orders to send: wanted minus kept; then Fisher-Yates shuffle
-            int sa[3], ss[3], sp[3], sq[3];
-            int ns = 0;
+            // orders to send (wanted minus kept), Fisher-Yates shuffled
+            int sa[3] = {0, 0, 0}, ss[3] = {0, 0, 0}, sp[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 const long long q = wq[i] - kept[i];
@@ -724,72 +898,130 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
                     const int i = ns - 1 - d;
                     if (i >= 1) {
                         const int jj = (int)bounded(sm_mix(key + GAMMA * (unsigned long long)(d + 1)), (unsigned)(i + 1));
-                        // swap entries i and jj (static indices only)
-                        int ta = 0, ts_ = 0, tp = 0, tq = 0, ua = 0, us = 0, up = 0, uq = 0;
+                        int ta = 0, tb = 0, tp = 0, tq = 0, ua = 0, ub = 0, up = 0, uq = 0;
 #pragma unroll
                         for (int u = 0; u < 3; u++) {
-                            if (u == i) { ta = sa[u]; ts_ = ss[u]; tp = sp[u]; tq = sq[u]; }
-                            if (u == jj) { ua = sa[u]; us = ss[u]; up = sp[u]; uq = sq[u]; }
+                            if (u == i) { ta = sa[u]; tb = ss[u]; tp = sp[u]; tq = sq[u]; }
+                            if (u == jj) { ua = sa[u]; ub = ss[u]; up = sp[u]; uq = sq[u]; }
                         }
 #pragma unroll
                         for (int u = 0; u < 3; u++) {
-                            if (u == i) { sa[u] = ua; ss[u] = us; sp[u] = up; sq[u] = uq; }
-                            else if (u == jj) { sa[u] = ta; ss[u] = ts_; sp[u] = tp; sq[u] = tq; }
+                            if (u == i) { sa[u] = ua; ss[u] = ub; sp[u] = up; sq[u] = uq; }
+                            else if (u == jj) { sa[u] = ta; ss[u] = tb; sp[u] = tp; sq[u] = tq; }
                         }
                     }
                 }
             }
+            // the agents' orders become the first records of the step
+            if (lane < ns) {
+                int ma = 0, ms = 0, mp = 0, mq = 0;
 #pragma unroll
-            for (int u = 0; u < 3; u++) {
-                if (u < ns) {
-                    const long long oid = -(1 + (long long)sa[u] + 2LL * c.seq_next);
-                    c.seq_next++;
-                    process_msg<K>(bid, ask, cap, LOB_ADD, ss[u], sp[u], sq[u], oid, true, c, lane);
-                    if (snap_env && snap_n < p.snap_cap)
-                        write_snapshot<K>(bid, ask, cap, p.snaps + snap_n * snap_bytes, lane);
-                    snap_n++;
-                    c.msg_idx++;
-                }
+                for (int u = 0; u < 3; u++)
+                    if (u == lane) { ma = sa[u]; ms = ss[u]; mp = sp[u]; mq = sq[u]; }
+                DevMsg r;
+                r.ts = 0;
+                r.oid = -(1 + (long long)ma + 2LL * (c.seq_next + lane));
+                r.px = mp; r.qty = mq; r.type = (short)LOB_ADD; r.side = (short)ms; r.pad = 0;
+                sm.amsg[lane] = r;
             }
+            c.seq_next += ns;
+            __syncwarp();
         }
 
-        // ---- 4. market-replay messages, staged tile by tile
-        for (int tix = 0; tix < ntiles; tix++) {
-            const unsigned buf = (tile0 + tix) & 1u;
-            const unsigned phase = ((tile0 + tix) >> 1) & 1u;
-            if (!mbar_wait(&sm.bar[buf], phase, p.wait_budget)) {
-                c.status |= ST_TIMEOUT;
-                mbar_wait(&sm.bar[buf], phase, p.wait_budget);  // let the copy in flight land
-                timed_out = true;
-                break;
-            }
-            if (tix + 1 < ntiles) {
-                __syncwarp();
-                if (lane == 0) {
-                    fence_proxy_async_smem();
-                    const int cntm = min(TILE, nmsg - (tix + 1) * TILE);
-                    tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(tix + 1) * TILE,
-                                 (unsigned)cntm * 32u, &sm.bar[pipe.tiles & 1]);
+        // ---- 4. the agents' orders, then the market-replay messages.  Chunk -1
+        // is the agents' records, chunk j >= 0 the j-th staged tile; inside a
+        // chunk the next record is read one message ahead (a read past the
+        // chunk end stays inside this warp's shared memory and is unused).
+        constexpr int KEY_ADD_B = LOB_ADD | (1 << 16), KEY_ADD_S = (int)(0xFFFF0000u | LOB_ADD);
+        constexpr int KEY_MKT_B = LOB_MARKET | (1 << 16), KEY_MKT_S = (int)(0xFFFF0000u | LOB_MARKET);
+        constexpr int KEY_PAR_B = LOB_PARTIAL | (1 << 16), KEY_PAR_S = (int)(0xFFFF0000u | LOB_PARTIAL);
+        constexpr int KEY_DEL_B = LOB_DELETE | (1 << 16), KEY_DEL_S = (int)(0xFFFF0000u | LOB_DELETE);
+        for (int ch = ns > 0 ? -1 : 0; ch < ntiles && !timed_out; ch++) {
+            const DevMsg *base;
+            int cnt_ch;
+            const int agent = ch < 0 ? 1 : 0;
+            if (ch < 0) {
+                base = sm.amsg;
+                cnt_ch = ns;
+            } else {
+                const unsigned buf = (tile0 + ch) & 1u;
+                const unsigned phase = ((tile0 + ch) >> 1) & 1u;
+                if (!mbar_wait(&sm.bar[buf], phase, p.wait_budget)) {
+                    c.status |= ST_TIMEOUT;
+                    mbar_wait(&sm.bar[buf], phase, p.wait_budget);  // let the copy in flight land
+                    timed_out = true;
+                    break;
                 }
-                pipe.tiles++;
+                if (ch + 1 < ntiles) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        fence_proxy_async_smem();
+                        tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(ch + 1) * TILE,
+                                     (unsigned)min(TILE, nmsg - (ch + 1) * TILE) * 32u, &sm.bar[pipe.tiles & 1]);
+                    }
+                    pipe.tiles++;
+                }
+                base = sm.tile[buf];
+                cnt_ch = min(TILE, nmsg - ch * TILE);
             }
-            const int cnt_t = min(TILE, nmsg - tix * TILE);
-            for (int i = 0; i < cnt_t; i++) {
-                const int4 w0 = *reinterpret_cast<const int4 *>(&sm.tile[buf][i]);
-                const int4 w1 = *(reinterpret_cast<const int4 *>(&sm.tile[buf][i]) + 1);
+            const int4 *rp = reinterpret_cast<const int4 *>(base);
+            int4 w0 = rp[0], w1 = rp[1];
+            for (int i = 0; i < cnt_ch; i++) {
+                const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
                 const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                const int type = (short)(w1.z & 0xffff);
-                const int side = (short)((unsigned)w1.z >> 16);
-                process_msg<K>(bid, ask, cap, type, side, w1.x, w1.y, oid, false, c, lane);
-                if (snap_env && snap_n < p.snap_cap)
-                    write_snapshot<K>(bid, ask, cap, p.snaps + snap_n * snap_bytes, lane);
-                snap_n++;
+                const int key = w1.z;
+                const int px = w1.x;
+                int qty = w1.y;
+                c.c_msgs += 1;
+                c.c_agent += agent;
+                if (key == KEY_ADD_B || key == KEY_MKT_B) {
+                    if (qty <= 0) {
+                        c.c_bad += 1; c.status |= ST_BADMSG;
+                    } else {
+                        const bool lim = key == KEY_ADD_B;
+                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                        if (ask.n > 0 && (!lim || px >= ask.fpx))
+                            qty = side_take<K, false>(ask, sm.pool[1], lim, px, qty, oid, LOB_BUY, c, lane);
+                        if (!lim) c.c_mkt_disc += qty;
+                        else if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                    }
+                } else if (key == KEY_ADD_S || key == KEY_MKT_S) {
+                    if (qty <= 0) {
+                        c.c_bad += 1; c.status |= ST_BADMSG;
+                    } else {
+                        const bool lim = key == KEY_ADD_S;
+                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                        if (bid.n > 0 && (!lim || px <= bid.fpx))
+                            qty = side_take<K, true>(bid, sm.pool[0], lim, px, qty, oid, LOB_SELL, c, lane);
+                        if (!lim) c.c_mkt_disc += qty;
+                        else if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                    }
+                } else if (key == KEY_DEL_B || (key == KEY_PAR_B && qty > 0)) {
+                    side_cancel<K>(bid, sm.pool[0], key & 0xffff, px, qty, oid, c, lane);
+                } else if (key == KEY_DEL_S || (key == KEY_PAR_S && qty > 0)) {
+                    side_cancel<K>(ask, sm.pool[1], key & 0xffff, px, qty, oid, c, lane);
+                } else {
+                    c.c_bad += 1;
+                    c.status |= ST_BADMSG;
+                }
+                if (snap_env) {
+                    __syncwarp();
+                    if (snap_n < p.snap_cap) write_snapshot<K>(bid, ask, sm, cap, p.snaps + snap_n * snap_bytes, lane);
+                    snap_n++;
+                }
                 c.msg_idx++;
+                w0 = n0;
+                w1 = n1;
             }
         }
         if (timed_out) break;
 
-        // ---- 5. step outcomes
+        // ---- 5. step outcomes (and, after the last step, the book write-back)
+        __syncwarp();
+        int bpx[K], bqt[K], apx[K], aqt[K];
+        long long bid_id[K], bts[K], aid[K], ats[K];
+        side_gather<K>(bid, sm.pool[0], bpx, bqt, bid_id, bts);
+        side_gather<K>(ask, sm.pool[1], apx, aqt, aid, ats);
         const long long obs_base = ((long long)step * p.n_envs + e);
         if (A > 0) {
             const int L = p.L;
@@ -798,19 +1030,18 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
                 (&sm.lvl_px[0][0])[i] = 0;
             }
             __syncwarp();
-            const int nlb = side_levels<K, true>(bid, L, sm.lvl_px[0], sm.lvl_q[0], lane);
-            const int nla = side_levels<K, false>(ask, L, sm.lvl_px[1], sm.lvl_q[1], lane);
-            __syncwarp();
-            const long long bb = bid.n ? bid.best : c.last_px;
-            const long long ba = ask.n ? ask.best : c.last_px;
+            const int nlb = side_levels<K>(bpx, bqt, bid.n, L, sm.lvl_px[0], sm.lvl_q[0], lane);
+            const int nla = side_levels<K>(apx, aqt, ask.n, L, sm.lvl_px[1], sm.lvl_q[1], lane);
+            const long long bb = bid.n ? bid.fpx : c.last_px;
+            const long long ba = ask.n ? ask.fpx : c.last_px;
             const long long s2 = bb + ba;
             const long long anchor = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
             long long own0 = 0, own1 = 0;
 #pragma unroll
             for (int r = 0; r < K; r++) {
-                const int j = lane * K + r;
-                if (j < bid.n && bid.id[r] < 0) { if ((~bid.id[r]) & 1) own1 += bid.qty[r]; else own0 += bid.qty[r]; }
-                if (j < ask.n && ask.id[r] < 0) { if ((~ask.id[r]) & 1) own1 += ask.qty[r]; else own0 += ask.qty[r]; }
+                const int q = lane * K + r;
+                if (q < bid.n && bid_id[r] < 0) { if ((~bid_id[r]) & 1) own1 += bqt[r]; else own0 += bqt[r]; }
+                if (q < ask.n && aid[r] < 0) { if ((~aid[r]) & 1) own1 += aqt[r]; else own0 += aqt[r]; }
             }
             own0 = warp_sum(own0);
             own1 = warp_sum(own1);
@@ -824,27 +1055,31 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
             c.pv0 = pv0; c.pv1 = pv1;
             const float tl = __fdiv_rn((float)(p.T - (t + 1)), (float)p.T);
             const int D = p.D;
+            __syncwarp();
             float *ob = p.obs ? p.obs + obs_base * A * D : nullptr;
             if (ob) {
-                for (int idx = lane; idx < A * D; idx += 32) {
-                    const int a = idx / D, f = idx % D;
-                    float v;
-                    if (f < 4 * L) {
-                        const int s = f / (2 * L);
-                        const int i = (f % (2 * L)) >> 1;
-                        const int nl = s == 0 ? nlb : nla;
-                        if (i >= nl) v = 0.0f;
-                        else if (f & 1) v = __ll2float_rn(sm.lvl_q[s][i]);
-                        else v = __ll2float_rn((long long)sm.lvl_px[s][i] - anchor);
-                    } else {
-                        const int g = f - 4 * L;
-                        if (g == 0) v = __ll2float_rn(a == 0 ? c.inv0 : c.inv1);
-                        else if (g == 1) v = __ll2float_rn(a == 0 ? c.cash0 : c.cash1);
-                        else if (g == 2) v = tl;
-                        else if (g == 3) v = a == 0 ? __ll2float_rn((long long)p.exec_target - c.exec_done) : 0.0f;
-                        else v = __ll2float_rn(a == 0 ? own0 : own1);
-                    }
+                // level entries: the same for both agents
+                for (int idx = lane; idx < 4 * L; idx += 32) {
+                    const int sd = idx >= 2 * L ? 1 : 0;
+                    const int i = (idx - sd * 2 * L) >> 1;
+                    const int nl = sd == 0 ? nlb : nla;
+                    const long long lq = sm.lvl_q[sd][i];
+                    const long long lp = (long long)sm.lvl_px[sd][i] - anchor;
+                    const float v = i >= nl ? 0.0f : __ll2float_rn((idx & 1) ? lq : lp);
                     ob[idx] = v;
+                    ob[D + idx] = v;
+                }
+                // five agent scalars per agent: lanes 0..9
+                if (lane < 10) {
+                    const int a = lane >= 5 ? 1 : 0;
+                    const int g = lane - 5 * a;
+                    const long long iv = a == 0 ? c.inv0 : c.inv1;
+                    const long long cs = a == 0 ? c.cash0 : c.cash1;
+                    const long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    const long long own = a == 0 ? own0 : own1;
+                    const long long x = g == 0 ? iv : g == 1 ? cs : g == 3 ? rem : own;
+                    const float v = g == 2 ? tl : __ll2float_rn(x);
+                    ob[a * D + 4 * L + g] = v;
                 }
             }
             if (lane == 0) {
@@ -856,17 +1091,19 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
         if (lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
         if (lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
+        if (step + 1 == p.n_steps) {
+            side_store<K, true>(bid, bpx, bqt, bid_id, bts, blk, lane);
+            side_store<K, false>(ask, apx, aqt, aid, ats, blk, lane);
+        }
     }
 
-    // ---- write back: counters, env scalars, book
-    const long long cv = warp_sum(c.l_cancel_vol);
-    const long long ev = warp_sum(c.l_evict_vol);
+    // ---- counters and env scalars
     const int any_status = __reduce_or_sync(FULL, (unsigned)c.status);
     if (lane == 0) {
         if (any_status) atomicOr(p.status, any_status);
         cnt[0] = c.c_msgs; cnt[1] = c.c_agent; cnt[2] = c.c_fills; cnt[3] = c.c_fill_vol;
-        cnt[4] = c.c_add_vol; cnt[5] = c.c_mkt_vol; cnt[6] = c.c_mkt_disc; cnt[7] += cv;
-        cnt[8] = c.c_cancel_miss; cnt[9] = c.c_drop_vol; cnt[10] = c.c_drop_cnt; cnt[11] += ev;
+        cnt[4] = c.c_add_vol; cnt[5] = c.c_mkt_vol; cnt[6] = c.c_mkt_disc; cnt[7] = c.c_cancel_vol;
+        cnt[8] = c.c_cancel_miss; cnt[9] = c.c_drop_vol; cnt[10] = c.c_drop_cnt; cnt[11] = c.c_evict_vol;
         cnt[12] = c.c_evict_cnt; cnt[13] = c.c_bad; cnt[14] = c.bg_cash; cnt[15] = c.bg_inv;
     }
     if (timed_out) return;
@@ -877,8 +1114,6 @@ __device__ void run_env(const KParams &p, int e, WarpSmem &sm, MsgPipe &pipe, in
         st->last_px = c.last_px; st->n[0] = bid.n; st->n[1] = ask.n;
         st->t = p.t0 + p.n_steps;
     }
-    book_store<K, true>(bid, blk, CAPS, lane);
-    book_store<K, false>(ask, blk, CAPS, lane);
 }
 
 template <int K>
@@ -886,24 +1121,24 @@ __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[wib];
+    WarpSmem<K> &sm = reinterpret_cast<WarpSmem<K> *>(smem_raw)[wib];
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
     }
     __syncwarp();
-    MsgPipe pipe{0u, 0u};
+    MsgPipe pipe{0u};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K>(p, p.env_list[w], sm, pipe, lane);
+        if (w < p.n_list) run_env<K>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K>(p, p.env_list[w], sm, pipe, lane);
+            run_env<K>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
         }
     }
 }
