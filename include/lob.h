@@ -137,7 +137,9 @@ int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_off
 
 /* Start a new episode in every env: empty books, zero agent state and
  * counters, step t = 0.  d_env_seeds: device [n_envs] uint64 keys for the
- * shuffle and the random policy. */
+ * shuffle and the random policy.  The observation buffer then holds the reset
+ * observation (empty book: all levels (0, 0), zero inventory and cash, time
+ * left 1, the full execution target for agent 0). */
 int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream);
 
 /* One environment step for every env (stages 1-5 above), consuming the next
@@ -157,6 +159,44 @@ int lob_observe(lob_handle *h, float *d_obs, int64_t *d_rewards, uint8_t *d_done
  * d_actions [n_steps][n_envs][2]. */
 int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float *d_obs,
                 int64_t *d_rewards, uint8_t *d_done, void *stream);
+
+/* ---- Actor-critic policy (IPPO networks, Sec. 4.2: separate weights per
+ * agent).  Per agent: x = obs * s (fixed per-feature input scale: level
+ * prices 1/10, level sizes 1/1000, inventory 1/100, cash 1e-6, time left 1,
+ * remaining target and own resting quantity 1/100), h1 = tanh(W1 x + b1),
+ * h2 = tanh(W2 h1 + b2), y = W3 h2 + b3 with 128 hidden units; y[0..11] are
+ * the logits of the 12 actions, y[12] the value; the action is the argmax of
+ * the logits (ties to the lowest index). */
+#define LOB_POLICY_HIDDEN 128
+#define LOB_PREC_FP32 0   /* FP32 FMAs on the CUDA cores */
+#define LOB_PREC_BF16 1   /* BF16 operands, FP32 accumulation, tcgen05 tensor cores */
+typedef struct lob_policy lob_policy;
+/* Floats per agent in the parameter block: W1 [128][obs_dim], b1 [128],
+ * W2 [128][128], b2 [128], W3 [13][128], b3 [13], in that order (row-major,
+ * W[out][in]).  0 for an unsupported obs_dim (1..128). */
+int64_t lob_policy_param_count(int32_t obs_dim);
+/* Upload n_agents (1 or 2) consecutive parameter blocks from the host; the
+ * library keeps an FP32 copy and a BF16 copy packed for the tensor cores. */
+int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float *h_params, lob_policy **out);
+int lob_policy_destroy(lob_policy *pol);   /* synchronises the device */
+/* Forward of every (env, agent) row: d_obs float [n_envs][n_agents][obs_dim];
+ * outputs (any may be NULL) d_logits float [n_envs][n_agents][12], d_values
+ * float [n_envs][n_agents], d_actions int32 [n_envs][n_agents]. */
+int lob_policy_forward(lob_policy *pol, const float *d_obs, int32_t n_envs, int32_t precision, float *d_logits,
+                       float *d_values, int32_t *d_actions, void *stream);
+/* Wait for `stream` and report the policy's device status (LOB_ETIMEOUT if a
+ * bounded tensor-core wait expired). */
+int lob_policy_sync(lob_policy *pol, void *stream);
+/* Rollout with the policy in the loop (the handle must use LOB_ACT_HOST):
+ * for each of n_steps steps, the policy acts on the current observation
+ * (after lob_reset: the reset observation) and lob_step runs with those
+ * actions, all enqueued on `stream` with no host synchronisation, so the
+ * sequence can be captured in a CUDA graph.  Per-step outputs (any may be
+ * NULL): d_obs [n_steps][n_envs][2][obs_dim] (observation after step i),
+ * d_rewards [n_steps][n_envs][2], d_done [n_steps][n_envs], d_actions
+ * [n_steps][n_envs][2] (the actions taken at step i). */
+int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
+                       int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream);
 
 /* Host-buffer convenience step: copies this step's background messages
  * (h_msgs[h_offsets[e] .. h_offsets[e + 1]], h_offsets [n_envs + 1]) and

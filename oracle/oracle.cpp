@@ -493,7 +493,14 @@ void orc_reset(void *h, const uint64_t *env_seeds) {
         E.asks.is_bid = false;
         E.seed = env_seeds[e];
         E.last_px = g->cfg.c.start_px;
-        E.obs.assign((size_t)g->cfg.c.n_agents * g->cfg.obs_dim(), 0.0f);
+        // reset observation: empty book, nothing held, the whole episode and
+        // (for the execution agent) the whole target still ahead
+        const int D = g->cfg.obs_dim(), L = g->cfg.c.top_levels;
+        E.obs.assign((size_t)g->cfg.c.n_agents * D, 0.0f);
+        for (int a = 0; a < g->cfg.c.n_agents; a++) {
+            E.obs[(size_t)a * D + 4 * L + 2] = (float)g->cfg.c.episode_len / (float)g->cfg.c.episode_len;
+            if (a == 0) E.obs[(size_t)a * D + 4 * L + 3] = (float)g->cfg.c.exec_target;
+        }
     }
 }
 

@@ -14,6 +14,7 @@
 
 #include "lob.h"
 #include "lob_device.cuh"
+#include "policy_internal.h"
 
 using namespace lobk;
 
@@ -44,25 +45,30 @@ size_t warp_smem_bytes(int K) {
     }
 }
 
-// Launch the step kernel of class K; opts into the dynamic shared memory the
-// launch shape needs (once per K and size).
-cudaError_t launch_k(int K, int blocks, int wpb, cudaStream_t s, const KParams &p) {
-    const size_t smem = (size_t)wpb * warp_smem_bytes(K);
-    static size_t opted[64][9];   // per device, per K: largest size opted into so far
+// Opt every step-kernel class into the shared memory of the widest launch
+// shape (8 warps per block), once per device; done when a handle is created
+// so that launches themselves never change function attributes.
+cudaError_t ensure_optin() {
+    static bool done[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (smem > opted[dev][K]) {
-        switch (K) {
-            case 1: e = cudaFuncSetAttribute(k_env_steps<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-            case 2: e = cudaFuncSetAttribute(k_env_steps<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-            case 4: e = cudaFuncSetAttribute(k_env_steps<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-            default: e = cudaFuncSetAttribute(k_env_steps<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-        }
-        if (e != cudaSuccess) return e;
-        opted[dev][K] = smem;
-    }
+    if (done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_env_steps<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(1)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_steps<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(2)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_steps<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(4)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_steps<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(8)));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// Launch the step kernel of class K (shared memory opted in by ensure_optin).
+cudaError_t launch_k(int K, int blocks, int wpb, cudaStream_t s, const KParams &p) {
+    const size_t smem = (size_t)wpb * warp_smem_bytes(K);
     switch (K) {
         case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
         case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
@@ -182,7 +188,7 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     h->caps = caps;
     h->D = lob_obs_dim(cfg);
     if (c.warps_per_block > 0) h->wpb = c.warps_per_block;
-    if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return LOB_ECUDA; }
+    if (cudaGetDevice(&h->dev) != cudaSuccess || ensure_optin() != cudaSuccess) { delete h; return LOB_ECUDA; }
     cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev);
 
     // group envs by capacity class; book blocks are 256-byte aligned
@@ -275,9 +281,16 @@ int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_off
 
 // zero the state of every env
 __global__ void k_reset(EnvState *st, long long *cnt, unsigned long long *seeds_dst,
-                        const unsigned long long *seeds_src, int n, int start_px) {
+                        const unsigned long long *seeds_src, int n, int start_px, float *obs, int A, int D,
+                        int L, int exec_target) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
+    for (int a = 0; a < A; a++) {
+        float *o = obs + ((long long)e * A + a) * D;
+        for (int f = 0; f < D; f++) o[f] = 0.0f;
+        o[4 * L + 2] = 1.0f;                                   // time left T / T
+        if (a == 0) o[4 * L + 3] = __ll2float_rn(exec_target);  // remaining target
+    }
     EnvState z;
     memset(&z, 0, sizeof(z));
     z.last_px = start_px;
@@ -381,7 +394,8 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
     const int n = h->cfg.n_envs;
     k_reset<<<(n + 127) / 128, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                              reinterpret_cast<const unsigned long long *>(d_env_seeds), n,
-                                             h->cfg.start_px);
+                                             h->cfg.start_px, h->d_obs, h->cfg.n_agents, h->D, h->cfg.top_levels,
+                                             h->cfg.exec_target);
     h->launches++;
     if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
     h->t = 0;
@@ -632,6 +646,7 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return LOB_ECUDA;
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LOB_ECUDA;
+        if (ensure_optin() != cudaSuccess) return LOB_ECUDA;
         g_noalloc_n_sm[dev] = nsm;
         g_noalloc_dev_ptr[dev] = static_cast<unsigned char *>(ptr);
     }
@@ -677,4 +692,38 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     const int blocks = std::min((n + wpb - 1) / wpb, g_noalloc_n_sm[dev] * std::max(1, 32 / wpb));
     if (launch_k(K, blocks, wpb, s, p) != cudaSuccess) return LOB_ECUDA;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
+                                  int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream) {
+    if (!h || !pol || n_steps < 1) return LOB_EINVAL;
+    if (h->cfg.n_agents != 2 || h->cfg.action_mode != LOB_ACT_HOST) return LOB_EINVAL;
+    if (policy_n_agents(pol) != 2 || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
+    if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
+    if (!h->reset_done || !h->offsets || h->cursor + n_steps > h->win_steps || h->t + n_steps > h->cfg.episode_len)
+        return LOB_ESTATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D;
+    for (int i = 0; i < n_steps; i++) {
+        // the policy acts on the current observation (kept in the handle's buffer)
+        int rc = policy_forward_internal(pol, h->d_obs, h->cfg.n_envs, precision, nullptr, nullptr, h->d_act, s);
+        if (rc != LOB_OK) return rc;
+        if (d_actions && cudaMemcpyAsync(d_actions + (size_t)i * n * 2, h->d_act, n * 2 * 4,
+                                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return LOB_ECUDA;
+        rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, 1, h->d_act, 0, h->d_obs, h->d_rew,
+                          h->d_done, s);
+        if (rc != LOB_OK) return rc;
+        h->cursor++;
+        h->t++;
+        if (d_obs && cudaMemcpyAsync(d_obs + (size_t)i * n * 2 * D, h->d_obs, n * 2 * D * 4,
+                                     cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return LOB_ECUDA;
+        if (d_rewards && cudaMemcpyAsync(d_rewards + (size_t)i * n * 2, h->d_rew, n * 2 * 8,
+                                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return LOB_ECUDA;
+        if (d_done && cudaMemcpyAsync(d_done + (size_t)i * n, h->d_done, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return LOB_ECUDA;
+    }
+    return LOB_OK;
 }

@@ -20,8 +20,9 @@ _ROOT = os.path.dirname(_PKG)
 _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_PKG, "liblob.so")
-_SOURCES = [os.path.join(_CSRC, "lob_api.cu")]
-_DEPS = _SOURCES + [os.path.join(_CSRC, "lob_device.cuh"), os.path.join(_INC, "lob.h")]
+_SOURCES = [os.path.join(_CSRC, "lob_api.cu"), os.path.join(_CSRC, "policy_api.cu")]
+_DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.cuh", "policy_internal.h")] + \
+    [os.path.join(_INC, "lob.h")]
 _lock = threading.Lock()
 _lib = None
 
@@ -40,7 +41,11 @@ EXPORTS = [
     "lob_observe", "lob_rollout", "lob_step_host", "lob_book_bytes", "lob_get_book",
     "lob_get_counters", "lob_get_agents", "lob_get_env_misc", "lob_get_actions", "lob_set_trace",
     "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
+    "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
+    "lob_policy_sync", "lob_rollout_policy",
 ]
+LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
+POLICY_HIDDEN = 128
 LOB_NOALLOC_MAX_ENVS = 16384
 
 
@@ -122,6 +127,12 @@ def _load():
         "lob_kernel_launches": (I64, [P]),
         "lob_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lob_step_noalloc": (ctypes.c_int, [ctypes.POINTER(lob_noalloc_args), P]),
+        "lob_policy_param_count": (I64, [I32]),
+        "lob_policy_create": (ctypes.c_int, [I32, I32, P, ctypes.POINTER(P)]),
+        "lob_policy_destroy": (ctypes.c_int, [P]),
+        "lob_policy_forward": (ctypes.c_int, [P, P, I32, I32, P, P, P, P]),
+        "lob_policy_sync": (ctypes.c_int, [P, P]),
+        "lob_rollout_policy": (ctypes.c_int, [P, P, I32, I32, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +264,49 @@ def noalloc_book_block_bytes(cap: int) -> int:
     while S < cap:
         S *= 2
     return ((48 * S + 255) // 256) * 256
+
+
+def lob_policy_param_count(obs_dim: int) -> int:
+    return _load().lob_policy_param_count(obs_dim)
+
+
+def lob_policy_create(n_agents, obs_dim, params):
+    """params: host float32 array [n_agents, lob_policy_param_count(obs_dim)]."""
+    w = np.ascontiguousarray(params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(_load().lob_policy_create(n_agents, obs_dim, w.ctypes.data, ctypes.byref(h)), "lob_policy_create")
+    return h
+
+
+def lob_policy_destroy(pol):
+    return _check(_load().lob_policy_destroy(pol), "lob_policy_destroy")
+
+
+def lob_policy_forward(pol, obs, n_envs, precision, logits=None, values=None, actions=None, stream=None):
+    return _check(_load().lob_policy_forward(pol, _dp(obs), n_envs, precision, _dp(logits), _dp(values),
+                                             _dp(actions), _stream(stream)), "lob_policy_forward")
+
+
+def lob_policy_sync(pol, stream=None):
+    return _load().lob_policy_sync(pol, _stream(stream))
+
+
+def lob_rollout_policy(h, pol, n_steps, precision, obs=None, rewards=None, done=None, actions=None, stream=None):
+    return _check(_load().lob_rollout_policy(h, pol, n_steps, precision, _dp(obs), _dp(rewards), _dp(done),
+                                             _dp(actions), _stream(stream)), "lob_rollout_policy")
+
+
+def init_policy_params(seed: int, n_agents: int, obs_dim: int) -> np.ndarray:
+    """Weights N(0, 1/fan_in), biases 0, per agent (float32, host)."""
+    rng = np.random.default_rng(seed)
+    H = POLICY_HIDDEN
+    out = []
+    for _ in range(n_agents):
+        w1 = rng.standard_normal((H, obs_dim)) / np.sqrt(obs_dim)
+        w2 = rng.standard_normal((H, H)) / np.sqrt(H)
+        w3 = rng.standard_normal((13, H)) / np.sqrt(H)
+        out.append(np.concatenate([w1.ravel(), np.zeros(H), w2.ravel(), np.zeros(H), w3.ravel(), np.zeros(13)]))
+    return np.stack(out).astype(np.float32)
 
 
 def lob_strerror(code) -> str:

@@ -64,7 +64,12 @@ class BruteEnv:
                       mkt_discard_vol=0, cancel_vol=0, cancel_miss=0, drop_vol=0, drop_cnt=0,
                       evict_vol=0, evict_cnt=0, bad_msgs=0)
         self.fills = []
-        self.obs = None
+        D = 4 * top_levels + 5
+        self.obs = [[0.0] * D for _ in range(n_agents)]
+        for a in range(n_agents):
+            self.obs[a][4 * top_levels + 2] = 1.0
+            if a == 0:
+                self.obs[a][4 * top_levels + 3] = float(exec_target)
         self.rew = [0] * n_agents
         self.done = 0
         self.acts = [0] * n_agents
