@@ -107,7 +107,7 @@ typedef struct lob_config {
     int32_t reserved[4];   /* must be zero */
 } lob_config;
 
-#define LOB_MAX_CAP 256    /* per-side capacity supported by this build */
+#define LOB_MAX_CAP 1024   /* per-side capacity supported by this build */
 
 typedef struct lob_handle lob_handle;
 
@@ -261,9 +261,10 @@ int64_t lob_kernel_launches(const lob_handle *h);
  * It runs one env step for every env (the same stages, kernel and results as
  * lob_step in persistent mode) on caller-owned state:
  *   cfg           uniform capacity cap_per_side, trace must be 0,
- *                 warps_per_block 0..8 (0 = 4); n_envs <= LOB_NOALLOC_MAX_ENVS
+ *                 warps_per_block 0..8 (0 = 4, fewer where a block's shared
+ *                 memory cannot hold that many books); n_envs <= LOB_NOALLOC_MAX_ENVS
  *   d_books       n_envs book blocks, each 48*S bytes rounded up to a multiple
- *                 of 256, S = the smallest of 32, 64, 128, 256 that is >= cap
+ *                 of 256, S = the smallest power of two >= max(cap, 32)
  *   d_env_state   n_envs * 128 bytes of per-env scalars (opaque)
  *   d_counters    int64 [n_envs][LOB_NCOUNTERS]
  *   d_env_seeds   uint64 [n_envs]

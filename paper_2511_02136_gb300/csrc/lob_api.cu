@@ -20,8 +20,9 @@ using namespace lobk;
 
 namespace {
 
-constexpr int NCLASS = 4;                 // K = 1, 2, 4, 8
-constexpr int CLASS_K[NCLASS] = {1, 2, 4, 8};
+constexpr int NCLASS = 6;                 // K = 1, 2, 4, 8, 16, 32 (32 .. 1024 slots per side)
+constexpr int CLASS_K[NCLASS] = {1, 2, 4, 8, 16, 32};
+constexpr size_t SMEM_PER_BLOCK_MAX = 227 * 1024;
 constexpr long long DEFAULT_WAIT_BUDGET = 2000000000LL;  // ~1 s of SM cycles
 
 int class_of(int cap) {
@@ -41,13 +42,27 @@ size_t warp_smem_bytes(int K) {
         case 1: return sizeof(WarpSmem<1>);
         case 2: return sizeof(WarpSmem<2>);
         case 4: return sizeof(WarpSmem<4>);
-        default: return sizeof(WarpSmem<8>);
+        case 8: return sizeof(WarpSmem<8>);
+        case 16: return sizeof(WarpSmem<16>);
+        default: return sizeof(WarpSmem<32>);
     }
 }
 
-// Opt every step-kernel class into the shared memory of the widest launch
-// shape (8 warps per block), once per device; done when a handle is created
-// so that launches themselves never change function attributes.
+// Most warps (envs) per block whose shared memory fits one block.
+int max_wpb(int K) {
+    const int m = (int)(SMEM_PER_BLOCK_MAX / warp_smem_bytes(K));
+    return m < 8 ? m : 8;
+}
+
+template <int K>
+cudaError_t optin_k() {
+    return cudaFuncSetAttribute(k_env_steps<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(max_wpb(K) * warp_smem_bytes(K)));
+}
+
+// Opt every step-kernel class into the shared memory of its widest launch
+// shape, once per device; done when a handle is created so that launches
+// themselves never change function attributes.
 cudaError_t ensure_optin() {
     static bool done[64];
     int dev = 0;
@@ -55,25 +70,27 @@ cudaError_t ensure_optin() {
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_env_steps<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(1)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_env_steps<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(2)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_env_steps<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(4)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_env_steps<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * warp_smem_bytes(8)));
-    if (e == cudaSuccess) done[dev] = true;
-    return e;
+    if ((e = optin_k<1>()) != cudaSuccess || (e = optin_k<2>()) != cudaSuccess || (e = optin_k<4>()) != cudaSuccess ||
+        (e = optin_k<8>()) != cudaSuccess || (e = optin_k<16>()) != cudaSuccess || (e = optin_k<32>()) != cudaSuccess)
+        return e;
+    done[dev] = true;
+    return cudaSuccess;
 }
 
-// Launch the step kernel of class K (shared memory opted in by ensure_optin).
-cudaError_t launch_k(int K, int blocks, int wpb, cudaStream_t s, const KParams &p) {
+// Launch the step kernel of class K (shared memory opted in by ensure_optin);
+// the warps per block are capped by what one block's shared memory holds.
+cudaError_t launch_k(int K, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s, const KParams &p) {
+    wpb = wpb < max_wpb(K) ? wpb : max_wpb(K);
+    int blocks = (n_list + wpb - 1) / wpb;
+    if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
     const size_t smem = (size_t)wpb * warp_smem_bytes(K);
     switch (K) {
         case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
         case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
         case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        default: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 16: k_env_steps<16><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        default: k_env_steps<32><<<blocks, 32 * wpb, smem, s>>>(p); break;
     }
     return cudaGetLastError();
 }
@@ -378,10 +395,8 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
         p.uni_block = uniform ? h->uni_block : 0;
         p.n_list = cnt;
         p.queue = h->persistent ? h->d_queue + k : nullptr;
-        int blocks = (cnt + wpb - 1) / wpb;
-        if (h->persistent) blocks = std::min(blocks, h->n_sm * std::max(1, 32 / wpb));
         h->launches++;
-        if (launch_k(CLASS_K[k], blocks, wpb, s, p) != cudaSuccess) return LOB_ECUDA;
+        if (launch_k(CLASS_K[k], cnt, wpb, h->persistent != 0, h->n_sm, s, p) != cudaSuccess) return LOB_ECUDA;
     }
     return LOB_OK;
 }
@@ -689,8 +704,7 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
     const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;
-    const int blocks = std::min((n + wpb - 1) / wpb, g_noalloc_n_sm[dev] * std::max(1, 32 / wpb));
-    if (launch_k(K, blocks, wpb, s, p) != cudaSuccess) return LOB_ECUDA;
+    if (launch_k(K, n, wpb, true, g_noalloc_n_sm[dev], s, p) != cudaSuccess) return LOB_ECUDA;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 

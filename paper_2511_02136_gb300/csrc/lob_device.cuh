@@ -177,61 +177,99 @@ struct WarpSmem {
 };
 
 // ---------------------------------------------------------------- book side
+// Pool slot s of a side belongs to one lane, which scans it in its register
+// index r:  K <= 8: s = lane*K + r, with the slot's price and id kept in
+// registers;  K >= 16: s = r*32 + lane, price and id read from shared memory
+// (consecutive lanes -> consecutive banks).  Index entries (slot numbers) are
+// 8 bits wide for pools of up to 256 slots, 16 bits beyond.
 template <int K>
 struct Side {
-    static constexpr int NW = (K + 3) / 4;           // index words per lane
-    static constexpr int BPW = K < 4 ? K : 4;        // index bytes used per word
-    static constexpr unsigned ALLB = BPW == 4 ? 0xffffffffu : ((1u << (8 * BPW)) - 1u);
+    static constexpr bool REG = K <= 8;
+    static constexpr int IXB = K <= 8 ? 8 : 16;           // bits per index entry
+    static constexpr int EPW = 32 / IXB;                  // entries per 32-bit word
+    static constexpr int NW = (K + EPW - 1) / EPW;        // index words per lane
+    static constexpr int BPW = K < EPW ? K : EPW;         // entries used per word
+    static constexpr unsigned EMASK = (1u << IXB) - 1u;
+    static constexpr unsigned ALLB = BPW * IXB == 32 ? 0xffffffffu : ((1u << (BPW * IXB)) - 1u);
+    static constexpr unsigned REP = IXB == 8 ? 0x01010101u : 0x00010001u;
     static constexpr unsigned KMASK = K == 32 ? 0xffffffffu : ((1u << K) - 1u);
-    int px[K];          // price of pool slot lane*K + r
-    long long id[K];    // id of pool slot lane*K + r
-    unsigned occ;       // occupied pool slots of this lane (bit r)
-    unsigned ix[NW];    // index bytes for positions lane*K .. lane*K+K-1
+    static constexpr int RK = REG ? K : 1;
+    int px[RK];         // price of slot (lane, r) (registers mode only)
+    long long id[RK];   // id of slot (lane, r) (registers mode only)
+    unsigned occ;       // occupied slots of this lane (bit r)
+    unsigned ix[NW];    // index entries for positions lane*K .. lane*K+K-1
     int n;              // live orders (warp-uniform)
     int fpx, fqty, fslot;  // front order (position 0), valid when n > 0
     long long fid;
 };
 
+template <int K> __device__ __forceinline__ int slot_of(int lane, int r) {
+    return Side<K>::REG ? lane * K + r : r * 32 + lane;
+}
+template <int K> __device__ __forceinline__ int slot_lane(int s) { return Side<K>::REG ? s / K : (s & 31); }
+template <int K> __device__ __forceinline__ int slot_r(int s) { return Side<K>::REG ? s % K : (s >> 5); }
+template <int K>
+__device__ __forceinline__ int spx(const Side<K> &S, const PoolSmem<K> &P, int r, int lane) {
+    if constexpr (Side<K>::REG) return S.px[r];
+    else return P.px[r * 32 + lane];
+}
+template <int K>
+__device__ __forceinline__ long long sid(const Side<K> &S, const PoolSmem<K> &P, int r, int lane) {
+    if constexpr (Side<K>::REG) return S.id[r];
+    else return P.id[r * 32 + lane];
+}
+
 template <bool BID>
 __device__ __forceinline__ bool at_least(int a, int p) { return BID ? a >= p : a <= p; }
 
-// Byte (slot number) at local position j of this lane.
+// Index entry (slot number) at local position j of this lane.
 template <int K>
-__device__ __forceinline__ int ix_byte(const Side<K> &S, int j) {
-    return (S.ix[j >> 2] >> (8 * (j & 3))) & 0xff;
+__device__ __forceinline__ int ix_ent(const Side<K> &S, int j) {
+    constexpr int EPW = Side<K>::EPW, IXB = Side<K>::IXB;
+    return (S.ix[j / EPW] >> (IXB * (j % EPW))) & Side<K>::EMASK;
 }
 
 // Slot number at uniform position q (q < 32*K).
 template <int K>
 __device__ __forceinline__ int slot_at(const Side<K> &S, int q) {
+    constexpr int EPW = Side<K>::EPW, IXB = Side<K>::IXB;
     const int j = q % K;
     unsigned w = S.ix[0];
 #pragma unroll
     for (int i = 1; i < Side<K>::NW; i++)
-        if ((j >> 2) == i) w = S.ix[i];
+        if (j / EPW == i) w = S.ix[i];
     w = __shfl_sync(FULL, w, q / K);
-    return (w >> (8 * (j & 3))) & 0xff;
+    return (w >> (IXB * (j % EPW))) & Side<K>::EMASK;
+}
+
+// Per-word mask of the entries at positions below `lim` (positions of word w
+// of this lane start at lane*K + EPW*w).
+template <int K>
+__device__ __forceinline__ unsigned ix_below(int lim, int lane, int w) {
+    constexpr int BPW = Side<K>::BPW, IXB = Side<K>::IXB;
+    const int d = lim - (lane * K + Side<K>::EPW * w);
+    return d <= 0 ? 0u : (d >= BPW ? Side<K>::ALLB : ((1u << (IXB * d)) - 1u));
 }
 
 // Insert slot f at position pos; positions >= pos move up by one.
 template <int K>
 __device__ __forceinline__ void ix_insert(Side<K> &S, int pos, int f, int lane) {
-    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
-    constexpr unsigned ALLB = Side<K>::ALLB;
-    const unsigned top = (S.ix[NW - 1] >> (8 * (BPW - 1))) & 0xffu;
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB, EPW = Side<K>::EPW;
+    constexpr unsigned ALLB = Side<K>::ALLB, EMASK = Side<K>::EMASK;
+    const unsigned top = (S.ix[NW - 1] >> (IXB * (BPW - 1))) & EMASK;
     const unsigned carry = __shfl_up_sync(FULL, top, 1);
     unsigned shifted[NW];
 #pragma unroll
     for (int w = 0; w < NW; w++) {
-        const unsigned in = w == 0 ? carry : (S.ix[w - 1] >> 24);
-        shifted[w] = ((S.ix[w] << 8) | in) & ALLB;
+        const unsigned in = w == 0 ? carry : (S.ix[w - 1] >> (IXB * (BPW - 1)));
+        shifted[w] = ((S.ix[w] << IXB) | in) & ALLB;
     }
-    const unsigned fb = (unsigned)f * 0x01010101u;
+    const unsigned fb = (unsigned)f * Side<K>::REP;
 #pragma unroll
     for (int w = 0; w < NW; w++) {
-        const int d = pos - (lane * K + 4 * w);
-        const unsigned keep = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
-        const unsigned fm = (d >= 0 && d < BPW) ? (0xffu << (8 * d)) : 0u;
+        const int d = pos - (lane * K + EPW * w);
+        const unsigned keep = ix_below<K>(pos, lane, w);
+        const unsigned fm = (d >= 0 && d < BPW) ? (EMASK << (IXB * d)) : 0u;
         S.ix[w] = (S.ix[w] & keep) | (fb & fm) | (shifted[w] & ~(keep | fm));
     }
 }
@@ -239,19 +277,18 @@ __device__ __forceinline__ void ix_insert(Side<K> &S, int pos, int f, int lane) 
 // Remove position q; positions > q move down by one.
 template <int K>
 __device__ __forceinline__ void ix_remove(Side<K> &S, int q, int lane) {
-    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
-    constexpr unsigned ALLB = Side<K>::ALLB;
-    const unsigned nxt = __shfl_down_sync(FULL, S.ix[0] & 0xffu, 1);
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB;
+    constexpr unsigned ALLB = Side<K>::ALLB, EMASK = Side<K>::EMASK;
+    const unsigned nxt = __shfl_down_sync(FULL, S.ix[0] & EMASK, 1);
     unsigned shifted[NW];
 #pragma unroll
     for (int w = 0; w < NW; w++) {
-        const unsigned in = w + 1 < NW ? (S.ix[w + 1] & 0xffu) : nxt;
-        shifted[w] = ((S.ix[w] >> 8) | (in << (8 * (BPW - 1)))) & ALLB;
+        const unsigned in = w + 1 < NW ? (S.ix[w + 1] & EMASK) : nxt;
+        shifted[w] = ((S.ix[w] >> IXB) | (in << (IXB * (BPW - 1)))) & ALLB;
     }
 #pragma unroll
     for (int w = 0; w < NW; w++) {
-        const int d = q - (lane * K + 4 * w);
-        const unsigned keep = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
+        const unsigned keep = ix_below<K>(q, lane, w);
         S.ix[w] = (S.ix[w] & keep) | (shifted[w] & ~keep);
     }
 }
@@ -259,15 +296,14 @@ __device__ __forceinline__ void ix_remove(Side<K> &S, int q, int lane) {
 // Position of slot s among the n live positions.
 template <int K>
 __device__ __forceinline__ int ix_find(const Side<K> &S, int s, int lane) {
-    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW;
-    constexpr unsigned ALLB = Side<K>::ALLB;
+    constexpr int NW = Side<K>::NW, IXB = Side<K>::IXB, EPW = Side<K>::EPW;
     int local = -1;
 #pragma unroll
     for (int w = NW - 1; w >= 0; w--) {
-        const int d = S.n - (lane * K + 4 * w);
-        const unsigned valid = d <= 0 ? 0u : (d >= BPW ? ALLB : ((1u << (8 * d)) - 1u));
-        const unsigned m = __vcmpeq4(S.ix[w], (unsigned)s * 0x01010101u) & valid;
-        if (m) local = 4 * w + ((__ffs(m) - 1) >> 3);
+        const unsigned key = (unsigned)s * Side<K>::REP;
+        const unsigned eq = IXB == 8 ? __vcmpeq4(S.ix[w], key) : __vcmpeq2(S.ix[w], key);
+        const unsigned m = eq & ix_below<K>(S.n, lane, w);
+        if (m) local = EPW * w + (__ffs(m) - 1) / IXB;
     }
     const unsigned lanes = __ballot_sync(FULL, local >= 0);
     const int L = __ffs(lanes) - 1;
@@ -276,7 +312,7 @@ __device__ __forceinline__ int ix_find(const Side<K> &S, int s, int lane) {
 
 template <int K>
 __device__ __forceinline__ void slot_clear(Side<K> &S, int s, int lane) {
-    if (lane == s / K) S.occ &= ~(1u << (s % K));
+    if (lane == slot_lane<K>(s)) S.occ &= ~(1u << slot_r<K>(s));
 }
 
 // Refresh the cached front order from position 0.
@@ -385,10 +421,10 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
     const int vic_q = P.qty[vic];
     const unsigned fr = ~S.occ & Side<K>::KMASK;
     const unsigned flanes = __ballot_sync(FULL, fr != 0);
-    const int free_slot = __shfl_sync(FULL, lane * K + __ffs(fr) - 1, __ffs(flanes) - 1);
+    const int free_slot = __shfl_sync(FULL, slot_of<K>(lane, __ffs(fr) - 1), __ffs(flanes) - 1);
     int cnt = 0;
 #pragma unroll
-    for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p));
+    for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(spx<K>(S, P, r, lane), p));
     const int pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
     const bool full = S.n >= cap;
     if (full && pos >= S.n) {  // not strictly better than the worst resting price
@@ -402,11 +438,13 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
         c.c_evict_cnt += 1;
         S.n--;
     }
-    const int fl = f / K, fr_ = f % K;
+    const int fl = slot_lane<K>(f), fr_ = slot_r<K>(f);
     if (lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
+    if constexpr (Side<K>::REG) {
 #pragma unroll
-    for (int r = 0; r < K; r++)
-        if (lane == fl && r == fr_) { S.px[r] = p; S.id[r] = oid; }
+        for (int r = 0; r < K; r++)
+            if (lane == fl && r == fr_) { S.px[r] = p; S.id[r] = oid; }
+    }
     P.px[f] = p; P.qty[f] = q; P.id[f] = oid; P.ts[f] = c.ts_next;   // same value from every lane
     c.ts_next++;
     ix_insert<K>(S, pos, f, lane);
@@ -432,7 +470,7 @@ __device__ __forceinline__ int first_dup_slot(const Side<K> &S, const PoolSmem<K
     for (int j = K - 1; j >= 0; j--) {
         const int q = lane * K + j;
         if (q < S.n) {
-            const int s = ix_byte<K>(S, j);
+            const int s = ix_ent<K>(S, j);
             if (P.px[s] == p && P.id[s] == oid) best = j;
         }
     }
@@ -449,7 +487,7 @@ __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type
     unsigned m = 0;
 #pragma unroll
     for (int r = 0; r < K; r++)
-        if (((S.occ >> r) & 1u) && S.px[r] == p && S.id[r] == oid) m |= 1u << r;
+        if (((S.occ >> r) & 1u) && spx<K>(S, P, r, lane) == p && sid<K>(S, P, r, lane) == oid) m |= 1u << r;
     const unsigned lanes = __ballot_sync(FULL, m != 0);
     if (lanes == 0) {
         c.c_cancel_miss += 1;
@@ -459,7 +497,7 @@ __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type
     int s;
     if (!dup) {
         const int L = __ffs(lanes) - 1;
-        s = __shfl_sync(FULL, lane * K + __ffs(m) - 1, L);
+        s = __shfl_sync(FULL, slot_of<K>(lane, __ffs(m) - 1), L);
     } else {
         s = first_dup_slot<K>(S, P, p, oid, lane);
     }
@@ -475,105 +513,103 @@ __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type
 }
 
 // ---------------------------------------------------------------- load / store / gather
+// Load one side's block (positions in priority order, lane l loading
+// positions l*K .. l*K+K-1 with vector loads); position q goes to pool slot q,
+// so the index starts as the identity.  Occupancy is set once n is known.
 template <int K, bool BID>
-__device__ __forceinline__ void side_load(Side<K> &S, PoolSmem<K> &P, const unsigned char *blk, int n, int lane) {
+__device__ __forceinline__ void side_load(Side<K> &S, PoolSmem<K> &P, const unsigned char *blk, int lane) {
     constexpr int SL = 32 * K;
     const int s = BID ? 0 : 1;
     const int *gpx = reinterpret_cast<const int *>(blk) + s * SL + lane * K;
     const int *gqt = reinterpret_cast<const int *>(blk) + 2 * SL + s * SL + lane * K;
     const long long *gid = reinterpret_cast<const long long *>(blk + 16 * SL) + s * SL + lane * K;
     const long long *gts = reinterpret_cast<const long long *>(blk + 32 * SL) + s * SL + lane * K;
-    int qt[K];
-    long long ts[K];
-    if constexpr (K % 4 == 0) {
+    constexpr int G = K < 4 ? K : 4;   // positions per vector group
 #pragma unroll
-        for (int v = 0; v < K / 4; v++) {
-            const int4 a = reinterpret_cast<const int4 *>(gpx)[v];
-            const int4 b = reinterpret_cast<const int4 *>(gqt)[v];
-            S.px[4 * v] = a.x; S.px[4 * v + 1] = a.y; S.px[4 * v + 2] = a.z; S.px[4 * v + 3] = a.w;
-            qt[4 * v] = b.x; qt[4 * v + 1] = b.y; qt[4 * v + 2] = b.z; qt[4 * v + 3] = b.w;
+    for (int g = 0; g < K; g += G) {
+        int px[G], qt[G];
+        long long id[G], ts[G];
+        if constexpr (G == 4) {
+            const int4 a = *reinterpret_cast<const int4 *>(gpx + g);
+            const int4 b = *reinterpret_cast<const int4 *>(gqt + g);
+            px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
+            qt[0] = b.x; qt[1] = b.y; qt[2] = b.z; qt[3] = b.w;
+            const longlong2 c0 = *reinterpret_cast<const longlong2 *>(gid + g);
+            const longlong2 c1 = *reinterpret_cast<const longlong2 *>(gid + g + 2);
+            const longlong2 d0 = *reinterpret_cast<const longlong2 *>(gts + g);
+            const longlong2 d1 = *reinterpret_cast<const longlong2 *>(gts + g + 2);
+            id[0] = c0.x; id[1] = c0.y; id[2] = c1.x; id[3] = c1.y;
+            ts[0] = d0.x; ts[1] = d0.y; ts[2] = d1.x; ts[3] = d1.y;
+        } else {
+#pragma unroll
+            for (int u = 0; u < G; u++) { px[u] = gpx[g + u]; qt[u] = gqt[g + u]; id[u] = gid[g + u]; ts[u] = gts[g + u]; }
         }
-    } else {
 #pragma unroll
-        for (int r = 0; r < K; r++) { S.px[r] = gpx[r]; qt[r] = gqt[r]; }
-    }
-    if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < K / 2; v++) {
-            const longlong2 a = reinterpret_cast<const longlong2 *>(gid)[v];
-            const longlong2 b = reinterpret_cast<const longlong2 *>(gts)[v];
-            S.id[2 * v] = a.x; S.id[2 * v + 1] = a.y; ts[2 * v] = b.x; ts[2 * v + 1] = b.y;
+        for (int u = 0; u < G; u++) {
+            const int slot = lane * K + g + u;
+            P.px[slot] = px[u]; P.qty[slot] = qt[u]; P.id[slot] = id[u]; P.ts[slot] = ts[u];
+            if constexpr (Side<K>::REG) { S.px[g + u] = px[u]; S.id[g + u] = id[u]; }
         }
-    } else {
-#pragma unroll
-        for (int r = 0; r < K; r++) { S.id[r] = gid[r]; ts[r] = gts[r]; }
-    }
-    // slot = position after a load; index bytes are the identity
-    S.n = n;
-    S.occ = 0;
-#pragma unroll
-    for (int r = 0; r < K; r++) {
-        const int slot = lane * K + r;
-        if (slot < n) S.occ |= 1u << r;
-        P.px[slot] = S.px[r]; P.qty[slot] = qt[r]; P.id[slot] = S.id[r]; P.ts[slot] = ts[r];
     }
 #pragma unroll
     for (int w = 0; w < Side<K>::NW; w++) {
         unsigned v = 0;
 #pragma unroll
-        for (int b = 0; b < Side<K>::BPW; b++) v |= (unsigned)(lane * K + 4 * w + b) << (8 * b);
+        for (int b = 0; b < Side<K>::BPW; b++)
+            v |= (unsigned)(lane * K + Side<K>::EPW * w + b) << (Side<K>::IXB * b);
         S.ix[w] = v;
     }
 }
 
-// Position-ordered copies of this lane's K positions (priority order).
+// Mark slots 0 .. n-1 occupied (the identity index after a load).
 template <int K>
-__device__ __forceinline__ void side_gather(const Side<K> &S, const PoolSmem<K> &P, int (&px)[K], int (&qt)[K],
-                                            long long (&id)[K], long long (&ts)[K]) {
+__device__ __forceinline__ void side_set_count(Side<K> &S, int n, int lane) {
+    S.n = n;
+    S.occ = 0;
 #pragma unroll
-    for (int j = 0; j < K; j++) {
-        const int s = ix_byte<K>(S, j);
-        px[j] = P.px[s]; qt[j] = P.qty[s]; id[j] = P.id[s]; ts[j] = P.ts[s];
-    }
+    for (int r = 0; r < K; r++)
+        if (slot_of<K>(lane, r) < n) S.occ |= 1u << r;
 }
 
+// Store one side in priority order (this lane's K positions, gathered from
+// the pool), vector stores as in the load.
 template <int K, bool BID>
-__device__ __forceinline__ void side_store(const Side<K> &S, const int (&px)[K], const int (&qt)[K],
-                                           const long long (&id)[K], const long long (&ts)[K],
-                                           unsigned char *blk, int lane) {
+__device__ __forceinline__ void side_store(const Side<K> &S, const PoolSmem<K> &P, unsigned char *blk, int lane) {
     constexpr int SL = 32 * K;
-    const int s = BID ? 0 : 1;
-    int *gpx = reinterpret_cast<int *>(blk) + s * SL + lane * K;
-    int *gqt = reinterpret_cast<int *>(blk) + 2 * SL + s * SL + lane * K;
-    long long *gid = reinterpret_cast<long long *>(blk + 16 * SL) + s * SL + lane * K;
-    long long *gts = reinterpret_cast<long long *>(blk + 32 * SL) + s * SL + lane * K;
-    if (lane * K >= S.n) return;
-    if constexpr (K % 4 == 0) {
+    const int sd = BID ? 0 : 1;
+    int *gpx = reinterpret_cast<int *>(blk) + sd * SL + lane * K;
+    int *gqt = reinterpret_cast<int *>(blk) + 2 * SL + sd * SL + lane * K;
+    long long *gid = reinterpret_cast<long long *>(blk + 16 * SL) + sd * SL + lane * K;
+    long long *gts = reinterpret_cast<long long *>(blk + 32 * SL) + sd * SL + lane * K;
+    constexpr int G = K < 4 ? K : 4;
 #pragma unroll
-        for (int v = 0; v < K / 4; v++) {
-            reinterpret_cast<int4 *>(gpx)[v] = make_int4(px[4 * v], px[4 * v + 1], px[4 * v + 2], px[4 * v + 3]);
-            reinterpret_cast<int4 *>(gqt)[v] = make_int4(qt[4 * v], qt[4 * v + 1], qt[4 * v + 2], qt[4 * v + 3]);
+    for (int g = 0; g < K; g += G) {
+        if (lane * K + g >= S.n) break;
+        int px[G], qt[G];
+        long long id[G], ts[G];
+#pragma unroll
+        for (int u = 0; u < G; u++) {
+            const int s = ix_ent<K>(S, g + u);
+            px[u] = P.px[s]; qt[u] = P.qty[s]; id[u] = P.id[s]; ts[u] = P.ts[s];
         }
-    } else {
+        if constexpr (G == 4) {
+            *reinterpret_cast<int4 *>(gpx + g) = make_int4(px[0], px[1], px[2], px[3]);
+            *reinterpret_cast<int4 *>(gqt + g) = make_int4(qt[0], qt[1], qt[2], qt[3]);
+            *reinterpret_cast<longlong2 *>(gid + g) = make_longlong2(id[0], id[1]);
+            *reinterpret_cast<longlong2 *>(gid + g + 2) = make_longlong2(id[2], id[3]);
+            *reinterpret_cast<longlong2 *>(gts + g) = make_longlong2(ts[0], ts[1]);
+            *reinterpret_cast<longlong2 *>(gts + g + 2) = make_longlong2(ts[2], ts[3]);
+        } else {
 #pragma unroll
-        for (int r = 0; r < K; r++) { gpx[r] = px[r]; gqt[r] = qt[r]; }
-    }
-    if constexpr (K % 2 == 0) {
-#pragma unroll
-        for (int v = 0; v < K / 2; v++) {
-            reinterpret_cast<longlong2 *>(gid)[v] = make_longlong2(id[2 * v], id[2 * v + 1]);
-            reinterpret_cast<longlong2 *>(gts)[v] = make_longlong2(ts[2 * v], ts[2 * v + 1]);
+            for (int u = 0; u < G; u++) { gpx[g + u] = px[u]; gqt[g + u] = qt[u]; gid[g + u] = id[u]; gts[g + u] = ts[u]; }
         }
-    } else {
-#pragma unroll
-        for (int r = 0; r < K; r++) { gid[r] = id[r]; gts[r] = ts[r]; }
     }
 }
 
 // Book of env 0 after a message, canonical layout (trace mode only).
 template <int K>
 __device__ __forceinline__ void write_snapshot(const Side<K> &B, const Side<K> &A, const WarpSmem<K> &sm, int C,
-                                            unsigned char *rec, int lane) {
+                                               unsigned char *rec, int lane) {
     int *n2 = reinterpret_cast<int *>(rec);
     int *px = n2 + 2;
     int *qt = px + 2 * C;
@@ -585,7 +621,7 @@ __device__ __forceinline__ void write_snapshot(const Side<K> &B, const Side<K> &
         const int q = lane * K + j;
         if (q < C) {
             const bool vb = q < B.n, va = q < A.n;
-            const int sb = ix_byte<K>(B, j), sa = ix_byte<K>(A, j);
+            const int sb = ix_ent<K>(B, j), sa = ix_ent<K>(A, j);
             px[q] = vb ? sm.pool[0].px[sb] : 0; qt[q] = vb ? sm.pool[0].qty[sb] : 0;
             id[q] = vb ? sm.pool[0].id[sb] : 0; ts[q] = vb ? sm.pool[0].ts[sb] : 0;
             px[C + q] = va ? sm.pool[1].px[sa] : 0; qt[C + q] = va ? sm.pool[1].qty[sa] : 0;
@@ -601,21 +637,22 @@ __device__ __forceinline__ long long warp_sum(long long v) {
     return v;
 }
 
-// Aggregated top-L levels of one side (positions in priority order, this
-// lane's K positions in px/qt); sums runs within the lane before the
-// shared-memory atomics.  Returns the number of levels.
+// Aggregated top-L levels of one side, read from the pool in priority order
+// in two passes over this lane's positions (level starts, then run sums into
+// shared-memory int64 atomics).  Also returns the resting quantity of each
+// agent on this side (own0 / own1, warp totals).  Returns the level count.
 template <int K>
-__device__ __forceinline__ int side_levels(const int (&px)[K], const int (&qt)[K], int n, int L, int *lvl_px,
-                                           long long *lvl_q, int lane) {
-    const int ppx = __shfl_up_sync(FULL, px[K - 1], 1);
-    bool start[K];
-    int cnt = 0;
+__device__ __forceinline__ int side_levels(const Side<K> &S, const PoolSmem<K> &P, int L, int *lvl_px,
+                                           long long *lvl_q, long long &own0, long long &own1, int lane) {
+    const int n = S.n;
+    const int ppx = __shfl_up_sync(FULL, P.px[ix_ent<K>(S, K - 1)], 1);
+    int cnt = 0, prev = ppx;
 #pragma unroll
-    for (int r = 0; r < K; r++) {
-        const int q = lane * K + r;
-        const int prev = r == 0 ? ppx : px[r - 1];
-        start[r] = q < n && (q == 0 || px[r] != prev);
-        cnt += start[r];
+    for (int j = 0; j < K; j++) {
+        const int q = lane * K + j;
+        const int px = P.px[ix_ent<K>(S, j)];
+        cnt += (q < n && (q == 0 || px != prev)) ? 1 : 0;
+        prev = px;
     }
     int incl = cnt;
 #pragma unroll
@@ -624,21 +661,34 @@ __device__ __forceinline__ int side_levels(const int (&px)[K], const int (&qt)[K
         if (lane >= d) incl += y;
     }
     int lv = incl - cnt - 1;
-    long long run = 0;
+    long long run = 0, o0 = 0, o1 = 0;
     int run_lv = -1;
+    prev = ppx;
 #pragma unroll
-    for (int r = 0; r < K; r++) {
-        const int q = lane * K + r;
-        if (start[r]) {
-            if (run_lv >= 0 && run_lv < L) atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[run_lv]), (unsigned long long)run);
-            lv++;
-            run = 0;
-            if (lv < L) lvl_px[lv] = px[r];
+    for (int j = 0; j < K; j++) {
+        const int q = lane * K + j;
+        const int s = ix_ent<K>(S, j);
+        const int px = P.px[s];
+        if (q < n) {
+            const int qt = P.qty[s];
+            const long long id = P.id[s];
+            if (q == 0 || px != prev) {
+                if (run_lv >= 0 && run_lv < L)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[run_lv]), (unsigned long long)run);
+                lv++;
+                run = 0;
+                if (lv < L) lvl_px[lv] = px;
+            }
+            run += qt;
+            run_lv = lv;
+            if (id < 0) { if ((~id) & 1) o1 += qt; else o0 += qt; }
         }
-        if (q < n) { run += qt[r]; run_lv = lv; }
+        prev = px;
     }
     if (run_lv >= 0 && run_lv < L && run != 0)
         atomicAdd(reinterpret_cast<unsigned long long *>(&lvl_q[run_lv]), (unsigned long long)run);
+    own0 += warp_sum(o0);
+    own1 += warp_sum(o1);
     return __shfl_sync(FULL, incl, 31);
 }
 
@@ -653,14 +703,16 @@ __device__ __forceinline__ unsigned side_carry(const Side<K> &S, const PoolSmem<
     unsigned cmask = 0;
 #pragma unroll
     for (int r = 0; r < K; r++) {
-        const int slot = lane * K + r;
+        const int slot = slot_of<K>(lane, r);
         unsigned char flag = 0;
-        if (((S.occ >> r) & 1u) && S.id[r] < 0) {
-            const int a = (int)((~S.id[r]) & 1);
+        const long long oid = sid<K>(S, P, r, lane);
+        if (((S.occ >> r) & 1u) && oid < 0) {
+            const int a = (int)((~oid) & 1);
+            const int opx = spx<K>(S, P, r, lane);
             int m = -1;
 #pragma unroll
             for (int i = 0; i < 3; i++)
-                if (i < nw && wa[i] == a && ws[i] == side && wp[i] == S.px[r]) m = i;
+                if (i < nw && wa[i] == a && ws[i] == side && wp[i] == opx) m = i;
             if (m < 0) {
                 flag = (unsigned char)(1 + a);
                 cmask |= 1u << r;
@@ -682,7 +734,7 @@ __device__ __forceinline__ void side_cancel_set(Side<K> &S, PoolSmem<K> &P, unsi
     unsigned vol = 0;
 #pragma unroll
     for (int r = 0; r < K; r++)
-        if ((cmask >> r) & 1u) vol += (unsigned)P.qty[lane * K + r];
+        if ((cmask >> r) & 1u) vol += (unsigned)P.qty[slot_of<K>(lane, r)];
     const int ncan = (int)__reduce_add_sync(FULL, (unsigned)__popc(cmask));
     if (ncan == 0) return;
     c.c_cancel_vol += (long long)__reduce_add_sync(FULL, vol);
@@ -693,7 +745,7 @@ __device__ __forceinline__ void side_cancel_set(Side<K> &S, PoolSmem<K> &P, unsi
         const unsigned lanes = __ballot_sync(FULL, cmask != 0);
         if (lanes == 0) break;
         const int L = __ffs(lanes) - 1;
-        const int s = __shfl_sync(FULL, lane * K + __ffs(cmask) - 1, L);
+        const int s = __shfl_sync(FULL, slot_of<K>(lane, __ffs(cmask) - 1), L);
         if (lane == L) cmask &= cmask - 1;
         side_remove_slot<K>(S, P, s, lane);
     }
@@ -710,7 +762,7 @@ __device__ __forceinline__ void side_agent_cancels(Side<K> &S, PoolSmem<K> &P, u
         int first = -1;
 #pragma unroll
         for (int j = K - 1; j >= 0; j--)
-            if (lane * K + j < S.n && cand[ix_byte<K>(S, j)] == 1 + a) first = j;
+            if (lane * K + j < S.n && cand[ix_ent<K>(S, j)] == 1 + a) first = j;
         const unsigned lanes = __ballot_sync(FULL, first >= 0);
         if (lanes == 0) break;
         const int L = __ffs(lanes) - 1;
@@ -752,8 +804,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     long long me = p.offsets[(long long)e * p.off_stride + p.k0 + 1];
 
     Side<K> bid, ask;
-    side_load<K, true>(bid, sm.pool[0], blk, 0, lane);
-    side_load<K, false>(ask, sm.pool[1], blk, 0, lane);
+    side_load<K, true>(bid, sm.pool[0], blk, lane);
+    side_load<K, false>(ask, sm.pool[1], blk, lane);
 
     Ctx c;
     c.ts_next = st->ts_next; c.seq_next = st->seq_next;
@@ -772,15 +824,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     c.fill_log = p.fills ? p.fills + (long long)e * p.fill_cap : nullptr;
     c.fill_cap = p.fill_cap;
     // live counts arrive with the state: mark occupancy now
-    bid.occ = 0;
-    ask.occ = 0;
-#pragma unroll
-    for (int r = 0; r < K; r++) {
-        if (lane * K + r < nb0) bid.occ |= 1u << r;
-        if (lane * K + r < na0) ask.occ |= 1u << r;
-    }
-    bid.n = nb0;
-    ask.n = na0;
+    side_set_count<K>(bid, nb0, lane);
+    side_set_count<K>(ask, na0, lane);
     __syncwarp();
     front_refresh<K>(bid, sm.pool[0]);
     front_refresh<K>(ask, sm.pool[1]);
@@ -1018,10 +1063,6 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
 
         // ---- 5. step outcomes (and, after the last step, the book write-back)
         __syncwarp();
-        int bpx[K], bqt[K], apx[K], aqt[K];
-        long long bid_id[K], bts[K], aid[K], ats[K];
-        side_gather<K>(bid, sm.pool[0], bpx, bqt, bid_id, bts);
-        side_gather<K>(ask, sm.pool[1], apx, aqt, aid, ats);
         const long long obs_base = ((long long)step * p.n_envs + e);
         if (A > 0) {
             const int L = p.L;
@@ -1030,21 +1071,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 (&sm.lvl_px[0][0])[i] = 0;
             }
             __syncwarp();
-            const int nlb = side_levels<K>(bpx, bqt, bid.n, L, sm.lvl_px[0], sm.lvl_q[0], lane);
-            const int nla = side_levels<K>(apx, aqt, ask.n, L, sm.lvl_px[1], sm.lvl_q[1], lane);
+            long long own0 = 0, own1 = 0;
+            const int nlb = side_levels<K>(bid, sm.pool[0], L, sm.lvl_px[0], sm.lvl_q[0], own0, own1, lane);
+            const int nla = side_levels<K>(ask, sm.pool[1], L, sm.lvl_px[1], sm.lvl_q[1], own0, own1, lane);
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
             const long long s2 = bb + ba;
             const long long anchor = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
-            long long own0 = 0, own1 = 0;
-#pragma unroll
-            for (int r = 0; r < K; r++) {
-                const int q = lane * K + r;
-                if (q < bid.n && bid_id[r] < 0) { if ((~bid_id[r]) & 1) own1 += bqt[r]; else own0 += bqt[r]; }
-                if (q < ask.n && aid[r] < 0) { if ((~aid[r]) & 1) own1 += aqt[r]; else own0 += aqt[r]; }
-            }
-            own0 = warp_sum(own0);
-            own1 = warp_sum(own1);
             // Eq. 1: PV = Q_inv * P_ref + Cash, P_ref the liquidation touch
             const long long pref0 = c.inv0 > 0 ? bb : (c.inv0 < 0 ? ba : 0);
             const long long pref1 = c.inv1 > 0 ? bb : (c.inv1 < 0 ? ba : 0);
@@ -1092,8 +1125,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         if (lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
         if (step + 1 == p.n_steps) {
-            side_store<K, true>(bid, bpx, bqt, bid_id, bts, blk, lane);
-            side_store<K, false>(ask, apx, aqt, aid, ats, blk, lane);
+            side_store<K, true>(bid, sm.pool[0], blk, lane);
+            side_store<K, false>(ask, sm.pool[1], blk, lane);
         }
     }
 

@@ -32,7 +32,7 @@ LOB_OK, LOB_EINVAL, LOB_ENOMEM, LOB_ECUDA, LOB_ETIMEOUT, LOB_ECAPACITY, LOB_EBAD
     0, -1, -2, -3, -4, -5, -6, -7
 LOB_ACT_HOST, LOB_ACT_RANDOM = 0, 1
 LOB_NCOUNTERS = 16
-LOB_MAX_CAP = 256
+LOB_MAX_CAP = 1024
 FILL_BYTES = 32
 
 # Every entry point include/lob.h declares (checked by the test suite).

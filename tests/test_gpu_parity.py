@@ -83,13 +83,13 @@ def test_tiny_capacities_every_branch(seed):
 
 
 def test_uneven_caps_and_poisson_counts():
-    """Capacities from {50, 100, 200, 256} (all register classes) and
+    """Capacities from 20 to 1,000 (every capacity class) and
     M_t ~ Poisson(lambda_env), including empty steps."""
     n, T = 96, 15
-    caps = mbogen.env_caps(3, n, choices=(20, 50, 100, 200, 256))
+    caps = mbogen.env_caps(3, n, choices=(20, 50, 100, 200, 256, 500, 1000))
     st = mbogen.generate(mbogen.MessageModel(poisson=True, lam_lo=0.5, lam_hi=300.0), mbogen.env_seeds(13, n), T)
     assert (st.counts == 0).any()
-    pr = Pair(n, st, caps=caps, cap=256, exec_target=100, fill_cap=1024)
+    pr = Pair(n, st, caps=caps, cap=1000, exec_target=100, fill_cap=1024)
     for _ in range(T):
         pr.step()
         pr.check_outputs()
@@ -217,3 +217,107 @@ def test_create_rejects_bad_configs():
         with pytest.raises(lob.LobError) as ei:
             lob.lob_create(c)
         assert ei.value.code == code, field
+
+
+def test_stress_mix_cap1000_top20():
+    """Heavy-tailed mix at capacity 1,000 per side: 30 % aggressive orders,
+    Pareto(1.5) sizes capped at 10,000, delete bursts, top-20 levels."""
+    n, T = 48, 6
+    st = mbogen.generate(mbogen.STRESS_MODEL, mbogen.env_seeds(51, n), T)
+    pr = Pair(n, st, cap=1000, top_levels=20, exec_target=2000, fill_cap=4096)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    pr.close()
+
+
+def _sampled_pair_check(n_all, sample, model, T, cap=None, caps=None, top_levels=10, exec_target=500,
+                        rollout=False, graph=False):
+    """All n_all envs on the GPU; the oracle runs the sampled envs only (env
+    streams depend on their own seed only) and must agree on them exactly."""
+    import oracle
+    import torch
+    from harness import to_dev
+    seeds = mbogen.env_seeds(77, n_all)
+    st = mbogen.generate(model, seeds, T)
+    caps_all = caps
+    env = lob.LobEnv(n_all, cap=cap or 100, top_levels=top_levels, episode_len=T, exec_target=exec_target,
+                     action_mode=lob.LOB_ACT_RANDOM, caps=caps_all)
+    lob.lob_set_launch(env.h, 4, 1)
+    md, od = to_dev(st.msgs), to_dev(st.offsets)
+    env.load_messages(md, od)
+    env.reset(to_dev(seeds))
+    D = env.D
+    obs_last = None
+    if rollout:
+        obs = torch.zeros((T, n_all, 2, D), dtype=torch.float32, device="cuda")
+        rew = torch.zeros((T, n_all, 2), dtype=torch.int64, device="cuda")
+        if graph:
+            s_ = torch.cuda.Stream()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s_):
+                lob.lob_rollout(env.h, T, None, obs, rew, None, stream=s_)
+            g.replay()
+        else:
+            lob.lob_rollout(env.h, T, None, obs, rew, None)
+        torch.cuda.synchronize()
+        obs_last = obs[T - 1].cpu().numpy()
+        rew_sum = rew.sum(0).cpu().numpy()
+    else:
+        rew_sum = torch.zeros((n_all, 2), dtype=torch.int64, device="cuda")
+        for _ in range(T):
+            env.step()
+            rew_sum += env.observe()[1]
+        obs_last = env.observe()[0].cpu().numpy()
+        rew_sum = rew_sum.cpu().numpy()
+    assert env.sync() == 0
+    g_cnt = env.counters().cpu().numpy()
+    g_books = env.books()
+    g_agents = env.agents().cpu().numpy()
+    env.close()
+    o = oracle.Oracle(len(sample), cap=cap or 100, top_levels=top_levels, episode_len=T, exec_target=exec_target,
+                      action_mode=1, n_threads=os.cpu_count() or 1,
+                      caps=None if caps is None else np.asarray(caps)[sample])
+    sub = mbogen.generate(model, seeds[sample], T)
+    o.reset(sub.seeds)
+    o.load_messages(sub.msgs, sub.offsets)
+    o_rsum = np.zeros((len(sample), 2), np.int64)
+    for _ in range(T):
+        o.step()
+        o_rsum += o.observe()[1]
+    o_obs = o.observe()[0]
+    np.testing.assert_array_equal(rew_sum[sample], o_rsum)
+    np.testing.assert_allclose(obs_last[sample], o_obs, rtol=1e-6, atol=0)
+    np.testing.assert_array_equal(g_cnt[sample], o.counters())
+    np.testing.assert_array_equal(g_agents[sample], o.agents())
+    for i, e in enumerate(sample):
+        n2, px, qty, oid, ts = o.book(i)
+        b = g_books[e]
+        assert b["n"].tolist() == n2.tolist()
+        for sd in range(2):
+            k = n2[sd]
+            np.testing.assert_array_equal(b["px"][sd][:k], px[sd][:k])
+            np.testing.assert_array_equal(b["qty"][sd][:k], qty[sd][:k])
+            np.testing.assert_array_equal(b["id"][sd][:k], oid[sd][:k])
+            np.testing.assert_array_equal(b["ts"][sd][:k], ts[sd][:k])
+
+
+def test_uneven_batch_8192_envs_one_graph_launch():
+    """8,192 envs, capacities uniform in {50, 100, 200, 500}, M_t ~ Poisson with
+    lambda log-uniform in [10, 500]; all steps in one persistent launch under a
+    captured CUDA graph; every 64th env checked against the oracle."""
+    n = 8192
+    caps = mbogen.env_caps(5, n)
+    _sampled_pair_check(n, np.arange(0, n, 64), mbogen.MessageModel(poisson=True), 40, cap=500, caps=caps,
+                        rollout=True, graph=True)
+
+
+def test_stress_65536_envs_cap1000():
+    """65,536 envs x capacity 1,000 x 1,000 messages of the heavy-tailed mix,
+    top-20 levels (a window of 4 steps); every 256th env checked."""
+    n = 65536
+    _sampled_pair_check(n, np.arange(0, n, 256), mbogen.STRESS_MODEL, 4, cap=1000, top_levels=20,
+                        exec_target=2000)
