@@ -343,6 +343,151 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- other workloads
+def _flush_and_time(run, reps, dev):
+    """Time `run()` `reps` times with CUDA events, writing 256 MiB between runs."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    out = []
+    for i in range(reps):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b) / 1e3)
+    return out
+
+
+def run_workload(args):
+    """Secondary lines: the uneven 8,192-env batch, the fused-policy rollout and
+    the capacity-1,000 stress window (one JSON line each)."""
+    import torch
+    from paper_2511_02136_gb300 import autotune, lob, mbogen
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lob.build()
+    wl = args.workload
+
+    def upload(st, seeds):
+        return (torch.from_numpy(st.msgs.view(np.uint8)).to(dev), torch.from_numpy(st.offsets).to(dev),
+                torch.from_numpy(seeds.view(np.int64).copy()).to(dev))
+
+    if wl == "uneven8192":
+        n, T = 8192, 500
+        seeds = mbogen.env_seeds(2, n)
+        caps = mbogen.env_caps(2, n)
+        st = mbogen.generate(mbogen.MessageModel(poisson=True), seeds, T)
+        md, od, sd = upload(st, seeds)
+        env = lob.LobEnv(n, cap=500, episode_len=T, exec_target=500, action_mode=lob.LOB_ACT_RANDOM, caps=caps)
+        slots = np.array([max(32, 1 << int(np.ceil(np.log2(c)))) for c in caps], np.float64)
+        costs = (st.lambdas * (1.0 + slots / 128.0)).astype(np.float32)
+        D = env.D
+        obs = torch.zeros((T, n, 2, D), dtype=torch.float32, device=dev)
+        rew = torch.zeros((T, n, 2), dtype=torch.int64, device=dev)
+        T_tune = 25
+
+        def tune_run():
+            env.load_messages(md, od)
+            env.reset(sd)
+            lob.lob_rollout(env.h, T_tune, None, obs[:T_tune], rew[:T_tune], None)
+
+        choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1)
+        stream = torch.cuda.Stream()
+        env.load_messages(md, od)
+        env.reset(sd, stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            lob.lob_rollout(env.h, T, None, obs, rew, None, stream=stream)
+
+        # the reset before each replay is outside the timed region
+        times = []
+        for i in range(args.reps):
+            env.load_messages(md, od)
+            env.reset(sd)
+            torch.cuda.synchronize()
+            times += _flush_and_time(g.replay, 1, dev)
+        msgs = float(env.counters()[:, 0].sum().item())
+        t = min(times)
+        line = {"workload": "uneven8192", "metric": METRIC, "value": msgs / t, "unit": "msgs/s",
+                "env_steps_per_s": n * T / t, "seconds_per_rollout": t, "steps": T, "n_gpus": 1,
+                "config": {"workload": "8192 envs, caps uniform {50,100,200,500}, M_t ~ Poisson(lambda), "
+                                       "lambda log-uniform [10,500], 500 steps, random policy, one graph-captured "
+                                       "lob_rollout (persistent, classes on concurrent streams)",
+                           "autotuned": choice.__dict__, "messages": msgs},
+                "dtype": "int64", "data": "synthetic"}
+        env.close()
+    elif wl == "policy4096":
+        n, T = 4096, 128
+        seeds = mbogen.env_seeds(3, n)
+        st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), seeds, T)
+        md, od, sd = upload(st, seeds)
+        env = lob.LobEnv(n, cap=200, episode_len=T, exec_target=512, action_mode=lob.LOB_ACT_HOST)
+        params = lob.init_policy_params(5, 2, env.D)
+        pol = lob.lob_policy_create(2, env.D, params)
+        acts = torch.zeros((T, n, 2), dtype=torch.int32, device=dev)
+        res = {}
+        for prec, name in ((lob.LOB_PREC_BF16, "bf16"), (lob.LOB_PREC_FP32, "fp32")):
+            stream = torch.cuda.Stream()
+            env.load_messages(md, od)
+            env.reset(sd)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                lob.lob_rollout_policy(env.h, pol, T, prec, None, None, None, acts, stream=stream)
+            times = []
+            for i in range(args.reps):
+                env.load_messages(md, od)
+                env.reset(sd)
+                torch.cuda.synchronize()
+                times += _flush_and_time(g.replay, 1, dev)
+            msgs = float(env.counters()[:, 0].sum().item())
+            t = min(times)
+            res[name] = {"msgs_per_s": msgs / t, "env_steps_per_s": n * T / t, "seconds_per_rollout": t}
+            # policy forward alone on the final observations
+            ob = torch.zeros((n, 2, env.D), dtype=torch.float32, device=dev)
+            lob.lob_observe(env.h, ob)
+            pt = _flush_and_time(lambda: lob.lob_policy_forward(pol, ob, n, prec, None, None, acts[0]), 20, dev)
+            res[name]["policy_forward_us"] = 1e6 * float(np.median(pt))
+        lob.lob_policy_destroy(pol)
+        env.close()
+        line = {"workload": "policy4096", "metric": METRIC, "value": res["bf16"]["msgs_per_s"], "unit": "msgs/s",
+                "env_steps_per_s": res["bf16"]["env_steps_per_s"], "bf16": res["bf16"], "fp32": res["fp32"],
+                "config": {"workload": "4096 envs x cap 200 x 100 msgs x 128 steps, per-agent MLP 45-128-128-13 "
+                                       "(tanh) in the loop, one graph-captured lob_rollout_policy"},
+                "dtype": "int64 book / bf16 policy", "data": "synthetic", "n_gpus": 1, "steps": T}
+    elif wl == "stress65536":
+        n, T = 65536, args.stress_steps
+        seeds = mbogen.env_seeds(4, n)
+        st = mbogen.generate(mbogen.STRESS_MODEL, seeds, T)
+        md, od, sd = upload(st, seeds)
+        env = lob.LobEnv(n, cap=1000, top_levels=20, episode_len=T, exec_target=2000,
+                         action_mode=lob.LOB_ACT_HOST)
+        params = lob.init_policy_params(7, 2, env.D)
+        pol = lob.lob_policy_create(2, env.D, params)
+        lob.lob_set_launch(env.h, 4, 1)
+        times = []
+        for i in range(args.reps):
+            env.load_messages(md, od)
+            env.reset(sd)
+            torch.cuda.synchronize()
+            times += _flush_and_time(lambda: lob.lob_rollout_policy(env.h, pol, T, lob.LOB_PREC_BF16), 1, dev)
+        msgs = float(env.counters()[:, 0].sum().item())
+        t = min(times)
+        lob.lob_policy_destroy(pol)
+        env.close()
+        line = {"workload": "stress65536", "metric": METRIC, "value": msgs / t, "unit": "msgs/s",
+                "env_steps_per_s": n * T / t, "seconds": t, "steps": T, "n_gpus": 1,
+                "config": {"workload": f"65536 envs x cap 1000 x 1000 msgs (30% aggressive, Pareto(1.5) sizes "
+                                       f"capped at 1e4, delete bursts) x {T} steps, top-20 obs, BF16 policy in the loop"},
+                "dtype": "int64 book / bf16 policy", "data": "synthetic"}
+    else:
+        raise SystemExit(f"unknown workload {wl}")
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,6 +498,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="envs1024",
+                    choices=["envs1024", "uneven8192", "policy4096", "stress65536"],
+                    help="envs1024 is the benchmark line; the others print secondary lines")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--stress-steps", type=int, default=4)
     ap.add_argument("--gen-steps", type=int, default=T,
                     help="steps of messages generated (the episode wraps there; default: the full episode)")
     args = ap.parse_args()
@@ -360,6 +510,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "envs1024":
+        run_workload(args)
     else:
         run_gpu(args)
 

@@ -237,6 +237,10 @@ int lob_sync(lob_handle *h, void *stream);
 /* Launch-shape control used by the autotuner: warps per block for the step
  * kernels (1..32) and whether they take envs from a work queue. */
 int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
+/* Work hint for the persistent (work-queue) launches: h_cost [n_envs] host
+ * floats, larger = more work; each capacity class then hands out its envs
+ * longest first.  NULL restores env order. */
+int lob_set_env_costs(lob_handle *h, const float *h_cost);
 /* Number of kernels the library launched since creation (for accounting). */
 int64_t lob_kernel_launches(const lob_handle *h);
 

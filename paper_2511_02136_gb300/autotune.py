@@ -1,0 +1,79 @@
+"""Launch-shape autotuner for the batched env step (driver over the C ABI).
+
+For a workload it times every candidate launch shape -- warps (envs) per
+block, plain grid or persistent work queue, and env order (as created, or
+longest first from a per-env cost estimate) -- with CUDA events around a
+caller-supplied run, keeps the fastest, and caches the choice per workload
+signature in a JSON file.  The kernels themselves are unchanged: the shape is
+set through lob_set_launch / lob_set_env_costs before the timed runs.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass, asdict
+
+from . import lob
+
+DEFAULT_CANDIDATES = [(wpb, pers) for pers in (0, 1) for wpb in (1, 2, 4, 8)]
+
+
+@dataclass
+class Choice:
+    warps_per_block: int
+    persistent: int
+    longest_first: bool
+    ms: float
+
+
+def signature(n_envs, caps_hist, mean_msgs, steps, extra=""):
+    return f"n{n_envs}|caps{sorted(caps_hist.items())}|m{round(mean_msgs)}|s{steps}|{extra}"
+
+
+def apply(h, choice: Choice, costs=None):
+    lob.lob_set_launch(h, choice.warps_per_block, choice.persistent)
+    lob.lob_set_env_costs(h, costs if (choice.longest_first and costs is not None) else None)
+
+
+def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=None, key=None):
+    """`run()` performs one timed unit of work on the current stream (it must
+    reset/rebind whatever it consumes); returns the fastest Choice."""
+    import torch
+    if cache and key and os.path.exists(cache):
+        with open(cache) as f:
+            got = json.load(f).get(key)
+        if got:
+            ch = Choice(**got)
+            apply(h, ch, costs)
+            return ch
+    results = []
+    orders = (False, True) if costs is not None else (False,)
+    for wpb, pers in candidates:
+        for lf in orders:
+            if lf and not pers:
+                continue          # the order only matters to the work queue
+            ch = Choice(wpb, pers, lf, 0.0)
+            apply(h, ch, costs)
+            run()                  # warm-up
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(repeats):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                run()
+                b.record()
+                torch.cuda.synchronize()
+                best = min(best, a.elapsed_time(b))
+            ch.ms = best
+            results.append(ch)
+    win = min(results, key=lambda c: c.ms)
+    apply(h, win, costs)
+    if cache and key:
+        data = {}
+        if os.path.exists(cache):
+            with open(cache) as f:
+                data = json.load(f)
+        data[key] = asdict(win)
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return win

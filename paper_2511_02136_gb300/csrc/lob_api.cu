@@ -118,7 +118,9 @@ struct lob_handle {
     int *d_env_list = nullptr;
     int *d_queue = nullptr;
     bool uniform_cap = false;
+    bool custom_order = false;
     long long uni_block = 0;
+    std::vector<int> env_list_h;
     int class_begin[NCLASS] = {0, 0, 0, 0};
     int class_count[NCLASS] = {0, 0, 0, 0};
     long long book_bytes = 0, canon_bytes = 0;
@@ -142,6 +144,11 @@ struct lob_handle {
     int persistent = 0;
     int n_sm = 0;
     int64_t launches = 0;
+    // per-class streams: several capacity classes run concurrently (fork/join
+    // with events, so the pattern also captures into a CUDA graph)
+    cudaStream_t cls_stream[NCLASS] = {};
+    cudaEvent_t ev_fork = nullptr, cls_done[NCLASS] = {};
+    int n_active_classes = 0;
     // host-step staging
     lob_msg *d_stage_msgs = nullptr;
     size_t stage_cap = 0;
@@ -152,6 +159,11 @@ struct lob_handle {
 static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LOB_OK : LOB_ECUDA; }
 
 static void free_all(lob_handle *h) {
+    for (int k = 0; k < NCLASS; k++) {
+        if (h->cls_stream[k]) cudaStreamDestroy(h->cls_stream[k]);
+        if (h->cls_done[k]) cudaEventDestroy(h->cls_done[k]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     void *ptrs[] = {h->d_books, h->d_book_off, h->d_canon_off, h->d_caps, h->d_state, h->d_counters,
                     h->d_seeds, h->d_status, h->d_obs, h->d_rew, h->d_done, h->d_act, h->d_env_list,
                     h->d_queue, h->d_stage_msgs, h->d_stage_off, h->d_stage_act};
@@ -261,6 +273,16 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     rc |= cuda_ok(cudaMemcpy(h->d_canon_off, coff.data(), n * 8, cudaMemcpyHostToDevice));
     rc |= cuda_ok(cudaMemcpy(h->d_caps, caps.data(), n * 4, cudaMemcpyHostToDevice));
     rc |= cuda_ok(cudaMemcpy(h->d_env_list, list.data(), n * 4, cudaMemcpyHostToDevice));
+    h->env_list_h = list;
+    for (int k = 0; k < NCLASS; k++) h->n_active_classes += h->class_count[k] > 0;
+    if (h->n_active_classes > 1) {
+        rc |= cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        for (int k = 0; k < NCLASS; k++) {
+            if (h->class_count[k] == 0) continue;
+            rc |= cuda_ok(cudaStreamCreateWithFlags(&h->cls_stream[k], cudaStreamNonBlocking));
+            rc |= cuda_ok(cudaEventCreateWithFlags(&h->cls_done[k], cudaEventDisableTiming));
+        }
+    }
     rc |= cuda_ok(cudaMemset(h->d_status, 0, 4));
     rc |= cuda_ok(cudaMemset(h->d_obs, 0, n * (size_t)(A * h->D) * 4 + 0));
     if (rc != LOB_OK) {
@@ -386,18 +408,29 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     if (h->persistent) {
         if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
     }
+    const bool fork = h->n_active_classes > 1;
+    if (fork && cudaEventRecord(h->ev_fork, s) != cudaSuccess) return LOB_ECUDA;
     for (int k = 0; k < NCLASS; k++) {
         const int cnt = h->class_count[k];
         if (cnt == 0) continue;
-        const bool uniform = cnt == c.n_envs && h->uniform_cap;
+        cudaStream_t ks = s;
+        if (fork) {
+            ks = h->cls_stream[k];
+            if (cudaStreamWaitEvent(ks, h->ev_fork, 0) != cudaSuccess) return LOB_ECUDA;
+        }
+        const bool uniform = cnt == c.n_envs && h->uniform_cap && !h->custom_order;
         p.env_list = uniform ? nullptr : h->d_env_list + h->class_begin[k];
         p.uni_cap = uniform ? c.cap_per_side : 0;
         p.uni_block = uniform ? h->uni_block : 0;
         p.n_list = cnt;
         p.queue = h->persistent ? h->d_queue + k : nullptr;
         h->launches++;
-        if (launch_k(CLASS_K[k], cnt, wpb, h->persistent != 0, h->n_sm, s, p) != cudaSuccess) return LOB_ECUDA;
+        if (launch_k(CLASS_K[k], cnt, wpb, h->persistent != 0, h->n_sm, ks, p) != cudaSuccess) return LOB_ECUDA;
+        if (fork && cudaEventRecord(h->cls_done[k], ks) != cudaSuccess) return LOB_ECUDA;
     }
+    if (fork)
+        for (int k = 0; k < NCLASS; k++)
+            if (h->class_count[k] && cudaStreamWaitEvent(s, h->cls_done[k], 0) != cudaSuccess) return LOB_ECUDA;
     return LOB_OK;
 }
 
@@ -594,6 +627,21 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
 }
 
 int64_t lob_kernel_launches(const lob_handle *h) { return h ? h->launches : 0; }
+
+int lob_set_env_costs(lob_handle *h, const float *h_cost) {
+    if (!h) return LOB_EINVAL;
+    std::vector<int> list = h->env_list_h;
+    if (h_cost) {
+        for (int k = 0; k < NCLASS; k++) {
+            auto b = list.begin() + h->class_begin[k];
+            std::stable_sort(b, b + h->class_count[k], [&](int x, int y) { return h_cost[x] > h_cost[y]; });
+        }
+    }
+    if (cudaMemcpy(h->d_env_list, list.data(), list.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return LOB_ECUDA;
+    h->custom_order = h_cost != nullptr;
+    return LOB_OK;
+}
 
 }  // extern "C"
 

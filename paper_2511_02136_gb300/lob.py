@@ -42,7 +42,7 @@ EXPORTS = [
     "lob_get_counters", "lob_get_agents", "lob_get_env_misc", "lob_get_actions", "lob_set_trace",
     "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
-    "lob_policy_sync", "lob_rollout_policy",
+    "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 POLICY_HIDDEN = 128
@@ -133,6 +133,7 @@ def _load():
         "lob_policy_forward": (ctypes.c_int, [P, P, I32, I32, P, P, P, P]),
         "lob_policy_sync": (ctypes.c_int, [P, P]),
         "lob_rollout_policy": (ctypes.c_int, [P, P, I32, I32, P, P, P, P, P]),
+        "lob_set_env_costs": (ctypes.c_int, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +248,11 @@ def lob_sync(h, stream=None):
 
 def lob_set_launch(h, warps_per_block, persistent):
     return _check(_load().lob_set_launch(h, warps_per_block, persistent), "lob_set_launch")
+
+
+def lob_set_env_costs(h, costs=None):
+    c = None if costs is None else np.ascontiguousarray(costs, dtype=np.float32)
+    return _check(_load().lob_set_env_costs(h, None if c is None else c.ctypes.data), "lob_set_env_costs")
 
 
 def lob_kernel_launches(h) -> int:
