@@ -14,6 +14,7 @@
 
 #include "lob.h"
 #include "lob_device.cuh"
+#include "lob_steps.h"
 #include "policy_internal.h"
 
 using namespace lobk;
@@ -54,10 +55,16 @@ int max_wpb(int K) {
     return m < 8 ? m : 8;
 }
 
-template <int K>
-cudaError_t optin_k() {
-    return cudaFuncSetAttribute(k_env_steps<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(max_wpb(K) * warp_smem_bytes(K)));
+cudaError_t optin_k(int K) {
+    const size_t smem = (size_t)max_wpb(K) * warp_smem_bytes(K);
+    switch (K) {
+        case 1: return optin_steps_1(smem);
+        case 2: return optin_steps_2(smem);
+        case 4: return optin_steps_4(smem);
+        case 8: return optin_steps_8(smem);
+        case 16: return optin_steps_16(smem);
+        default: return optin_steps_32(smem);
+    }
 }
 
 // Opt every step-kernel class into the shared memory of its widest launch
@@ -70,29 +77,28 @@ cudaError_t ensure_optin() {
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (done[dev]) return cudaSuccess;
-    if ((e = optin_k<1>()) != cudaSuccess || (e = optin_k<2>()) != cudaSuccess || (e = optin_k<4>()) != cudaSuccess ||
-        (e = optin_k<8>()) != cudaSuccess || (e = optin_k<16>()) != cudaSuccess || (e = optin_k<32>()) != cudaSuccess)
-        return e;
+    for (int k = 0; k < NCLASS; k++)
+        if ((e = optin_k(CLASS_K[k])) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
 
 // Launch the step kernel of class K (shared memory opted in by ensure_optin);
 // the warps per block are capped by what one block's shared memory holds.
-cudaError_t launch_k(int K, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s, const KParams &p) {
+cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s,
+                     const KParams &p) {
     wpb = wpb < max_wpb(K) ? wpb : max_wpb(K);
     int blocks = (n_list + wpb - 1) / wpb;
     if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
     const size_t smem = (size_t)wpb * warp_smem_bytes(K);
     switch (K) {
-        case 1: k_env_steps<1><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 2: k_env_steps<2><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 4: k_env_steps<4><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 8: k_env_steps<8><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        case 16: k_env_steps<16><<<blocks, 32 * wpb, smem, s>>>(p); break;
-        default: k_env_steps<32><<<blocks, 32 * wpb, smem, s>>>(p); break;
+        case 1: return launch_steps_1(trace, blocks, 32 * wpb, smem, s, p);
+        case 2: return launch_steps_2(trace, blocks, 32 * wpb, smem, s, p);
+        case 4: return launch_steps_4(trace, blocks, 32 * wpb, smem, s, p);
+        case 8: return launch_steps_8(trace, blocks, 32 * wpb, smem, s, p);
+        case 16: return launch_steps_16(trace, blocks, 32 * wpb, smem, s, p);
+        default: return launch_steps_32(trace, blocks, 32 * wpb, smem, s, p);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -425,7 +431,9 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
         p.n_list = cnt;
         p.queue = h->persistent ? h->d_queue + k : nullptr;
         h->launches++;
-        if (launch_k(CLASS_K[k], cnt, wpb, h->persistent != 0, h->n_sm, ks, p) != cudaSuccess) return LOB_ECUDA;
+        if (launch_k(CLASS_K[k], p.fills != nullptr || p.snaps != nullptr, cnt, wpb, h->persistent != 0, h->n_sm, ks, p) !=
+            cudaSuccess)
+            return LOB_ECUDA;
         if (fork && cudaEventRecord(h->cls_done[k], ks) != cudaSuccess) return LOB_ECUDA;
     }
     if (fork)
@@ -752,7 +760,7 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
     const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;
-    if (launch_k(K, n, wpb, true, g_noalloc_n_sm[dev], s, p) != cudaSuccess) return LOB_ECUDA;
+    if (launch_k(K, false, n, wpb, true, g_noalloc_n_sm[dev], s, p) != cudaSuccess) return LOB_ECUDA;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 

@@ -293,6 +293,40 @@ __device__ __forceinline__ void ix_remove(Side<K> &S, int q, int lane) {
     }
 }
 
+// The index words after removing position q, without modifying the side.
+template <int K>
+__device__ __forceinline__ void ix_removed(const Side<K> &S, int q, int lane, unsigned (&out)[Side<K>::NW]) {
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB;
+    constexpr unsigned ALLB = Side<K>::ALLB, EMASK = Side<K>::EMASK;
+    const unsigned nxt = __shfl_down_sync(FULL, S.ix[0] & EMASK, 1);
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const unsigned in = w + 1 < NW ? (S.ix[w + 1] & EMASK) : nxt;
+        const unsigned shifted = ((S.ix[w] >> IXB) | (in << (IXB * (BPW - 1)))) & ALLB;
+        const unsigned keep = ix_below<K>(q, lane, w);
+        out[w] = (S.ix[w] & keep) | (shifted & ~keep);
+    }
+}
+
+// The index words after inserting slot f at position pos.
+template <int K>
+__device__ __forceinline__ void ix_inserted(const Side<K> &S, int pos, int f, int lane, unsigned (&out)[Side<K>::NW]) {
+    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB, EPW = Side<K>::EPW;
+    constexpr unsigned ALLB = Side<K>::ALLB, EMASK = Side<K>::EMASK;
+    const unsigned top = (S.ix[NW - 1] >> (IXB * (BPW - 1))) & EMASK;
+    const unsigned carry = __shfl_up_sync(FULL, top, 1);
+    const unsigned fb = (unsigned)f * Side<K>::REP;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const unsigned in = w == 0 ? carry : (S.ix[w - 1] >> (IXB * (BPW - 1)));
+        const unsigned shifted = ((S.ix[w] << IXB) | in) & ALLB;
+        const int d = pos - (lane * K + EPW * w);
+        const unsigned keep = ix_below<K>(pos, lane, w);
+        const unsigned fm = (d >= 0 && d < BPW) ? (EMASK << (IXB * d)) : 0u;
+        out[w] = (S.ix[w] & keep) | (fb & fm) | (shifted & ~(keep | fm));
+    }
+}
+
 // Position of slot s among the n live positions.
 template <int K>
 __device__ __forceinline__ int ix_find(const Side<K> &S, int s, int lane) {
@@ -353,7 +387,7 @@ struct Ctx {
     }
 };
 
-__device__ __noinline__ void log_fill(lob_fill *log, int idx, long long maker, long long taker, int px, int f,
+static __device__ __noinline__ void log_fill(lob_fill *log, int idx, long long maker, long long taker, int px, int f,
                                       int msg_idx, int side) {
     lob_fill r;
     r.maker_id = maker; r.taker_id = taker; r.px = px; r.qty = f; r.msg_idx = msg_idx; r.taker_side = side;
@@ -362,6 +396,7 @@ __device__ __noinline__ void log_fill(lob_fill *log, int idx, long long maker, l
 
 // A trade at the resting order's price; cash and inventory move between the
 // owners of the two orders (0, 1 = agents, 2 = background).
+template <bool TRACE>
 __device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_id, long long taker_id,
                                         int taker_side, int lane) {
     const int om = c.owner(maker_id), ot = c.owner(taker_id);
@@ -379,16 +414,18 @@ __device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_i
     c.last_px = px;
     c.c_fills += 1;
     c.c_fill_vol += f;
-    if (c.fill_log != nullptr) {
-        if (lane == 0 && c.fill_n < c.fill_cap)
-            log_fill(c.fill_log, c.fill_n, maker_id, taker_id, px, f, c.msg_idx, taker_side);
-        c.fill_n++;
+    if constexpr (TRACE) {
+        if (c.fill_log != nullptr) {
+            if (lane == 0 && c.fill_n < c.fill_cap)
+                log_fill(c.fill_log, c.fill_n, maker_id, taker_id, px, f, c.msg_idx, taker_side);
+            c.fill_n++;
+        }
     }
 }
 
 // Take liquidity from resting side O (RBID: O holds bids), price first then
 // time, up to the limit (if any).  Returns the unfilled quantity.
-template <int K, bool RBID>
+template <int K, bool RBID, bool TRACE>
 __device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_limit, int limit, int q,
                                          long long taker_id, int taker_side, Ctx &c, int lane) {
     while (q > 0 && O.n > 0 && (!has_limit || at_least<RBID>(O.fpx, limit))) {
@@ -396,23 +433,28 @@ __device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_li
         const int s1 = slot_at<K>(O, 1);
         const int npx = P.px[s1], nqt = P.qty[s1];
         const long long nid = P.id[s1];
+        unsigned popped[Side<K>::NW];
+        ix_removed<K>(O, 0, lane, popped);
         const int f = min(q, O.fqty);
-        do_fill(c, O.fpx, f, O.fid, taker_id, taker_side, lane);
+        do_fill<TRACE>(c, O.fpx, f, O.fid, taker_id, taker_side, lane);
         q -= f;
-        if (f == O.fqty) {
-            slot_clear<K>(O, O.fslot, lane);
-            ix_remove<K>(O, 0, lane);
-            O.n--;
-            O.fpx = npx; O.fqty = nqt; O.fid = nid; O.fslot = s1;
-        } else {
-            O.fqty -= f;
-            P.qty[O.fslot] = O.fqty;   // every lane stores the same value
-        }
+        const bool gone = f == O.fqty;
+        const int left = O.fqty - f;
+        P.qty[O.fslot] = left;          // every lane stores the same value
+        if (gone && lane == slot_lane<K>(O.fslot)) O.occ &= ~(1u << slot_r<K>(O.fslot));
+#pragma unroll
+        for (int w = 0; w < Side<K>::NW; w++) O.ix[w] = gone ? popped[w] : O.ix[w];
+        O.n -= gone ? 1 : 0;
+        O.fpx = gone ? npx : O.fpx;
+        O.fqty = gone ? nqt : left;
+        O.fid = gone ? nid : O.fid;
+        O.fslot = gone ? s1 : O.fslot;
     }
     return q;
 }
 
-// Rest an order on its own side, applying the capacity rule.
+// Rest an order on its own side, applying the capacity rule.  Branch-free:
+// every outcome (drop, evict and insert, insert) is computed and selected.
 template <int K, bool BID>
 __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, int p, int q, long long oid,
                                           Ctx &c, int lane) {
@@ -422,34 +464,45 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
     const unsigned fr = ~S.occ & Side<K>::KMASK;
     const unsigned flanes = __ballot_sync(FULL, fr != 0);
     const int free_slot = __shfl_sync(FULL, slot_of<K>(lane, __ffs(fr) - 1), __ffs(flanes) - 1);
-    int cnt = 0;
+    int pos;
+    if constexpr (Side<K>::REG) {
+        pos = 0;
 #pragma unroll
-    for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(spx<K>(S, P, r, lane), p));
-    const int pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
+        for (int r = 0; r < K; r++)
+            pos += __popc(__ballot_sync(FULL, ((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p)));
+    } else {
+        int cnt = 0;
+#pragma unroll
+        for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(spx<K>(S, P, r, lane), p));
+        pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
+    }
     const bool full = S.n >= cap;
-    if (full && pos >= S.n) {  // not strictly better than the worst resting price
-        c.c_drop_vol += q;
-        c.c_drop_cnt += 1;
-        return;
-    }
+    const bool ins = !(full && pos >= S.n);   // a full side keeps only strictly better prices
+    const bool ev = full && ins;
+    c.c_drop_vol += ins ? 0 : q;
+    c.c_drop_cnt += ins ? 0 : 1;
+    c.c_evict_vol += ev ? vic_q : 0;
+    c.c_evict_cnt += ev ? 1 : 0;
     const int f = full ? vic : free_slot;
-    if (full) {
-        c.c_evict_vol += vic_q;
-        c.c_evict_cnt += 1;
-        S.n--;
-    }
     const int fl = slot_lane<K>(f), fr_ = slot_r<K>(f);
-    if (lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
+    if (ins && lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
     if constexpr (Side<K>::REG) {
 #pragma unroll
         for (int r = 0; r < K; r++)
-            if (lane == fl && r == fr_) { S.px[r] = p; S.id[r] = oid; }
+            if (ins && lane == fl && r == fr_) { S.px[r] = p; S.id[r] = oid; }
     }
-    P.px[f] = p; P.qty[f] = q; P.id[f] = oid; P.ts[f] = c.ts_next;   // same value from every lane
-    c.ts_next++;
-    ix_insert<K>(S, pos, f, lane);
-    S.n++;
-    if (pos == 0) { S.fpx = p; S.fqty = q; S.fid = oid; S.fslot = f; }
+    if (ins) { P.px[f] = p; P.qty[f] = q; P.id[f] = oid; P.ts[f] = c.ts_next; }   // same value from every lane
+    c.ts_next += ins ? 1 : 0;
+    unsigned nix[Side<K>::NW];
+    ix_inserted<K>(S, pos, f, lane, nix);
+#pragma unroll
+    for (int w = 0; w < Side<K>::NW; w++) S.ix[w] = ins ? nix[w] : S.ix[w];
+    S.n += (ins && !full) ? 1 : 0;
+    const bool front = ins && pos == 0;
+    S.fpx = front ? p : S.fpx;
+    S.fqty = front ? q : S.fqty;
+    S.fid = front ? oid : S.fid;
+    S.fslot = front ? f : S.fslot;
 }
 
 // Remove slot s (any position) and fix the front if it was there.
@@ -789,7 +842,7 @@ struct MsgPipe {
 };
 
 // Run n_steps env steps of env e with the book resident on chip.
-template <int K>
+template <int K, bool TRACE>
 __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe, int lane) {
     EnvState *st = p.st + e;
     const bool uni = p.uni_cap > 0;
@@ -821,7 +874,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     c.c_cancel_miss = cnt[8]; c.c_drop_vol = cnt[9]; c.c_drop_cnt = cnt[10]; c.c_evict_vol = cnt[11];
     c.c_evict_cnt = cnt[12]; c.c_bad = cnt[13]; c.bg_cash = cnt[14]; c.bg_inv = cnt[15];
     c.status = 0;
-    c.fill_log = p.fills ? p.fills + (long long)e * p.fill_cap : nullptr;
+    c.fill_log = (TRACE && p.fills) ? p.fills + (long long)e * p.fill_cap : nullptr;
     c.fill_cap = p.fill_cap;
     // live counts arrive with the state: mark occupancy now
     side_set_count<K>(bid, nb0, lane);
@@ -830,7 +883,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     front_refresh<K>(bid, sm.pool[0]);
     front_refresh<K>(ask, sm.pool[1]);
 
-    const bool snap_env = p.snaps != nullptr && e == 0;
+    const bool snap_env = TRACE && p.snaps != nullptr && e == 0;
     long long snap_n = 0;
     const long long snap_bytes = 8 + 48 * (long long)cap;
     bool timed_out = false;
@@ -911,7 +964,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             long long kept[3];
 #pragma unroll
             for (int i = 0; i < 3; i++) kept[i] = (long long)__reduce_add_sync(FULL, kept_u[i]);
-            if (snap_env) {
+            if (TRACE && snap_env) {
                 // trace mode: cancels one by one in the paper's order, a snapshot after each
 #pragma unroll
                 for (int a = 0; a < 2; a++) {
@@ -977,10 +1030,6 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         // is the agents' records, chunk j >= 0 the j-th staged tile; inside a
         // chunk the next record is read one message ahead (a read past the
         // chunk end stays inside this warp's shared memory and is unused).
-        constexpr int KEY_ADD_B = LOB_ADD | (1 << 16), KEY_ADD_S = (int)(0xFFFF0000u | LOB_ADD);
-        constexpr int KEY_MKT_B = LOB_MARKET | (1 << 16), KEY_MKT_S = (int)(0xFFFF0000u | LOB_MARKET);
-        constexpr int KEY_PAR_B = LOB_PARTIAL | (1 << 16), KEY_PAR_S = (int)(0xFFFF0000u | LOB_PARTIAL);
-        constexpr int KEY_DEL_B = LOB_DELETE | (1 << 16), KEY_DEL_S = (int)(0xFFFF0000u | LOB_DELETE);
         for (int ch = ns > 0 ? -1 : 0; ch < ntiles && !timed_out; ch++) {
             const DevMsg *base;
             int cnt_ch;
@@ -1019,37 +1068,46 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 int qty = w1.y;
                 c.c_msgs += 1;
                 c.c_agent += agent;
-                if (key == KEY_ADD_B || key == KEY_MKT_B) {
-                    if (qty <= 0) {
-                        c.c_bad += 1; c.status |= ST_BADMSG;
-                    } else {
-                        const bool lim = key == KEY_ADD_B;
-                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
-                        if (ask.n > 0 && (!lim || px >= ask.fpx))
-                            qty = side_take<K, false>(ask, sm.pool[1], lim, px, qty, oid, LOB_BUY, c, lane);
-                        if (!lim) c.c_mkt_disc += qty;
-                        else if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
-                    }
-                } else if (key == KEY_ADD_S || key == KEY_MKT_S) {
-                    if (qty <= 0) {
-                        c.c_bad += 1; c.status |= ST_BADMSG;
-                    } else {
-                        const bool lim = key == KEY_ADD_S;
-                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
-                        if (bid.n > 0 && (!lim || px <= bid.fpx))
-                            qty = side_take<K, true>(bid, sm.pool[0], lim, px, qty, oid, LOB_SELL, c, lane);
-                        if (!lim) c.c_mkt_disc += qty;
-                        else if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
-                    }
-                } else if (key == KEY_DEL_B || (key == KEY_PAR_B && qty > 0)) {
-                    side_cancel<K>(bid, sm.pool[0], key & 0xffff, px, qty, oid, c, lane);
-                } else if (key == KEY_DEL_S || (key == KEY_PAR_S && qty > 0)) {
-                    side_cancel<K>(ask, sm.pool[1], key & 0xffff, px, qty, oid, c, lane);
-                } else {
-                    c.c_bad += 1;
-                    c.status |= ST_BADMSG;
+                // one dense dispatch index: (type - 1) * 2 + (side is sell), 8 = malformed
+                const int type = key & 0xffff, side = key >> 16;
+                const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
+                                   (qty > 0 || type == LOB_DELETE);
+                const int didx = valid ? ((type - 1) << 1) | (side < 0 ? 1 : 0) : 8;
+                switch (didx) {
+                    case 0:   // add, buy
+                        c.c_add_vol += qty;
+                        if (ask.n > 0 && px >= ask.fpx)
+                            qty = side_take<K, false, TRACE>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
+                        if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                        break;
+                    case 1:   // add, sell
+                        c.c_add_vol += qty;
+                        if (bid.n > 0 && px <= bid.fpx)
+                            qty = side_take<K, true, TRACE>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
+                        if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                        break;
+                    case 2:   // partial cancel, buy
+                    case 4:   // delete, buy
+                        side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
+                        break;
+                    case 3:   // partial cancel, sell
+                    case 5:   // delete, sell
+                        side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+                        break;
+                    case 6:   // market, buy
+                        c.c_mkt_vol += qty;
+                        c.c_mkt_disc += side_take<K, false, TRACE>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
+                        break;
+                    case 7:   // market, sell
+                        c.c_mkt_vol += qty;
+                        c.c_mkt_disc += side_take<K, true, TRACE>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
+                        break;
+                    default:
+                        c.c_bad += 1;
+                        c.status |= ST_BADMSG;
+                        break;
                 }
-                if (snap_env) {
+                if (TRACE && snap_env) {
                     __syncwarp();
                     if (snap_n < p.snap_cap) write_snapshot<K>(bid, ask, sm, cap, p.snaps + snap_n * snap_bytes, lane);
                     snap_n++;
@@ -1121,8 +1179,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             }
         }
         if (lane == 0 && p.done) p.done[obs_base] = (unsigned char)(t + 1 == p.T);
-        if (lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
-        if (lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
+        if (TRACE && lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
+        if (TRACE && lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
         if (step + 1 == p.n_steps) {
             side_store<K, true>(bid, sm.pool[0], blk, lane);
@@ -1149,7 +1207,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     }
 }
 
-template <int K>
+template <int K, bool TRACE>
 __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1164,14 +1222,14 @@ __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     MsgPipe pipe{0u};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+        if (w < p.n_list) run_env<K, TRACE>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+            run_env<K, TRACE>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
         }
     }
 }

@@ -1,0 +1,3 @@
+// steps_k2.cu -- step kernels of capacity class K = 2 (64 slots per side).
+#define LOB_K 2
+#include "steps_inst.cuh"

@@ -20,9 +20,12 @@ _ROOT = os.path.dirname(_PKG)
 _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_PKG, "liblob.so")
-_SOURCES = [os.path.join(_CSRC, "lob_api.cu"), os.path.join(_CSRC, "policy_api.cu")]
-_DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.cuh", "policy_internal.h")] + \
+_SOURCES = [os.path.join(_CSRC, n) for n in
+            ["lob_api.cu", "policy_api.cu"] + [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
+_DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.cuh", "policy_internal.h",
+                                                      "lob_steps.h", "steps_inst.cuh")] + \
     [os.path.join(_INC, "lob.h")]
+_OBJDIR = os.path.join(_PKG, "_build")
 _lock = threading.Lock()
 _lib = None
 
@@ -80,19 +83,34 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def nvcc_cmd(out_path, extra=()):
-    return (["nvcc", "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-             "-I", _INC, "-o", out_path] + list(extra) + _SOURCES)
+def nvcc_cmd(out_path, extra=(), src=None):
+    """Compile command of one translation unit (all of them for the shared object when src is None)."""
+    base = ["nvcc", "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-Xcompiler", "-fPIC", "-I", _INC]
+    if src is None:
+        return base + ["-shared", "-o", out_path] + list(extra) + _SOURCES
+    return base + ["-c", "-o", out_path] + list(extra) + [src]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile liblob.so in-tree for sm_103a (nvcc cross-compiles without a GPU)."""
+    """Compile liblob.so in-tree for sm_103a: one nvcc per translation unit in
+    parallel, then one link (nvcc cross-compiles without a GPU)."""
     with _lock:
         if not force and not _stale(LIB_PATH, _DEPS):
             return LIB_PATH
+        os.makedirs(_OBJDIR, exist_ok=True)
+        extra = ["-Xptxas", "-v"] if verbose else []
+        procs, objs = [], []
+        for src in _SOURCES:
+            obj = os.path.join(_OBJDIR, os.path.basename(src) + f".{os.getpid()}.o")
+            objs.append(obj)
+            procs.append(subprocess.Popen(nvcc_cmd(obj, extra, src)))
+        failed = [p.wait() for p in procs]
+        if any(failed):
+            raise RuntimeError("nvcc failed while building liblob.so")
         tmp = LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = nvcc_cmd(tmp, ["-Xptxas", "-v"] if verbose else [])
-        subprocess.check_call(cmd)
+        subprocess.check_call(["nvcc", *ARCH_FLAGS, "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs)
+        for o in objs:
+            os.remove(o)
         os.replace(tmp, LIB_PATH)
         return LIB_PATH
 

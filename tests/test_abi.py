@@ -39,6 +39,6 @@ def test_host_only_entry_points():
 
 
 def test_built_for_sm103a_only():
-    cmd = lob.nvcc_cmd("x.so")
-    assert "arch=compute_103a,code=sm_103a" in cmd
-    assert sum(1 for c in cmd if c == "-gencode") == 1
+    for cmd in [lob.nvcc_cmd("x.so")] + [lob.nvcc_cmd("x.o", src=s) for s in lob._SOURCES]:
+        assert "arch=compute_103a,code=sm_103a" in cmd
+        assert sum(1 for c in cmd if c == "-gencode") == 1
