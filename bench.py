@@ -235,7 +235,7 @@ def run_gpu(args):
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "timing": "CUDA events per step on the launching stream, summed"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                          "kernel": "k_env_steps<4>", "alg_bytes_per_launch": alg_bytes,
                          "mean_live_slots_per_env": live},
