@@ -43,6 +43,26 @@ def _dist():
     return rank, world
 
 
+def aggregate_over_ranks(total_s, msgs, device="cpu"):
+    """Whole-job figures across ranks: the slowest rank's time and every rank's messages.
+    Each rank runs its own replica (independent envs), so nothing but these two numbers
+    crosses ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_s, msgs
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(msgs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    return t.item(), m.item()
+
+
+def replica_seed(base, rank):
+    """Each rank replays its own synthetic episode (weak scaling)."""
+    return base + rank
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -135,7 +155,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     lob.build()
     gen = min(T, args.gen_steps)
-    seeds, st = make_inputs(1 + rank, gen)
+    seeds, st = make_inputs(replica_seed(1, rank), gen)
     dev = torch.device("cuda", local)
     msgs_d = torch.from_numpy(st.msgs.view(np.uint8)).to(dev)
     off_d = torch.from_numpy(st.offsets).to(dev)
@@ -196,14 +216,7 @@ def run_gpu(args):
     if rc != 0:
         raise RuntimeError(f"device status {lob.lob_strerror(rc)}")
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = tt.item()
-        mt = torch.tensor([float(msgs_total)], device=dev)
-        dist.all_reduce(mt, op=dist.ReduceOp.SUM)
-        msgs_total = mt.item()
+    total_s, msgs_total = aggregate_over_ranks(total_s, msgs_total, dev)
     env_steps = K * N_ENVS * world
     value = msgs_total / total_s
     # algorithmic bytes per launch (one launch per step): messages, book
