@@ -237,6 +237,18 @@ int lob_sync(lob_handle *h, void *stream);
 /* Launch-shape control used by the autotuner: warps per block for the step
  * kernels (1..32) and whether they take envs from a work queue. */
 int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
+/* ---- Checkpoint / resume of every env (books, per-env scalars, counters,
+ * seeds, the last step's outputs, the step t and the window cursor).  The
+ * bound message window is not part of it: bind the same window before
+ * continuing.  dst / src may be host or device memory (copied with
+ * cudaMemcpyDefault semantics on `stream`; host memory should be pinned).
+ * lob_load requires a handle created with the same configuration and
+ * capacities; it returns LOB_EINVAL for a checkpoint of another shape.  Both
+ * calls synchronise `stream`. */
+int64_t lob_checkpoint_bytes(const lob_handle *h);
+int lob_save(lob_handle *h, void *dst, void *stream);
+int lob_load(lob_handle *h, const void *src, void *stream);
+
 /* Work hint for the persistent (work-queue) launches: h_cost [n_envs] host
  * floats, larger = more work; each capacity class then hands out its envs
  * longest first.  NULL restores env order. */

@@ -797,3 +797,87 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
     }
     return LOB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: a 64-byte header, then books, EnvState, counters,
+// seeds, obs, rewards, done -- each region copied as one block.
+namespace {
+struct CkptHeader {
+    uint64_t magic;
+    int64_t n_envs, book_bytes, obs_bytes;
+    int32_t t, cursor, n_agents, D;
+    int32_t cap_sig, pad[3];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header");
+constexpr uint64_t CKPT_MAGIC = 0x4C4F42434B505431ull;
+
+int cap_signature(const lob_handle *h) {
+    unsigned x = 2166136261u;
+    for (int c : h->caps) x = (x ^ (unsigned)c) * 16777619u;
+    return (int)x;
+}
+
+struct Region { void *dev; size_t bytes; };
+std::vector<Region> ckpt_regions(lob_handle *h) {
+    const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
+    return {{h->d_books, (size_t)h->book_bytes}, {h->d_state, n * sizeof(EnvState)},
+            {h->d_counters, n * 8 * LOB_NCOUNTERS}, {h->d_seeds, n * 8}, {h->d_obs, n * A * D * 4},
+            {h->d_rew, n * A * 8}, {h->d_done, n}};
+}
+}  // namespace
+
+extern "C" int64_t lob_checkpoint_bytes(const lob_handle *h) {
+    if (!h) return 0;
+    size_t b = sizeof(CkptHeader);
+    for (const Region &r : ckpt_regions(const_cast<lob_handle *>(h))) b += r.bytes;
+    return (int64_t)b;
+}
+
+extern "C" int lob_save(lob_handle *h, void *dst, void *stream) {
+    if (!h || !dst) return LOB_EINVAL;
+    if (!h->reset_done) return LOB_ESTATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = CKPT_MAGIC;
+    hd.n_envs = h->cfg.n_envs;
+    hd.book_bytes = h->book_bytes;
+    hd.obs_bytes = (int64_t)h->cfg.n_envs * h->cfg.n_agents * h->D * 4;
+    hd.t = h->t;
+    hd.cursor = h->cursor;
+    hd.n_agents = h->cfg.n_agents;
+    hd.D = h->D;
+    hd.cap_sig = cap_signature(h);
+    char *out = static_cast<char *>(dst);
+    if (cudaMemcpyAsync(out, &hd, sizeof(hd), cudaMemcpyDefault, s) != cudaSuccess) return LOB_ECUDA;
+    size_t off = sizeof(hd);
+    for (const Region &r : ckpt_regions(h)) {
+        if (cudaMemcpyAsync(out + off, r.dev, r.bytes, cudaMemcpyDefault, s) != cudaSuccess) return LOB_ECUDA;
+        off += r.bytes;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? LOB_OK : LOB_ECUDA;   // the header lives on this stack
+}
+
+extern "C" int lob_load(lob_handle *h, const void *src, void *stream) {
+    if (!h || !src) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CkptHeader hd;
+    if (cudaMemcpyAsync(&hd, src, sizeof(hd), cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LOB_ECUDA;
+    if (hd.magic != CKPT_MAGIC || hd.n_envs != h->cfg.n_envs || hd.book_bytes != h->book_bytes ||
+        hd.n_agents != h->cfg.n_agents || hd.D != h->D || hd.cap_sig != cap_signature(h) || hd.t < 0 ||
+        hd.t > h->cfg.episode_len)
+        return LOB_EINVAL;
+    const char *in = static_cast<const char *>(src);
+    size_t off = sizeof(hd);
+    for (const Region &r : ckpt_regions(h)) {
+        if (cudaMemcpyAsync(r.dev, in + off, r.bytes, cudaMemcpyDefault, s) != cudaSuccess) return LOB_ECUDA;
+        off += r.bytes;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LOB_ECUDA;
+    h->t = hd.t;
+    h->cursor = hd.cursor;
+    h->reset_done = true;
+    return LOB_OK;
+}

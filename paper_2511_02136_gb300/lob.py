@@ -46,6 +46,7 @@ EXPORTS = [
     "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
+    "lob_checkpoint_bytes", "lob_save", "lob_load",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 POLICY_HIDDEN = 128
@@ -152,6 +153,9 @@ def _load():
         "lob_policy_sync": (ctypes.c_int, [P, P]),
         "lob_rollout_policy": (ctypes.c_int, [P, P, I32, I32, P, P, P, P, P]),
         "lob_set_env_costs": (ctypes.c_int, [P, P]),
+        "lob_checkpoint_bytes": (I64, [P]),
+        "lob_save": (ctypes.c_int, [P, P, P]),
+        "lob_load": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -271,6 +275,25 @@ def lob_set_launch(h, warps_per_block, persistent):
 def lob_set_env_costs(h, costs=None):
     c = None if costs is None else np.ascontiguousarray(costs, dtype=np.float32)
     return _check(_load().lob_set_env_costs(h, None if c is None else c.ctypes.data), "lob_set_env_costs")
+
+
+def lob_checkpoint_bytes(h) -> int:
+    return _load().lob_checkpoint_bytes(h)
+
+
+def _anyp(buf):
+    """Pointer of a torch tensor (host or device) or a numpy array."""
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr()
+    return buf.ctypes.data
+
+
+def lob_save(h, dst, stream=None):
+    return _check(_load().lob_save(h, _anyp(dst), _stream(stream)), "lob_save")
+
+
+def lob_load(h, src, stream=None):
+    return _check(_load().lob_load(h, _anyp(src), _stream(stream)), "lob_load")
 
 
 def lob_kernel_launches(h) -> int:

@@ -321,3 +321,57 @@ def test_stress_65536_envs_cap1000():
     n = 65536
     _sampled_pair_check(n, np.arange(0, n, 256), mbogen.STRESS_MODEL, 4, cap=1000, top_levels=20,
                         exec_target=2000)
+
+
+def test_checkpoint_resume_bit_identical():
+    """Save after 5 steps, run 6 more; restore (same handle, and a fresh handle
+    from a host copy) and run the 6 steps again: identical outputs and state."""
+    import torch
+    from harness import to_dev
+    n, T = 61, 11
+    caps = mbogen.env_caps(8, n, choices=(50, 100, 200))
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=80), mbogen.env_seeds(81, n), T)
+    md, od, sd = to_dev(st.msgs), to_dev(st.offsets), to_dev(st.seeds)
+
+    def make():
+        env = lob.LobEnv(n, cap=200, caps=caps, episode_len=T, exec_target=60, action_mode=lob.LOB_ACT_RANDOM)
+        env.load_messages(md, od)
+        return env
+
+    def run(env, k):
+        outs = []
+        for _ in range(k):
+            env.step()
+            o, r, d = env.observe()
+            outs.append((o.clone(), r.clone(), d.clone()))
+        return outs
+
+    env = make()
+    env.reset(sd)
+    run(env, 5)
+    ck = torch.zeros(lob.lob_checkpoint_bytes(env.h), dtype=torch.uint8, device="cuda")
+    lob.lob_save(env.h, ck)
+    host = torch.zeros(ck.numel(), dtype=torch.uint8).pin_memory()
+    lob.lob_save(env.h, host)
+    first = run(env, 6)
+    final_books = env.books()
+    final_cnt = env.counters().cpu().numpy()
+    lob.lob_load(env.h, ck)
+    again = run(env, 6)
+    env2 = make()
+    lob.lob_load(env2.h, host)
+    third = run(env2, 6)
+    for a, b, c in zip(first, again, third):
+        for x, y, z in zip(a, b, c):
+            assert torch.equal(x, y) and torch.equal(x, z)
+    for got in (env.books(), env2.books()):
+        for b0, b1 in zip(final_books, got):
+            assert b0.tobytes() == b1.tobytes()
+    np.testing.assert_array_equal(final_cnt, env2.counters().cpu().numpy())
+    # a checkpoint of another shape is refused
+    other = lob.LobEnv(n + 1, cap=100, episode_len=T, action_mode=lob.LOB_ACT_RANDOM)
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_load(other.h, host)
+    assert ei.value.code == lob.LOB_EINVAL
+    for e in (env, env2, other):
+        e.close()
