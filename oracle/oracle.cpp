@@ -115,6 +115,8 @@ struct Side {
 
 struct Agent {
     int64_t inv = 0, cash = 0, pv_prev = 0, exec_done = 0;
+    // this step's fills, split by direction (for the Eq. 3 / Eq. 4 rewards)
+    int64_t buy_q = 0, buy_n = 0, sell_q = 0, sell_n = 0;
 };
 
 // ---- SplitMix64 (Steele, Lea & Flood 2014) and Lemire's bounded map ------
@@ -221,6 +223,8 @@ struct Engine {
         };
         credit(buyer, -notional, f);
         credit(seller, notional, -(int64_t)f);
+        if (buyer != A) { E.ag[buyer].buy_q += f; E.ag[buyer].buy_n = wadd(E.ag[buyer].buy_n, notional); }
+        if (seller != A) { E.ag[seller].sell_q += f; E.ag[seller].sell_n = wadd(E.ag[seller].sell_n, notional); }
         if (A > 0) {
             int task_owner = cfg.c.exec_dir == SELL ? seller : buyer;
             if (task_owner == 0) E.ag[0].exec_done += f;
@@ -337,6 +341,8 @@ struct Engine {
         E.fills.clear();
         E.msg_idx = 0;
         if (E.snaps) E.snaps->clear();
+        for (int a = 0; a < 2; a++) E.ag[a].buy_q = E.ag[a].buy_n = E.ag[a].sell_q = E.ag[a].sell_n = 0;
+        const int64_t mid2_start = ref_bid(E) + ref_ask(E);   // twice the mid when the step begins
         std::vector<NewOrder> want;
         std::vector<Msg> cancels;
         if (A == 2) {
@@ -452,6 +458,32 @@ struct Engine {
                 int64_t pv = wadd(wmul(g.inv, pref), g.cash);
                 E.rew[a] = wsub(pv, g.pv_prev);
                 g.pv_prev = pv;
+                if (a == 1 && c.reward_mode != 0) {
+                    // Sec. 5: trading PnL against the average mid over the step,
+                    // read as the mean of its start and end mids, so 4*Mbar is
+                    // an integer and the reward is exact in quarter-tick*qty.
+                    const int64_t mid2_end = bb + ba;
+                    const int64_t m4 = mid2_start + mid2_end;
+                    const int64_t psi_b4 = wsub(wmul(m4, g.buy_q), wmul(4, g.buy_n));      // 4 * Psi_b
+                    const int64_t psi_s4 = wsub(wmul(4, g.sell_n), wmul(m4, g.sell_q));    // 4 * Psi_s
+                    int64_t r4 = wadd(psi_b4, psi_s4);                                   // Eq. 4
+                    if (c.reward_mode == 2) {
+                        // Eq. 3: + Psi_INV - (1 - lambda) max(0, Psi_INV), Psi_INV = I_t (M_t - M_{t-1})
+                        const int64_t psi_inv4 = wmul(wmul(2, g.inv), mid2_end - mid2_start);
+                        // the damping is rounded up, so the reward is the floor of its exact value
+                        const int64_t damp =
+                            (wmul(100 - c.spooner_lambda_pct, std::max<int64_t>(0, psi_inv4)) + 99) / 100;
+                        r4 = wsub(wadd(r4, psi_inv4), damp);
+                    }
+                    E.rew[a] = r4;
+                }
+                if (a == 1 && c.inv_penalty != 0)   // quadratic inventory penalty
+                    E.rew[a] = wsub(E.rew[a], wmul(c.inv_penalty, wmul(g.inv, g.inv)));
+                if (a == 0 && c.exec_penalty_milli != 0 && t + 1 == c.episode_len) {
+                    // Table 2: penalty on the part of the task still unfilled at the end
+                    const int64_t unfilled = std::max<int64_t>(0, (int64_t)c.exec_target - g.exec_done);
+                    E.rew[a] = wsub(E.rew[a], (wmul(c.exec_penalty_milli, unfilled) + 999) / 1000);  // rounded up
+                }
             }
         }
         E.done = (uint8_t)(t + 1 == c.episode_len);

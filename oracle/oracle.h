@@ -38,6 +38,13 @@ typedef struct orc_config {
     int32_t trace;        /* bit0: keep the step's fill log; bit1: book snapshot of env 0 after every message */
     int32_t start_px;     /* reference price before the first trade */
     int32_t n_threads;
+    int32_t reward_mode;  /* 0: PV change (Eq. 1) for both agents; 1: BuySell (Eq. 4) and
+                             2: Spooner (Eq. 3) for the market maker, in quarter-tick*qty */
+    int32_t spooner_lambda_pct;  /* lambda of Eq. 3 in percent (0..100) */
+    int32_t inv_penalty;  /* quadratic inventory penalty of the market maker, per unit^2 */
+    int32_t exec_penalty_milli; /* end-of-episode penalty per unfilled unit of the execution
+                             task, in thousandths of a tick; every reward is the floor of
+                             its exact value */
 } orc_config;
 
 void   *orc_create(const orc_config *cfg, const int32_t *caps /* [n_envs] or NULL */);

@@ -7,6 +7,8 @@ level structure, no iterators and no special cases to share mistakes with.
 """
 from __future__ import annotations
 
+from fractions import Fraction
+
 BUY, SELL = 1, -1
 ADD, PARTIAL, DELETE, MARKET = 1, 2, 3, 4
 M64 = (1 << 64) - 1
@@ -45,10 +47,13 @@ def wrap(v):
 
 class BruteEnv:
     def __init__(self, cap, n_agents=0, top_levels=2, episode_len=10, mm_lot=1,
-                 exec_target=10, exec_dir=SELL, start_px=10_000, seed=0, action_mode=0):
+                 exec_target=10, exec_dir=SELL, start_px=10_000, seed=0, action_mode=0,
+                 reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0):
         self.cap, self.A, self.L, self.T = cap, n_agents, top_levels, episode_len
         self.mm_lot, self.exec_target, self.exec_dir = mm_lot, exec_target, exec_dir
         self.action_mode, self.seed = action_mode, seed
+        self.reward_mode, self.lam_pct = reward_mode, spooner_lambda_pct
+        self.inv_penalty, self.exec_penalty_milli = inv_penalty, exec_penalty_milli
         self.orders = {BUY: [], SELL: []}   # dicts: px, qty, id, ts
         self.ts_next = 0
         self.seq_next = 0
@@ -102,6 +107,7 @@ class BruteEnv:
         buyer, seller = (ot, om) if taker_side == BUY else (om, ot)
         self._credit(buyer, -maker["px"] * f, f)
         self._credit(seller, maker["px"] * f, -f)
+        self.step_fills.append((buyer, seller, maker["px"], f))
         if self.A and (seller if self.exec_dir == SELL else buyer) == 0:
             self.exec_done += f
         self.last_px = maker["px"]
@@ -175,7 +181,9 @@ class BruteEnv:
     # -- one env step ---------------------------------------------------------
     def step(self, msgs, actions=None):
         self.fills = []
+        self.step_fills = []   # (buyer, seller, price, qty) of this step
         self.msg_idx = 0
+        mid_before = (self.touch(BUY) + self.touch(SELL)) / 2
         if self.A == 2:
             if self.action_mode == 1:
                 self.acts = [bounded(keyed_draws(self.seed, self.t, TAG_POLICY, 2)[a], 12) for a in range(2)]
@@ -261,8 +269,29 @@ class BruteEnv:
                 pv = wrap(self.inv[a] * pref + self.cash[a])
                 self.rew[a] = wrap(pv - self.pv_prev[a])
                 self.pv_prev[a] = pv
+                if a == 1 and self.reward_mode:
+                    self.rew[a] = self._mm_reward(mid_before, (bb + ba) / 2)
+                if a == 1:
+                    self.rew[a] -= self.inv_penalty * self.inv[a] ** 2
+                if a == 0 and self.t + 1 == self.T:
+                    unfilled = max(0, self.exec_target - self.exec_done)
+                    self.rew[a] = self.rew[a] - self.exec_penalty_milli * unfilled / Fraction(1000)
+                    self.rew[a] = self.rew[a].numerator // self.rew[a].denominator
         self.done = int(self.t + 1 == self.T)
         self.t += 1
+
+    def _mm_reward(self, mid_before, mid_after):
+        """Eqs. 3-4 from the fill list, with exact fractions, returned in quarter ticks."""
+        Fr = Fraction
+        mbar = (Fr(mid_before) + Fr(mid_after)) / 2
+        psi_b = sum(((mbar - p) * q for b, s, p, q in self.step_fills if b == 1), Fr(0))
+        psi_s = sum(((p - mbar) * q for b, s, p, q in self.step_fills if s == 1), Fr(0))
+        r = psi_b + psi_s
+        if self.reward_mode == 2:
+            psi_inv = self.inv[1] * (Fr(mid_after) - Fr(mid_before))
+            r += psi_inv - Fr(100 - self.lam_pct, 100) * max(Fr(0), psi_inv)
+        r4 = 4 * r
+        return r4.numerator // r4.denominator   # floor: only the lambda damping can be fractional
 
     def book_arrays(self):
         out = []

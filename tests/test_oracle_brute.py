@@ -27,6 +27,19 @@ def _compare(o, b, env, step_fills):
 
 @pytest.mark.parametrize("seed", range(12))
 def test_oracle_matches_brute(seed):
+    _run_against_brute(seed, {})
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_oracle_matches_brute_reward_variants(seed):
+    """Eqs. 3-4 and the Table 2 penalties, against exact fractions in the brute env."""
+    rng = np.random.default_rng(500 + seed)
+    rw = dict(reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=int(rng.integers(0, 101)),
+              inv_penalty=int(rng.integers(0, 3)), exec_penalty_milli=int(rng.choice([0, 10, 50, 100, 2500])))
+    _run_against_brute(100 + seed, rw)
+
+
+def _run_against_brute(seed, rw):
     rng = np.random.default_rng(seed)
     cap = int(rng.integers(1, 9))
     T = 10
@@ -39,7 +52,7 @@ def test_oracle_matches_brute(seed):
     host = seed % 2 == 0
     kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)),
               exec_target=int(rng.integers(5, 60)), exec_dir=int(rng.choice([-1, 1])),
-              start_px=10_000)
+              start_px=10_000, **rw)
     o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
     o.reset(seeds)
     o.load_messages(st.msgs, st.offsets)

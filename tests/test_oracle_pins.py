@@ -107,6 +107,57 @@ def test_hand_worked_two_agent_episode():
     assert o.agents()[0].tolist() == g["final_agents"]
 
 
+def _reward_cases():
+    for sc in _gold("reward_variants.json")["scenarios"]:
+        for ex in sc["expected"]:
+            yield pytest.param(sc, ex, id=sc["name"] + "-" + "-".join(f"{k}{v}" for k, v in ex.items()
+                                                                     if k != "rewards"))
+
+
+@pytest.mark.parametrize("sc,ex", list(_reward_cases()))
+def test_hand_worked_reward_variants(sc, ex):
+    c = sc["config"]
+    kw = {k: v for k, v in ex.items() if k != "rewards"}
+    msgs, off = single_env_stream([s["msgs"] for s in sc["steps"]])
+    o = oracle.Oracle(1, n_agents=2, cap=c["cap"], top_levels=c["top_levels"],
+                      episode_len=c["episode_len"], exec_target=c["exec_target"],
+                      exec_dir=c["exec_dir"], mm_lot=c["mm_lot"], start_px=c["start_px"],
+                      action_mode=0, **kw)
+    o.reset(np.array([7], np.uint64))
+    o.load_messages(msgs, off)
+    got = []
+    for s in sc["steps"]:
+        assert o.step(np.array([s["actions"]], np.int32)) == 0
+        got.append(o.observe()[1][0].tolist())
+    assert got == ex["rewards"]
+
+
+def test_reward_variants_leave_book_and_obs_alone():
+    """The variants change the reward alone: books, observations and counters are those of mode 0."""
+    seeds = mbogen.env_seeds(77, 4)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=40), seeds, 6)
+    outs = []
+    for rw in (dict(), dict(reward_mode=2, spooner_lambda_pct=40, inv_penalty=3, exec_penalty_milli=100)):
+        o = oracle.Oracle(4, n_agents=2, cap=16, episode_len=6, action_mode=1, exec_target=30, **rw)
+        o.reset(seeds)
+        o.load_messages(st.msgs, st.offsets)
+        rec = []
+        for _ in range(6):
+            o.step()
+            obs, rew, done = o.observe()
+            rec.append((obs.copy(), o.counters().copy(), o.agents().copy(), rew.copy()))
+        outs.append(rec)
+    differs = False
+    for a, b in zip(*outs):
+        for x, y in zip(a[:3], b[:3]):
+            np.testing.assert_array_equal(x, y)
+        differs |= not np.array_equal(a[3][:, 1], b[3][:, 1])
+    # the execution agent's reward differs from Eq. 1 only by the penalty at the last step
+    for a, b in zip(outs[0][:-1], outs[1][:-1]):
+        np.testing.assert_array_equal(a[3][:, 0], b[3][:, 0])
+    assert differs
+
+
 def _setup_two_quotes(start_px, exec_dir, actions):
     """Step 0 places a bid 99 x 50 and an ask 104 x 50; step 1 runs `actions`."""
     msgs, off = single_env_stream([[[1, BUY, 99, 50, 0], [1, SELL, 104, 50, 1]], []])
