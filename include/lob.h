@@ -104,8 +104,28 @@ typedef struct lob_config {
     int32_t trace;         /* bit0: fill log; bit1: env 0 book snapshot after every message */
     int32_t start_px;      /* reference price before the first trade (e.g. 10000) */
     int32_t warps_per_block; /* launch shape hint; 0 = library default */
-    int32_t reserved[4];   /* must be zero */
+    /* Reward of the market maker (Sec. 5):
+     *   LOB_REWARD_PV       change of PV = Q_inv * P_ref + Cash (Eq. 1), ticks x qty;
+     *   LOB_REWARD_BUYSELL  Psi_b + Psi_s (Eq. 4), in quarter ticks x qty;
+     *   LOB_REWARD_SPOONER  Psi_b + Psi_s + Psi_INV - (1 - lambda) max(0, Psi_INV) (Eq. 3),
+     *                       in quarter ticks x qty.
+     * Psi_b = sum over this step's buys of (Mbar - P) Q, Psi_s = sum over its sells of
+     * (P - Mbar) Q, Mbar = mean of the mids at the start and the end of the step,
+     * Psi_INV = I (M_end - M_start) with I the inventory at the end of the step; a mid
+     * is that of the reference touches (last trade price on an empty side).  The
+     * execution agent's reward is always the Eq. 1 change.  Every reward is the floor
+     * of its exact value. */
+    int32_t reward_mode;
+    int32_t spooner_lambda_pct;  /* lambda of Eq. 3 in percent, 0..100 */
+    int32_t inv_penalty;         /* rho >= 0: market maker's reward -= rho * inventory^2 (Table 2) */
+    int32_t exec_penalty_milli;  /* >= 0: at the last step of the episode the execution agent's
+                                    reward -= this * unfilled units / 1000 (Table 2's unfilled
+                                    order penalty, in thousandths of a tick per unit) */
 } lob_config;
+
+#define LOB_REWARD_PV      0
+#define LOB_REWARD_BUYSELL 1
+#define LOB_REWARD_SPOONER 2
 
 #define LOB_MAX_CAP 1024   /* per-side capacity supported by this build */
 

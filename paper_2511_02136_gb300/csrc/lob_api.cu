@@ -38,6 +38,14 @@ long long exec_lot(const lob_config &c) {
     return q0 < 1 ? 1 : q0;
 }
 
+// Reward selection and penalties of the agents (Sec. 5, Eqs. 3-4, Table 2).
+static void set_rewards(KParams &p, const lob_config &c) {
+    p.reward_mode = c.reward_mode;
+    p.lam_pct = c.spooner_lambda_pct;
+    p.inv_penalty = c.inv_penalty;
+    p.exec_pen_milli = c.exec_penalty_milli;
+}
+
 size_t warp_smem_bytes(int K) {
     switch (K) {
         case 1: return sizeof(WarpSmem<1>);
@@ -208,8 +216,9 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
         (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace < 0 || c.trace > 3 ||
         c.warps_per_block < 0 || c.warps_per_block > 8)
         return LOB_EINVAL;
-    for (int i = 0; i < 4; i++)
-        if (c.reserved[i] != 0) return LOB_EINVAL;
+    if (c.reward_mode < LOB_REWARD_PV || c.reward_mode > LOB_REWARD_SPOONER || c.spooner_lambda_pct < 0 ||
+        c.spooner_lambda_pct > 100 || c.inv_penalty < 0 || c.exec_penalty_milli < 0)
+        return LOB_EINVAL;
     std::vector<int> caps((size_t)c.n_envs);
     for (int e = 0; e < c.n_envs; e++) {
         const int cp = h_caps ? h_caps[e] : c.cap_per_side;
@@ -410,6 +419,7 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.snap_count = (c.trace & 2) ? reinterpret_cast<long long *>(h->d_snap_count) : nullptr;
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
+    set_rewards(p, c);
     const int wpb = h->wpb;
     if (h->persistent) {
         if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
@@ -759,6 +769,7 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     p.queue = reinterpret_cast<int *>(scratch);
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
+    set_rewards(p, c);
     const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;
     if (launch_k(K, false, n, wpb, true, g_noalloc_n_sm[dev], s, p) != cudaSuccess) return LOB_ECUDA;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;

@@ -24,6 +24,7 @@
 // matching (Sec. 2.1) and the step outcomes (observation, Eq. 1 portfolio-
 // value reward, termination flag).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include "lob.h"
 
@@ -92,6 +93,9 @@ struct KParams {
     int uni_cap;
     long long uni_block;
     long long exec_q0;     // max(1, ceil(exec_target / T)), computed on the host
+    int reward_mode, lam_pct;        // market maker's reward (Eq. 1, 4 or 3), lambda in percent
+    long long inv_penalty;           // rho of the quadratic inventory penalty
+    long long exec_pen_milli;        // unfilled-task penalty, thousandths of a tick per unit
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -164,9 +168,11 @@ struct PoolSmem {
     int qty[32 * K];
 };
 
-// Per-warp shared memory.
+// Per-warp shared memory.  Warps index an array of these, so the size is a
+// multiple of 16 bytes: each warp's message tiles stay on the 16-byte boundary
+// that bulk copies need.
 template <int K>
-struct WarpSmem {
+struct __align__(16) WarpSmem {
     DevMsg tile[2][TILE];
     DevMsg amsg[4];                // the step's agent orders, after the shuffle
     unsigned long long bar[2];
@@ -174,7 +180,12 @@ struct WarpSmem {
     long long lvl_q[2][LMAX];
     int lvl_px[2][LMAX];
     unsigned char cand[2][32 * K]; // carry-over cancel flags per slot
+    long long rw[3];               // step start: twice the mid, MM inventory, MM cash (lane 0)
 };
+static_assert(sizeof(WarpSmem<1>) % 16 == 0 && sizeof(WarpSmem<2>) % 16 == 0 && sizeof(WarpSmem<4>) % 16 == 0 &&
+                  sizeof(WarpSmem<8>) % 16 == 0 && sizeof(WarpSmem<16>) % 16 == 0 && sizeof(WarpSmem<32>) % 16 == 0,
+              "per-warp shared memory must keep 16-byte alignment across warps");
+static_assert(offsetof(WarpSmem<1>, tile) == 0 && offsetof(WarpSmem<32>, tile) == 0, "tiles lead the block");
 
 // ---------------------------------------------------------------- book side
 // Pool slot s of a side belongs to one lane, which scans it in its register
@@ -837,6 +848,42 @@ __device__ __forceinline__ void side_agent_cancels(Side<K> &S, PoolSmem<K> &P, u
 }
 
 // Message pipeline state of one warp (tiles issued so far).
+// Sec. 5 rewards of the market maker and the Table 2 penalties, in wrapping
+// 64-bit arithmetic.  With Mbar the step's average mid, Psi_b + Psi_s (Eq. 4)
+// sums (Mbar - P) Q over buys and (P - Mbar) Q over sells, which is
+// Mbar * (inventory change) + (cash change) of the step, so it is formed from
+// the step-start inventory and cash without a per-fill record.  Values are in
+// quarter ticks (4 Mbar = start + end of twice the mid); the lambda damping of
+// Eq. 3 and the unfilled-task penalty round up, so each reward is the floor of
+// its exact value.  Arguments pass by value, so none of the caller's register
+// state is addressed.
+static __device__ __noinline__ longlong2 reward_variants(int mode, int lam_pct, long long rho, long long pen_milli,
+                                                         bool last_step, long long unfilled, long long mid2_start,
+                                                         long long mid2_end, long long inv_start, long long cash_start,
+                                                         long long inv1, long long cash1, long long r0, long long r1) {
+    typedef unsigned long long u64;
+    if (mode != LOB_REWARD_PV) {
+        const u64 m4 = (u64)mid2_start + (u64)mid2_end;
+        const u64 dinv = (u64)inv1 - (u64)inv_start;
+        const u64 dcash = (u64)cash1 - (u64)cash_start;
+        u64 r4 = m4 * dinv + 4ull * dcash;
+        if (mode == LOB_REWARD_SPOONER) {
+            const long long psi_inv4 = (long long)(2ull * (u64)inv1 * ((u64)mid2_end - (u64)mid2_start));
+            const long long pos = psi_inv4 > 0 ? psi_inv4 : 0;
+            const long long damp = (long long)((u64)(100 - lam_pct) * (u64)pos + 99ull) / 100;
+            r4 = r4 + (u64)psi_inv4 - (u64)damp;
+        }
+        r1 = (long long)r4;
+    }
+    r1 = (long long)((u64)r1 - (u64)rho * ((u64)inv1 * (u64)inv1));
+    if (last_step && pen_milli != 0) {
+        unfilled = unfilled > 0 ? unfilled : 0;
+        const long long pen = (long long)((u64)pen_milli * (u64)unfilled + 999ull) / 1000;
+        r0 = (long long)((u64)r0 - (u64)pen);
+    }
+    return make_longlong2(r0, r1);
+}
+
 struct MsgPipe {
     unsigned tiles;
 };
@@ -925,6 +972,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             }
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
+            if (p.reward_mode != LOB_REWARD_PV && lane == 0) {
+                sm.rw[0] = bb + ba; sm.rw[1] = c.inv1; sm.rw[2] = c.cash1;
+            }
             int wa[3] = {0, 0, 0}, ws[3] = {0, 0, 0}, wp[3] = {0, 0, 0};
             long long wq[3] = {0, 0, 0};
             int nw = 0;
@@ -1141,8 +1191,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             const long long pref1 = c.inv1 > 0 ? bb : (c.inv1 < 0 ? ba : 0);
             const long long pv0 = (long long)((unsigned long long)c.inv0 * (unsigned long long)pref0 + (unsigned long long)c.cash0);
             const long long pv1 = (long long)((unsigned long long)c.inv1 * (unsigned long long)pref1 + (unsigned long long)c.cash1);
-            const long long r0 = (long long)((unsigned long long)pv0 - (unsigned long long)c.pv0);
-            const long long r1 = (long long)((unsigned long long)pv1 - (unsigned long long)c.pv1);
+            long long r0 = (long long)((unsigned long long)pv0 - (unsigned long long)c.pv0);
+            long long r1 = (long long)((unsigned long long)pv1 - (unsigned long long)c.pv1);
             c.pv0 = pv0; c.pv1 = pv1;
             const float tl = __fdiv_rn((float)(p.T - (t + 1)), (float)p.T);
             const int D = p.D;
@@ -1174,6 +1224,12 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 }
             }
             if (lane == 0) {
+                if (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0) {
+                    const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
+                                                        t + 1 == p.T, (long long)p.exec_target - c.exec_done,
+                                                        sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
+                    r0 = r.x; r1 = r.y;
+                }
                 if (p.rew) { p.rew[obs_base * A] = r0; p.rew[obs_base * A + 1] = r1; }
                 if (p.act_out) { p.act_out[2LL * e] = act0; p.act_out[2LL * e + 1] = act1; }
             }

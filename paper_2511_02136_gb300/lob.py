@@ -49,6 +49,7 @@ EXPORTS = [
     "lob_checkpoint_bytes", "lob_save", "lob_load",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
+LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
 POLICY_HIDDEN = 128
 LOB_NOALLOC_MAX_ENVS = 16384
 
@@ -63,8 +64,8 @@ class LobError(RuntimeError):
 class lob_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_envs", "n_agents", "cap_per_side", "top_levels", "episode_len", "mm_lot",
-        "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block")] + \
-        [("reserved", ctypes.c_int32 * 4)]
+        "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block",
+        "reward_mode", "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli")]
 
 
 class lob_noalloc_args(ctypes.Structure):
@@ -374,11 +375,13 @@ class LobEnv:
 
     def __init__(self, n_envs, n_agents=2, cap=100, top_levels=10, episode_len=1000, mm_lot=1,
                  exec_target=500, exec_dir=-1, action_mode=LOB_ACT_RANDOM, start_px=10_000,
-                 warps_per_block=0, caps=None):
+                 warps_per_block=0, caps=None, reward_mode=0, spooner_lambda_pct=0, inv_penalty=0,
+                 exec_penalty_milli=0):
         import torch
         self.torch = torch
         self.cfg = lob_config(n_envs, n_agents, cap, top_levels, episode_len, mm_lot, exec_target,
-                              exec_dir, action_mode, 0, start_px, warps_per_block)
+                              exec_dir, action_mode, 0, start_px, warps_per_block, reward_mode,
+                              spooner_lambda_pct, inv_penalty, exec_penalty_milli)
         self.caps = caps
         self.h = lob_create(self.cfg, caps)
         self.n_envs, self.n_agents = n_envs, n_agents

@@ -30,7 +30,7 @@ class Pair:
 
     def __init__(self, n_envs, st, *, n_agents=2, cap=100, caps=None, top_levels=10, episode_len=None,
                  mm_lot=1, exec_target=500, exec_dir=-1, action_mode=lob.LOB_ACT_RANDOM, start_px=10_000,
-                 fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1):
+                 fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1, rewards=None):
         import torch
         self.torch = torch
         T = st.offsets.shape[1] - 1 if episode_len is None else episode_len
@@ -39,13 +39,13 @@ class Pair:
         self.env = lob.LobEnv(n_envs, n_agents=n_agents, cap=cap, top_levels=top_levels, episode_len=T,
                               mm_lot=mm_lot, exec_target=exec_target, exec_dir=exec_dir,
                               action_mode=action_mode, start_px=start_px, warps_per_block=warps_per_block,
-                              caps=caps)
+                              caps=caps, **(rewards or {}))
         if warps_per_block or persistent:
             lob.lob_set_launch(self.env.h, warps_per_block or 4, persistent)
         self.orc = oracle.Oracle(n_envs, n_agents=n_agents, cap=cap, top_levels=top_levels, episode_len=T,
                                  mm_lot=mm_lot, exec_target=exec_target, exec_dir=exec_dir,
                                  action_mode=action_mode, trace=(1 if fill_cap else 0) | (2 if snap_cap else 0),
-                                 start_px=start_px, n_threads=n_threads, caps=caps)
+                                 start_px=start_px, n_threads=n_threads, caps=caps, **(rewards or {}))
         self.msgs_d = to_dev(st.msgs) if len(st.msgs) else torch.zeros(32, dtype=torch.uint8, device="cuda")
         self.off_d = to_dev(st.offsets)
         self.env.load_messages(self.msgs_d, self.off_d)

@@ -211,12 +211,81 @@ def test_create_rejects_bad_configs():
     for field, val, code in (("n_envs", 0, lob.LOB_EINVAL), ("n_agents", 1, lob.LOB_EINVAL),
                              ("cap_per_side", lob.LOB_MAX_CAP + 1, lob.LOB_ECAPACITY),
                              ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 0, lob.LOB_EINVAL),
-                             ("action_mode", 7, lob.LOB_EINVAL)):
+                             ("action_mode", 7, lob.LOB_EINVAL), ("reward_mode", 3, lob.LOB_EINVAL),
+                             ("spooner_lambda_pct", 101, lob.LOB_EINVAL), ("inv_penalty", -1, lob.LOB_EINVAL),
+                             ("exec_penalty_milli", -5, lob.LOB_EINVAL)):
         c = lob.lob_config(4, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
         setattr(c, field, val)
         with pytest.raises(lob.LobError) as ei:
             lob.lob_create(c)
         assert ei.value.code == code, field
+
+
+REWARD_CASES = [
+    dict(reward_mode=lob.LOB_REWARD_BUYSELL),
+    dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=50),
+    dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=33, inv_penalty=50, exec_penalty_milli=100),
+    dict(reward_mode=lob.LOB_REWARD_PV, inv_penalty=2, exec_penalty_milli=2500),
+]
+
+
+@pytest.mark.parametrize("rw", REWARD_CASES, ids=lambda r: "-".join(f"{k}{v}" for k, v in r.items()))
+def test_reward_variants_random_policy(rw):
+    """Eqs. 3-4 and the Table 2 penalties: every reward of every step, whole
+    episodes (the penalty lands on the last step), envs in every capacity class."""
+    n, T = 96, 24
+    caps = np.array([[5, 40, 100, 300, 700, 1000][e % 6] for e in range(n)], np.int32)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=60), mbogen.env_seeds(31, n), T)
+    pr = Pair(n, st, caps=caps, cap=int(caps.max()), exec_target=150, rewards=rw)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+    pr.check_state()
+    pr.close()
+
+
+def test_reward_variants_host_actions_buy_task():
+    n, T = 33, 16
+    rng = np.random.default_rng(8)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=50), mbogen.env_seeds(32, n), T)
+    pr = Pair(n, st, cap=100, exec_target=300, exec_dir=1, mm_lot=4, action_mode=lob.LOB_ACT_HOST,
+              rewards=dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=71, inv_penalty=1,
+                           exec_penalty_milli=10))
+    for _ in range(T):
+        pr.step(rng.integers(0, 12, size=(n, 2)).astype(np.int32))
+        pr.check_outputs()
+    pr.close()
+
+
+def _gold(name):
+    import json
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+def test_reward_variants_hand_worked_on_gpu():
+    """The hand-worked Sec. 5 / Table 2 fixture, through the kernel directly."""
+    import torch
+    from conftest import single_env_stream
+    for sc in _gold("reward_variants.json")["scenarios"]:
+        c = sc["config"]
+        msgs, off = single_env_stream([s["msgs"] for s in sc["steps"]])
+        for ex in sc["expected"]:
+            rw = {k: v for k, v in ex.items() if k != "rewards"}
+            env = lob.LobEnv(1, cap=c["cap"], top_levels=c["top_levels"], episode_len=c["episode_len"],
+                             mm_lot=c["mm_lot"], exec_target=c["exec_target"], exec_dir=c["exec_dir"],
+                             action_mode=lob.LOB_ACT_HOST, start_px=c["start_px"], **rw)
+            md = torch.from_numpy(msgs.view(np.uint8).copy()).cuda() if len(msgs) else \
+                torch.zeros(32, dtype=torch.uint8, device="cuda")
+            env.load_messages(md, torch.from_numpy(off.copy()).cuda())
+            env.reset(torch.tensor([7], dtype=torch.int64, device="cuda"))
+            got = []
+            for s in sc["steps"]:
+                env.step(torch.tensor([s["actions"]], dtype=torch.int32, device="cuda"))
+                got.append(env.observe()[1][0].cpu().tolist())
+            assert got == ex["rewards"], (sc["name"], rw)
+            assert env.sync() == 0
+            env.close()
 
 
 def test_stress_mix_cap1000_top20():
