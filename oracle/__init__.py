@@ -35,6 +35,9 @@ FILL_DTYPE = np.dtype([("maker_id", "<i8"), ("taker_id", "<i8"), ("px", "<i4"),
                        ("qty", "<i4"), ("msg_idx", "<i4"), ("taker_side", "<i4")])
 TAG_SHUFFLE = 0x5348554646000001
 TAG_POLICY = 0x504F4C4943590002
+TAG_EPISODE = 0x4550495344450003
+INIT_ID = 0x4000000000000000
+START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
 
 
 class OrcConfig(ctypes.Structure):
@@ -70,6 +73,10 @@ def _load():
         lib.orc_step.restype = ctypes.c_int
         lib.orc_step.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int32]
         lib.orc_observe.argtypes = [P, P, P, P]
+        lib.orc_set_episodes.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int64]
+        lib.orc_step_episodes.restype = ctypes.c_int
+        lib.orc_step_episodes.argtypes = [P, P]
+        lib.orc_get_episode.argtypes = [P, P]
         lib.orc_obs_dim.restype = ctypes.c_int32
         lib.orc_obs_dim.argtypes = [P]
         lib.orc_get_book.argtypes = [P, ctypes.c_int64, P, P, P, P, P]
@@ -125,6 +132,7 @@ class Oracle:
         self.n_envs, self.n_agents = n_envs, n_agents
         self.obs_dim = self.lib.orc_obs_dim(self.h)
         self._msgs = self._offsets = None
+        self._ep = None
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -143,8 +151,28 @@ class Oracle:
         self._offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         self._k = 0
 
+    def set_episodes(self, msgs, step_offsets, starts, levels):
+        """Episode mode over one shared stream: msgs MSG_DTYPE[N], step_offsets
+        int64[n_data_steps + 1], starts START_DTYPE[n_starts], levels
+        int32[n_starts, 2, levels_per_side, 2] (price, quantity), best first."""
+        msgs = np.ascontiguousarray(msgs)
+        off = np.ascontiguousarray(step_offsets, dtype=np.int64)
+        starts = np.ascontiguousarray(starts, dtype=START_DTYPE)
+        levels = np.ascontiguousarray(levels, dtype=np.int32)
+        self._ep = (msgs, off, starts, levels)   # msgs must outlive the handle's use
+        self.lib.orc_set_episodes(self.h, msgs.ctypes.data if len(msgs) else None, off.ctypes.data,
+                                  len(off) - 1, starts.ctypes.data, levels.ctypes.data,
+                                  levels.shape[2], len(starts))
+
+    def episode_starts(self):
+        out = np.zeros(self.n_envs, np.int64)
+        self.lib.orc_get_episode(self.h, out.ctypes.data)
+        return out
+
     def step(self, actions=None):
         acts = None if actions is None else np.ascontiguousarray(actions, dtype=np.int32)
+        if self._ep is not None:
+            return self.lib.orc_step_episodes(self.h, _ptr(acts))
         rc = self.lib.orc_step(self.h, _ptr(acts), self._msgs.ctypes.data,
                                self._offsets.ctypes.data, self._offsets.shape[1], self._k)
         self._k += 1

@@ -29,7 +29,15 @@
 //     shuffled new orders, then the step's background messages in order;
 //   * reward: change of portfolio value PV = Q_inv * P_ref + Cash (Eq. 1) with
 //     P_ref the touch one would liquidate at (best bid if long, best ask if
-//     short); an empty side's touch is the last trade price.
+//     short); an empty side's touch is the last trade price;
+//   * episodes (Sec. 3, parallelisation over episodes): one contiguous message
+//     array with per-data-step start indices; episode k of an env starts at
+//     the snapshot drawn with a SplitMix64 draw keyed by (env seed, k); the
+//     snapshot's levels become resting orders (one per level, bids then asks,
+//     best first, arrival stamps 0, 1, ...; ids INIT_ID + the same index);
+//     agents start flat; after the episode's last step the env starts the
+//     next episode and reports that episode's first observation, with the
+//     finished step's rewards and done flag.
 #include "oracle.h"
 
 #include <algorithm>
@@ -137,6 +145,8 @@ uint32_t lemire(uint64_t x, uint32_t n) {
 }
 const uint64_t TAG_SHUFFLE = 0x5348554646000001ULL;
 const uint64_t TAG_POLICY = 0x504F4C4943590002ULL;
+const uint64_t TAG_EPISODE = 0x4550495344450003ULL;
+const int64_t INIT_ID = 0x4000000000000000LL;   // ids of a snapshot's resting orders
 
 int64_t floor_half(int64_t s) { return s >= 0 ? s / 2 : -((-s + 1) / 2); }
 int64_t ceil_half(int64_t s) { return -floor_half(-s); }
@@ -161,6 +171,7 @@ struct Env {
     int32_t act[2] = {0, 0};
     bool bad = false;
     int32_t msg_idx = 0;                // processing index within the current step
+    int64_t ep_start = 0;               // episode mode: first data step of the current episode
     std::vector<unsigned char> *snaps = nullptr;  // env 0 book after every message
 };
 
@@ -175,6 +186,13 @@ struct Engine {
     std::vector<Env> envs;
     int64_t t = 0;  // steps taken since reset
     std::vector<unsigned char> snaps;
+    // episode mode
+    bool ep_mode = false;
+    const Msg *ep_msgs = nullptr;
+    std::vector<int64_t> ep_off;
+    std::vector<orc_start> ep_starts;
+    std::vector<int32_t> ep_levels;   // [n_starts][2][ep_ls][2]
+    int32_t ep_ls = 0;
 
     Side &side_book(Env &E, int side) { return side == BUY ? E.bids : E.asks; }
 
@@ -333,6 +351,60 @@ struct Engine {
         E.msg_idx++;
     }
 
+    // Start episode k of env E from its drawn snapshot (episode mode).
+    void begin_episode(Env &E, int64_t k) {
+        const uint32_t j = lemire(draw(E.seed, k, TAG_EPISODE, 0), (uint32_t)ep_starts.size());
+        const orc_start &st = ep_starts[j];
+        E.bids.levels.clear(); E.bids.count = 0;
+        E.asks.levels.clear(); E.asks.count = 0;
+        E.ts_next = 0;
+        E.seq_next = 0;
+        for (int a = 0; a < 2; a++) E.ag[a] = Agent();
+        E.last_px = st.last_px;
+        E.ep_start = st.data_step;
+        int64_t idx = 0;
+        for (int s = 0; s < 2; s++) {
+            Side &side = s == 0 ? E.bids : E.asks;
+            const int n = s == 0 ? st.n_bid : st.n_ask;
+            for (int i = 0; i < n; i++) {
+                const int32_t *lv = ep_levels.data() + (((size_t)j * 2 + s) * ep_ls + i) * 2;
+                side.levels[lv[0]].push_back(Order{INIT_ID + idx, E.ts_next++, lv[0], lv[1]});
+                side.count++;
+                idx++;
+            }
+        }
+    }
+
+    // Observation of every agent (Sec. 4.1.1): top-L aggregated levels per
+    // side relative to the anchor, inventory, cash, time left, remaining
+    // execution target, own resting quantity.
+    void write_obs(Env &E, float tl) {
+        const orc_config &c = cfg.c;
+        const int A = c.n_agents, L = c.top_levels, D = cfg.obs_dim();
+        int64_t bb = ref_bid(E), ba = ref_ask(E);
+        int64_t anchor = floor_half(bb + ba);
+        E.obs.assign((size_t)A * D, 0.0f);
+        std::vector<std::pair<int32_t, int64_t>> lv[2] = {E.bids.aggregated(), E.asks.aggregated()};
+        std::vector<int64_t> own_rest(A, 0);
+        for (int s = 0; s < 2; s++)
+            for (const Order &o : (s == 0 ? E.bids : E.asks).ordered())
+                if (o.id < 0) own_rest[owner(o.id, A)] += o.qty;
+        for (int a = 0; a < A; a++) {
+            float *ob = E.obs.data() + (size_t)a * D;
+            for (int s = 0; s < 2; s++)
+                for (int i = 0; i < L && i < (int)lv[s].size(); i++) {
+                    ob[s * 2 * L + 2 * i] = (float)(lv[s][i].first - anchor);
+                    ob[s * 2 * L + 2 * i + 1] = (float)lv[s][i].second;
+                }
+            const Agent &g = E.ag[a];
+            ob[4 * L + 0] = (float)g.inv;
+            ob[4 * L + 1] = (float)g.cash;
+            ob[4 * L + 2] = tl;
+            ob[4 * L + 3] = a == 0 ? (float)((int64_t)c.exec_target - g.exec_done) : 0.0f;
+            ob[4 * L + 4] = (float)own_rest[a];
+        }
+    }
+
     struct NewOrder { int agent, side; int32_t px, qty; };
 
     void env_step(Env &E, int64_t e, const int32_t *actions, const Msg *bg, int64_t nbg) {
@@ -429,30 +501,14 @@ struct Engine {
         for (int64_t i = 0; i < nbg; i++) process(E, bg[i], false);
 
         // -- Step outcomes (Sec. 4): observation, reward, termination
+        // (te: step within the episode; episodes restart only in episode mode)
+        const int64_t te = ep_mode ? t % c.episode_len : t;
+        const bool last = te + 1 == c.episode_len;
         if (A > 0) {
             int64_t bb = ref_bid(E), ba = ref_ask(E);
-            int64_t anchor = floor_half(bb + ba);
-            const int L = c.top_levels, D = cfg.obs_dim();
-            E.obs.assign((size_t)A * D, 0.0f);
-            std::vector<std::pair<int32_t, int64_t>> lv[2] = {E.bids.aggregated(), E.asks.aggregated()};
-            std::vector<int64_t> own_rest(A, 0);
-            for (int s = 0; s < 2; s++)
-                for (const Order &o : (s == 0 ? E.bids : E.asks).ordered())
-                    if (o.id < 0) own_rest[owner(o.id, A)] += o.qty;
-            float tl = (float)(c.episode_len - (t + 1)) / (float)c.episode_len;
+            write_obs(E, (float)(c.episode_len - (te + 1)) / (float)c.episode_len);
             for (int a = 0; a < A; a++) {
-                float *ob = E.obs.data() + (size_t)a * D;
-                for (int s = 0; s < 2; s++)
-                    for (int i = 0; i < L && i < (int)lv[s].size(); i++) {
-                        ob[s * 2 * L + 2 * i] = (float)(lv[s][i].first - anchor);
-                        ob[s * 2 * L + 2 * i + 1] = (float)lv[s][i].second;
-                    }
                 Agent &g = E.ag[a];
-                ob[4 * L + 0] = (float)g.inv;
-                ob[4 * L + 1] = (float)g.cash;
-                ob[4 * L + 2] = tl;
-                ob[4 * L + 3] = a == 0 ? (float)((int64_t)c.exec_target - g.exec_done) : 0.0f;
-                ob[4 * L + 4] = (float)own_rest[a];
                 // PV = Q_inv * P_ref + Cash (Eq. 1), P_ref the liquidation touch
                 int64_t pref = g.inv > 0 ? bb : g.inv < 0 ? ba : 0;
                 int64_t pv = wadd(wmul(g.inv, pref), g.cash);
@@ -479,14 +535,19 @@ struct Engine {
                 }
                 if (a == 1 && c.inv_penalty != 0)   // quadratic inventory penalty
                     E.rew[a] = wsub(E.rew[a], wmul(c.inv_penalty, wmul(g.inv, g.inv)));
-                if (a == 0 && c.exec_penalty_milli != 0 && t + 1 == c.episode_len) {
+                if (a == 0 && c.exec_penalty_milli != 0 && last) {
                     // Table 2: penalty on the part of the task still unfilled at the end
                     const int64_t unfilled = std::max<int64_t>(0, (int64_t)c.exec_target - g.exec_done);
                     E.rew[a] = wsub(E.rew[a], (wmul(c.exec_penalty_milli, unfilled) + 999) / 1000);  // rounded up
                 }
             }
         }
-        E.done = (uint8_t)(t + 1 == c.episode_len);
+        E.done = (uint8_t)last;
+        if (ep_mode && last) {
+            // the next episode begins; its first observation is what the agents see
+            begin_episode(E, t / c.episode_len + 1);
+            if (A > 0) write_obs(E, (float)c.episode_len / (float)c.episode_len);
+        }
     }
 };
 
@@ -525,14 +586,11 @@ void orc_reset(void *h, const uint64_t *env_seeds) {
         E.asks.is_bid = false;
         E.seed = env_seeds[e];
         E.last_px = g->cfg.c.start_px;
-        // reset observation: empty book, nothing held, the whole episode and
-        // (for the execution agent) the whole target still ahead
-        const int D = g->cfg.obs_dim(), L = g->cfg.c.top_levels;
-        E.obs.assign((size_t)g->cfg.c.n_agents * D, 0.0f);
-        for (int a = 0; a < g->cfg.c.n_agents; a++) {
-            E.obs[(size_t)a * D + 4 * L + 2] = (float)g->cfg.c.episode_len / (float)g->cfg.c.episode_len;
-            if (a == 0) E.obs[(size_t)a * D + 4 * L + 3] = (float)g->cfg.c.exec_target;
-        }
+        if (g->ep_mode) g->begin_episode(E, 0);
+        // reset observation: the starting book (empty outside episode mode),
+        // nothing held, the whole episode and (for the execution agent) the
+        // whole target still ahead
+        g->write_obs(E, (float)g->cfg.c.episode_len / (float)g->cfg.c.episode_len);
     }
 }
 
@@ -562,6 +620,52 @@ int orc_step(void *h, const int32_t *actions, const void *msgs, const int64_t *o
     int rc = 0;
     for (Env &E : g->envs) if (E.bad) { rc = -6; E.bad = false; }
     return rc;
+}
+
+void orc_set_episodes(void *h, const void *msgs, const int64_t *step_off, int64_t n_data_steps,
+                      const orc_start *starts, const int32_t *levels, int32_t levels_per_side, int64_t n_starts) {
+    Engine *g = (Engine *)h;
+    g->ep_mode = true;
+    g->ep_msgs = (const Msg *)msgs;
+    g->ep_off.assign(step_off, step_off + n_data_steps + 1);
+    g->ep_starts.assign(starts, starts + n_starts);
+    g->ep_levels.assign(levels, levels + (size_t)n_starts * 2 * levels_per_side * 2);
+    g->ep_ls = levels_per_side;
+}
+
+int orc_step_episodes(void *h, const int32_t *actions) {
+    Engine *g = (Engine *)h;
+    const int64_t n = (int64_t)g->envs.size(), T = g->cfg.c.episode_len;
+    const int64_t te = g->t % T;
+    auto run = [&](int64_t lo, int64_t hi) {
+        for (int64_t e = lo; e < hi; e++) {
+            Env &E = g->envs[(size_t)e];
+            const int64_t d = E.ep_start + te;   // this step's data step
+            const int64_t b = g->ep_off[(size_t)d], en = g->ep_off[(size_t)d + 1];
+            g->env_step(E, e, actions, g->ep_msgs + b, en - b);
+        }
+    };
+    int nt = std::max(1, g->cfg.c.n_threads);
+    if (nt == 1 || n < 2) {
+        run(0, n);
+    } else {
+        std::vector<std::thread> th;
+        int64_t per = (n + nt - 1) / nt;
+        for (int i = 0; i < nt; i++) {
+            int64_t lo = i * per, hi = std::min(n, lo + per);
+            if (lo < hi) th.emplace_back(run, lo, hi);
+        }
+        for (auto &x : th) x.join();
+    }
+    g->t++;
+    int rc = 0;
+    for (Env &E : g->envs) if (E.bad) { rc = -6; E.bad = false; }
+    return rc;
+}
+
+void orc_get_episode(void *h, int64_t *out) {
+    Engine *g = (Engine *)h;
+    for (size_t e = 0; e < g->envs.size(); e++) out[e] = g->envs[e].ep_start;
 }
 
 int32_t orc_obs_dim(void *h) { return ((Engine *)h)->cfg.obs_dim(); }

@@ -55,6 +55,26 @@ void    orc_reset(void *h, const uint64_t *env_seeds);
  * when some message was malformed (it is skipped and counted). */
 int     orc_step(void *h, const int32_t *actions, const void *msgs, const int64_t *offsets,
                  int64_t stride, int32_t k);
+/* Episodes over one shared message stream (Sec. 3, parallelisation over
+ * episodes): all messages of the data set in one contiguous array `msgs`,
+ * data step d covering msgs[step_off[d] .. step_off[d+1]).  An episode starts
+ * at one of n_starts snapshots: starts[j] gives its first data step, the last
+ * trade price at that time and its level counts; levels[j][side][i] = (price,
+ * quantity) of level i, side 0 bids best-first, side 1 asks best-first, each
+ * side of levels_per_side entries.  After this call orc_reset and
+ * orc_step_episodes run in episode mode: at the start of episode k each env
+ * draws its snapshot, the book is the snapshot's levels as resting orders,
+ * and after the last step of an episode the env starts the next one.  The
+ * arrays are copied; msgs must stay valid. */
+typedef struct orc_start {
+    int32_t data_step, last_px, n_bid, n_ask;
+} orc_start;
+void    orc_set_episodes(void *h, const void *msgs, const int64_t *step_off, int64_t n_data_steps,
+                         const orc_start *starts, const int32_t *levels, int32_t levels_per_side,
+                         int64_t n_starts);
+int     orc_step_episodes(void *h, const int32_t *actions);
+/* First data step of every env's current episode. */
+void    orc_get_episode(void *h, int64_t *out);
 void    orc_observe(void *h, float *obs, int64_t *rewards, uint8_t *done);
 int32_t orc_obs_dim(void *h);
 void    orc_get_book(void *h, int64_t env, int32_t *n2, int32_t *px, int32_t *qty, int64_t *id, int64_t *ts);

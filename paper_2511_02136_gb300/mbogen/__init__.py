@@ -116,7 +116,7 @@ def _load():
         lib.mbogen_generate.restype = ctypes.c_int
         lib.mbogen_generate.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                        ctypes.c_void_p, ctypes.c_int32]
+                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
         lib.mbogen_env_caps.restype = None
         lib.mbogen_env_caps.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p]
@@ -151,6 +151,7 @@ class Streams:
     counts: np.ndarray      # int32 [n_envs, n_steps]
     lambdas: np.ndarray     # float64 [n_envs]
     seeds: np.ndarray       # uint64 [n_envs]
+    mids: np.ndarray | None = None   # int32 [n_envs, n_steps + 1]: latent mid at each step boundary
 
 
 def generate(model: MessageModel, seeds: np.ndarray, n_steps: int, n_threads: int | None = None) -> Streams:
@@ -168,8 +169,45 @@ def generate(model: MessageModel, seeds: np.ndarray, n_steps: int, n_threads: in
     msgs = np.empty(max(total, 1), dtype=MSG_DTYPE)[:total]
     if n_threads is None:
         n_threads = min(os.cpu_count() or 1, 64)
+    mids = np.full((n_envs, n_steps + 1), model.start_mid, dtype=np.int32)
     if total and lib.mbogen_generate(ctypes.byref(p), n_envs, seeds.ctypes.data, n_steps,
                                      counts.ctypes.data, offsets.ctypes.data,
-                                     msgs.ctypes.data, n_threads):
+                                     msgs.ctypes.data, n_threads, mids.ctypes.data):
         raise RuntimeError("mbogen_generate failed")
-    return Streams(msgs=msgs, offsets=offsets, counts=counts, lambdas=lambdas, seeds=seeds)
+    return Streams(msgs=msgs, offsets=offsets, counts=counts, lambdas=lambdas, seeds=seeds, mids=mids)
+
+
+START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
+
+
+def start_books(seed: int, mids: np.ndarray, start_steps, levels_per_side: int, min_levels: int = 0,
+                max_gap: int = 3, qty_max: int = 50):
+    """Synthetic book snapshots at episode starts (the role of the data set's
+    order-book file at the start of each episode).
+
+    For start j at data step s = start_steps[j] around the stream's latent mid m
+    = mids[s]: best bid m - U{0..2}, best ask m + 1 + U{0..2}, further levels
+    each 1 + U{0..max_gap-1} ticks away, level counts U{min_levels..levels_per_side}
+    per side, sizes U{1..qty_max}; last trade price m.  Returns
+    (starts START_DTYPE[n], levels int32[n, 2, levels_per_side, 2]) with
+    (price, quantity) pairs best-first (bids descending, asks ascending).
+    """
+    rng = np.random.default_rng(seed)
+    steps = np.asarray(start_steps, dtype=np.int64)
+    n = len(steps)
+    starts = np.zeros(n, START_DTYPE)
+    levels = np.zeros((n, 2, levels_per_side, 2), np.int32)
+    for j, s in enumerate(steps):
+        m = int(mids[s])
+        nb = int(rng.integers(min_levels, levels_per_side + 1))
+        na = int(rng.integers(min_levels, levels_per_side + 1))
+        px = m - int(rng.integers(0, 3))
+        for i in range(nb):
+            levels[j, 0, i] = (px, int(rng.integers(1, qty_max + 1)))
+            px -= 1 + int(rng.integers(0, max_gap))
+        px = m + 1 + int(rng.integers(0, 3))
+        for i in range(na):
+            levels[j, 1, i] = (px, int(rng.integers(1, qty_max + 1)))
+            px += 1 + int(rng.integers(0, max_gap))
+        starts[j] = (int(s), m, nb, na)
+    return starts, levels

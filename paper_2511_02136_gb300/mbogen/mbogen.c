@@ -26,7 +26,9 @@
  *   - optional cancel bursts: with probability p_burst per env-step the step
  *     starts with min(floor(pool/2), M) deletes of pool orders;
  *   - messages per step fixed (M) or Poisson(lambda_env) with lambda_env
- *     log-uniform in [lam_lo, lam_hi].
+ *     log-uniform in [lam_lo, lam_hi];
+ *   - optionally the latent mid at every step boundary, from which the
+ *     Python side draws synthetic book snapshots for episode starts.
  *
  * All random draws are integers: SplitMix64 outputs compared against uint64
  * CDF threshold tables.  The tables are built with IEEE double + - * / only
@@ -194,6 +196,7 @@ typedef struct shared_ctx {
     const int32_t *counts; /* [n_envs][n_steps] */
     const int64_t *offsets;/* [n_envs][n_steps+1] absolute */
     mbo_msg *out;
+    int32_t *mids;         /* [n_envs][n_steps+1] latent mid at each step boundary, or NULL */
     cdf_table geom_price, size_tab;
     uint64_t thr_move, thr_add, thr_partial, thr_delete, thr_burst;
     int64_t next_env;
@@ -212,6 +215,7 @@ static int gen_env(shared_ctx *c, int64_t e) {
     for (int32_t t = 0; t < c->n_steps; t++) {
         int32_t m = c->counts[e * (int64_t)c->n_steps + t];
         mbo_msg *o = c->out + c->offsets[e * (int64_t)(c->n_steps + 1) + t];
+        if (c->mids) c->mids[e * (int64_t)(c->n_steps + 1) + t] = mid;
         int32_t n_burst = 0;
         if (c->thr_burst) {
             uint64_t u = sm_next(&s);
@@ -275,6 +279,7 @@ static int gen_env(shared_ctx *c, int64_t e) {
             }
         }
     }
+    if (c->mids) c->mids[e * (int64_t)(c->n_steps + 1) + c->n_steps] = mid;
     free(pool);
     return 0;
 }
@@ -330,11 +335,11 @@ int64_t mbogen_offsets(int64_t n_envs, int32_t n_steps, const int32_t *counts, i
 
 int mbogen_generate(const mbogen_params *p, int64_t n_envs, const uint64_t *env_seeds,
                     int32_t n_steps, const int32_t *counts, const int64_t *offsets,
-                    void *out_msgs, int32_t n_threads) {
+                    void *out_msgs, int32_t n_threads, int32_t *mids_out) {
     shared_ctx c;
     memset(&c, 0, sizeof(c));
     c.p = p; c.env_seeds = env_seeds; c.n_envs = n_envs; c.n_steps = n_steps;
-    c.counts = counts; c.offsets = offsets; c.out = (mbo_msg *)out_msgs;
+    c.counts = counts; c.offsets = offsets; c.out = (mbo_msg *)out_msgs; c.mids = mids_out;
     double tot = p->mix_add + p->mix_partial + p->mix_delete + p->mix_market;
     if (!(tot > 0.0)) return -1;
     c.thr_move = prob_to_u64(p->p_move);

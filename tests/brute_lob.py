@@ -15,6 +15,8 @@ M64 = (1 << 64) - 1
 GAMMA = 0x9E3779B97F4A7C15
 TAG_SHUFFLE = 0x5348554646000001
 TAG_POLICY = 0x504F4C4943590002
+TAG_EPISODE = 0x4550495344450003
+INIT_ID = 1 << 62
 
 
 def _mix(z):
@@ -78,6 +80,45 @@ class BruteEnv:
         self.rew = [0] * n_agents
         self.done = 0
         self.acts = [0] * n_agents
+
+    # -- episodes over one shared stream ----------------------------------------
+    def set_episodes(self, msgs, step_offsets, starts, levels):
+        self.ep = (msgs, step_offsets, starts, levels)
+
+    def begin_episode(self, k):
+        msgs, off, starts, levels = self.ep
+        j = bounded(keyed_draws(self.seed, k, TAG_EPISODE, 1)[0], len(starts))
+        st = starts[j]
+        self.orders = {BUY: [], SELL: []}
+        self.ts_next = 0
+        self.seq_next = 0
+        self.inv = [0] * self.A
+        self.cash = [0] * self.A
+        self.pv_prev = [0] * self.A
+        self.exec_done = 0
+        self.last_px = int(st["last_px"])
+        self.ep_start = int(st["data_step"])
+        idx = 0
+        for s, side in enumerate((BUY, SELL)):
+            for i in range(int(st["n_bid"] if s == 0 else st["n_ask"])):
+                px, q = (int(v) for v in levels[j, s, i])
+                self.orders[side].append(dict(px=px, qty=q, id=INIT_ID + idx, ts=self.ts_next))
+                self.ts_next += 1
+                idx += 1
+
+    def reset_obs(self):
+        """Observation at an episode start: the starting book, flat agents, full time and target."""
+        self._write_obs(1.0)
+
+    def step_episode(self, actions=None):
+        msgs, off, starts, levels = self.ep
+        te = self.t % self.T
+        d = self.ep_start + te
+        self.step(msgs[off[d]:off[d + 1]], actions, te=te)
+        if te + 1 == self.T:
+            self.begin_episode(self.t // self.T)
+            if self.A:
+                self.reset_obs()
 
     # -- book helpers -------------------------------------------------------
     def ranked(self, side):
@@ -179,7 +220,9 @@ class BruteEnv:
         self.msg_idx += 1
 
     # -- one env step ---------------------------------------------------------
-    def step(self, msgs, actions=None):
+    def step(self, msgs, actions=None, te=None):
+        """One env step; te is the step within the episode (the global step when None)."""
+        te = self.t if te is None else te
         self.fills = []
         self.step_fills = []   # (buyer, seller, price, qty) of this step
         self.msg_idx = 0
@@ -237,34 +280,8 @@ class BruteEnv:
             self.process(int(m["type"]), int(m["side"]), int(m["px"]), int(m["qty"]), int(m["oid"]))
         if self.A:
             bb, ba = self.touch(BUY), self.touch(SELL)
-            anchor = (bb + ba) // 2
-            D = 4 * self.L + 5
-            self.obs = [[0.0] * D for _ in range(self.A)]
-            levels = {}
-            for s, side in enumerate((BUY, SELL)):
-                lv = []
-                for o in self.ranked(side):
-                    if lv and lv[-1][0] == o["px"]:
-                        lv[-1][1] += o["qty"]
-                    else:
-                        lv.append([o["px"], o["qty"]])
-                levels[s] = lv
-            rest = [0] * self.A
-            for side in (BUY, SELL):
-                for o in self.orders[side]:
-                    if o["id"] < 0:
-                        rest[self.owner(o["id"])] += o["qty"]
+            self._write_obs((self.T - (te + 1)) / self.T)
             for a in range(self.A):
-                ob = self.obs[a]
-                for s in range(2):
-                    for i, (p, q) in enumerate(levels[s][: self.L]):
-                        ob[s * 2 * self.L + 2 * i] = float(p - anchor)
-                        ob[s * 2 * self.L + 2 * i + 1] = float(q)
-                ob[4 * self.L] = float(self.inv[a])
-                ob[4 * self.L + 1] = float(self.cash[a])
-                ob[4 * self.L + 2] = (self.T - (self.t + 1)) / self.T
-                ob[4 * self.L + 3] = float(self.exec_target - self.exec_done) if a == 0 else 0.0
-                ob[4 * self.L + 4] = float(rest[a])
                 pref = bb if self.inv[a] > 0 else ba if self.inv[a] < 0 else 0
                 pv = wrap(self.inv[a] * pref + self.cash[a])
                 self.rew[a] = wrap(pv - self.pv_prev[a])
@@ -273,12 +290,43 @@ class BruteEnv:
                     self.rew[a] = self._mm_reward(mid_before, (bb + ba) / 2)
                 if a == 1:
                     self.rew[a] -= self.inv_penalty * self.inv[a] ** 2
-                if a == 0 and self.t + 1 == self.T:
+                if a == 0 and te + 1 == self.T:
                     unfilled = max(0, self.exec_target - self.exec_done)
                     self.rew[a] = self.rew[a] - self.exec_penalty_milli * unfilled / Fraction(1000)
                     self.rew[a] = self.rew[a].numerator // self.rew[a].denominator
-        self.done = int(self.t + 1 == self.T)
+        self.done = int(te + 1 == self.T)
         self.t += 1
+
+    def _write_obs(self, time_left):
+        bb, ba = self.touch(BUY), self.touch(SELL)
+        anchor = (bb + ba) // 2
+        D = 4 * self.L + 5
+        self.obs = [[0.0] * D for _ in range(self.A)]
+        levels = {}
+        for s, side in enumerate((BUY, SELL)):
+            lv = []
+            for o in self.ranked(side):
+                if lv and lv[-1][0] == o["px"]:
+                    lv[-1][1] += o["qty"]
+                else:
+                    lv.append([o["px"], o["qty"]])
+            levels[s] = lv
+        rest = [0] * self.A
+        for side in (BUY, SELL):
+            for o in self.orders[side]:
+                if o["id"] < 0:
+                    rest[self.owner(o["id"])] += o["qty"]
+        for a in range(self.A):
+            ob = self.obs[a]
+            for s in range(2):
+                for i, (p, q) in enumerate(levels[s][: self.L]):
+                    ob[s * 2 * self.L + 2 * i] = float(p - anchor)
+                    ob[s * 2 * self.L + 2 * i + 1] = float(q)
+            ob[4 * self.L] = float(self.inv[a])
+            ob[4 * self.L + 1] = float(self.cash[a])
+            ob[4 * self.L + 2] = time_left
+            ob[4 * self.L + 3] = float(self.exec_target - self.exec_done) if a == 0 else 0.0
+            ob[4 * self.L + 4] = float(rest[a])
 
     def _mm_reward(self, mid_before, mid_after):
         """Eqs. 3-4 from the fill list, with exact fractions, returned in quarter ticks."""

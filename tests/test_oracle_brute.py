@@ -90,3 +90,52 @@ def test_oracle_matches_brute_replay_only():
             fl = o.fills(0)
             _compare(o, b, 0, [(f["maker_id"], f["taker_id"], f["px"], f["qty"], f["msg_idx"], f["taker_side"])
                                for f in fl])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_oracle_matches_brute_episodes(seed):
+    """Episode mode over one shared stream: overlapping starts, snapshots with
+    empty sides, several episodes per env, both action modes."""
+    rng = np.random.default_rng(900 + seed)
+    cap = int(rng.integers(2, 9))
+    T = int(rng.integers(2, 5))
+    n_data = 30
+    n_env = 3
+    model = mbogen.MessageModel(price_p=float(rng.uniform(0.4, 0.8)), size_p=0.3,
+                                msgs_per_step=int(rng.integers(3, 20)), mix_market=0.15)
+    st = mbogen.generate(model, mbogen.env_seeds(2000 + seed, 1), n_data)
+    start_steps = rng.integers(0, n_data - T + 1, size=int(rng.integers(1, 6)))
+    starts, levels = mbogen.start_books(seed, st.mids[0], start_steps, cap, min_levels=0)
+    host = seed % 2 == 0
+    kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)),
+              exec_target=int(rng.integers(5, 40)), exec_dir=int(rng.choice([-1, 1])), start_px=10_000,
+              reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=30, inv_penalty=int(rng.integers(0, 2)),
+              exec_penalty_milli=int(rng.choice([0, 100])))
+    seeds = mbogen.env_seeds(3000 + seed, n_env)
+    o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
+    o.set_episodes(st.msgs, st.offsets[0], starts, levels)
+    o.reset(seeds)
+    brutes = []
+    for e in range(n_env):
+        b = brute_lob.BruteEnv(cap, n_agents=2, seed=int(seeds[e]), action_mode=0 if host else 1, **kw)
+        b.set_episodes(st.msgs, st.offsets[0], starts, levels)
+        b.begin_episode(0)
+        b.reset_obs()
+        brutes.append(b)
+    obs, _, _ = o.observe()
+    for e in range(n_env):
+        np.testing.assert_array_equal(obs[e], np.array(brutes[e].obs, np.float32))
+    for t in range(4 * T + 1):
+        acts = rng.integers(0, 12, size=(n_env, 2)).astype(np.int32) if host else None
+        o.step(acts)
+        obs, rew, done = o.observe()
+        for e in range(n_env):
+            b = brutes[e]
+            b.step_episode(None if acts is None else acts[e].tolist())
+            fl = o.fills(e)
+            _compare(o, b, e, [(f["maker_id"], f["taker_id"], f["px"], f["qty"], f["msg_idx"], f["taker_side"])
+                               for f in fl])
+            np.testing.assert_array_equal(obs[e], np.array(b.obs, np.float32))
+            assert rew[e].tolist() == b.rew
+            assert int(done[e]) == b.done
+            assert o.episode_starts()[e] == b.ep_start

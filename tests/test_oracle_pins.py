@@ -382,3 +382,98 @@ def test_arrival_stamps_unique_and_increasing():
         live = np.concatenate([ts[0, :n2[0]], ts[1, :n2[1]]])
         assert len(set(live.tolist())) == len(live)
         assert np.all(live < misc[e, 0])
+
+
+# ---------------------------------------------------------------- episodes
+
+def _episode_inputs(g, levels_per_side=4):
+    msgs, off = single_env_stream(g["data_steps"])
+    n = len(g["starts"])
+    starts = np.zeros(n, oracle.START_DTYPE)
+    levels = np.zeros((n, 2, levels_per_side, 2), np.int32)
+    for j, s in enumerate(g["starts"]):
+        starts[j] = (s["data_step"], s["last_px"], len(s["bids"]), len(s["asks"]))
+        for side, key in enumerate(("bids", "asks")):
+            for i, lv in enumerate(s[key]):
+                levels[j, side, i] = lv
+    return msgs, off[0], starts, levels
+
+
+def _labelled_book(o, env=0):
+    out = []
+    for side in _book_rows(o, env):
+        rows = []
+        for px, q, oid, ts in side:
+            init = oid >= oracle.INIT_ID
+            rows.append([px, q, "init" if init else "bg", oid - oracle.INIT_ID if init else oid, ts])
+        out.append(rows)
+    return out
+
+
+def test_hand_worked_episodes_over_shared_stream():
+    g = _gold("episodes.json")
+    c = g["config"]
+    msgs, step_off, starts, levels = _episode_inputs(g)
+    o = oracle.Oracle(1, n_agents=2, cap=c["cap"], top_levels=c["top_levels"], episode_len=c["episode_len"],
+                      exec_target=c["exec_target"], exec_dir=c["exec_dir"], mm_lot=c["mm_lot"],
+                      start_px=c["start_px"], action_mode=0, trace=1)
+    o.set_episodes(msgs, step_off, starts, levels)
+    o.reset(np.array([c["seed"]], np.uint64))
+    r = g["reset"]
+    assert o.episode_starts().tolist() == [r["episode_start"]]
+    assert _labelled_book(o) == [r["bids"], r["asks"]]
+    obs, _, _ = o.observe()
+    np.testing.assert_array_equal(obs[0, 0], np.array(r["obs"], np.float32))
+    for s in g["steps"]:
+        assert o.step(np.array([s["actions"]], np.int32)) == 0
+        assert o.episode_starts().tolist() == [s["episode_start"]]
+        assert _labelled_book(o) == [s["bids"], s["asks"]]
+        fills = [[int(f["maker_id"]) - oracle.INIT_ID if f["maker_id"] >= oracle.INIT_ID else int(f["maker_id"]),
+                  int(f["taker_id"]), int(f["px"]), int(f["qty"])] for f in o.fills(0)]
+        assert fills == s["fills"]
+        obs, rew, done = o.observe()
+        np.testing.assert_array_equal(obs[0, 0], np.array(s["obs"], np.float32))
+        np.testing.assert_array_equal(obs[0, 1], np.array(s["obs"], np.float32))
+        assert rew[0].tolist() == s["rewards"]
+        assert int(done[0]) == s["done"]
+    cnt = dict(zip(oracle.COUNTER_NAMES, o.counters()[0].tolist()))
+    for k, v in g["final_counters"].items():
+        assert cnt[k] == v, k
+
+
+def test_episode_start_draws_match_restatement():
+    """The start of episode k is snapshot Lemire(first SplitMix64 output keyed
+    by (seed, k), n_starts): checked against the brute env's own SplitMix64."""
+    import brute_lob
+    n_data, T = 40, 3
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=5), mbogen.env_seeds(5, 1), n_data)
+    starts, levels = mbogen.start_books(9, st.mids[0], np.arange(0, n_data - T + 1, 2), 3)
+    seeds = mbogen.env_seeds(44, 16)
+    o = oracle.Oracle(16, n_agents=0, cap=8, episode_len=T)
+    o.set_episodes(st.msgs, st.offsets[0], starts, levels)
+    o.reset(seeds)
+    for k in range(5):
+        want = [int(starts[brute_lob.bounded(brute_lob.keyed_draws(int(s), k, brute_lob.TAG_EPISODE, 1)[0],
+                                             len(starts))]["data_step"]) for s in seeds]
+        assert o.episode_starts().tolist() == want
+        for _ in range(T):
+            o.step()
+
+
+def test_episodes_counters_accumulate_and_books_restart():
+    """Across an episode boundary the book is exactly the drawn snapshot and
+    counters keep counting; with one snapshot every episode replays the same data."""
+    n_data, T = 12, 4
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=30), mbogen.env_seeds(6, 1), n_data)
+    starts, levels = mbogen.start_books(2, st.mids[0], [3], 6, min_levels=2)
+    o = oracle.Oracle(2, n_agents=2, cap=16, episode_len=T, action_mode=1, exec_target=20)
+    o.set_episodes(st.msgs, st.offsets[0], starts, levels)
+    o.reset(mbogen.env_seeds(7, 2))
+    first = _book_rows(o)
+    msgs_per_episode = int(st.offsets[0, 3 + T] - st.offsets[0, 3])
+    for ep in range(3):
+        for _ in range(T):
+            o.step()
+        assert _book_rows(o) == first
+        assert o.counters()[0][oracle.COUNTER_NAMES.index("msgs")] >= (ep + 1) * msgs_per_episode
+        assert o.agents()[0].tolist() == [[0, 0, 0, 0], [0, 0, 0, 0]]
