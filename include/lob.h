@@ -155,17 +155,60 @@ int lob_destroy(lob_handle *h);   /* frees device state; synchronises the device
 int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets,
                       int32_t n_steps, int64_t stride);
 
-/* Start a new episode in every env: empty books, zero agent state and
- * counters, step t = 0.  d_env_seeds: device [n_envs] uint64 keys for the
- * shuffle and the random policy.  The observation buffer then holds the reset
- * observation (empty book: all levels (0, 0), zero inventory and cash, time
- * left 1, the full execution target for agent 0). */
+/* ---- Episodes over one shared message stream (Sec. 3: the whole data set
+ * in one contiguous array, runtime indexing of episode starts, episodes free
+ * to overlap; the book at an episode start initialised from the state of the
+ * book at that time).
+ *
+ * d_msgs / d_step_offsets (device, borrowed, must stay alive): data step d
+ * covers d_msgs[d_step_offsets[d] .. d_step_offsets[d + 1]), d < n_data_steps.
+ * h_starts [n_starts] and h_levels [n_starts][2][levels_per_side][2] (host,
+ * copied): snapshot j starts episodes at data step h_starts[j].data_step
+ * (<= n_data_steps - T) with last trade price last_px; levels (price,
+ * quantity) best first, side 0 bids (prices strictly falling), side 1 asks
+ * (strictly rising), n_bid / n_ask of them (<= levels_per_side and <= the
+ * capacity), quantities >= 1, best bid < best ask when both sides exist.
+ *
+ * In episode mode episode k of env e starts at snapshot
+ * j = Lemire(SplitMix64 output 1 from key(seed_e, k, LOB_TAG_EPISODE), n_starts)
+ * (key(s, k, tag) = mix(mix(s ^ tag) + GAMMA (k + 1)), the keying of the
+ * shuffle and the random policy): its book is the snapshot's levels as one
+ * resting order each, bids then asks, best first, arrival stamps 0, 1, ...,
+ * ids LOB_INIT_ID + the same index; agents start flat.  Step t reads data
+ * step start + (t mod T).  After an episode's last step the env starts the
+ * next episode at once: that step reports its own rewards and done = 1 with
+ * the new episode's first observation.  Steps never run out (no LOB_ESTATE
+ * at t == T).  Requires one capacity for all envs (no h_caps at create).
+ * The mode holds until lob_load_messages; either call requires lob_reset
+ * before the next step.  LOB_EINVAL on a table that breaks the rules above. */
+#define LOB_INIT_ID 0x4000000000000000LL
+#define LOB_TAG_EPISODE 0x4550495344450003ULL
+typedef struct lob_start {
+    int32_t data_step;
+    int32_t last_px;
+    int32_t n_bid, n_ask;
+} lob_start;
+int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                     const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
+                     int64_t n_starts);
+/* Device int32 [n_envs]: the first data step of every env's current episode
+ * (episode mode; 0 otherwise). */
+int lob_get_episode_starts(lob_handle *h, int32_t *d_out, void *stream);
+
+/* Start a new episode in every env: zero agent state and counters, step
+ * t = 0, and an empty book (episode mode: the book of the drawn snapshot).
+ * d_env_seeds: device [n_envs] uint64 keys for the shuffle, the random policy
+ * and the episode draws.  The observation buffer then holds the reset
+ * observation (the starting book's levels -- all (0, 0) for an empty book --,
+ * zero inventory and cash, time left 1, the full execution target for
+ * agent 0). */
 int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream);
 
 /* One environment step for every env (stages 1-5 above), consuming the next
  * window step of bound messages.  d_actions: device int32 [n_envs][2] in
  * LOB_ACT_HOST mode, ignored (may be NULL) otherwise.  Fails with LOB_ESTATE
- * when the episode is over (t == T) or the window is exhausted. */
+ * when the episode is over (t == T) or the window is exhausted (outside
+ * episode mode). */
 int lob_step(lob_handle *h, const int32_t *d_actions, void *stream);
 
 /* Outputs of the last step: d_obs float [n_envs][n_agents][obs_dim],

@@ -168,6 +168,15 @@ struct lob_handle {
     size_t stage_cap = 0;
     int64_t *d_stage_off = nullptr;
     int32_t *d_stage_act = nullptr;
+    // episode mode (one shared stream, snapshot table, auto-reset)
+    bool ep_mode = false;
+    const int64_t *ep_off = nullptr;
+    int64_t n_data_steps = 0;
+    int32_t n_starts = 0;
+    lob_start *d_ep_starts = nullptr;
+    int32_t *d_ep_levels = nullptr;
+    unsigned char *d_ep_images = nullptr;
+    float *d_ep_obs = nullptr;
 };
 
 static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LOB_OK : LOB_ECUDA; }
@@ -180,7 +189,8 @@ static void free_all(lob_handle *h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     void *ptrs[] = {h->d_books, h->d_book_off, h->d_canon_off, h->d_caps, h->d_state, h->d_counters,
                     h->d_seeds, h->d_status, h->d_obs, h->d_rew, h->d_done, h->d_act, h->d_env_list,
-                    h->d_queue, h->d_stage_msgs, h->d_stage_off, h->d_stage_act};
+                    h->d_queue, h->d_stage_msgs, h->d_stage_off, h->d_stage_act, h->d_ep_starts,
+                    h->d_ep_levels, h->d_ep_images, h->d_ep_obs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -323,6 +333,8 @@ int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_off
     if (!d_msgs && n_steps > 0) {
         // an all-empty window may pass a NULL message pointer; offsets still needed
     }
+    if (h->ep_mode) h->reset_done = false;   // leaving episode mode: the books need a reset
+    h->ep_mode = false;
     h->msgs = d_msgs;
     h->offsets = d_offsets;
     h->win_steps = n_steps;
@@ -351,6 +363,95 @@ __global__ void k_reset(EnvState *st, long long *cnt, unsigned long long *seeds_
     st[e] = z;
     for (int i = 0; i < LOB_NCOUNTERS; i++) cnt[(long long)e * LOB_NCOUNTERS + i] = 0;
     seeds_dst[e] = seeds_src[e];
+}
+
+// Episode-start book images in the book block layout (priority order: px,
+// qty int32 [2][S], then id, ts int64 [2][S]); one block per snapshot.
+__global__ void k_ep_images(const lob_start *starts, const int *levels, int ls, int slots, long long block,
+                            unsigned char *images) {
+    const int j = blockIdx.x;
+    const lob_start st = starts[j];
+    unsigned char *blk = images + (long long)j * block;
+    int *px = reinterpret_cast<int *>(blk);
+    int *qt = px + 2 * slots;
+    long long *id = reinterpret_cast<long long *>(blk + 16LL * slots);
+    long long *ts = id + 2 * slots;
+    for (int i = threadIdx.x; i < 2 * slots; i += blockDim.x) {
+        const int sd = i / slots, q = i % slots;
+        const int n = sd == 0 ? st.n_bid : st.n_ask;
+        const bool live = q < n;
+        const int *lv = levels + (((long long)j * 2 + sd) * ls + (live ? q : 0)) * 2;
+        const long long idx = (sd == 0 ? 0 : st.n_bid) + q;   // bids, then asks, best first
+        px[i] = live ? lv[0] : 0;
+        qt[i] = live ? lv[1] : 0;
+        id[i] = live ? LOB_INIT_ID + idx : 0;
+        ts[i] = live ? idx : 0;
+    }
+}
+
+// First observation of an episode started at each snapshot: its levels
+// against anchor floor((bb + ba) / 2) (an empty side's touch is the last
+// trade price), flat agents, time left 1, the full target for agent 0.
+__global__ void k_ep_obs(const lob_start *starts, const int *levels, int ls, int A, int D, int L, int exec_target,
+                         float *obs) {
+    const int j = blockIdx.x;
+    const lob_start st = starts[j];
+    const int *bl = levels + (long long)j * 2 * ls * 2;
+    const int *al = bl + ls * 2;
+    const long long bb = st.n_bid > 0 ? bl[0] : st.last_px;
+    const long long ba = st.n_ask > 0 ? al[0] : st.last_px;
+    const long long s2 = bb + ba;
+    const long long anchor = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
+    for (int i = threadIdx.x; i < A * D; i += blockDim.x) {
+        const int a = i / D, f = i % D;
+        float v = 0.0f;
+        if (f < 4 * L) {
+            const int sd = f >= 2 * L ? 1 : 0;
+            const int lvl = (f - sd * 2 * L) >> 1;
+            const int n = sd == 0 ? st.n_bid : st.n_ask;
+            const int *lv = (sd == 0 ? bl : al) + lvl * 2;
+            if (lvl < n) v = __ll2float_rn((f & 1) ? (long long)lv[1] : (long long)lv[0] - anchor);
+        } else if (f == 4 * L + 2) {
+            v = 1.0f;
+        } else if (f == 4 * L + 3 && a == 0) {
+            v = __ll2float_rn(exec_target);
+        }
+        obs[(long long)j * A * D + i] = v;
+    }
+}
+
+// Episode-mode reset: each env draws its first snapshot, copies its image
+// into the env's book block and starts from it.
+__global__ void k_reset_ep(EnvState *st, long long *cnt, unsigned long long *seeds_dst,
+                           const unsigned long long *seeds_src, int n, unsigned char *books,
+                           const long long *book_off, const unsigned char *images, long long block,
+                           const lob_start *starts, int n_starts, const float *ep_obs, float *obs, int A, int D) {
+    const int e = blockIdx.x;
+    if (e >= n) return;
+    const unsigned long long seed = seeds_src[e];
+    const unsigned j = bounded(sm_mix(step_key(seed, 0, LOB_TAG_EPISODE) + GAMMA), (unsigned)n_starts);
+    const int4 *src = reinterpret_cast<const int4 *>(images + (long long)j * block);
+    int4 *dst = reinterpret_cast<int4 *>(books + book_off[e]);
+    for (long long i = threadIdx.x; i < block / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < A * D; i += blockDim.x) obs[(long long)e * A * D + i] = ep_obs[(long long)j * A * D + i];
+    if (threadIdx.x < LOB_NCOUNTERS) cnt[(long long)e * LOB_NCOUNTERS + threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        const lob_start S = starts[j];
+        EnvState z;
+        memset(&z, 0, sizeof(z));
+        z.ts_next = S.n_bid + S.n_ask;
+        z.last_px = S.last_px;
+        z.n[0] = S.n_bid;
+        z.n[1] = S.n_ask;
+        z.ep_start = S.data_step;
+        st[e] = z;
+        seeds_dst[e] = seed;
+    }
+}
+
+__global__ void k_get_ep_start(const EnvState *st, int *out, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = st[e].ep_start;
 }
 
 // internal blocked layout -> canonical priority-ordered record per env
@@ -398,6 +499,15 @@ __global__ void k_get_agents(const EnvState *st, long long *out, int n, int A, i
     }
 }
 
+// Whether n more steps may run: episode mode never runs out; otherwise the
+// bound window and the episode bound the steps.
+static bool steps_left(const lob_handle *h, int n) {
+    if (!h->reset_done) return false;
+    if (h->ep_mode) return (int64_t)h->t + n <= 0x7fffffffLL;
+    return h->offsets && h->cursor + n <= h->win_steps && h->t + n <= h->cfg.episode_len;
+}
+static const int64_t *step_offsets(const lob_handle *h) { return h->ep_mode ? h->ep_off : h->offsets; }
+
 static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
                         int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
                         long long *rew, unsigned char *done, cudaStream_t s) {
@@ -420,6 +530,14 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
     set_rewards(p, c);
+    if (h->ep_mode) {
+        p.ep_mode = 1;
+        p.n_starts = h->n_starts;
+        p.ep_block = h->uni_block;
+        p.ep_starts = h->d_ep_starts;
+        p.ep_images = h->d_ep_images;
+        p.ep_obs = h->d_ep_obs;
+    }
     const int wpb = h->wpb;
     if (h->persistent) {
         if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
@@ -454,10 +572,85 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
 
 extern "C" {
 
+int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                     const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
+                     int64_t n_starts) {
+    if (!h || !d_step_offsets || !h_starts || !h_levels || levels_per_side < 1 || n_starts < 1 ||
+        n_starts > 0x7fffffffLL || n_data_steps < h->cfg.episode_len || !h->uniform_cap)
+        return LOB_EINVAL;
+    const int cap = h->cfg.cap_per_side, T = h->cfg.episode_len;
+    const int ls = levels_per_side;
+    for (int64_t j = 0; j < n_starts; j++) {
+        const lob_start &S = h_starts[j];
+        if (S.data_step < 0 || (int64_t)S.data_step + T > n_data_steps) return LOB_EINVAL;
+        if (S.n_bid < 0 || S.n_ask < 0 || S.n_bid > ls || S.n_ask > ls || S.n_bid > cap || S.n_ask > cap)
+            return LOB_EINVAL;
+        const int32_t *bl = h_levels + (size_t)j * 2 * ls * 2, *al = bl + (size_t)ls * 2;
+        for (int i = 0; i < S.n_bid; i++)
+            if (bl[2 * i + 1] < 1 || (i > 0 && bl[2 * i] >= bl[2 * i - 2])) return LOB_EINVAL;
+        for (int i = 0; i < S.n_ask; i++)
+            if (al[2 * i + 1] < 1 || (i > 0 && al[2 * i] <= al[2 * i - 2])) return LOB_EINVAL;
+        if (S.n_bid > 0 && S.n_ask > 0 && bl[0] >= al[0]) return LOB_EINVAL;
+    }
+    void *old[] = {h->d_ep_starts, h->d_ep_levels, h->d_ep_images, h->d_ep_obs};
+    if (cudaDeviceSynchronize() != cudaSuccess) return LOB_ECUDA;
+    for (void *p : old)
+        if (p) cudaFree(p);
+    h->d_ep_starts = nullptr; h->d_ep_levels = nullptr; h->d_ep_images = nullptr; h->d_ep_obs = nullptr;
+    h->ep_mode = false;
+    h->reset_done = false;
+    const size_t A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
+    const size_t lv_bytes = (size_t)n_starts * 2 * ls * 2 * 4;
+    if (cudaMalloc(&h->d_ep_starts, (size_t)n_starts * sizeof(lob_start)) != cudaSuccess ||
+        cudaMalloc(&h->d_ep_levels, lv_bytes) != cudaSuccess ||
+        cudaMalloc(&h->d_ep_images, (size_t)n_starts * (size_t)h->uni_block) != cudaSuccess ||
+        cudaMalloc(&h->d_ep_obs, (size_t)n_starts * (A * D > 0 ? A * D : 1) * 4) != cudaSuccess)
+        return LOB_ENOMEM;
+    if (cudaMemcpy(h->d_ep_starts, h_starts, (size_t)n_starts * sizeof(lob_start), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(h->d_ep_levels, h_levels, lv_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return LOB_ECUDA;
+    const int slots = 32 * CLASS_K[class_of(cap)];   // pool slots per side of this capacity
+    k_ep_images<<<(unsigned)n_starts, 128>>>(h->d_ep_starts, h->d_ep_levels, ls, slots, h->uni_block,
+                                              h->d_ep_images);
+    h->launches++;
+    if (A > 0) {
+        k_ep_obs<<<(unsigned)n_starts, 128>>>(h->d_ep_starts, h->d_ep_levels, ls, (int)A, (int)D,
+                                               h->cfg.top_levels, h->cfg.exec_target, h->d_ep_obs);
+        h->launches++;
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return LOB_ECUDA;
+    h->ep_mode = true;
+    h->msgs = d_msgs;
+    h->ep_off = d_step_offsets;
+    h->n_data_steps = n_data_steps;
+    h->n_starts = (int32_t)n_starts;
+    return LOB_OK;
+}
+
+int lob_get_episode_starts(lob_handle *h, int32_t *d_out, void *stream) {
+    if (!h || !d_out) return LOB_EINVAL;
+    const int n = h->cfg.n_envs;
+    k_get_ep_start<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->d_state, d_out, n);
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
 int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
     if (!h || !d_env_seeds) return LOB_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->cfg.n_envs;
+    if (h->ep_mode) {
+        k_reset_ep<<<n, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
+                                     reinterpret_cast<const unsigned long long *>(d_env_seeds), n, h->d_books,
+                                     h->d_book_off, h->d_ep_images, h->uni_block, h->d_ep_starts, h->n_starts,
+                                     h->d_ep_obs, h->d_obs, h->cfg.n_agents, h->D);
+        h->launches++;
+        if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+        h->t = 0;
+        h->reset_done = true;
+        return LOB_OK;
+    }
     k_reset<<<(n + 127) / 128, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                              reinterpret_cast<const unsigned long long *>(d_env_seeds), n,
                                              h->cfg.start_px, h->d_obs, h->cfg.n_agents, h->D, h->cfg.top_levels,
@@ -471,10 +664,9 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
 
 int lob_step(lob_handle *h, const int32_t *d_actions, void *stream) {
     if (!h) return LOB_EINVAL;
-    if (!h->reset_done || !h->offsets || h->cursor >= h->win_steps || h->t >= h->cfg.episode_len)
-        return LOB_ESTATE;
+    if (!steps_left(h, 1)) return LOB_ESTATE;
     if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
-    int rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, 1, d_actions, 0, h->d_obs, h->d_rew,
+    int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, d_actions, 0, h->d_obs, h->d_rew,
                           h->d_done, (cudaStream_t)stream);
     if (rc != LOB_OK) return rc;
     h->cursor++;
@@ -485,12 +677,10 @@ int lob_step(lob_handle *h, const int32_t *d_actions, void *stream) {
 int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float *d_obs, int64_t *d_rewards,
                 uint8_t *d_done, void *stream) {
     if (!h || n_steps < 1) return LOB_EINVAL;
-    if (!h->reset_done || !h->offsets || h->cursor + n_steps > h->win_steps ||
-        h->t + n_steps > h->cfg.episode_len)
-        return LOB_ESTATE;
+    if (!steps_left(h, n_steps)) return LOB_ESTATE;
     if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, n_steps, d_actions,
+    int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, n_steps, d_actions,
                           2LL * h->cfg.n_envs, d_obs, reinterpret_cast<long long *>(d_rewards), d_done, s);
     if (rc != LOB_OK) return rc;
     // keep the last step's outputs for lob_observe
@@ -518,7 +708,7 @@ int lob_observe(lob_handle *h, float *d_obs, int64_t *d_rewards, uint8_t *d_done
 int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets, const int32_t *h_actions,
                   float *h_obs, int64_t *h_rewards, uint8_t *h_done, void *stream) {
     if (!h || !h_offsets) return LOB_EINVAL;
-    if (!h->reset_done || h->t >= h->cfg.episode_len) return LOB_ESTATE;
+    if (!h->reset_done || h->ep_mode || h->t >= h->cfg.episode_len) return LOB_ESTATE;
     const lob_config &c = h->cfg;
     if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST && !h_actions) return LOB_EINVAL;
     const int n = c.n_envs;
@@ -781,8 +971,7 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
     if (h->cfg.n_agents != 2 || h->cfg.action_mode != LOB_ACT_HOST) return LOB_EINVAL;
     if (policy_n_agents(pol) != 2 || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
     if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
-    if (!h->reset_done || !h->offsets || h->cursor + n_steps > h->win_steps || h->t + n_steps > h->cfg.episode_len)
-        return LOB_ESTATE;
+    if (!steps_left(h, n_steps)) return LOB_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D;
     for (int i = 0; i < n_steps; i++) {
@@ -792,7 +981,7 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
         if (d_actions && cudaMemcpyAsync(d_actions + (size_t)i * n * 2, h->d_act, n * 2 * 4,
                                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return LOB_ECUDA;
-        rc = launch_steps(h, h->msgs, h->offsets, h->stride, h->cursor, 1, h->d_act, 0, h->d_obs, h->d_rew,
+        rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, h->d_act, 0, h->d_obs, h->d_rew,
                           h->d_done, s);
         if (rc != LOB_OK) return rc;
         h->cursor++;
@@ -859,6 +1048,7 @@ extern "C" int lob_save(lob_handle *h, void *dst, void *stream) {
     hd.n_agents = h->cfg.n_agents;
     hd.D = h->D;
     hd.cap_sig = cap_signature(h);
+    hd.pad[0] = h->ep_mode ? 1 : 0;
     char *out = static_cast<char *>(dst);
     if (cudaMemcpyAsync(out, &hd, sizeof(hd), cudaMemcpyDefault, s) != cudaSuccess) return LOB_ECUDA;
     size_t off = sizeof(hd);
@@ -878,7 +1068,7 @@ extern "C" int lob_load(lob_handle *h, const void *src, void *stream) {
         return LOB_ECUDA;
     if (hd.magic != CKPT_MAGIC || hd.n_envs != h->cfg.n_envs || hd.book_bytes != h->book_bytes ||
         hd.n_agents != h->cfg.n_agents || hd.D != h->D || hd.cap_sig != cap_signature(h) || hd.t < 0 ||
-        hd.t > h->cfg.episode_len)
+        hd.pad[0] != (h->ep_mode ? 1 : 0) || (!h->ep_mode && hd.t > h->cfg.episode_len))
         return LOB_EINVAL;
     const char *in = static_cast<const char *>(src);
     size_t off = sizeof(hd);
@@ -887,6 +1077,17 @@ extern "C" int lob_load(lob_handle *h, const void *src, void *stream) {
         off += r.bytes;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return LOB_ECUDA;
+    if (h->ep_mode) {
+        // every env's episode must lie inside the data this handle now indexes
+        std::vector<EnvState> st((size_t)h->cfg.n_envs);
+        if (cudaMemcpy(st.data(), h->d_state, st.size() * sizeof(EnvState), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return LOB_ECUDA;
+        for (const EnvState &x : st)
+            if (x.ep_start < 0 || (int64_t)x.ep_start + h->cfg.episode_len > h->n_data_steps) {
+                h->reset_done = false;
+                return LOB_EINVAL;
+            }
+    }
     h->t = hd.t;
     h->cursor = hd.cursor;
     h->reset_done = true;

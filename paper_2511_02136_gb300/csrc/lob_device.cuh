@@ -53,7 +53,8 @@ struct __align__(16) EnvState {
     int n[2];
     int act[2];
     int t;
-    int pad[8];
+    int ep_start;          // episode mode: first data step of the current episode
+    int pad[7];
 };
 static_assert(sizeof(EnvState) == 128, "env state");
 
@@ -96,6 +97,14 @@ struct KParams {
     int reward_mode, lam_pct;        // market maker's reward (Eq. 1, 4 or 3), lambda in percent
     long long inv_penalty;           // rho of the quadratic inventory penalty
     long long exec_pen_milli;        // unfilled-task penalty, thousandths of a tick per unit
+    // episode mode (one shared stream; offsets index data steps): start table,
+    // prebuilt book images (ep_block bytes each) and first observations
+    int ep_mode;
+    int n_starts;
+    long long ep_block;
+    const lob_start *ep_starts;
+    const unsigned char *ep_images;
+    const float *ep_obs;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -899,9 +908,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     const unsigned long long seed = p.seeds[e];
     long long *cnt = p.counters + (long long)e * LOB_NCOUNTERS;
 
-    // first message window, issued before anything waits on memory
-    long long mb = p.offsets[(long long)e * p.off_stride + p.k0];
-    long long me = p.offsets[(long long)e * p.off_stride + p.k0 + 1];
+    // first message window, issued before anything waits on memory.  dcur is
+    // the offsets index of the step's data: the env's window position, or in
+    // episode mode its episode's first data step plus the step within it.
+    int ep_start = p.ep_mode ? st->ep_start : 0;
+    long long dcur = p.ep_mode ? (long long)ep_start + p.t0 % p.T : (long long)e * p.off_stride + p.k0;
+    long long mb = p.offsets[dcur];
+    long long me = p.offsets[dcur + 1];
 
     Side<K> bid, ask;
     side_load<K, true>(bid, sm.pool[0], blk, lane);
@@ -937,9 +950,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
 
     for (int step = 0; step < p.n_steps && !timed_out; step++) {
         const int t = p.t0 + step;
+        const int te = p.ep_mode ? t % p.T : t;   // step within the episode
         if (step > 0) {
-            mb = p.offsets[(long long)e * p.off_stride + p.k0 + step];
-            me = p.offsets[(long long)e * p.off_stride + p.k0 + step + 1];
+            mb = p.offsets[dcur];
+            me = p.offsets[dcur + 1];
         }
         const int nmsg = (int)(me - mb);
         const int ntiles = (nmsg + TILE - 1) / TILE;
@@ -1170,6 +1184,12 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         if (timed_out) break;
 
         // ---- 5. step outcomes (and, after the last step, the book write-back)
+        // Episode mode: after the episode's last step the env starts the next
+        // episode from snapshot ep_j; the step reports that episode's first
+        // observation with its own rewards and done flag.
+        const bool ep_end = p.ep_mode && te + 1 == p.T;
+        const unsigned ep_j =
+            ep_end ? bounded(sm_mix(step_key(seed, t / p.T + 1, LOB_TAG_EPISODE) + GAMMA), (unsigned)p.n_starts) : 0u;
         __syncwarp();
         const long long obs_base = ((long long)step * p.n_envs + e);
         if (A > 0) {
@@ -1194,11 +1214,14 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             long long r0 = (long long)((unsigned long long)pv0 - (unsigned long long)c.pv0);
             long long r1 = (long long)((unsigned long long)pv1 - (unsigned long long)c.pv1);
             c.pv0 = pv0; c.pv1 = pv1;
-            const float tl = __fdiv_rn((float)(p.T - (t + 1)), (float)p.T);
+            const float tl = __fdiv_rn((float)(p.T - (te + 1)), (float)p.T);
             const int D = p.D;
             __syncwarp();
             float *ob = p.obs ? p.obs + obs_base * A * D : nullptr;
-            if (ob) {
+            if (ob && ep_end) {
+                const float *src = p.ep_obs + (long long)ep_j * A * D;
+                for (int i = lane; i < A * D; i += 32) ob[i] = src[i];
+            } else if (ob) {
                 // level entries: the same for both agents
                 for (int idx = lane; idx < 4 * L; idx += 32) {
                     const int sd = idx >= 2 * L ? 1 : 0;
@@ -1226,7 +1249,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             if (lane == 0) {
                 if (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0) {
                     const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
-                                                        t + 1 == p.T, (long long)p.exec_target - c.exec_done,
+                                                        te + 1 == p.T, (long long)p.exec_target - c.exec_done,
                                                         sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
                     r0 = r.x; r1 = r.y;
                 }
@@ -1234,10 +1257,31 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 if (p.act_out) { p.act_out[2LL * e] = act0; p.act_out[2LL * e + 1] = act1; }
             }
         }
-        if (lane == 0 && p.done) p.done[obs_base] = (unsigned char)(t + 1 == p.T);
+        if (lane == 0 && p.done) p.done[obs_base] = (unsigned char)(te + 1 == p.T);
         if (TRACE && lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
         if (TRACE && lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
+        if (ep_end) {
+            // the next episode: snapshot book, flat agents, its first data step
+            const lob_start S = p.ep_starts[ep_j];
+            const unsigned char *img = p.ep_images + (long long)ep_j * p.ep_block;
+            __syncwarp();
+            side_load<K, true>(bid, sm.pool[0], img, lane);
+            side_load<K, false>(ask, sm.pool[1], img, lane);
+            side_set_count<K>(bid, S.n_bid, lane);
+            side_set_count<K>(ask, S.n_ask, lane);
+            __syncwarp();
+            front_refresh<K>(bid, sm.pool[0]);
+            front_refresh<K>(ask, sm.pool[1]);
+            c.ts_next = S.n_bid + S.n_ask;
+            c.seq_next = 0;
+            c.inv0 = 0; c.inv1 = 0; c.cash0 = 0; c.cash1 = 0; c.pv0 = 0; c.pv1 = 0; c.exec_done = 0;
+            c.last_px = S.last_px;
+            ep_start = S.data_step;
+            dcur = S.data_step;
+        } else {
+            dcur++;
+        }
         if (step + 1 == p.n_steps) {
             side_store<K, true>(bid, sm.pool[0], blk, lane);
             side_store<K, false>(ask, sm.pool[1], blk, lane);
@@ -1260,6 +1304,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         st->pv_prev[0] = c.pv0; st->pv_prev[1] = c.pv1; st->exec_done = c.exec_done;
         st->last_px = c.last_px; st->n[0] = bid.n; st->n[1] = ask.n;
         st->t = p.t0 + p.n_steps;
+        st->ep_start = ep_start;
     }
 }
 

@@ -46,10 +46,12 @@ EXPORTS = [
     "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
-    "lob_checkpoint_bytes", "lob_save", "lob_load",
+    "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
+LOB_INIT_ID = 0x4000000000000000
+START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
 POLICY_HIDDEN = 128
 LOB_NOALLOC_MAX_ENVS = 16384
 
@@ -157,6 +159,8 @@ def _load():
         "lob_checkpoint_bytes": (I64, [P]),
         "lob_save": (ctypes.c_int, [P, P, P]),
         "lob_load": (ctypes.c_int, [P, P, P]),
+        "lob_set_episodes": (ctypes.c_int, [P, P, P, I64, P, P, I32, I64]),
+        "lob_get_episode_starts": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -297,6 +301,22 @@ def lob_load(h, src, stream=None):
     return _check(_load().lob_load(h, _anyp(src), _stream(stream)), "lob_load")
 
 
+def lob_set_episodes(h, msgs_dev, step_offsets_dev, starts, levels):
+    """Episode mode over one shared stream.  msgs_dev / step_offsets_dev: device
+    tensors (32-byte records; int64 [n_data_steps + 1]); starts START_DTYPE[n]
+    and levels int32 [n, 2, levels_per_side, 2] on the host (copied)."""
+    starts = np.ascontiguousarray(starts, dtype=START_DTYPE)
+    levels = np.ascontiguousarray(levels, dtype=np.int32)
+    n_data = step_offsets_dev.shape[0] - 1
+    return _check(_load().lob_set_episodes(h, _dp(msgs_dev), _dp(step_offsets_dev), n_data,
+                                           starts.ctypes.data, levels.ctypes.data, levels.shape[2],
+                                           len(starts)), "lob_set_episodes")
+
+
+def lob_get_episode_starts(h, out, stream=None):
+    return _check(_load().lob_get_episode_starts(h, _dp(out), _stream(stream)), "lob_get_episode_starts")
+
+
 def lob_kernel_launches(h) -> int:
     return _load().lob_kernel_launches(h)
 
@@ -408,6 +428,15 @@ class LobEnv:
         """msgs_dev: uint8/int64 tensor of 32-byte records; offsets_dev int64 [n_envs, n_steps+1]."""
         self._keep = [msgs_dev, offsets_dev]
         lob_load_messages(self.h, msgs_dev, offsets_dev, offsets_dev.shape[1] - 1, offsets_dev.shape[1])
+
+    def set_episodes(self, msgs_dev, step_offsets_dev, starts, levels):
+        self._keep = [msgs_dev, step_offsets_dev]
+        lob_set_episodes(self.h, msgs_dev, step_offsets_dev, starts, levels)
+
+    def episode_starts(self):
+        out = self.torch.zeros(self.n_envs, dtype=self.torch.int32, device=self.dev)
+        lob_get_episode_starts(self.h, out)
+        return out
 
     def reset(self, seeds_dev, stream=None):
         self._seeds = seeds_dev

@@ -30,7 +30,10 @@ class Pair:
 
     def __init__(self, n_envs, st, *, n_agents=2, cap=100, caps=None, top_levels=10, episode_len=None,
                  mm_lot=1, exec_target=500, exec_dir=-1, action_mode=lob.LOB_ACT_RANDOM, start_px=10_000,
-                 fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1, rewards=None):
+                 fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1, rewards=None,
+                 episodes=None, seeds=None):
+        """episodes: (starts, levels) puts both sides in episode mode over the
+        single shared stream st (env 0 of st); seeds then gives the env seeds."""
         import torch
         self.torch = torch
         T = st.offsets.shape[1] - 1 if episode_len is None else episode_len
@@ -48,11 +51,16 @@ class Pair:
                                  start_px=start_px, n_threads=n_threads, caps=caps, **(rewards or {}))
         self.msgs_d = to_dev(st.msgs) if len(st.msgs) else torch.zeros(32, dtype=torch.uint8, device="cuda")
         self.off_d = to_dev(st.offsets)
-        self.env.load_messages(self.msgs_d, self.off_d)
-        self.orc.load_messages(st.msgs, st.offsets)
-        self.seeds_d = to_dev(st.seeds)
+        if episodes is None:
+            self.env.load_messages(self.msgs_d, self.off_d)
+            self.orc.load_messages(st.msgs, st.offsets)
+        else:
+            self.env.set_episodes(self.msgs_d, self.off_d[0], *episodes)
+            self.orc.set_episodes(st.msgs, st.offsets[0], *episodes)
+        seeds = st.seeds if seeds is None else np.ascontiguousarray(seeds, np.uint64)
+        self.seeds_d = to_dev(seeds)
         self.env.reset(self.seeds_d)
-        self.orc.reset(st.seeds)
+        self.orc.reset(seeds)
         self.fill_cap, self.snap_cap = fill_cap, snap_cap
         if fill_cap or snap_cap:
             C = cap if caps is None else int(caps[0])
@@ -81,6 +89,8 @@ class Pair:
             np.testing.assert_array_equal(rew.cpu().numpy(), o_rew)
             np.testing.assert_array_equal(self.env.actions().cpu().numpy(), self.orc.actions())
         np.testing.assert_array_equal(done.cpu().numpy(), o_done)
+        if self.orc._ep is not None:
+            np.testing.assert_array_equal(self.env.episode_starts().cpu().numpy(), self.orc.episode_starts())
         return g_obs, o_obs
 
     def check_state(self, envs=None):
