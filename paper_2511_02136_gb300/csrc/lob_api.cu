@@ -99,13 +99,15 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     int blocks = (n_list + wpb - 1) / wpb;
     if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
     const size_t smem = (size_t)wpb * warp_smem_bytes(K);
+    // the extended kernel when episode mode or a reward variant is on
+    const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0;
     switch (K) {
-        case 1: return launch_steps_1(trace, blocks, 32 * wpb, smem, s, p);
-        case 2: return launch_steps_2(trace, blocks, 32 * wpb, smem, s, p);
-        case 4: return launch_steps_4(trace, blocks, 32 * wpb, smem, s, p);
-        case 8: return launch_steps_8(trace, blocks, 32 * wpb, smem, s, p);
-        case 16: return launch_steps_16(trace, blocks, 32 * wpb, smem, s, p);
-        default: return launch_steps_32(trace, blocks, 32 * wpb, smem, s, p);
+        case 1: return launch_steps_1(trace, ext, blocks, 32 * wpb, smem, s, p);
+        case 2: return launch_steps_2(trace, ext, blocks, 32 * wpb, smem, s, p);
+        case 4: return launch_steps_4(trace, ext, blocks, 32 * wpb, smem, s, p);
+        case 8: return launch_steps_8(trace, ext, blocks, 32 * wpb, smem, s, p);
+        case 16: return launch_steps_16(trace, ext, blocks, 32 * wpb, smem, s, p);
+        default: return launch_steps_32(trace, ext, blocks, 32 * wpb, smem, s, p);
     }
 }
 

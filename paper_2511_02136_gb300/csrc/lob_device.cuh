@@ -897,8 +897,10 @@ struct MsgPipe {
     unsigned tiles;
 };
 
-// Run n_steps env steps of env e with the book resident on chip.
-template <int K, bool TRACE>
+// Run n_steps env steps of env e with the book resident on chip.  EXT
+// compiles in episode mode and the reward variants; without it those
+// settings are ignored, so the host launches EXT whenever one is set.
+template <int K, bool TRACE, bool EXT>
 __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe, int lane) {
     EnvState *st = p.st + e;
     const bool uni = p.uni_cap > 0;
@@ -908,13 +910,15 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     const unsigned long long seed = p.seeds[e];
     long long *cnt = p.counters + (long long)e * LOB_NCOUNTERS;
 
-    // first message window, issued before anything waits on memory.  dcur is
-    // the offsets index of the step's data: the env's window position, or in
-    // episode mode its episode's first data step plus the step within it.
-    int ep_start = p.ep_mode ? st->ep_start : 0;
-    long long dcur = p.ep_mode ? (long long)ep_start + p.t0 % p.T : (long long)e * p.off_stride + p.k0;
-    long long mb = p.offsets[dcur];
-    long long me = p.offsets[dcur + 1];
+    // first message window, issued before anything waits on memory.  The
+    // offsets index of a step's data is the env's window position, or in
+    // episode mode (dcur) its episode's first data step plus the step within it.
+    const bool ep_mode = EXT && p.ep_mode;
+    int ep_start = ep_mode ? st->ep_start : 0;
+    long long dcur = ep_mode ? (long long)ep_start + p.t0 % p.T : 0;
+    const long long d0 = ep_mode ? dcur : (long long)e * p.off_stride + p.k0;
+    long long mb = p.offsets[d0];
+    long long me = p.offsets[d0 + 1];
 
     Side<K> bid, ask;
     side_load<K, true>(bid, sm.pool[0], blk, lane);
@@ -950,10 +954,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
 
     for (int step = 0; step < p.n_steps && !timed_out; step++) {
         const int t = p.t0 + step;
-        const int te = p.ep_mode ? t % p.T : t;   // step within the episode
+        const int te = ep_mode ? t % p.T : t;   // step within the episode
         if (step > 0) {
-            mb = p.offsets[dcur];
-            me = p.offsets[dcur + 1];
+            const long long d = ep_mode ? dcur : (long long)e * p.off_stride + p.k0 + step;
+            mb = p.offsets[d];
+            me = p.offsets[d + 1];
         }
         const int nmsg = (int)(me - mb);
         const int ntiles = (nmsg + TILE - 1) / TILE;
@@ -986,7 +991,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             }
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
-            if (p.reward_mode != LOB_REWARD_PV && lane == 0) {
+            if (EXT && p.reward_mode != LOB_REWARD_PV && lane == 0) {
                 sm.rw[0] = bb + ba; sm.rw[1] = c.inv1; sm.rw[2] = c.cash1;
             }
             int wa[3] = {0, 0, 0}, ws[3] = {0, 0, 0}, wp[3] = {0, 0, 0};
@@ -1187,7 +1192,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         // Episode mode: after the episode's last step the env starts the next
         // episode from snapshot ep_j; the step reports that episode's first
         // observation with its own rewards and done flag.
-        const bool ep_end = p.ep_mode && te + 1 == p.T;
+        const bool ep_end = ep_mode && te + 1 == p.T;
         const unsigned ep_j =
             ep_end ? bounded(sm_mix(step_key(seed, t / p.T + 1, LOB_TAG_EPISODE) + GAMMA), (unsigned)p.n_starts) : 0u;
         __syncwarp();
@@ -1247,7 +1252,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 }
             }
             if (lane == 0) {
-                if (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0) {
+                if (EXT && (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0)) {
                     const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
                                                         te + 1 == p.T, (long long)p.exec_target - c.exec_done,
                                                         sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
@@ -1279,7 +1284,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             c.last_px = S.last_px;
             ep_start = S.data_step;
             dcur = S.data_step;
-        } else {
+        } else if (ep_mode) {
             dcur++;
         }
         if (step + 1 == p.n_steps) {
@@ -1304,11 +1309,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         st->pv_prev[0] = c.pv0; st->pv_prev[1] = c.pv1; st->exec_done = c.exec_done;
         st->last_px = c.last_px; st->n[0] = bid.n; st->n[1] = ask.n;
         st->t = p.t0 + p.n_steps;
-        st->ep_start = ep_start;
+        if (EXT) st->ep_start = ep_start;
     }
 }
 
-template <int K, bool TRACE>
+template <int K, bool TRACE, bool EXT>
 __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1323,14 +1328,14 @@ __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     MsgPipe pipe{0u};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K, TRACE>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+        if (w < p.n_list) run_env<K, TRACE, EXT>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K, TRACE>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+            run_env<K, TRACE, EXT>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
         }
     }
 }

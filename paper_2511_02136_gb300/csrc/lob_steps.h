@@ -6,8 +6,8 @@
 
 namespace lobk {
 #define LOB_DECL_CLASS(k)                                                                              \
-    cudaError_t launch_steps_##k(bool trace, int blocks, int threads, size_t smem, cudaStream_t s,    \
-                                 const KParams &p);                                                    \
+    cudaError_t launch_steps_##k(bool trace, bool ext, int blocks, int threads, size_t smem,          \
+                                 cudaStream_t s, const KParams &p);                                    \
     cudaError_t optin_steps_##k(size_t smem);
 LOB_DECL_CLASS(1)
 LOB_DECL_CLASS(2)
