@@ -148,6 +148,9 @@ const uint64_t TAG_POLICY = 0x504F4C4943590002ULL;
 const uint64_t TAG_EPISODE = 0x4550495344450003ULL;
 const int64_t INIT_ID = 0x4000000000000000LL;   // ids of a snapshot's resting orders
 
+// Number of market-maker actions of each action space (Sec. 4.1.1).
+int mm_actions(int space) { return space == 1 ? 8 : space == 2 ? 3 : 12; }
+
 int64_t floor_half(int64_t s) { return s >= 0 ? s / 2 : -((-s + 1) / 2); }
 int64_t ceil_half(int64_t s) { return -floor_half(-s); }
 
@@ -419,9 +422,10 @@ struct Engine {
         std::vector<Msg> cancels;
         if (A == 2) {
             // -- Action conversion (Sec. 4): actions -> new orders
+            const uint32_t n_act[2] = {12, (uint32_t)mm_actions(c.mm_space)};
             for (int a = 0; a < 2; a++) {
                 if (c.action_mode == 1)
-                    E.act[a] = (int32_t)lemire(draw(E.seed, t, TAG_POLICY, a), 12);
+                    E.act[a] = (int32_t)lemire(draw(E.seed, t, TAG_POLICY, a), n_act[a]);
                 else
                     E.act[a] = actions[e * 2 + a];
             }
@@ -444,18 +448,39 @@ struct Engine {
                 }
                 want.push_back({0, c.exec_dir, (int32_t)px, (int32_t)qty});
             }
-            // agent 1, market making: one lot each side around the touch
+            // agent 1, market making (Sec. 4.1.1): quotes of mm_lot around the touch
             int a = E.act[1];
             int64_t bid = 0, ask = 0;
-            bool quote = true;
-            if (a >= 1 && a <= 9) { bid = bb - (a - 1) / 3; ask = ba + (a - 1) % 3; }
-            else if (a == 10) { bid = bb + 1; ask = ba; }
-            else if (a == 11) { bid = bb; ask = ba - 1; }
-            else quote = false;
-            if (quote) {
-                want.push_back({1, BUY, (int32_t)bid, c.mm_lot});
-                want.push_back({1, SELL, (int32_t)ask, c.mm_lot});
+            bool has_bid = false, has_ask = false;
+            if (c.mm_space == 0) {
+                // 12-way head: bid / ask each 0, 1 or 2 ticks behind the touch,
+                // or one tick into the spread on one side
+                has_bid = has_ask = a >= 1 && a <= 11;
+                if (a >= 1 && a <= 9) { bid = bb - (a - 1) / 3; ask = ba + (a - 1) % 3; }
+                else if (a == 10) { bid = bb + 1; ask = ba; }
+                else if (a == 11) { bid = bb; ask = ba - 1; }
+            } else if (c.mm_space == 1) {
+                // Fixed Quantity, 8 options: none; 2 / 4 ticks behind both
+                // touches; one tick into the spread on both; 2 ticks behind on
+                // the bid only / the ask only; 5 ticks behind on one side with
+                // one tick into the spread on the other
+                switch (a) {
+                    case 1: bid = bb - 2; ask = ba + 2; has_bid = has_ask = true; break;
+                    case 2: bid = bb - 4; ask = ba + 4; has_bid = has_ask = true; break;
+                    case 3: bid = bb + 1; ask = ba - 1; has_bid = has_ask = true; break;
+                    case 4: bid = bb - 2; has_bid = true; break;
+                    case 5: ask = ba + 2; has_ask = true; break;
+                    case 6: bid = bb - 5; ask = ba - 1; has_bid = has_ask = true; break;
+                    case 7: bid = bb + 1; ask = ba + 5; has_bid = has_ask = true; break;
+                    default: break;
+                }
+            } else {
+                // directional trading: a bid at the best bid, an ask at the best ask, or nothing
+                if (a == 1) { bid = bb; has_bid = true; }
+                if (a == 2) { ask = ba; has_ask = true; }
             }
+            if (has_bid) want.push_back({1, BUY, (int32_t)bid, c.mm_lot});
+            if (has_ask) want.push_back({1, SELL, (int32_t)ask, c.mm_lot});
             // -- carry-over: keep same-(side, price) resting orders, cancel the rest
             std::vector<int64_t> kept(want.size(), 0);
             for (int ag = 0; ag < A; ag++) {

@@ -45,6 +45,8 @@ typedef struct orc_config {
     int32_t exec_penalty_milli; /* end-of-episode penalty per unfilled unit of the execution
                              task, in thousandths of a tick; every reward is the floor of
                              its exact value */
+    int32_t mm_space;     /* market maker's action space (Sec. 4.1): 0 the 12-way spread/skew
+                             head, 1 Fixed Quantity (8 options), 2 directional trading (3) */
 } orc_config;
 
 void   *orc_create(const orc_config *cfg, const int32_t *caps /* [n_envs] or NULL */);

@@ -50,12 +50,13 @@ def wrap(v):
 class BruteEnv:
     def __init__(self, cap, n_agents=0, top_levels=2, episode_len=10, mm_lot=1,
                  exec_target=10, exec_dir=SELL, start_px=10_000, seed=0, action_mode=0,
-                 reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0):
+                 reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0, mm_space=0):
         self.cap, self.A, self.L, self.T = cap, n_agents, top_levels, episode_len
         self.mm_lot, self.exec_target, self.exec_dir = mm_lot, exec_target, exec_dir
         self.action_mode, self.seed = action_mode, seed
         self.reward_mode, self.lam_pct = reward_mode, spooner_lambda_pct
         self.inv_penalty, self.exec_penalty_milli = inv_penalty, exec_penalty_milli
+        self.mm_space = mm_space
         self.orders = {BUY: [], SELL: []}   # dicts: px, qty, id, ts
         self.ts_next = 0
         self.seq_next = 0
@@ -229,7 +230,8 @@ class BruteEnv:
         mid_before = (self.touch(BUY) + self.touch(SELL)) / 2
         if self.A == 2:
             if self.action_mode == 1:
-                self.acts = [bounded(keyed_draws(self.seed, self.t, TAG_POLICY, 2)[a], 12) for a in range(2)]
+                n_mm = (12, 8, 3)[self.mm_space]
+                self.acts = [bounded(keyed_draws(self.seed, self.t, TAG_POLICY, 2)[a], (12, n_mm)[a]) for a in range(2)]
             else:
                 self.acts = list(actions)
             bb, ba = self.touch(BUY), self.touch(SELL)
@@ -246,12 +248,20 @@ class BruteEnv:
                     prices = (ba, (bb + ba) // 2, bb, bb - 2)
                 want.append((0, self.exec_dir, prices[a // 3], qty))
             a = self.acts[1]
-            if 1 <= a <= 9:
-                want += [(1, BUY, bb - (a - 1) // 3, self.mm_lot), (1, SELL, ba + (a - 1) % 3, self.mm_lot)]
-            elif a == 10:
-                want += [(1, BUY, bb + 1, self.mm_lot), (1, SELL, ba, self.mm_lot)]
-            elif a == 11:
-                want += [(1, BUY, bb, self.mm_lot), (1, SELL, ba - 1, self.mm_lot)]
+            if self.mm_space == 0:
+                if 1 <= a <= 9:
+                    quotes = (bb - (a - 1) // 3, ba + (a - 1) % 3)
+                else:
+                    quotes = {10: (bb + 1, ba), 11: (bb, ba - 1)}.get(a, (None, None))
+            elif self.mm_space == 1:
+                quotes = {1: (bb - 2, ba + 2), 2: (bb - 4, ba + 4), 3: (bb + 1, ba - 1), 4: (bb - 2, None),
+                          5: (None, ba + 2), 6: (bb - 5, ba - 1), 7: (bb + 1, ba + 5)}.get(a, (None, None))
+            else:
+                quotes = {1: (bb, None), 2: (None, ba)}.get(a, (None, None))
+            if quotes[0] is not None:
+                want.append((1, BUY, quotes[0], self.mm_lot))
+            if quotes[1] is not None:
+                want.append((1, SELL, quotes[1], self.mm_lot))
             kept = [0] * len(want)
             cancels = []
             for ag in range(self.A):

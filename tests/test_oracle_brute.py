@@ -35,7 +35,8 @@ def test_oracle_matches_brute_reward_variants(seed):
     """Eqs. 3-4 and the Table 2 penalties, against exact fractions in the brute env."""
     rng = np.random.default_rng(500 + seed)
     rw = dict(reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=int(rng.integers(0, 101)),
-              inv_penalty=int(rng.integers(0, 3)), exec_penalty_milli=int(rng.choice([0, 10, 50, 100, 2500])))
+              inv_penalty=int(rng.integers(0, 3)), exec_penalty_milli=int(rng.choice([0, 10, 50, 100, 2500])),
+              mm_space=int(rng.integers(0, 3)))
     _run_against_brute(100 + seed, rw)
 
 
@@ -110,7 +111,7 @@ def test_oracle_matches_brute_episodes(seed):
     kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)),
               exec_target=int(rng.integers(5, 40)), exec_dir=int(rng.choice([-1, 1])), start_px=10_000,
               reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=30, inv_penalty=int(rng.integers(0, 2)),
-              exec_penalty_milli=int(rng.choice([0, 100])))
+              exec_penalty_milli=int(rng.choice([0, 100])), mm_space=seed % 3)
     seeds = mbogen.env_seeds(3000 + seed, n_env)
     o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
     o.set_episodes(st.msgs, st.offsets[0], starts, levels)

@@ -158,11 +158,12 @@ def test_reward_variants_leave_book_and_obs_alone():
     assert differs
 
 
-def _setup_two_quotes(start_px, exec_dir, actions):
+def _setup_two_quotes(start_px, exec_dir, actions, mm_space=0):
     """Step 0 places a bid 99 x 50 and an ask 104 x 50; step 1 runs `actions`."""
     msgs, off = single_env_stream([[[1, BUY, 99, 50, 0], [1, SELL, 104, 50, 1]], []])
     o = oracle.Oracle(1, n_agents=2, cap=50, top_levels=2, episode_len=100, exec_target=100,
-                      exec_dir=exec_dir, mm_lot=1, start_px=start_px, action_mode=0, trace=1)
+                      exec_dir=exec_dir, mm_lot=1, start_px=start_px, action_mode=0, trace=1,
+                      mm_space=mm_space)
     o.reset(np.array([7], np.uint64))
     o.load_messages(msgs, off)
     o.step(np.array([[9, 0]], np.int32))
@@ -183,6 +184,35 @@ def test_mm_action_table():
         else:
             assert [r[0] for r in mb] == [want[0]] and [r[0] for r in ma] == [want[1]]
             assert mb[0][1] == 1 and ma[0][1] == 1
+
+
+@pytest.mark.parametrize("which,space", [("mm_fixed_quantity", 1), ("mm_directional", 2)])
+def test_mm_other_action_spaces(which, space):
+    g = _gold("action_tables.json")[which]
+    for k, (want_b, want_a) in g.items():
+        o, _ = _setup_two_quotes(200, SELL, [9, int(k)], mm_space=space)
+        bids, asks = _book_rows(o)
+        mb = [(r[0], r[1]) for r in bids if _owner(r[2]) == 1]
+        ma = [(r[0], r[1]) for r in asks if _owner(r[2]) == 1]
+        assert mb == ([] if want_b is None else [(want_b, 1)]), k
+        assert ma == ([] if want_a is None else [(want_a, 1)]), k
+
+
+@pytest.mark.parametrize("space,n", [(0, 12), (1, 8), (2, 3)])
+def test_random_policy_covers_each_mm_space(space, n):
+    """The random policy draws the market maker's action uniformly over its space's options."""
+    seeds = mbogen.env_seeds(3, 400)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=2), seeds, 1)
+    o = oracle.Oracle(400, n_agents=2, cap=8, episode_len=1, action_mode=1, mm_space=space)
+    o.reset(seeds)
+    o.load_messages(st.msgs, st.offsets)
+    o.step()
+    acts = o.actions()
+    assert acts[:, 1].min() == 0 and acts[:, 1].max() == n - 1
+    assert acts[:, 0].max() == 11
+    for e in range(0, 400, 37):
+        want = oracle.lemire(oracle.draw(int(seeds[e]), 0, oracle.TAG_POLICY, 1), n)
+        assert acts[e, 1] == want
 
 
 @pytest.mark.parametrize("which,exec_dir", [("exec_sell", SELL), ("exec_buy", BUY)])
