@@ -121,7 +121,22 @@ typedef struct lob_config {
     int32_t exec_penalty_milli;  /* >= 0: at the last step of the episode the execution agent's
                                     reward -= this * unfilled units / 1000 (Table 2's unfilled
                                     order penalty, in thousandths of a tick per unit) */
+    /* Market maker's action space (Sec. 4.1.1), each quote of mm_lot; bb / ba the touches:
+     *   LOB_MM_SPREAD_SKEW  12 actions: 0 none; 1..9 bid bb - (a-1)/3, ask ba + (a-1)%3;
+     *                       10 bid bb+1, ask ba; 11 bid bb, ask ba-1
+     *   LOB_MM_FIXED_QUANT   8 actions: 0 none; 1 bb-2 / ba+2; 2 bb-4 / ba+4; 3 bb+1 / ba-1;
+     *                       4 bid bb-2 only; 5 ask ba+2 only; 6 bb-5 / ba-1; 7 bb+1 / ba+5
+     *   LOB_MM_DIRECTIONAL   3 actions: 0 none; 1 bid at bb; 2 ask at ba
+     * The random policy draws the market maker's action over its space; host
+     * actions outside it give LOB_EINVAL.  lob_rollout_policy (12 logits)
+     * needs LOB_MM_SPREAD_SKEW. */
+    int32_t mm_space;
+    int32_t reserved[3];         /* must be zero */
 } lob_config;
+
+#define LOB_MM_SPREAD_SKEW 0
+#define LOB_MM_FIXED_QUANT 1
+#define LOB_MM_DIRECTIONAL 2
 
 #define LOB_REWARD_PV      0
 #define LOB_REWARD_BUYSELL 1

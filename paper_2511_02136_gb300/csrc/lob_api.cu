@@ -44,6 +44,7 @@ static void set_rewards(KParams &p, const lob_config &c) {
     p.lam_pct = c.spooner_lambda_pct;
     p.inv_penalty = c.inv_penalty;
     p.exec_pen_milli = c.exec_penalty_milli;
+    p.mm_space = c.mm_space;
 }
 
 size_t warp_smem_bytes(int K) {
@@ -93,21 +94,46 @@ cudaError_t ensure_optin() {
 
 // Launch the step kernel of class K (shared memory opted in by ensure_optin);
 // the warps per block are capped by what one block's shared memory holds.
+// Resident blocks per SM of the wide step kernel, per (class, extended,
+// warps per block); queried once (the launch shape fixes the shared memory).
+int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
+    static int cache[NCLASS][2][9];   // 0 = not queried yet
+    const int k = class_of(32 * K);
+    int &c = cache[k][ext ? 1 : 0][wpb];
+    if (c == 0) {
+        int nb = 0;
+        switch (K) {
+            case 1: nb = wide_blocks_per_sm_1(ext, 32 * wpb, smem); break;
+            case 2: nb = wide_blocks_per_sm_2(ext, 32 * wpb, smem); break;
+            case 4: nb = wide_blocks_per_sm_4(ext, 32 * wpb, smem); break;
+            case 8: nb = wide_blocks_per_sm_8(ext, 32 * wpb, smem); break;
+            case 16: nb = wide_blocks_per_sm_16(ext, 32 * wpb, smem); break;
+            default: nb = wide_blocks_per_sm_32(ext, 32 * wpb, smem); break;
+        }
+        c = nb > 0 ? nb : -1;
+    }
+    return c > 0 ? c : 0;
+}
+
 cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s,
                      const KParams &p) {
     wpb = wpb < max_wpb(K) ? wpb : max_wpb(K);
     int blocks = (n_list + wpb - 1) / wpb;
     if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
     const size_t smem = (size_t)wpb * warp_smem_bytes(K);
-    // the extended kernel when episode mode or a reward variant is on
-    const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0;
+    // the extended kernel when episode mode, a reward variant or another
+    // action space is on
+    const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
+                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW;
+    // the wide register budget when every block is resident at once (one wave)
+    const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     switch (K) {
-        case 1: return launch_steps_1(trace, ext, blocks, 32 * wpb, smem, s, p);
-        case 2: return launch_steps_2(trace, ext, blocks, 32 * wpb, smem, s, p);
-        case 4: return launch_steps_4(trace, ext, blocks, 32 * wpb, smem, s, p);
-        case 8: return launch_steps_8(trace, ext, blocks, 32 * wpb, smem, s, p);
-        case 16: return launch_steps_16(trace, ext, blocks, 32 * wpb, smem, s, p);
-        default: return launch_steps_32(trace, ext, blocks, 32 * wpb, smem, s, p);
+        case 1: return launch_steps_1(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        case 2: return launch_steps_2(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        case 4: return launch_steps_4(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        case 8: return launch_steps_8(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        case 16: return launch_steps_16(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        default: return launch_steps_32(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
     }
 }
 
@@ -229,8 +255,11 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
         c.warps_per_block < 0 || c.warps_per_block > 8)
         return LOB_EINVAL;
     if (c.reward_mode < LOB_REWARD_PV || c.reward_mode > LOB_REWARD_SPOONER || c.spooner_lambda_pct < 0 ||
-        c.spooner_lambda_pct > 100 || c.inv_penalty < 0 || c.exec_penalty_milli < 0)
+        c.spooner_lambda_pct > 100 || c.inv_penalty < 0 || c.exec_penalty_milli < 0 ||
+        c.mm_space < LOB_MM_SPREAD_SKEW || c.mm_space > LOB_MM_DIRECTIONAL)
         return LOB_EINVAL;
+    for (int i = 0; i < 3; i++)
+        if (c.reserved[i] != 0) return LOB_EINVAL;
     std::vector<int> caps((size_t)c.n_envs);
     for (int e = 0; e < c.n_envs; e++) {
         const int cp = h_caps ? h_caps[e] : c.cap_per_side;
@@ -970,7 +999,8 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
 extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
                                   int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream) {
     if (!h || !pol || n_steps < 1) return LOB_EINVAL;
-    if (h->cfg.n_agents != 2 || h->cfg.action_mode != LOB_ACT_HOST) return LOB_EINVAL;
+    if (h->cfg.n_agents != 2 || h->cfg.action_mode != LOB_ACT_HOST || h->cfg.mm_space != LOB_MM_SPREAD_SKEW)
+        return LOB_EINVAL;
     if (policy_n_agents(pol) != 2 || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
     if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
     if (!steps_left(h, n_steps)) return LOB_ESTATE;

@@ -97,6 +97,7 @@ struct KParams {
     int reward_mode, lam_pct;        // market maker's reward (Eq. 1, 4 or 3), lambda in percent
     long long inv_penalty;           // rho of the quadratic inventory penalty
     long long exec_pen_milli;        // unfilled-task penalty, thousandths of a tick per unit
+    int mm_space;                    // market maker's action space (Sec. 4.1.1)
     // episode mode (one shared stream; offsets index data steps): start table,
     // prebuilt book images (ep_block bytes each) and first observations
     int ep_mode;
@@ -979,15 +980,17 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         // ---- 1-3. action conversion, carry-over cancels, shuffle
         int act0 = 0, act1 = 0, ns = 0;
         if (A == 2) {
+            // market maker's action count: 12, or (extended kernel) 8 / 3
+            const int n_mm = !EXT ? 12 : p.mm_space == LOB_MM_FIXED_QUANT ? 8 : p.mm_space == LOB_MM_DIRECTIONAL ? 3 : 12;
             if (p.action_mode == LOB_ACT_RANDOM) {
                 const unsigned long long key = step_key(seed, t, TAG_POLICY);
                 act0 = (int)bounded(sm_mix(key + GAMMA), 12);
-                act1 = (int)bounded(sm_mix(key + 2 * GAMMA), 12);
+                act1 = (int)bounded(sm_mix(key + 2 * GAMMA), (unsigned)n_mm);
             } else {
                 const int *ap = p.actions + (long long)step * p.act_step_stride + 2LL * e;
                 act0 = ap[0];
                 act1 = ap[1];
-                if (act0 < 0 || act0 >= 12 || act1 < 0 || act1 >= 12) c.status |= ST_BADACT;
+                if (act0 < 0 || act0 >= 12 || act1 < 0 || act1 >= n_mm) c.status |= ST_BADACT;
             }
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
@@ -1012,19 +1015,56 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 wa[0] = 0; ws[0] = p.exec_dir; wp[0] = (int)wpx; wq[0] = qty;
                 nw = 1;
             }
-            if (act1 >= 1 && act1 < 12) {
-                long long qb, qa;
-                if (act1 <= 9) { qb = bb - (act1 - 1) / 3; qa = ba + (act1 - 1) % 3; }
-                else if (act1 == 10) { qb = bb + 1; qa = ba; }
-                else { qb = bb; qa = ba - 1; }
-                if (nw == 0) {
-                    wa[0] = 1; ws[0] = LOB_BUY; wp[0] = (int)qb; wq[0] = p.mm_lot;
-                    wa[1] = 1; ws[1] = LOB_SELL; wp[1] = (int)qa; wq[1] = p.mm_lot;
-                } else {
-                    wa[1] = 1; ws[1] = LOB_BUY; wp[1] = (int)qb; wq[1] = p.mm_lot;
-                    wa[2] = 1; ws[2] = LOB_SELL; wp[2] = (int)qa; wq[2] = p.mm_lot;
+            if (!EXT || p.mm_space == LOB_MM_SPREAD_SKEW) {
+                if (act1 >= 1 && act1 < 12) {
+                    long long qb, qa;
+                    if (act1 <= 9) { qb = bb - (act1 - 1) / 3; qa = ba + (act1 - 1) % 3; }
+                    else if (act1 == 10) { qb = bb + 1; qa = ba; }
+                    else { qb = bb; qa = ba - 1; }
+                    if (nw == 0) {
+                        wa[0] = 1; ws[0] = LOB_BUY; wp[0] = (int)qb; wq[0] = p.mm_lot;
+                        wa[1] = 1; ws[1] = LOB_SELL; wp[1] = (int)qa; wq[1] = p.mm_lot;
+                    } else {
+                        wa[1] = 1; ws[1] = LOB_BUY; wp[1] = (int)qb; wq[1] = p.mm_lot;
+                        wa[2] = 1; ws[2] = LOB_SELL; wp[2] = (int)qa; wq[2] = p.mm_lot;
+                    }
+                    nw += 2;
                 }
-                nw += 2;
+            } else {
+                // Fixed Quantity (8 options) or directional (3): quotes that may be one-sided
+                bool hb = false, ha = false;
+                long long qb = 0, qa = 0;
+                if (p.mm_space == LOB_MM_FIXED_QUANT) {
+                    switch (act1) {
+                        case 1: qb = bb - 2; qa = ba + 2; hb = ha = true; break;
+                        case 2: qb = bb - 4; qa = ba + 4; hb = ha = true; break;
+                        case 3: qb = bb + 1; qa = ba - 1; hb = ha = true; break;
+                        case 4: qb = bb - 2; hb = true; break;
+                        case 5: qa = ba + 2; ha = true; break;
+                        case 6: qb = bb - 5; qa = ba - 1; hb = ha = true; break;
+                        case 7: qb = bb + 1; qa = ba + 5; hb = ha = true; break;
+                        default: break;
+                    }
+                } else {
+                    if (act1 == 1) { qb = bb; hb = true; }
+                    if (act1 == 2) { qa = ba; ha = true; }
+                }
+                // constant array indices only, so the wanted orders stay in registers
+                const int q1s = ha ? LOB_SELL : LOB_BUY;      // a one-sided quote
+                const int q1p = (int)(ha ? qa : qb);
+                if (hb && ha) {
+                    if (nw == 0) {
+                        wa[0] = 1; ws[0] = LOB_BUY; wp[0] = (int)qb; wq[0] = p.mm_lot;
+                        wa[1] = 1; ws[1] = LOB_SELL; wp[1] = (int)qa; wq[1] = p.mm_lot;
+                    } else {
+                        wa[1] = 1; ws[1] = LOB_BUY; wp[1] = (int)qb; wq[1] = p.mm_lot;
+                        wa[2] = 1; ws[2] = LOB_SELL; wp[2] = (int)qa; wq[2] = p.mm_lot;
+                    }
+                } else if (hb || ha) {
+                    if (nw == 0) { wa[0] = 1; ws[0] = q1s; wp[0] = q1p; wq[0] = p.mm_lot; }
+                    else { wa[1] = 1; ws[1] = q1s; wp[1] = q1p; wq[1] = p.mm_lot; }
+                }
+                nw += (hb ? 1 : 0) + (ha ? 1 : 0);
             }
             // carry-over: keep resting orders at a wanted (agent, side, price)
             unsigned kept_u[3] = {0u, 0u, 0u};
@@ -1313,8 +1353,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     }
 }
 
+// One warp per env; with a work queue (p.queue) warps take envs until none is left.
 template <int K, bool TRACE, bool EXT>
-__global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
+__device__ __forceinline__ void env_steps_body(const KParams &p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -1338,6 +1379,21 @@ __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
             run_env<K, TRACE, EXT>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
         }
     }
+}
+
+// The step kernel in two register budgets.  k_env_steps leaves the budget
+// to the compiler, which keeps two blocks' worth of warps resident (better
+// for launches of several waves of small books); k_env_steps_wide may use the
+// whole register file (one block per SM minimum): fewer spills and a shorter
+// per-message path, the better choice when the launch fits one wave or when
+// shared memory bounds residency anyway (K >= 8).
+template <int K, bool TRACE, bool EXT>
+__global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
+    env_steps_body<K, TRACE, EXT>(p);
+}
+template <int K, bool TRACE, bool EXT>
+__global__ void __launch_bounds__(256, 1) k_env_steps_wide(const KParams p) {
+    env_steps_body<K, TRACE, EXT>(p);
 }
 
 }  // namespace lobk

@@ -1,7 +1,8 @@
 // steps_inst.cuh -- instantiates the step kernel of one capacity class
 // (K = LOB_K slots per lane per side) in a translation unit of its own so
 // that the classes compile in parallel: the plain kernel, the extended one
-// (episode mode, reward variants) and the traced extended one.
+// (episode mode, reward variants, other action spaces) and the traced
+// extended one, in the register budgets below.
 #include "lob_device.cuh"
 #include "lob_steps.h"
 
@@ -9,20 +10,46 @@
 #define LOB_CAT(a, b) LOB_CAT2(a, b)
 
 namespace lobk {
-cudaError_t LOB_CAT(launch_steps_, LOB_K)(bool trace, bool ext, int blocks, int threads, size_t smem,
+// K >= 8: every instance in the wide register budget; K <= 4: the plain and
+// extended kernels in both budgets (the host picks by batch size), the traced
+// one wide.
+constexpr bool kAlwaysWide = LOB_K >= 8;
+
+cudaError_t LOB_CAT(launch_steps_, LOB_K)(bool trace, bool ext, bool wide, int blocks, int threads, size_t smem,
                                           cudaStream_t s, const KParams &p) {
-    if (trace) k_env_steps<LOB_K, true, true><<<blocks, threads, smem, s>>>(p);
-    else if (ext) k_env_steps<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
-    else k_env_steps<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
+    if (trace) k_env_steps_wide<LOB_K, true, true><<<blocks, threads, smem, s>>>(p);
+    else if constexpr (kAlwaysWide) {
+        if (ext) k_env_steps_wide<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
+        else k_env_steps_wide<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
+    } else {
+        if (ext && wide) k_env_steps_wide<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
+        else if (ext) k_env_steps<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
+        else if (wide) k_env_steps_wide<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
+        else k_env_steps<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
+    }
     return cudaGetLastError();
 }
+
+// Resident blocks per SM of the wide plain / extended kernel at this shape.
+int LOB_CAT(wide_blocks_per_sm_, LOB_K)(bool ext, int threads, size_t smem) {
+    int nb = 0;
+    cudaError_t e = ext ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_steps_wide<LOB_K, false, true>,
+                                                                        threads, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env_steps_wide<LOB_K, false, false>,
+                                                                        threads, smem);
+    return e == cudaSuccess ? nb : 0;
+}
+
 cudaError_t LOB_CAT(optin_steps_, LOB_K)(size_t smem) {
     const int b = (int)smem;
-    cudaError_t e = cudaFuncSetAttribute(k_env_steps<LOB_K, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, true, true>, A, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, false, true>, A, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, false, false>, A, b);
+    if constexpr (!kAlwaysWide) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, true>, A, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, false>, A, b);
+    }
     return e;
 }
 }  // namespace lobk

@@ -213,7 +213,7 @@ def test_create_rejects_bad_configs():
                              ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 0, lob.LOB_EINVAL),
                              ("action_mode", 7, lob.LOB_EINVAL), ("reward_mode", 3, lob.LOB_EINVAL),
                              ("spooner_lambda_pct", 101, lob.LOB_EINVAL), ("inv_penalty", -1, lob.LOB_EINVAL),
-                             ("exec_penalty_milli", -5, lob.LOB_EINVAL)):
+                             ("exec_penalty_milli", -5, lob.LOB_EINVAL), ("mm_space", 3, lob.LOB_EINVAL)):
         c = lob.lob_config(4, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
         setattr(c, field, val)
         with pytest.raises(lob.LobError) as ei:
@@ -254,6 +254,36 @@ def test_reward_variants_host_actions_buy_task():
     for _ in range(T):
         pr.step(rng.integers(0, 12, size=(n, 2)).astype(np.int32))
         pr.check_outputs()
+    pr.close()
+
+
+@pytest.mark.parametrize("space,n_mm", [(lob.LOB_MM_FIXED_QUANT, 8), (lob.LOB_MM_DIRECTIONAL, 3)])
+def test_mm_action_spaces(space, n_mm):
+    """Fixed Quantity and directional market-maker heads (Sec. 4.1.1): random
+    policy and host actions, every step's outputs and the final books."""
+    n, T = 40, 15
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=60), mbogen.env_seeds(41 + space, n), T)
+    pr = Pair(n, st, cap=100, exec_target=60, fill_cap=256, mm_space=space)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    pr.close()
+    rng = np.random.default_rng(space)
+    pr = Pair(n, st, cap=100, exec_target=60, mm_space=space, action_mode=lob.LOB_ACT_HOST)
+    for _ in range(T - 1):
+        acts = np.stack([rng.integers(0, 12, n), rng.integers(0, n_mm, n)], axis=1).astype(np.int32)
+        pr.step(acts)
+        pr.check_outputs()
+    pr.check_state()
+    assert pr.env.sync() == 0
+    # an action outside the space is reported
+    import torch
+    bad = np.zeros((n, 2), np.int32)
+    bad[3, 1] = n_mm
+    pr.env.step(torch.from_numpy(bad).cuda())
+    assert pr.env.sync() == lob.LOB_EINVAL
     pr.close()
 
 
