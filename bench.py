@@ -471,6 +471,48 @@ def run_workload(args):
                 "config": {"workload": "4096 envs x cap 200 x 100 msgs x 128 steps, per-agent MLP 45-128-128-13 "
                                        "(tanh) in the loop, one graph-captured lob_rollout_policy"},
                 "dtype": "int64 book / bf16 policy", "data": "synthetic", "n_gpus": 1, "steps": T}
+    elif wl == "episodes4096":
+        # Table 2's training setup on one shared stream: 64-step episodes
+        # starting every 64 data steps from book snapshots (top 10 levels),
+        # 100 msgs/step, capacity 100, order size 10, execution task 600,
+        # Fixed Quantity market maker with the Spooner reward and the
+        # quadratic inventory penalty (rho 50), unfilled-task penalty 0.1;
+        # 256 steps = 4 episodes per env in one lob_rollout launch
+        n, T, EP = 4096, 256, 64
+        n_data = 64 * 130
+        dseed = mbogen.env_seeds(6, 1)
+        st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), dseed, n_data)
+        starts, levels = mbogen.start_books(6, st.mids[0], np.arange(0, n_data - EP + 1, EP), 10, min_levels=5)
+        seeds = mbogen.env_seeds(7, n)
+        env = lob.LobEnv(n, cap=100, episode_len=EP, mm_lot=10, exec_target=600, action_mode=lob.LOB_ACT_RANDOM,
+                         reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=50, inv_penalty=50,
+                         exec_penalty_milli=100, mm_space=lob.LOB_MM_FIXED_QUANT)
+        md = torch.from_numpy(st.msgs.view(np.uint8)).to(dev)
+        od = torch.from_numpy(st.offsets[0].copy()).to(dev)
+        sd = torch.from_numpy(seeds.view(np.int64).copy()).to(dev)
+        env.set_episodes(md, od, starts, levels)
+        D = env.D
+        obs = torch.zeros((T, n, 2, D), dtype=torch.float32, device=dev)
+        rew = torch.zeros((T, n, 2), dtype=torch.int64, device=dev)
+        done = torch.zeros((T, n), dtype=torch.uint8, device=dev)
+        times, msgs = [], 0.0
+        for i in range(args.reps):
+            env.reset(sd)
+            torch.cuda.synchronize()
+            times += _flush_and_time(lambda: lob.lob_rollout(env.h, T, None, obs, rew, done), 1, dev)
+            msgs = float(env.counters()[:, 0].sum().item())
+        assert env.sync() == 0
+        assert int(done.sum().item()) == n * (T // EP)
+        env.close()
+        t = min(times)
+        line = {"workload": "episodes4096", "metric": METRIC, "value": msgs / t, "unit": "msgs/s",
+                "env_steps_per_s": n * T / t, "seconds_per_rollout": t, "steps": T, "n_gpus": 1,
+                "config": {"workload": "4096 envs, one shared stream of 8,320 data steps x 100 msgs, 64-step "
+                                       "episodes from 130 snapshot starts (every 64 data steps, top-10 levels), "
+                                       "auto-reset in the kernel, cap 100, lot 10, exec task 600, Fixed Quantity "
+                                       "MM, Spooner reward (lambda 0.5) + rho 50 + unfilled penalty 0.1, random "
+                                       "policy, 256 steps in one lob_rollout", "messages": msgs},
+                "dtype": "int64", "data": "synthetic"}
     elif wl == "stress65536":
         n, T = 65536, args.stress_steps
         seeds = mbogen.env_seeds(4, n)
@@ -512,7 +554,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="envs1024",
-                    choices=["envs1024", "uneven8192", "policy4096", "stress65536"],
+                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stress-steps", type=int, default=4)
