@@ -165,13 +165,13 @@ struct Env {
     int64_t ts_next = 0, seq_next = 0;
     int32_t last_px = 0;
     uint64_t seed = 0;
-    Agent ag[2];
+    std::vector<Agent> ag;              // A agents: execution 0..P-1, market making P..2P-1
     int64_t cnt[ORC_NCOUNTERS] = {};
     std::vector<Fill> fills;
     std::vector<float> obs;
-    int64_t rew[2] = {0, 0};
+    std::vector<int64_t> rew;
     uint8_t done = 0;
-    int32_t act[2] = {0, 0};
+    std::vector<int32_t> act;
     bool bad = false;
     int32_t msg_idx = 0;                // processing index within the current step
     int64_t ep_start = 0;               // episode mode: first data step of the current episode
@@ -247,8 +247,9 @@ struct Engine {
         if (buyer != A) { E.ag[buyer].buy_q += f; E.ag[buyer].buy_n = wadd(E.ag[buyer].buy_n, notional); }
         if (seller != A) { E.ag[seller].sell_q += f; E.ag[seller].sell_n = wadd(E.ag[seller].sell_n, notional); }
         if (A > 0) {
+            // the side of the execution task: its owner, if an execution agent, progresses
             int task_owner = cfg.c.exec_dir == SELL ? seller : buyer;
-            if (task_owner == 0) E.ag[0].exec_done += f;
+            if (task_owner < A / 2) E.ag[task_owner].exec_done += f;
         }
         E.last_px = maker.px;
         E.cnt[C_FILLS] += 1;
@@ -362,7 +363,7 @@ struct Engine {
         E.asks.levels.clear(); E.asks.count = 0;
         E.ts_next = 0;
         E.seq_next = 0;
-        for (int a = 0; a < 2; a++) E.ag[a] = Agent();
+        for (Agent &g : E.ag) g = Agent();
         E.last_px = st.last_px;
         E.ep_start = st.data_step;
         int64_t idx = 0;
@@ -403,7 +404,7 @@ struct Engine {
             ob[4 * L + 0] = (float)g.inv;
             ob[4 * L + 1] = (float)g.cash;
             ob[4 * L + 2] = tl;
-            ob[4 * L + 3] = a == 0 ? (float)((int64_t)c.exec_target - g.exec_done) : 0.0f;
+            ob[4 * L + 3] = a < A / 2 ? (float)((int64_t)c.exec_target - g.exec_done) : 0.0f;
             ob[4 * L + 4] = (float)own_rest[a];
         }
     }
@@ -416,24 +417,27 @@ struct Engine {
         E.fills.clear();
         E.msg_idx = 0;
         if (E.snaps) E.snaps->clear();
-        for (int a = 0; a < 2; a++) E.ag[a].buy_q = E.ag[a].buy_n = E.ag[a].sell_q = E.ag[a].sell_n = 0;
+        for (Agent &g : E.ag) g.buy_q = g.buy_n = g.sell_q = g.sell_n = 0;
         const int64_t mid2_start = ref_bid(E) + ref_ask(E);   // twice the mid when the step begins
         std::vector<NewOrder> want;
         std::vector<Msg> cancels;
-        if (A == 2) {
-            // -- Action conversion (Sec. 4): actions -> new orders
-            const uint32_t n_act[2] = {12, (uint32_t)mm_actions(c.mm_space)};
-            for (int a = 0; a < 2; a++) {
+        if (A > 0) {
+            // -- Action conversion (Sec. 4): actions -> new orders.  Agents
+            // 0..P-1 execute, P..2P-1 make markets (P agents per type).
+            const int P = A / 2;
+            for (int a = 0; a < A; a++) {
+                const uint32_t n_act = a < P ? 12u : (uint32_t)mm_actions(c.mm_space);
                 if (c.action_mode == 1)
-                    E.act[a] = (int32_t)lemire(draw(E.seed, t, TAG_POLICY, a), n_act[a]);
+                    E.act[a] = (int32_t)lemire(draw(E.seed, t, TAG_POLICY, a), n_act);
                 else
-                    E.act[a] = actions[e * 2 + a];
+                    E.act[a] = actions[e * A + a];
             }
             int64_t bb = ref_bid(E), ba = ref_ask(E);
-            // agent 0, execution (Sec. 4.1.2): 4 reference prices x {1,2,5} lots
-            int64_t remaining = (int64_t)c.exec_target - E.ag[0].exec_done;
-            if (remaining > 0) {
-                int a = E.act[0];
+            // execution agents (Sec. 4.1.2): 4 reference prices x {1,2,5} lots
+            for (int ag = 0; ag < P; ag++) {
+                int64_t remaining = (int64_t)c.exec_target - E.ag[ag].exec_done;
+                if (remaining <= 0) continue;
+                int a = E.act[ag];
                 int pi = a / 3;
                 int64_t mult = a % 3 == 0 ? 1 : a % 3 == 1 ? 2 : 5;
                 int64_t q0 = std::max<int64_t>(1, ((int64_t)c.exec_target + c.episode_len - 1) / c.episode_len);
@@ -446,41 +450,43 @@ struct Engine {
                     const int64_t p4[4] = {ba, floor_half(bb + ba), bb, bb - 2};
                     px = p4[pi];
                 }
-                want.push_back({0, c.exec_dir, (int32_t)px, (int32_t)qty});
+                want.push_back({ag, c.exec_dir, (int32_t)px, (int32_t)qty});
             }
-            // agent 1, market making (Sec. 4.1.1): quotes of mm_lot around the touch
-            int a = E.act[1];
-            int64_t bid = 0, ask = 0;
-            bool has_bid = false, has_ask = false;
-            if (c.mm_space == 0) {
-                // 12-way head: bid / ask each 0, 1 or 2 ticks behind the touch,
-                // or one tick into the spread on one side
-                has_bid = has_ask = a >= 1 && a <= 11;
-                if (a >= 1 && a <= 9) { bid = bb - (a - 1) / 3; ask = ba + (a - 1) % 3; }
-                else if (a == 10) { bid = bb + 1; ask = ba; }
-                else if (a == 11) { bid = bb; ask = ba - 1; }
-            } else if (c.mm_space == 1) {
-                // Fixed Quantity, 8 options: none; 2 / 4 ticks behind both
-                // touches; one tick into the spread on both; 2 ticks behind on
-                // the bid only / the ask only; 5 ticks behind on one side with
-                // one tick into the spread on the other
-                switch (a) {
-                    case 1: bid = bb - 2; ask = ba + 2; has_bid = has_ask = true; break;
-                    case 2: bid = bb - 4; ask = ba + 4; has_bid = has_ask = true; break;
-                    case 3: bid = bb + 1; ask = ba - 1; has_bid = has_ask = true; break;
-                    case 4: bid = bb - 2; has_bid = true; break;
-                    case 5: ask = ba + 2; has_ask = true; break;
-                    case 6: bid = bb - 5; ask = ba - 1; has_bid = has_ask = true; break;
-                    case 7: bid = bb + 1; ask = ba + 5; has_bid = has_ask = true; break;
-                    default: break;
+            // market makers (Sec. 4.1.1): quotes of mm_lot around the touch
+            for (int ag = P; ag < A; ag++) {
+                int a = E.act[ag];
+                int64_t bid = 0, ask = 0;
+                bool has_bid = false, has_ask = false;
+                if (c.mm_space == 0) {
+                    // 12-way head: bid / ask each 0, 1 or 2 ticks behind the touch,
+                    // or one tick into the spread on one side
+                    has_bid = has_ask = a >= 1 && a <= 11;
+                    if (a >= 1 && a <= 9) { bid = bb - (a - 1) / 3; ask = ba + (a - 1) % 3; }
+                    else if (a == 10) { bid = bb + 1; ask = ba; }
+                    else if (a == 11) { bid = bb; ask = ba - 1; }
+                } else if (c.mm_space == 1) {
+                    // Fixed Quantity, 8 options: none; 2 / 4 ticks behind both
+                    // touches; one tick into the spread on both; 2 ticks behind on
+                    // the bid only / the ask only; 5 ticks behind on one side with
+                    // one tick into the spread on the other
+                    switch (a) {
+                        case 1: bid = bb - 2; ask = ba + 2; has_bid = has_ask = true; break;
+                        case 2: bid = bb - 4; ask = ba + 4; has_bid = has_ask = true; break;
+                        case 3: bid = bb + 1; ask = ba - 1; has_bid = has_ask = true; break;
+                        case 4: bid = bb - 2; has_bid = true; break;
+                        case 5: ask = ba + 2; has_ask = true; break;
+                        case 6: bid = bb - 5; ask = ba - 1; has_bid = has_ask = true; break;
+                        case 7: bid = bb + 1; ask = ba + 5; has_bid = has_ask = true; break;
+                        default: break;
+                    }
+                } else {
+                    // directional trading: a bid at the best bid, an ask at the best ask, or nothing
+                    if (a == 1) { bid = bb; has_bid = true; }
+                    if (a == 2) { ask = ba; has_ask = true; }
                 }
-            } else {
-                // directional trading: a bid at the best bid, an ask at the best ask, or nothing
-                if (a == 1) { bid = bb; has_bid = true; }
-                if (a == 2) { ask = ba; has_ask = true; }
+                if (has_bid) want.push_back({ag, BUY, (int32_t)bid, c.mm_lot});
+                if (has_ask) want.push_back({ag, SELL, (int32_t)ask, c.mm_lot});
             }
-            if (has_bid) want.push_back({1, BUY, (int32_t)bid, c.mm_lot});
-            if (has_ask) want.push_back({1, SELL, (int32_t)ask, c.mm_lot});
             // -- carry-over: keep same-(side, price) resting orders, cancel the rest
             std::vector<int64_t> kept(want.size(), 0);
             for (int ag = 0; ag < A; ag++) {
@@ -539,7 +545,8 @@ struct Engine {
                 int64_t pv = wadd(wmul(g.inv, pref), g.cash);
                 E.rew[a] = wsub(pv, g.pv_prev);
                 g.pv_prev = pv;
-                if (a == 1 && c.reward_mode != 0) {
+                const bool mm = a >= A / 2;
+                if (mm && c.reward_mode != 0) {
                     // Sec. 5: trading PnL against the average mid over the step,
                     // read as the mean of its start and end mids, so 4*Mbar is
                     // an integer and the reward is exact in quarter-tick*qty.
@@ -558,9 +565,9 @@ struct Engine {
                     }
                     E.rew[a] = r4;
                 }
-                if (a == 1 && c.inv_penalty != 0)   // quadratic inventory penalty
+                if (mm && c.inv_penalty != 0)   // quadratic inventory penalty
                     E.rew[a] = wsub(E.rew[a], wmul(c.inv_penalty, wmul(g.inv, g.inv)));
-                if (a == 0 && c.exec_penalty_milli != 0 && last) {
+                if (!mm && c.exec_penalty_milli != 0 && last) {
                     // Table 2: penalty on the part of the task still unfilled at the end
                     const int64_t unfilled = std::max<int64_t>(0, (int64_t)c.exec_target - g.exec_done);
                     E.rew[a] = wsub(E.rew[a], (wmul(c.exec_penalty_milli, unfilled) + 999) / 1000);  // rounded up
@@ -581,7 +588,8 @@ struct Engine {
 extern "C" {
 
 void *orc_create(const orc_config *cfg, const int32_t *caps) {
-    if (!cfg || cfg->n_envs < 0 || (cfg->n_agents != 0 && cfg->n_agents != 2)) return nullptr;
+    if (!cfg || cfg->n_envs < 0 || cfg->n_agents < 0 || cfg->n_agents % 2 != 0 || cfg->n_agents > 2 * ORC_MAX_PER_TYPE)
+        return nullptr;
     Engine *g = new Engine();
     g->cfg.c = *cfg;
     g->envs.resize((size_t)cfg->n_envs);
@@ -590,6 +598,9 @@ void *orc_create(const orc_config *cfg, const int32_t *caps) {
         E.cap = caps ? caps[e] : cfg->cap;
         E.bids.is_bid = true;
         E.asks.is_bid = false;
+        E.ag.assign((size_t)cfg->n_agents, Agent());
+        E.rew.assign((size_t)cfg->n_agents, 0);
+        E.act.assign((size_t)cfg->n_agents, 0);
     }
     if (cfg->n_envs > 0 && (cfg->trace & 2)) g->envs[0].snaps = &g->snaps;
     return g;
@@ -611,9 +622,12 @@ void orc_reset(void *h, const uint64_t *env_seeds) {
         E.asks.is_bid = false;
         E.seed = env_seeds[e];
         E.last_px = g->cfg.c.start_px;
+        E.ag.assign((size_t)g->cfg.c.n_agents, Agent());
+        E.rew.assign((size_t)g->cfg.c.n_agents, 0);
+        E.act.assign((size_t)g->cfg.c.n_agents, 0);
         if (g->ep_mode) g->begin_episode(E, 0);
         // reset observation: the starting book (empty outside episode mode),
-        // nothing held, the whole episode and (for the execution agent) the
+        // nothing held, the whole episode and (for the execution agents) the
         // whole target still ahead
         g->write_obs(E, (float)g->cfg.c.episode_len / (float)g->cfg.c.episode_len);
     }

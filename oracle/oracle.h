@@ -24,10 +24,12 @@ extern "C" {
 #endif
 
 #define ORC_NCOUNTERS 16
+#define ORC_MAX_PER_TYPE 16   /* agents per type (Table 1 runs 1, 5 and 10) */
 
 typedef struct orc_config {
     int32_t n_envs;
-    int32_t n_agents;     /* 0 (pure replay) or 2 (agent 0 executes, agent 1 makes markets) */
+    int32_t n_agents;     /* 0 (pure replay) or 2P: P execution agents (0..P-1), then P market
+                             makers (P..2P-1), P <= ORC_MAX_PER_TYPE */
     int32_t cap;          /* book capacity per side when no per-env array is given */
     int32_t top_levels;   /* L aggregated levels per side in the observation */
     int32_t episode_len;  /* T */

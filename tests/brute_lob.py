@@ -65,7 +65,8 @@ class BruteEnv:
         self.inv = [0] * n_agents
         self.cash = [0] * n_agents
         self.pv_prev = [0] * n_agents
-        self.exec_done = 0
+        self.P = n_agents // 2            # agents per type: 0..P-1 execute, P..2P-1 make markets
+        self.exec_done = [0] * n_agents
         self.bg_cash = 0
         self.bg_inv = 0
         self.c = dict(msgs=0, agent_msgs=0, fills=0, fill_vol=0, add_vol=0, mkt_vol=0,
@@ -76,7 +77,7 @@ class BruteEnv:
         self.obs = [[0.0] * D for _ in range(n_agents)]
         for a in range(n_agents):
             self.obs[a][4 * top_levels + 2] = 1.0
-            if a == 0:
+            if a < n_agents // 2:
                 self.obs[a][4 * top_levels + 3] = float(exec_target)
         self.rew = [0] * n_agents
         self.done = 0
@@ -96,7 +97,7 @@ class BruteEnv:
         self.inv = [0] * self.A
         self.cash = [0] * self.A
         self.pv_prev = [0] * self.A
-        self.exec_done = 0
+        self.exec_done = [0] * self.A
         self.last_px = int(st["last_px"])
         self.ep_start = int(st["data_step"])
         idx = 0
@@ -150,8 +151,9 @@ class BruteEnv:
         self._credit(buyer, -maker["px"] * f, f)
         self._credit(seller, maker["px"] * f, -f)
         self.step_fills.append((buyer, seller, maker["px"], f))
-        if self.A and (seller if self.exec_dir == SELL else buyer) == 0:
-            self.exec_done += f
+        task_owner = seller if self.exec_dir == SELL else buyer
+        if self.A and task_owner < self.P:
+            self.exec_done[task_owner] += f
         self.last_px = maker["px"]
         self.c["fills"] += 1
         self.c["fill_vol"] += f
@@ -228,17 +230,21 @@ class BruteEnv:
         self.step_fills = []   # (buyer, seller, price, qty) of this step
         self.msg_idx = 0
         mid_before = (self.touch(BUY) + self.touch(SELL)) / 2
-        if self.A == 2:
+        if self.A:
+            P = self.P
+            n_mm = (12, 8, 3)[self.mm_space]
             if self.action_mode == 1:
-                n_mm = (12, 8, 3)[self.mm_space]
-                self.acts = [bounded(keyed_draws(self.seed, self.t, TAG_POLICY, 2)[a], (12, n_mm)[a]) for a in range(2)]
+                draws = keyed_draws(self.seed, self.t, TAG_POLICY, self.A)
+                self.acts = [bounded(draws[a], 12 if a < P else n_mm) for a in range(self.A)]
             else:
                 self.acts = list(actions)
             bb, ba = self.touch(BUY), self.touch(SELL)
             want = []   # (agent, side, px, qty)
-            remaining = self.exec_target - self.exec_done
-            if remaining > 0:
-                a = self.acts[0]
+            for ag in range(P):
+                remaining = self.exec_target - self.exec_done[ag]
+                if remaining <= 0:
+                    continue
+                a = self.acts[ag]
                 mult = (1, 2, 5)[a % 3]
                 q0 = max(1, -(-self.exec_target // self.T))
                 qty = min(mult * q0, remaining)
@@ -246,22 +252,23 @@ class BruteEnv:
                     prices = (bb, -((-(bb + ba)) // 2), ba, ba + 2)
                 else:
                     prices = (ba, (bb + ba) // 2, bb, bb - 2)
-                want.append((0, self.exec_dir, prices[a // 3], qty))
-            a = self.acts[1]
-            if self.mm_space == 0:
-                if 1 <= a <= 9:
-                    quotes = (bb - (a - 1) // 3, ba + (a - 1) % 3)
+                want.append((ag, self.exec_dir, prices[a // 3], qty))
+            for ag in range(P, self.A):
+                a = self.acts[ag]
+                if self.mm_space == 0:
+                    if 1 <= a <= 9:
+                        quotes = (bb - (a - 1) // 3, ba + (a - 1) % 3)
+                    else:
+                        quotes = {10: (bb + 1, ba), 11: (bb, ba - 1)}.get(a, (None, None))
+                elif self.mm_space == 1:
+                    quotes = {1: (bb - 2, ba + 2), 2: (bb - 4, ba + 4), 3: (bb + 1, ba - 1), 4: (bb - 2, None),
+                              5: (None, ba + 2), 6: (bb - 5, ba - 1), 7: (bb + 1, ba + 5)}.get(a, (None, None))
                 else:
-                    quotes = {10: (bb + 1, ba), 11: (bb, ba - 1)}.get(a, (None, None))
-            elif self.mm_space == 1:
-                quotes = {1: (bb - 2, ba + 2), 2: (bb - 4, ba + 4), 3: (bb + 1, ba - 1), 4: (bb - 2, None),
-                          5: (None, ba + 2), 6: (bb - 5, ba - 1), 7: (bb + 1, ba + 5)}.get(a, (None, None))
-            else:
-                quotes = {1: (bb, None), 2: (None, ba)}.get(a, (None, None))
-            if quotes[0] is not None:
-                want.append((1, BUY, quotes[0], self.mm_lot))
-            if quotes[1] is not None:
-                want.append((1, SELL, quotes[1], self.mm_lot))
+                    quotes = {1: (bb, None), 2: (None, ba)}.get(a, (None, None))
+                if quotes[0] is not None:
+                    want.append((ag, BUY, quotes[0], self.mm_lot))
+                if quotes[1] is not None:
+                    want.append((ag, SELL, quotes[1], self.mm_lot))
             kept = [0] * len(want)
             cancels = []
             for ag in range(self.A):
@@ -296,12 +303,12 @@ class BruteEnv:
                 pv = wrap(self.inv[a] * pref + self.cash[a])
                 self.rew[a] = wrap(pv - self.pv_prev[a])
                 self.pv_prev[a] = pv
-                if a == 1 and self.reward_mode:
-                    self.rew[a] = self._mm_reward(mid_before, (bb + ba) / 2)
-                if a == 1:
+                if a >= self.P and self.reward_mode:
+                    self.rew[a] = self._mm_reward(a, mid_before, (bb + ba) / 2)
+                if a >= self.P:
                     self.rew[a] -= self.inv_penalty * self.inv[a] ** 2
-                if a == 0 and te + 1 == self.T:
-                    unfilled = max(0, self.exec_target - self.exec_done)
+                if a < self.P and te + 1 == self.T:
+                    unfilled = max(0, self.exec_target - self.exec_done[a])
                     self.rew[a] = self.rew[a] - self.exec_penalty_milli * unfilled / Fraction(1000)
                     self.rew[a] = self.rew[a].numerator // self.rew[a].denominator
         self.done = int(te + 1 == self.T)
@@ -335,18 +342,18 @@ class BruteEnv:
             ob[4 * self.L] = float(self.inv[a])
             ob[4 * self.L + 1] = float(self.cash[a])
             ob[4 * self.L + 2] = time_left
-            ob[4 * self.L + 3] = float(self.exec_target - self.exec_done) if a == 0 else 0.0
+            ob[4 * self.L + 3] = float(self.exec_target - self.exec_done[a]) if a < self.P else 0.0
             ob[4 * self.L + 4] = float(rest[a])
 
-    def _mm_reward(self, mid_before, mid_after):
-        """Eqs. 3-4 from the fill list, with exact fractions, returned in quarter ticks."""
+    def _mm_reward(self, a, mid_before, mid_after):
+        """Eqs. 3-4 for agent a from the fill list, with exact fractions, returned in quarter ticks."""
         Fr = Fraction
         mbar = (Fr(mid_before) + Fr(mid_after)) / 2
-        psi_b = sum(((mbar - p) * q for b, s, p, q in self.step_fills if b == 1), Fr(0))
-        psi_s = sum(((p - mbar) * q for b, s, p, q in self.step_fills if s == 1), Fr(0))
+        psi_b = sum(((mbar - p) * q for b, s, p, q in self.step_fills if b == a), Fr(0))
+        psi_s = sum(((p - mbar) * q for b, s, p, q in self.step_fills if s == a), Fr(0))
         r = psi_b + psi_s
         if self.reward_mode == 2:
-            psi_inv = self.inv[1] * (Fr(mid_after) - Fr(mid_before))
+            psi_inv = self.inv[a] * (Fr(mid_after) - Fr(mid_before))
             r += psi_inv - Fr(100 - self.lam_pct, 100) * max(Fr(0), psi_inv)
         r4 = 4 * r
         return r4.numerator // r4.denominator   # floor: only the lambda damping can be fractional

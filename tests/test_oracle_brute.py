@@ -140,3 +140,50 @@ def test_oracle_matches_brute_episodes(seed):
             assert rew[e].tolist() == b.rew
             assert int(done[e]) == b.done
             assert o.episode_starts()[e] == b.ep_start
+
+
+@pytest.mark.parametrize("seed", range(9))
+def test_oracle_matches_brute_agents_per_type(seed):
+    """P = 2..10 agents per type (Table 1 runs 5 and 10): per-agent actions,
+    carry-over, shuffle over up to 3P new orders, fills, tasks, obs, rewards."""
+    rng = np.random.default_rng(700 + seed)
+    P = [2, 3, 5, 10][seed % 4]
+    A = 2 * P
+    cap = int(rng.integers(2, 12))
+    T = 8
+    n_env = 2
+    model = mbogen.MessageModel(price_p=0.6, size_p=0.3, msgs_per_step=int(rng.integers(3, 25)), mix_market=0.2)
+    seeds = mbogen.env_seeds(4000 + seed, n_env)
+    st = mbogen.generate(model, seeds, T)
+    host = seed % 2 == 0
+    space = seed % 3
+    n_mm = (12, 8, 3)[space]
+    kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)), exec_target=int(rng.integers(5, 40)),
+              exec_dir=int(rng.choice([-1, 1])), start_px=10_000, mm_space=space,
+              reward_mode=seed % 3, spooner_lambda_pct=60, inv_penalty=seed % 2, exec_penalty_milli=100)
+    o = oracle.Oracle(n_env, n_agents=A, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
+    o.reset(seeds)
+    o.load_messages(st.msgs, st.offsets)
+    brutes = [brute_lob.BruteEnv(cap, n_agents=A, seed=int(seeds[e]), action_mode=0 if host else 1, **kw)
+              for e in range(n_env)]
+    for t in range(T):
+        acts = None
+        if host:
+            acts = np.concatenate([rng.integers(0, 12, size=(n_env, P)), rng.integers(0, n_mm, size=(n_env, P))],
+                                  axis=1).astype(np.int32)
+        o.step(acts)
+        obs, rew, done = o.observe()
+        for e in range(n_env):
+            b = brutes[e]
+            msgs = st.msgs[st.offsets[e, t]:st.offsets[e, t + 1]]
+            b.step(msgs, None if acts is None else acts[e].tolist())
+            fl = o.fills(e)
+            _compare(o, b, e, [(f["maker_id"], f["taker_id"], f["px"], f["qty"], f["msg_idx"], f["taker_side"])
+                               for f in fl])
+            np.testing.assert_array_equal(obs[e], np.array(b.obs, np.float32))
+            assert rew[e].tolist() == b.rew
+            assert int(done[e]) == b.done
+            assert o.actions()[e].tolist() == b.acts
+        ag = o.agents()
+        for e in range(n_env):
+            assert ag[e, :, 3].tolist() == brutes[e].exec_done

@@ -107,6 +107,40 @@ def test_hand_worked_two_agent_episode():
     assert o.agents()[0].tolist() == g["final_agents"]
 
 
+def test_hand_worked_multi_agent_episode():
+    """Two agents per type (Sec. 3, Table 1): per-agent attribution of fills,
+    carry-over cancels, tasks, observations and rewards."""
+    g = _gold("multi_agent.json")
+    c = g["config"]
+    A = 2 * c["agents_per_type"]
+    msgs, off = single_env_stream([s["msgs"] for s in g["steps"]])
+    o = oracle.Oracle(1, n_agents=A, cap=c["cap"], top_levels=c["top_levels"], episode_len=c["episode_len"],
+                      exec_target=c["exec_target"], exec_dir=c["exec_dir"], mm_lot=c["mm_lot"],
+                      start_px=c["start_px"], action_mode=0, trace=1)
+    o.reset(np.array([5], np.uint64))
+    o.load_messages(msgs, off)
+    prev = 0
+    for s in g["steps"]:
+        assert o.step(np.array([s["actions"]], np.int32)) == 0
+        bids, asks = _book_rows(o)
+        assert [[r[0], r[1], _owner(r[2], A)] for r in bids] == s["bids"]
+        assert [[r[0], r[1], _owner(r[2], A)] for r in asks] == s["asks"]
+        fills = [[_owner(int(x["maker_id"]), A), _owner(int(x["taker_id"]), A), int(x["px"]), int(x["qty"])]
+                 for x in o.fills(0)]
+        assert fills == s["fills"]
+        obs, rew, done = o.observe()
+        np.testing.assert_array_equal(obs[0], np.array(s["obs"], np.float32))
+        assert rew[0].tolist() == s["rewards"]
+        assert int(done[0]) == s["done"]
+        am = int(o.counters()[0][oracle.COUNTER_NAMES.index("agent_msgs")])
+        assert am - prev == s["agent_msgs"]
+        prev = am
+    assert o.agents()[0].tolist() == g["final_agents"]
+    cnt = dict(zip(oracle.COUNTER_NAMES, o.counters()[0].tolist()))
+    for k, v in g["final_counters"].items():
+        assert cnt[k] == v, k
+
+
 def _reward_cases():
     for sc in _gold("reward_variants.json")["scenarios"]:
         for ex in sc["expected"]:
