@@ -91,9 +91,13 @@ typedef struct lob_fill {
     int32_t taker_side; /* LOB_BUY / LOB_SELL */
 } lob_fill;
 
+#define LOB_MAX_PER_TYPE 16   /* agents of each type per env (Table 1 runs 1, 5 and 10) */
+
 typedef struct lob_config {
     int32_t n_envs;        /* >= 1 */
-    int32_t n_agents;      /* 0 (replay only) or 2 (execution agent 0, market maker 1) */
+    int32_t n_agents;      /* 0 (replay only) or 2P, P <= LOB_MAX_PER_TYPE agents of each type (Sec. 3):
+                              agents 0..P-1 execute (each its own task), P..2P-1 make markets;
+                              P = 1 is the benchmark pair (execution agent 0, market maker 1) */
     int32_t cap_per_side;  /* book capacity per side, 1..LOB_MAX_CAP (Table 2: 100) */
     int32_t top_levels;    /* L aggregated levels per side in the observation, 1..64 */
     int32_t episode_len;   /* T steps per episode, >= 1 */

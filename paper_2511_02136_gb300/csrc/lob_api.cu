@@ -63,16 +63,23 @@ int max_wpb(int K) {
     const int m = (int)(SMEM_PER_BLOCK_MAX / warp_smem_bytes(K));
     return m < 8 ? m : 8;
 }
+// The same for the several-agents kernel (each warp also holds an agent block).
+int max_wpb_ma(int K) {
+    const int m = (int)(SMEM_PER_BLOCK_MAX / (warp_smem_bytes(K) + sizeof(AgentSmem)));
+    return m < 8 ? m : 8;
+}
 
 cudaError_t optin_k(int K) {
     const size_t smem = (size_t)max_wpb(K) * warp_smem_bytes(K);
+    const size_t smem_ma = (size_t)max_wpb_ma(K) * (warp_smem_bytes(K) + sizeof(AgentSmem));
+    cudaError_t e;
     switch (K) {
-        case 1: return optin_steps_1(smem);
-        case 2: return optin_steps_2(smem);
-        case 4: return optin_steps_4(smem);
-        case 8: return optin_steps_8(smem);
-        case 16: return optin_steps_16(smem);
-        default: return optin_steps_32(smem);
+        case 1: e = optin_steps_1(smem); return e == cudaSuccess ? optin_steps_ma_1(smem_ma) : e;
+        case 2: e = optin_steps_2(smem); return e == cudaSuccess ? optin_steps_ma_2(smem_ma) : e;
+        case 4: e = optin_steps_4(smem); return e == cudaSuccess ? optin_steps_ma_4(smem_ma) : e;
+        case 8: e = optin_steps_8(smem); return e == cudaSuccess ? optin_steps_ma_8(smem_ma) : e;
+        case 16: e = optin_steps_16(smem); return e == cudaSuccess ? optin_steps_ma_16(smem_ma) : e;
+        default: e = optin_steps_32(smem); return e == cudaSuccess ? optin_steps_ma_32(smem_ma) : e;
     }
 }
 
@@ -117,6 +124,21 @@ int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
 
 cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s,
                      const KParams &p) {
+    if (p.n_agents > 2) {
+        // several agents per type: the wide kernel with a per-warp agent block
+        wpb = wpb < max_wpb_ma(K) ? wpb : max_wpb_ma(K);
+        int blocks = (n_list + wpb - 1) / wpb;
+        if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
+        const size_t smem = (size_t)wpb * (warp_smem_bytes(K) + sizeof(AgentSmem));
+        switch (K) {
+            case 1: return launch_steps_ma_1(trace, blocks, 32 * wpb, smem, s, p);
+            case 2: return launch_steps_ma_2(trace, blocks, 32 * wpb, smem, s, p);
+            case 4: return launch_steps_ma_4(trace, blocks, 32 * wpb, smem, s, p);
+            case 8: return launch_steps_ma_8(trace, blocks, 32 * wpb, smem, s, p);
+            case 16: return launch_steps_ma_16(trace, blocks, 32 * wpb, smem, s, p);
+            default: return launch_steps_ma_32(trace, blocks, 32 * wpb, smem, s, p);
+        }
+    }
     wpb = wpb < max_wpb(K) ? wpb : max_wpb(K);
     int blocks = (n_list + wpb - 1) / wpb;
     if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
@@ -196,6 +218,8 @@ struct lob_handle {
     size_t stage_cap = 0;
     int64_t *d_stage_off = nullptr;
     int32_t *d_stage_act = nullptr;
+    // several agents per type: per-agent state [n_envs][n_agents]
+    AgentState *d_agents = nullptr;
     // episode mode (one shared stream, snapshot table, auto-reset)
     bool ep_mode = false;
     const int64_t *ep_off = nullptr;
@@ -218,7 +242,7 @@ static void free_all(lob_handle *h) {
     void *ptrs[] = {h->d_books, h->d_book_off, h->d_canon_off, h->d_caps, h->d_state, h->d_counters,
                     h->d_seeds, h->d_status, h->d_obs, h->d_rew, h->d_done, h->d_act, h->d_env_list,
                     h->d_queue, h->d_stage_msgs, h->d_stage_off, h->d_stage_act, h->d_ep_starts,
-                    h->d_ep_levels, h->d_ep_images, h->d_ep_obs};
+                    h->d_ep_levels, h->d_ep_images, h->d_ep_obs, h->d_agents};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -248,7 +272,8 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     if (!cfg || !out) return LOB_EINVAL;
     *out = nullptr;
     const lob_config &c = *cfg;
-    if (c.n_envs < 1 || (c.n_agents != 0 && c.n_agents != 2) || c.top_levels < 1 || c.top_levels > LMAX ||
+    if (c.n_envs < 1 || c.n_agents < 0 || c.n_agents % 2 != 0 || c.n_agents > 2 * LOB_MAX_PER_TYPE ||
+        c.top_levels < 1 || c.top_levels > LMAX ||
         c.episode_len < 1 || c.mm_lot < 1 || c.exec_target < 0 ||
         (c.exec_dir != LOB_SELL && c.exec_dir != LOB_BUY) ||
         (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace < 0 || c.trace > 3 ||
@@ -315,7 +340,8 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     alloc((void **)&h->d_obs, n * (size_t)(A * h->D) * 4);
     alloc((void **)&h->d_rew, n * (size_t)A * 8);
     alloc((void **)&h->d_done, n);
-    alloc((void **)&h->d_act, n * 2 * 4);
+    alloc((void **)&h->d_act, n * (size_t)(A > 2 ? A : 2) * 4);
+    if (A > 2) alloc((void **)&h->d_agents, n * (size_t)A * sizeof(AgentState));
     alloc((void **)&h->d_env_list, n * 4);
     alloc((void **)&h->d_queue, NCLASS * 4);
     if (fail) {
@@ -386,7 +412,7 @@ __global__ void k_reset(EnvState *st, long long *cnt, unsigned long long *seeds_
         float *o = obs + ((long long)e * A + a) * D;
         for (int f = 0; f < D; f++) o[f] = 0.0f;
         o[4 * L + 2] = 1.0f;                                   // time left T / T
-        if (a == 0) o[4 * L + 3] = __ll2float_rn(exec_target);  // remaining target
+        if (a < (A >> 1)) o[4 * L + 3] = __ll2float_rn(exec_target);  // remaining target (execution agents)
     }
     EnvState z;
     memset(&z, 0, sizeof(z));
@@ -444,7 +470,7 @@ __global__ void k_ep_obs(const lob_start *starts, const int *levels, int ls, int
             if (lvl < n) v = __ll2float_rn((f & 1) ? (long long)lv[1] : (long long)lv[0] - anchor);
         } else if (f == 4 * L + 2) {
             v = 1.0f;
-        } else if (f == 4 * L + 3 && a == 0) {
+        } else if (f == 4 * L + 3 && a < (A >> 1)) {
             v = __ll2float_rn(exec_target);
         }
         obs[(long long)j * A * D + i] = v;
@@ -483,6 +509,14 @@ __global__ void k_reset_ep(EnvState *st, long long *cnt, unsigned long long *see
 __global__ void k_get_ep_start(const EnvState *st, int *out, int n) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) out[e] = st[e].ep_start;
+}
+
+// Several agents per type: [inv, cash, pv_prev, exec_done] per (env, agent).
+__global__ void k_get_agents_ma(const AgentState *ag, long long *out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const AgentState x = ag[i];
+    out[4 * i + 0] = x.inv; out[4 * i + 1] = x.cash; out[4 * i + 2] = x.pv_prev; out[4 * i + 3] = x.exec_done;
 }
 
 // internal blocked layout -> canonical priority-ordered record per env
@@ -561,6 +595,7 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.wait_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
     set_rewards(p, c);
+    p.agents = h->d_agents;
     if (h->ep_mode) {
         p.ep_mode = 1;
         p.n_starts = h->n_starts;
@@ -678,10 +713,16 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
                                      h->d_ep_obs, h->d_obs, h->cfg.n_agents, h->D);
         h->launches++;
         if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
+        if (h->d_agents &&
+            cudaMemsetAsync(h->d_agents, 0, (size_t)n * h->cfg.n_agents * sizeof(AgentState), s) != cudaSuccess)
+            return LOB_ECUDA;
         h->t = 0;
         h->reset_done = true;
         return LOB_OK;
     }
+    if (h->d_agents &&
+        cudaMemsetAsync(h->d_agents, 0, (size_t)n * h->cfg.n_agents * sizeof(AgentState), s) != cudaSuccess)
+        return LOB_ECUDA;
     k_reset<<<(n + 127) / 128, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                              reinterpret_cast<const unsigned long long *>(d_env_seeds), n,
                                              h->cfg.start_px, h->d_obs, h->cfg.n_agents, h->D, h->cfg.top_levels,
@@ -696,7 +737,7 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
 int lob_step(lob_handle *h, const int32_t *d_actions, void *stream) {
     if (!h) return LOB_EINVAL;
     if (!steps_left(h, 1)) return LOB_ESTATE;
-    if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
+    if (h->cfg.n_agents > 0 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
     int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, d_actions, 0, h->d_obs, h->d_rew,
                           h->d_done, (cudaStream_t)stream);
     if (rc != LOB_OK) return rc;
@@ -709,10 +750,11 @@ int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float 
                 uint8_t *d_done, void *stream) {
     if (!h || n_steps < 1) return LOB_EINVAL;
     if (!steps_left(h, n_steps)) return LOB_ESTATE;
-    if (h->cfg.n_agents == 2 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
+    if (h->cfg.n_agents > 0 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, n_steps, d_actions,
-                          2LL * h->cfg.n_envs, d_obs, reinterpret_cast<long long *>(d_rewards), d_done, s);
+                          (long long)h->cfg.n_agents * h->cfg.n_envs, d_obs, reinterpret_cast<long long *>(d_rewards),
+                          d_done, s);
     if (rc != LOB_OK) return rc;
     // keep the last step's outputs for lob_observe
     const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
@@ -741,8 +783,9 @@ int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets
     if (!h || !h_offsets) return LOB_EINVAL;
     if (!h->reset_done || h->ep_mode || h->t >= h->cfg.episode_len) return LOB_ESTATE;
     const lob_config &c = h->cfg;
-    if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST && !h_actions) return LOB_EINVAL;
+    if (c.n_agents > 0 && c.action_mode == LOB_ACT_HOST && !h_actions) return LOB_EINVAL;
     const int n = c.n_envs;
+    const size_t na = (size_t)(c.n_agents > 2 ? c.n_agents : 2);   // action slots per env
     const int64_t base = h_offsets[0], total = h_offsets[n] - base;
     if (total < 0) return LOB_EINVAL;
     for (int e = 0; e < n; e++)
@@ -761,7 +804,7 @@ int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets
     }
     if (!h->d_stage_off) {
         if (cudaMalloc(&h->d_stage_off, ((size_t)n + 1) * 8) != cudaSuccess) return LOB_ENOMEM;
-        if (cudaMalloc(&h->d_stage_act, (size_t)n * 2 * 4) != cudaSuccess) return LOB_ENOMEM;
+        if (cudaMalloc(&h->d_stage_act, (size_t)n * na * 4) != cudaSuccess) return LOB_ENOMEM;
     }
     int rc = LOB_OK;
     if (total > 0)
@@ -771,8 +814,9 @@ int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets
     std::vector<int64_t> rel((size_t)n + 1);
     for (int e = 0; e <= n; e++) rel[(size_t)e] = h_offsets[e] - base;
     rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_off, rel.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, s));
-    if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST)
-        rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_act, h_actions, (size_t)n * 2 * 4, cudaMemcpyHostToDevice, s));
+    if (c.n_agents > 0 && c.action_mode == LOB_ACT_HOST)
+        rc |= cuda_ok(cudaMemcpyAsync(h->d_stage_act, h_actions, (size_t)n * c.n_agents * 4, cudaMemcpyHostToDevice,
+                                      s));
     if (rc != LOB_OK) return LOB_ECUDA;
     rc = launch_steps(h, h->d_stage_msgs, h->d_stage_off, 1, 0, 1, h->d_stage_act, 0, h->d_obs, h->d_rew,
                       h->d_done, s);
@@ -807,6 +851,13 @@ int lob_get_agents(lob_handle *h, int64_t *d_out, void *stream) {
     if (!h || !d_out) return LOB_EINVAL;
     if (h->cfg.n_agents == 0) return LOB_OK;
     const int n = h->cfg.n_envs;
+    if (h->d_agents) {
+        const long long m = (long long)n * h->cfg.n_agents;
+        k_get_agents_ma<<<(unsigned)((m + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+            h->d_agents, reinterpret_cast<long long *>(d_out), m);
+        h->launches++;
+        return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+    }
     k_get_agents<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(h->d_state, reinterpret_cast<long long *>(d_out),
                                                                      n, h->cfg.n_agents, 0);
     h->launches++;
@@ -825,6 +876,10 @@ int lob_get_env_misc(lob_handle *h, int64_t *d_out, void *stream) {
 int lob_get_actions(lob_handle *h, int32_t *d_out, void *stream) {
     if (!h || !d_out) return LOB_EINVAL;
     if (h->cfg.n_agents == 0) return LOB_OK;
+    if (h->d_agents)
+        return cuda_ok(cudaMemcpy2DAsync(d_out, 4, reinterpret_cast<const char *>(h->d_agents) + offsetof(AgentState, act),
+                                         sizeof(AgentState), 4, (size_t)h->cfg.n_envs * h->cfg.n_agents,
+                                         cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return cuda_ok(cudaMemcpy2DAsync(d_out, 8, reinterpret_cast<const char *>(h->d_state) + offsetof(EnvState, act),
                                      sizeof(EnvState), 8, (size_t)h->cfg.n_envs, cudaMemcpyDeviceToDevice,
                                      (cudaStream_t)stream));
@@ -1052,9 +1107,11 @@ int cap_signature(const lob_handle *h) {
 struct Region { void *dev; size_t bytes; };
 std::vector<Region> ckpt_regions(lob_handle *h) {
     const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
-    return {{h->d_books, (size_t)h->book_bytes}, {h->d_state, n * sizeof(EnvState)},
-            {h->d_counters, n * 8 * LOB_NCOUNTERS}, {h->d_seeds, n * 8}, {h->d_obs, n * A * D * 4},
-            {h->d_rew, n * A * 8}, {h->d_done, n}};
+    std::vector<Region> r = {{h->d_books, (size_t)h->book_bytes}, {h->d_state, n * sizeof(EnvState)},
+                             {h->d_counters, n * 8 * LOB_NCOUNTERS}, {h->d_seeds, n * 8}, {h->d_obs, n * A * D * 4},
+                             {h->d_rew, n * A * 8}, {h->d_done, n}};
+    if (h->d_agents) r.push_back({h->d_agents, n * A * sizeof(AgentState)});
+    return r;
 }
 }  // namespace
 

@@ -58,6 +58,16 @@ struct __align__(16) EnvState {
 };
 static_assert(sizeof(EnvState) == 128, "env state");
 
+// Several agents per type (Sec. 3, Table 1): per-agent state in HBM, one
+// record per (env, agent), agents 0..P-1 executing and P..2P-1 market making.
+constexpr int AMAX = 2 * LOB_MAX_PER_TYPE;
+struct __align__(16) AgentState {
+    long long inv, cash, pv_prev, exec_done;
+    int act;
+    int pad[3];
+};
+static_assert(sizeof(AgentState) == 48, "agent state");
+
 struct KParams {
     unsigned char *books;
     const long long *book_off;
@@ -106,6 +116,7 @@ struct KParams {
     const lob_start *ep_starts;
     const unsigned char *ep_images;
     const float *ep_obs;
+    AgentState *agents;              // several agents per type: [n_envs][n_agents]
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -196,6 +207,21 @@ static_assert(sizeof(WarpSmem<1>) % 16 == 0 && sizeof(WarpSmem<2>) % 16 == 0 && 
                   sizeof(WarpSmem<8>) % 16 == 0 && sizeof(WarpSmem<16>) % 16 == 0 && sizeof(WarpSmem<32>) % 16 == 0,
               "per-warp shared memory must keep 16-byte alignment across warps");
 static_assert(offsetof(WarpSmem<1>, tile) == 0 && offsetof(WarpSmem<32>, tile) == 0, "tiles lead the block");
+
+// Per-warp agent block of the several-agents kernel, after the WarpSmem
+// array: the step's agent orders (3 per agent pair at most, plus the record
+// read ahead), the agents' running state and the step's wanted orders.
+constexpr int AMSG_MA = 3 * LOB_MAX_PER_TYPE + 1;
+struct __align__(16) AgentSmem {
+    DevMsg amsg[AMSG_MA];
+    long long inv[AMAX], cash[AMAX], pv[AMAX], done[AMAX];
+    long long inv0[AMAX], cash0[AMAX];   // at the start of the step (reward variants)
+    long long own[AMAX];                 // resting quantity (observation)
+    long long kept[AMAX][2];             // carried-over quantity per wanted order
+    int want_px[AMAX][2], want_q[AMAX][2];   // [agent][0 bid, 1 ask]; q 0 = none
+    int act[AMAX];
+};
+static_assert(sizeof(AgentSmem) % 16 == 0, "agent block keeps 16-byte alignment");
 
 // ---------------------------------------------------------------- book side
 // Pool slot s of a side belongs to one lane, which scans it in its register
@@ -397,6 +423,7 @@ struct Ctx {
     int status;
     lob_fill *fill_log;
     int fill_cap;
+    AgentSmem *ag;   // several agents per type only
 
     __device__ __forceinline__ void credit(int who, long long dcash, long long dinv) {
         if (who == 0) { cash0 += dcash; inv0 += dinv; }
@@ -417,9 +444,40 @@ static __device__ __noinline__ void log_fill(lob_fill *log, int idx, long long m
 
 // A trade at the resting order's price; cash and inventory move between the
 // owners of the two orders (0, 1 = agents, 2 = background).
-template <bool TRACE>
+template <bool TRACE, bool MA = false>
 __device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_id, long long taker_id,
                                         int taker_side, int lane) {
+    if constexpr (MA) {
+        // owners: agent (-id - 1) mod A of a negative id, else background (A);
+        // agent state lives in shared memory, written by lane 0
+        const int A = c.A;
+        const int om = maker_id >= 0 ? A : (int)((unsigned long long)(~maker_id) % (unsigned)A);
+        const int ot = taker_id >= 0 ? A : (int)((unsigned long long)(~taker_id) % (unsigned)A);
+        const int buyer = taker_side == LOB_BUY ? ot : om;
+        const int seller = taker_side == LOB_BUY ? om : ot;
+        typedef unsigned long long u64;
+        const long long notional = (long long)((u64)(long long)px * (u64)(long long)f);
+        if (buyer == A) { c.bg_cash -= notional; c.bg_inv += f; }
+        if (seller == A) { c.bg_cash += notional; c.bg_inv -= f; }
+        if (lane == 0) {
+            AgentSmem &g = *c.ag;
+            if (buyer < A) { g.cash[buyer] = (long long)((u64)g.cash[buyer] - (u64)notional); g.inv[buyer] += f; }
+            if (seller < A) { g.cash[seller] = (long long)((u64)g.cash[seller] + (u64)notional); g.inv[seller] -= f; }
+            const int task = c.exec_dir == LOB_SELL ? seller : buyer;   // its owner, if executing, progresses
+            if (task < (A >> 1)) g.done[task] += f;
+        }
+        c.last_px = px;
+        c.c_fills += 1;
+        c.c_fill_vol += f;
+        if constexpr (TRACE) {
+            if (c.fill_log != nullptr) {
+                if (lane == 0 && c.fill_n < c.fill_cap)
+                    log_fill(c.fill_log, c.fill_n, maker_id, taker_id, px, f, c.msg_idx, taker_side);
+                c.fill_n++;
+            }
+        }
+        return;
+    }
     const int om = c.owner(maker_id), ot = c.owner(taker_id);
     const int buyer = taker_side == LOB_BUY ? ot : om;
     const int seller = taker_side == LOB_BUY ? om : ot;
@@ -446,7 +504,7 @@ __device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_i
 
 // Take liquidity from resting side O (RBID: O holds bids), price first then
 // time, up to the limit (if any).  Returns the unfilled quantity.
-template <int K, bool RBID, bool TRACE>
+template <int K, bool RBID, bool TRACE, bool MA = false>
 __device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_limit, int limit, int q,
                                          long long taker_id, int taker_side, Ctx &c, int lane) {
     while (q > 0 && O.n > 0 && (!has_limit || at_least<RBID>(O.fpx, limit))) {
@@ -457,7 +515,7 @@ __device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_li
         unsigned popped[Side<K>::NW];
         ix_removed<K>(O, 0, lane, popped);
         const int f = min(q, O.fqty);
-        do_fill<TRACE>(c, O.fpx, f, O.fid, taker_id, taker_side, lane);
+        do_fill<TRACE, MA>(c, O.fpx, f, O.fid, taker_id, taker_side, lane);
         q -= f;
         const bool gone = f == O.fqty;
         const int left = O.fqty - f;
@@ -857,7 +915,6 @@ __device__ __forceinline__ void side_agent_cancels(Side<K> &S, PoolSmem<K> &P, u
     }
 }
 
-// Message pipeline state of one warp (tiles issued so far).
 // Sec. 5 rewards of the market maker and the Table 2 penalties, in wrapping
 // 64-bit arithmetic.  With Mbar the step's average mid, Psi_b + Psi_s (Eq. 4)
 // sums (Mbar - P) Q over buys and (P - Mbar) Q over sells, which is
@@ -894,15 +951,170 @@ static __device__ __noinline__ longlong2 reward_variants(int mode, int lam_pct, 
     return make_longlong2(r0, r1);
 }
 
+// ---------------------------------------------------------------- several agents per type
+// Carry-over of one side for A agents: a resting agent order is kept when
+// its owner wants an order at its (side, price) -- its quantity adds to that
+// order's kept amount -- and flagged for cancellation (1 + owner) otherwise.
+template <int K>
+__device__ __forceinline__ unsigned side_carry_ma(const Side<K> &S, const PoolSmem<K> &P, unsigned char *cand, int sd,
+                                                  AgentSmem &ag, int A, int lane) {
+    unsigned cmask = 0;
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int slot = slot_of<K>(lane, r);
+        unsigned char flag = 0;
+        const long long oid = sid<K>(S, P, r, lane);
+        if (((S.occ >> r) & 1u) && oid < 0) {
+            const int a = (int)((unsigned long long)(~oid) % (unsigned)A);
+            if (ag.want_q[a][sd] > 0 && ag.want_px[a][sd] == spx<K>(S, P, r, lane)) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&ag.kept[a][sd]), (unsigned long long)P.qty[slot]);
+            } else {
+                flag = (unsigned char)(1 + a);
+                cmask |= 1u << r;
+            }
+        }
+        cand[slot] = flag;
+    }
+    return cmask;
+}
+
+// Resting quantity of every agent on one side (shared-memory atomics).
+template <int K>
+__device__ __forceinline__ void side_own_ma(const Side<K> &S, const PoolSmem<K> &P, AgentSmem &ag, int A, int lane) {
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const long long oid = sid<K>(S, P, r, lane);
+        if (((S.occ >> r) & 1u) && oid < 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&ag.own[(unsigned long long)(~oid) % (unsigned)A]),
+                      (unsigned long long)P.qty[slot_of<K>(lane, r)]);
+    }
+}
+
+// Action conversion of A = 2P agents (Sec. 4 with Sec. 3's agents of each
+// type), lanes over agents: the action (host or random policy), the
+// step-start state for the reward variants, and each agent's wanted orders
+// -- an execution agent one order at one of four reference prices times
+// {1, 2, 5} q0 while its task is unfinished, a market maker its space's
+// quotes of mm_lot.
+__device__ __forceinline__ void agent_wants_ma(const KParams &p, int e, int t, int step, unsigned long long seed,
+                                               long long bb, long long ba, AgentSmem &ag, Ctx &c, int lane) {
+    const int A = p.n_agents, P = A >> 1;
+    const int n_mm = p.mm_space == LOB_MM_FIXED_QUANT ? 8 : p.mm_space == LOB_MM_DIRECTIONAL ? 3 : 12;
+    const unsigned long long pkey = step_key(seed, t, TAG_POLICY);
+    for (int a = lane; a < A; a += 32) {
+        const int n_act = a < P ? 12 : n_mm;
+        int act;
+        if (p.action_mode == LOB_ACT_RANDOM) {
+            act = (int)bounded(sm_mix(pkey + GAMMA * (unsigned long long)(a + 1)), (unsigned)n_act);
+        } else {
+            act = p.actions[(long long)step * p.act_step_stride + (long long)e * A + a];
+            if (act < 0 || act >= n_act) c.status |= ST_BADACT;
+        }
+        ag.act[a] = act;
+        ag.inv0[a] = ag.inv[a];
+        ag.cash0[a] = ag.cash[a];
+        long long bpx = 0, apx = 0;
+        int bq = 0, aq = 0;
+        if (act >= 0 && act < n_act) {
+            if (a < P) {
+                const long long remaining = (long long)p.exec_target - ag.done[a];
+                if (remaining > 0) {
+                    const int pi = act / 3, mi = act % 3;
+                    const long long mult = mi == 0 ? 1 : (mi == 1 ? 2 : 5);
+                    long long qty = mult * p.exec_q0;
+                    qty = qty < remaining ? qty : remaining;
+                    const long long s2 = bb + ba;
+                    const long long fl = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
+                    const long long ce = s2 <= 0 ? -((-s2) / 2) : (s2 + 1) / 2;
+                    if (p.exec_dir == LOB_SELL) {
+                        apx = pi == 0 ? bb : pi == 1 ? ce : pi == 2 ? ba : ba + 2;
+                        aq = (int)qty;
+                    } else {
+                        bpx = pi == 0 ? ba : pi == 1 ? fl : pi == 2 ? bb : bb - 2;
+                        bq = (int)qty;
+                    }
+                }
+            } else if (p.mm_space == LOB_MM_SPREAD_SKEW) {
+                if (act >= 1) {
+                    if (act <= 9) { bpx = bb - (act - 1) / 3; apx = ba + (act - 1) % 3; }
+                    else if (act == 10) { bpx = bb + 1; apx = ba; }
+                    else { bpx = bb; apx = ba - 1; }
+                    bq = aq = p.mm_lot;
+                }
+            } else if (p.mm_space == LOB_MM_FIXED_QUANT) {
+                switch (act) {
+                    case 1: bpx = bb - 2; apx = ba + 2; bq = aq = p.mm_lot; break;
+                    case 2: bpx = bb - 4; apx = ba + 4; bq = aq = p.mm_lot; break;
+                    case 3: bpx = bb + 1; apx = ba - 1; bq = aq = p.mm_lot; break;
+                    case 4: bpx = bb - 2; bq = p.mm_lot; break;
+                    case 5: apx = ba + 2; aq = p.mm_lot; break;
+                    case 6: bpx = bb - 5; apx = ba - 1; bq = aq = p.mm_lot; break;
+                    case 7: bpx = bb + 1; apx = ba + 5; bq = aq = p.mm_lot; break;
+                    default: break;
+                }
+            } else {
+                if (act == 1) { bpx = bb; bq = p.mm_lot; }
+                if (act == 2) { apx = ba; aq = p.mm_lot; }
+            }
+        }
+        ag.want_px[a][0] = (int)bpx; ag.want_q[a][0] = bq;
+        ag.want_px[a][1] = (int)apx; ag.want_q[a][1] = aq;
+        ag.kept[a][0] = 0;
+        ag.kept[a][1] = 0;
+    }
+}
+
+// The orders the agents send after carry-over (wanted minus kept), in agent
+// order (an execution agent's order; a market maker's bid, then ask),
+// Fisher-Yates shuffled with the step's SplitMix64 draws, then given ids
+// -(1 + agent + A seq) in processing order.  Lane 0 writes them as message
+// records; returns their count on every lane.
+__device__ __forceinline__ int agent_orders_ma(const KParams &p, int t, unsigned long long seed, AgentSmem &ag,
+                                               Ctx &c, int lane) {
+    const int A = p.n_agents;
+    int ns = 0;
+    if (lane == 0) {
+        for (int a = 0; a < A; a++)
+            for (int sd = 0; sd < 2; sd++) {
+                const long long q = (long long)ag.want_q[a][sd] - ag.kept[a][sd];
+                if (ag.want_q[a][sd] > 0 && q > 0) {
+                    DevMsg r;
+                    r.ts = 0;
+                    r.oid = a;   // the owner until the ids are given
+                    r.px = ag.want_px[a][sd];
+                    r.qty = (int)q;
+                    r.type = (short)LOB_ADD;
+                    r.side = (short)(sd == 0 ? LOB_BUY : LOB_SELL);
+                    r.pad = 0;
+                    ag.amsg[ns++] = r;
+                }
+            }
+        const unsigned long long key = step_key(seed, t, TAG_SHUFFLE);
+        for (int i = ns - 1, d = 0; i >= 1; i--, d++) {
+            const int j = (int)bounded(sm_mix(key + GAMMA * (unsigned long long)(d + 1)), (unsigned)(i + 1));
+            const DevMsg x = ag.amsg[i];
+            ag.amsg[i] = ag.amsg[j];
+            ag.amsg[j] = x;
+        }
+        for (int u = 0; u < ns; u++)
+            ag.amsg[u].oid = -(1 + ag.amsg[u].oid + (long long)A * (c.seq_next + u));
+    }
+    return __shfl_sync(FULL, ns, 0);
+}
+
+// Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
 };
 
 // Run n_steps env steps of env e with the book resident on chip.  EXT
-// compiles in episode mode and the reward variants; without it those
-// settings are ignored, so the host launches EXT whenever one is set.
-template <int K, bool TRACE, bool EXT>
-__device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe, int lane) {
+// compiles in episode mode, the reward variants and the other action spaces;
+// without it those settings are ignored, so the host launches EXT whenever
+// one is set.  MA (which implies EXT) runs 2P agents with their state in the
+// warp's agent block agp; without it the agents are the benchmark pair.
+template <int K, bool TRACE, bool EXT, bool MA>
+__device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp, MsgPipe &pipe, int lane) {
+    constexpr bool XT = EXT || MA;
     EnvState *st = p.st + e;
     const bool uni = p.uni_cap > 0;
     const int cap = uni ? p.uni_cap : p.caps[e];
@@ -914,7 +1126,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     // first message window, issued before anything waits on memory.  The
     // offsets index of a step's data is the env's window position, or in
     // episode mode (dcur) its episode's first data step plus the step within it.
-    const bool ep_mode = EXT && p.ep_mode;
+    const bool ep_mode = XT && p.ep_mode;
     int ep_start = ep_mode ? st->ep_start : 0;
     long long dcur = ep_mode ? (long long)ep_start + p.t0 % p.T : 0;
     const long long d0 = ep_mode ? dcur : (long long)e * p.off_stride + p.k0;
@@ -941,6 +1153,14 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
     c.status = 0;
     c.fill_log = (TRACE && p.fills) ? p.fills + (long long)e * p.fill_cap : nullptr;
     c.fill_cap = p.fill_cap;
+    c.ag = agp;
+    if constexpr (MA) {
+        for (int a = lane; a < A; a += 32) {
+            const AgentState x = p.agents[(long long)e * A + a];
+            agp->inv[a] = x.inv; agp->cash[a] = x.cash; agp->pv[a] = x.pv_prev; agp->done[a] = x.exec_done;
+            agp->act[a] = x.act;
+        }
+    }
     // live counts arrive with the state: mark occupancy now
     side_set_count<K>(bid, nb0, lane);
     side_set_count<K>(ask, na0, lane);
@@ -979,9 +1199,35 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
 
         // ---- 1-3. action conversion, carry-over cancels, shuffle
         int act0 = 0, act1 = 0, ns = 0;
-        if (A == 2) {
+        if constexpr (MA) {
+            AgentSmem &ag = *agp;
+            const long long bb = bid.n ? bid.fpx : c.last_px;
+            const long long ba = ask.n ? ask.fpx : c.last_px;
+            if (lane == 0) sm.rw[0] = bb + ba;   // twice the mid at the start of the step
+            __syncwarp();
+            agent_wants_ma(p, e, t, step, seed, bb, ba, ag, c, lane);
+            __syncwarp();
+            const unsigned cm_b = side_carry_ma<K>(bid, sm.pool[0], sm.cand[0], 0, ag, A, lane);
+            const unsigned cm_a = side_carry_ma<K>(ask, sm.pool[1], sm.cand[1], 1, ag, A, lane);
+            __syncwarp();
+            if (TRACE && snap_env) {
+                // trace mode: cancels one by one in the paper's order, a snapshot after each
+                for (int a = 0; a < A; a++) {
+                    side_agent_cancels<K>(bid, sm.pool[0], sm.cand[0], a, c, lane, bid, ask, sm, snap_env, p, cap,
+                                          snap_n, snap_bytes);
+                    side_agent_cancels<K>(ask, sm.pool[1], sm.cand[1], a, c, lane, bid, ask, sm, snap_env, p, cap,
+                                          snap_n, snap_bytes);
+                }
+            } else {
+                side_cancel_set<K>(bid, sm.pool[0], cm_b, c, lane);
+                side_cancel_set<K>(ask, sm.pool[1], cm_a, c, lane);
+            }
+            ns = agent_orders_ma(p, t, seed, ag, c, lane);
+            c.seq_next += ns;
+            __syncwarp();
+        } else if (A == 2) {
             // market maker's action count: 12, or (extended kernel) 8 / 3
-            const int n_mm = !EXT ? 12 : p.mm_space == LOB_MM_FIXED_QUANT ? 8 : p.mm_space == LOB_MM_DIRECTIONAL ? 3 : 12;
+            const int n_mm = !XT ? 12 : p.mm_space == LOB_MM_FIXED_QUANT ? 8 : p.mm_space == LOB_MM_DIRECTIONAL ? 3 : 12;
             if (p.action_mode == LOB_ACT_RANDOM) {
                 const unsigned long long key = step_key(seed, t, TAG_POLICY);
                 act0 = (int)bounded(sm_mix(key + GAMMA), 12);
@@ -994,7 +1240,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             }
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
-            if (EXT && p.reward_mode != LOB_REWARD_PV && lane == 0) {
+            if (XT && p.reward_mode != LOB_REWARD_PV && lane == 0) {
                 sm.rw[0] = bb + ba; sm.rw[1] = c.inv1; sm.rw[2] = c.cash1;
             }
             int wa[3] = {0, 0, 0}, ws[3] = {0, 0, 0}, wp[3] = {0, 0, 0};
@@ -1015,7 +1261,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 wa[0] = 0; ws[0] = p.exec_dir; wp[0] = (int)wpx; wq[0] = qty;
                 nw = 1;
             }
-            if (!EXT || p.mm_space == LOB_MM_SPREAD_SKEW) {
+            if (!XT || p.mm_space == LOB_MM_SPREAD_SKEW) {
                 if (act1 >= 1 && act1 < 12) {
                     long long qb, qa;
                     if (act1 <= 9) { qb = bb - (act1 - 1) / 3; qa = ba + (act1 - 1) % 3; }
@@ -1144,7 +1390,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             int cnt_ch;
             const int agent = ch < 0 ? 1 : 0;
             if (ch < 0) {
-                base = sm.amsg;
+                base = MA ? agp->amsg : sm.amsg;
                 cnt_ch = ns;
             } else {
                 const unsigned buf = (tile0 + ch) & 1u;
@@ -1186,13 +1432,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                     case 0:   // add, buy
                         c.c_add_vol += qty;
                         if (ask.n > 0 && px >= ask.fpx)
-                            qty = side_take<K, false, TRACE>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
+                            qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
                         if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
                         break;
                     case 1:   // add, sell
                         c.c_add_vol += qty;
                         if (bid.n > 0 && px <= bid.fpx)
-                            qty = side_take<K, true, TRACE>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
+                            qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
                         if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
                         break;
                     case 2:   // partial cancel, buy
@@ -1205,11 +1451,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                         break;
                     case 6:   // market, buy
                         c.c_mkt_vol += qty;
-                        c.c_mkt_disc += side_take<K, false, TRACE>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
+                        c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
                         break;
                     case 7:   // market, sell
                         c.c_mkt_vol += qty;
-                        c.c_mkt_disc += side_take<K, true, TRACE>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
+                        c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
                         break;
                     default:
                         c.c_bad += 1;
@@ -1251,6 +1497,56 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             const long long ba = ask.n ? ask.fpx : c.last_px;
             const long long s2 = bb + ba;
             const long long anchor = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
+            if constexpr (MA) {
+                AgentSmem &ag = *agp;
+                const int P = A >> 1;
+                for (int a = lane; a < A; a += 32) ag.own[a] = 0;
+                __syncwarp();
+                side_own_ma<K>(bid, sm.pool[0], ag, A, lane);
+                side_own_ma<K>(ask, sm.pool[1], ag, A, lane);
+                __syncwarp();
+                const float tl = __fdiv_rn((float)(p.T - (te + 1)), (float)p.T);
+                const int D = p.D;
+                float *ob = p.obs ? p.obs + obs_base * A * D : nullptr;
+                if (ob && ep_end) {
+                    const float *src = p.ep_obs + (long long)ep_j * A * D;
+                    for (int i = lane; i < A * D; i += 32) ob[i] = src[i];
+                } else if (ob) {
+                    for (int idx = lane; idx < 4 * L; idx += 32) {
+                        const int sd = idx >= 2 * L ? 1 : 0;
+                        const int i = (idx - sd * 2 * L) >> 1;
+                        const int nl = sd == 0 ? nlb : nla;
+                        const long long lq = sm.lvl_q[sd][i];
+                        const long long lp = (long long)sm.lvl_px[sd][i] - anchor;
+                        const float v = i >= nl ? 0.0f : __ll2float_rn((idx & 1) ? lq : lp);
+                        for (int a = 0; a < A; a++) ob[a * D + idx] = v;
+                    }
+                    for (int i = lane; i < 5 * A; i += 32) {
+                        const int a = i / 5, g = i - 5 * a;
+                        const long long x = g == 0 ? ag.inv[a] : g == 1 ? ag.cash[a]
+                                          : g == 3 ? (a < P ? (long long)p.exec_target - ag.done[a] : 0) : ag.own[a];
+                        ob[a * D + 4 * L + g] = g == 2 ? tl : __ll2float_rn(x);
+                    }
+                }
+                // Eq. 1 per agent, then the variants and penalties of its type
+                __syncwarp();
+                for (int a = lane; a < A; a += 32) {
+                    typedef unsigned long long u64;
+                    const long long iv = ag.inv[a], cs = ag.cash[a];
+                    const long long pref = iv > 0 ? bb : (iv < 0 ? ba : 0);
+                    const long long pv = (long long)((u64)iv * (u64)pref + (u64)cs);
+                    long long r = (long long)((u64)pv - (u64)ag.pv[a]);
+                    ag.pv[a] = pv;
+                    if (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0) {
+                        const longlong2 rr = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
+                                                             te + 1 == p.T, (long long)p.exec_target - ag.done[a],
+                                                             sm.rw[0], s2, ag.inv0[a], ag.cash0[a], iv, cs, r, r);
+                        r = a < P ? rr.x : rr.y;
+                    }
+                    if (p.rew) p.rew[obs_base * A + a] = r;
+                    if (p.act_out) p.act_out[(long long)e * A + a] = ag.act[a];
+                }
+            } else {
             // Eq. 1: PV = Q_inv * P_ref + Cash, P_ref the liquidation touch
             const long long pref0 = c.inv0 > 0 ? bb : (c.inv0 < 0 ? ba : 0);
             const long long pref1 = c.inv1 > 0 ? bb : (c.inv1 < 0 ? ba : 0);
@@ -1292,7 +1588,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 }
             }
             if (lane == 0) {
-                if (EXT && (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0)) {
+                if (XT && (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0)) {
                     const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
                                                         te + 1 == p.T, (long long)p.exec_target - c.exec_done,
                                                         sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
@@ -1301,6 +1597,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
                 if (p.rew) { p.rew[obs_base * A] = r0; p.rew[obs_base * A + 1] = r1; }
                 if (p.act_out) { p.act_out[2LL * e] = act0; p.act_out[2LL * e + 1] = act1; }
             }
+            }  // the benchmark pair
         }
         if (lane == 0 && p.done) p.done[obs_base] = (unsigned char)(te + 1 == p.T);
         if (TRACE && lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
@@ -1322,6 +1619,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
             c.seq_next = 0;
             c.inv0 = 0; c.inv1 = 0; c.cash0 = 0; c.cash1 = 0; c.pv0 = 0; c.pv1 = 0; c.exec_done = 0;
             c.last_px = S.last_px;
+            if constexpr (MA) {
+                __syncwarp();
+                for (int a = lane; a < A; a += 32) { agp->inv[a] = 0; agp->cash[a] = 0; agp->pv[a] = 0; agp->done[a] = 0; }
+                __syncwarp();
+            }
             ep_start = S.data_step;
             dcur = S.data_step;
         } else if (ep_mode) {
@@ -1349,17 +1651,30 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, MsgPipe &pipe,
         st->pv_prev[0] = c.pv0; st->pv_prev[1] = c.pv1; st->exec_done = c.exec_done;
         st->last_px = c.last_px; st->n[0] = bid.n; st->n[1] = ask.n;
         st->t = p.t0 + p.n_steps;
-        if (EXT) st->ep_start = ep_start;
+        if (XT) st->ep_start = ep_start;
+    }
+    if constexpr (MA) {
+        __syncwarp();
+        for (int a = lane; a < A; a += 32) {
+            AgentState x;
+            x.inv = agp->inv[a]; x.cash = agp->cash[a]; x.pv_prev = agp->pv[a]; x.exec_done = agp->done[a];
+            x.act = agp->act[a];
+            x.pad[0] = x.pad[1] = x.pad[2] = 0;
+            p.agents[(long long)e * A + a] = x;
+        }
     }
 }
 
 // One warp per env; with a work queue (p.queue) warps take envs until none is left.
-template <int K, bool TRACE, bool EXT>
+template <int K, bool TRACE, bool EXT, bool MA>
 __device__ __forceinline__ void env_steps_body(const KParams &p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WarpSmem<K> &sm = reinterpret_cast<WarpSmem<K> *>(smem_raw)[wib];
+    // several agents: the warp's agent block follows the block's WarpSmem array
+    AgentSmem *agp = MA ? reinterpret_cast<AgentSmem *>(smem_raw + (blockDim.x >> 5) * sizeof(WarpSmem<K>)) + wib
+                        : nullptr;
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -1369,14 +1684,14 @@ __device__ __forceinline__ void env_steps_body(const KParams &p) {
     MsgPipe pipe{0u};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K, TRACE, EXT>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+        if (w < p.n_list) run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K, TRACE, EXT>(p, p.env_list ? p.env_list[w] : w, sm, pipe, lane);
+            run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, pipe, lane);
         }
     }
 }
@@ -1387,13 +1702,13 @@ __device__ __forceinline__ void env_steps_body(const KParams &p) {
 // whole register file (one block per SM minimum): fewer spills and a shorter
 // per-message path, the better choice when the launch fits one wave or when
 // shared memory bounds residency anyway (K >= 8).
-template <int K, bool TRACE, bool EXT>
+template <int K, bool TRACE, bool EXT, bool MA = false>
 __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
-    env_steps_body<K, TRACE, EXT>(p);
+    env_steps_body<K, TRACE, EXT, MA>(p);
 }
-template <int K, bool TRACE, bool EXT>
+template <int K, bool TRACE, bool EXT, bool MA = false>
 __global__ void __launch_bounds__(256, 1) k_env_steps_wide(const KParams p) {
-    env_steps_body<K, TRACE, EXT>(p);
+    env_steps_body<K, TRACE, EXT, MA>(p);
 }
 
 }  // namespace lobk

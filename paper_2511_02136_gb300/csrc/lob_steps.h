@@ -9,7 +9,10 @@ namespace lobk {
     cudaError_t launch_steps_##k(bool trace, bool ext, bool wide, int blocks, int threads, size_t smem,\
                                  cudaStream_t s, const KParams &p);                                    \
     int wide_blocks_per_sm_##k(bool ext, int threads, size_t smem);                                    \
-    cudaError_t optin_steps_##k(size_t smem);
+    cudaError_t optin_steps_##k(size_t smem);                                                          \
+    cudaError_t launch_steps_ma_##k(bool trace, int blocks, int threads, size_t smem, cudaStream_t s,  \
+                                    const KParams &p);                                                 \
+    cudaError_t optin_steps_ma_##k(size_t smem);
 LOB_DECL_CLASS(1)
 LOB_DECL_CLASS(2)
 LOB_DECL_CLASS(4)

@@ -12,22 +12,41 @@
 namespace lobk {
 // K >= 8: every instance in the wide register budget; K <= 4: the plain and
 // extended kernels in both budgets (the host picks by batch size), the traced
-// one wide.
-constexpr bool kAlwaysWide = LOB_K >= 8;
+// one wide.  The dispatch is a template so that the branches of the other
+// case are never instantiated.
+template <int KK, bool ALWAYS_WIDE = (KK >= 8)>
+struct StepLaunch {
+    static cudaError_t launch(bool trace, bool ext, bool wide, int blocks, int threads, size_t smem, cudaStream_t s,
+                              const KParams &p) {
+        if (trace) k_env_steps_wide<KK, true, true><<<blocks, threads, smem, s>>>(p);
+        else if constexpr (ALWAYS_WIDE) {
+            if (ext) k_env_steps_wide<KK, false, true><<<blocks, threads, smem, s>>>(p);
+            else k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
+        } else {
+            if (ext && wide) k_env_steps_wide<KK, false, true><<<blocks, threads, smem, s>>>(p);
+            else if (ext) k_env_steps<KK, false, true><<<blocks, threads, smem, s>>>(p);
+            else if (wide) k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
+            else k_env_steps<KK, false, false><<<blocks, threads, smem, s>>>(p);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t optin(size_t smem) {
+        const int b = (int)smem;
+        const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(k_env_steps_wide<KK, true, true>, A, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, true>, A, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, false>, A, b);
+        if constexpr (!ALWAYS_WIDE) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, true>, A, b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, false>, A, b);
+        }
+        return e;
+    }
+};
 
 cudaError_t LOB_CAT(launch_steps_, LOB_K)(bool trace, bool ext, bool wide, int blocks, int threads, size_t smem,
                                           cudaStream_t s, const KParams &p) {
-    if (trace) k_env_steps_wide<LOB_K, true, true><<<blocks, threads, smem, s>>>(p);
-    else if constexpr (kAlwaysWide) {
-        if (ext) k_env_steps_wide<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
-        else k_env_steps_wide<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
-    } else {
-        if (ext && wide) k_env_steps_wide<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
-        else if (ext) k_env_steps<LOB_K, false, true><<<blocks, threads, smem, s>>>(p);
-        else if (wide) k_env_steps_wide<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
-        else k_env_steps<LOB_K, false, false><<<blocks, threads, smem, s>>>(p);
-    }
-    return cudaGetLastError();
+    return StepLaunch<LOB_K>::launch(trace, ext, wide, blocks, threads, smem, s, p);
 }
 
 // Resident blocks per SM of the wide plain / extended kernel at this shape.
@@ -40,16 +59,5 @@ int LOB_CAT(wide_blocks_per_sm_, LOB_K)(bool ext, int threads, size_t smem) {
     return e == cudaSuccess ? nb : 0;
 }
 
-cudaError_t LOB_CAT(optin_steps_, LOB_K)(size_t smem) {
-    const int b = (int)smem;
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, true, true>, A, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, false, true>, A, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<LOB_K, false, false>, A, b);
-    if constexpr (!kAlwaysWide) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, true>, A, b);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<LOB_K, false, false>, A, b);
-    }
-    return e;
-}
+cudaError_t LOB_CAT(optin_steps_, LOB_K)(size_t smem) { return StepLaunch<LOB_K>::optin(smem); }
 }  // namespace lobk

@@ -21,9 +21,10 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_PKG, "liblob.so")
 _SOURCES = [os.path.join(_CSRC, n) for n in
-            ["lob_api.cu", "policy_api.cu"] + [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
+            ["lob_api.cu", "policy_api.cu"] + [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)] +
+            [f"steps_ma_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
 _DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.cuh", "policy_internal.h",
-                                                      "lob_steps.h", "steps_inst.cuh")] + \
+                                                      "lob_steps.h", "steps_inst.cuh", "steps_ma_inst.cuh")] + \
     [os.path.join(_INC, "lob.h")]
 _OBJDIR = os.path.join(_PKG, "_build")
 _lock = threading.Lock()
@@ -55,6 +56,7 @@ LOB_INIT_ID = 0x4000000000000000
 START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
 POLICY_HIDDEN = 128
 LOB_NOALLOC_MAX_ENVS = 16384
+LOB_MAX_PER_TYPE = 16
 
 
 class LobError(RuntimeError):
@@ -467,7 +469,7 @@ class LobEnv:
         return out
 
     def actions(self):
-        out = self.torch.zeros((self.n_envs, 2), dtype=self.torch.int32, device=self.dev)
+        out = self.torch.zeros((self.n_envs, max(self.n_agents, 2)), dtype=self.torch.int32, device=self.dev)
         lob_get_actions(self.h, out)
         return out[:, :self.n_agents]
 
