@@ -513,6 +513,47 @@ def run_workload(args):
                                        "MM, Spooner reward (lambda 0.5) + rho 50 + unfilled penalty 0.1, random "
                                        "policy, 256 steps in one lob_rollout", "messages": msgs},
                 "dtype": "int64", "data": "synthetic"}
+    elif wl == "table1":
+        # Table 1's speed benchmark: 4,000 envs x 50 steps, two agent types
+        # with 1, 5 or 10 agents each, 1 or 100 data messages per step, random
+        # policy; book capacity 100 and order size 10 (Table 2).  The paper's
+        # env-steps/s (JaxMARL-HFT on one L40S) is context for vs_baseline.
+        paper = {(100, 1): 21969, (1, 1): 351119, (100, 5): 14801, (1, 5): 89062, (100, 10): 10724, (1, 10): 48312}
+        n, T = 4000, 50
+        rows = []
+        for (m, per_type), ref in paper.items():
+            seeds = mbogen.env_seeds(10 + m + per_type, n)
+            st = mbogen.generate(mbogen.MessageModel(msgs_per_step=m), seeds, T)
+            md, od, sd = upload(st, seeds)
+            env = lob.LobEnv(n, n_agents=2 * per_type, cap=100, episode_len=T, mm_lot=10, exec_target=600,
+                             action_mode=lob.LOB_ACT_RANDOM)
+            A = 2 * per_type
+            # every step's observations, rewards and done flags are written, as the RL loop needs them
+            obs = torch.zeros((T, n, A, env.D), dtype=torch.float32, device=dev)
+            rew = torch.zeros((T, n, A), dtype=torch.int64, device=dev)
+            done = torch.zeros((T, n), dtype=torch.uint8, device=dev)
+            times = []
+            for i in range(args.reps):
+                env.load_messages(md, od)
+                env.reset(sd)
+                torch.cuda.synchronize()
+                times += _flush_and_time(lambda: lob.lob_rollout(env.h, T, None, obs, rew, done), 1, dev)
+            assert env.sync() == 0
+            msgs = float(env.counters()[:, 0].sum().item())
+            env.close()
+            t = min(times)
+            rows.append({"data_msgs_per_step": m, "agents_per_type": per_type, "seconds": t,
+                         "env_steps_per_s": n * T / t, "msgs_per_s": msgs / t,
+                         "paper_env_steps_per_s_l40s": ref, "vs_paper": n * T / t / ref})
+            del md, od, sd, obs, rew, done
+        line = {"workload": "table1", "metric": "env-steps/sec (Table 1 speed benchmark)",
+                "value": rows[0]["env_steps_per_s"], "unit": "env-steps/s", "higher_is_better": True,
+                "vs_baseline": rows[0]["vs_paper"], "rows": rows, "n_gpus": 1, "steps": T,
+                "config": {"workload": "4000 envs x 50 steps, 1 / 100 data msgs per step, 1 / 5 / 10 agents per "
+                                       "type (execution + market making), random policy, cap 100, lot 10, task "
+                                       "600; one lob_rollout launch per run writing every step's obs, rewards "
+                                       "and done flags, inputs resident, 256 MiB written before each run", "value_row": "100 msgs/step, 1 agent per type"},
+                "dtype": "int64", "data": "synthetic"}
     elif wl == "stress65536":
         n, T = 65536, args.stress_steps
         seeds = mbogen.env_seeds(4, n)
@@ -554,7 +595,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="envs1024",
-                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "stress65536"],
+                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "table1", "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stress-steps", type=int, default=4)
