@@ -152,7 +152,7 @@ typedef struct lob_handle lob_handle;
 
 /* Observation length per agent: 4 * top_levels + 5 (0 when n_agents == 0).
  * Layout per agent: [bid (px - anchor, qty) x L][ask (px - anchor, qty) x L],
- * inventory, cash, time left (T - t) / T, remaining execution target (agent 0)
+ * inventory, cash, time left (T - t) / T, remaining execution target (execution agents)
  * or 0, the agent's own resting quantity.  anchor = floor((best bid + best
  * ask) / 2); an empty side's touch is the last trade price; missing levels
  * are (0, 0). */
@@ -220,11 +220,11 @@ int lob_get_episode_starts(lob_handle *h, int32_t *d_out, void *stream);
  * and the episode draws.  The observation buffer then holds the reset
  * observation (the starting book's levels -- all (0, 0) for an empty book --,
  * zero inventory and cash, time left 1, the full execution target for
- * agent 0). */
+ * the execution agents). */
 int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream);
 
 /* One environment step for every env (stages 1-5 above), consuming the next
- * window step of bound messages.  d_actions: device int32 [n_envs][2] in
+ * window step of bound messages.  d_actions: device int32 [n_envs][n_agents] in
  * LOB_ACT_HOST mode, ignored (may be NULL) otherwise.  Fails with LOB_ESTATE
  * when the episode is over (t == T) or the window is exhausted (outside
  * episode mode). */
@@ -238,7 +238,7 @@ int lob_observe(lob_handle *h, float *d_obs, int64_t *d_rewards, uint8_t *d_done
 /* Several steps in one persistent launch, the book kept on chip between
  * steps.  Outputs of step i go to d_obs + i * n_envs * n_agents * obs_dim etc.
  * (any may be NULL).  Actions: LOB_ACT_RANDOM, or LOB_ACT_HOST with
- * d_actions [n_steps][n_envs][2]. */
+ * d_actions [n_steps][n_envs][n_agents]. */
 int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float *d_obs,
                 int64_t *d_rewards, uint8_t *d_done, void *stream);
 
