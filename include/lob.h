@@ -287,6 +287,21 @@ int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t 
 int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets,
                   const int32_t *h_actions, float *h_obs, int64_t *h_rewards,
                   uint8_t *h_done, void *stream);
+/* The same step, pipelined; returns without synchronising.  When every
+ * buffer is page-locked host memory that the GPU maps at the same address
+ * (cudaMallocHost, cudaHostAlloc, pinned torch tensors) and the messages are
+ * 16-byte aligned, the step kernel itself reads the messages, offsets and
+ * actions and writes the outputs in host memory over the coherent CPU-GPU
+ * link (zero copy): one launch per call, and the handle's own output buffers
+ * (lob_observe) are not updated by such a call.  Otherwise the inputs go up
+ * on the handle's copy stream into one of two device staging slots (so they
+ * overlap the previous step), and the outputs come back on `stream`.  The
+ * caller keeps the input buffers unchanged until `stream` has run past this
+ * step, and reads the outputs only after synchronising it.  h_offsets is read
+ * during the call.  Same errors as lob_step_host. */
+int lob_step_host_async(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets,
+                        const int32_t *h_actions, float *h_obs, int64_t *h_rewards,
+                        uint8_t *h_done, void *stream);
 
 /* Book of every env in the canonical layout, per env a record of
  * 8 + 48 * C bytes (C = that env's capacity): int32 n[2]; int32 px[2][C];

@@ -146,7 +146,7 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     // the extended kernel when episode mode, a reward variant or another
     // action space is on
     const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
-                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW;
+                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0;
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     switch (K) {
@@ -218,6 +218,19 @@ struct lob_handle {
     size_t stage_cap = 0;
     int64_t *d_stage_off = nullptr;
     int32_t *d_stage_act = nullptr;
+    // pipelined host steps: two staging slots filled on a copy stream
+    struct AsyncSlot {
+        lob_msg *d_msgs = nullptr;
+        size_t cap = 0;
+        int64_t *d_off = nullptr;
+        int32_t *d_act = nullptr;
+        int64_t *h_off = nullptr;              // pinned, the rebased offsets
+        cudaEvent_t in_ready = nullptr;        // copies of this slot done
+        cudaEvent_t free = nullptr;            // the step that read this slot done
+    } aslot[2];
+    cudaStream_t copy_stream = nullptr;
+    int64_t async_calls = 0;
+    const void *mapped_ok[6] = {};   // last host pointers found mapped, per argument
     // several agents per type: per-agent state [n_envs][n_agents]
     AgentState *d_agents = nullptr;
     // episode mode (one shared stream, snapshot table, auto-reset)
@@ -234,6 +247,15 @@ struct lob_handle {
 static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LOB_OK : LOB_ECUDA; }
 
 static void free_all(lob_handle *h) {
+    for (auto &a : h->aslot) {
+        if (a.d_msgs) cudaFree(a.d_msgs);
+        if (a.d_off) cudaFree(a.d_off);
+        if (a.d_act) cudaFree(a.d_act);
+        if (a.h_off) cudaFreeHost(a.h_off);
+        if (a.in_ready) cudaEventDestroy(a.in_ready);
+        if (a.free) cudaEventDestroy(a.free);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (int k = 0; k < NCLASS; k++) {
         if (h->cls_stream[k]) cudaStreamDestroy(h->cls_stream[k]);
         if (h->cls_done[k]) cudaEventDestroy(h->cls_done[k]);
@@ -575,7 +597,7 @@ static const int64_t *step_offsets(const lob_handle *h) { return h->ep_mode ? h-
 
 static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
                         int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
-                        long long *rew, unsigned char *done, cudaStream_t s) {
+                        long long *rew, unsigned char *done, cudaStream_t s, bool msgs_sysmem = false) {
     const lob_config &c = h->cfg;
     KParams p;
     memset(&p, 0, sizeof(p));
@@ -596,6 +618,7 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.exec_q0 = exec_lot(c);
     set_rewards(p, c);
     p.agents = h->d_agents;
+    p.msgs_sysmem = msgs_sysmem ? 1 : 0;
     if (h->ep_mode) {
         p.ep_mode = 1;
         p.n_starts = h->n_starts;
@@ -829,6 +852,110 @@ int lob_step_host(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets
     rc |= cuda_ok(cudaStreamSynchronize(s));
     if (rc != LOB_OK) return LOB_ECUDA;
     return LOB_OK;
+}
+
+// Whether p is page-locked host memory mapped at the same device address;
+// the last answer per argument slot is remembered.
+static bool host_mapped(lob_handle *h, int slot, const void *p) {
+    if (!p) return false;
+    if (h->mapped_ok[slot] == p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const bool ok = at.type == cudaMemoryTypeHost && at.devicePointer == p;
+    if (ok) h->mapped_ok[slot] = p;
+    return ok;
+}
+
+// The pipelined form of lob_step_host: inputs go up on the handle's copy
+// stream into one of two staging slots while the previous step runs; the
+// step waits for its slot's copies, and the outputs come back on `stream`.
+int lob_step_host_async(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_offsets, const int32_t *h_actions,
+                        float *h_obs, int64_t *h_rewards, uint8_t *h_done, void *stream) {
+    if (!h || !h_offsets) return LOB_EINVAL;
+    if (!h->reset_done || h->ep_mode || h->t >= h->cfg.episode_len) return LOB_ESTATE;
+    const lob_config &c = h->cfg;
+    if (c.n_agents > 0 && c.action_mode == LOB_ACT_HOST && !h_actions) return LOB_EINVAL;
+    const int n = c.n_envs;
+    const int64_t base = h_offsets[0], total = h_offsets[n] - base;
+    if (total < 0) return LOB_EINVAL;
+    for (int e = 0; e < n; e++)
+        if (h_offsets[e + 1] < h_offsets[e]) return LOB_EINVAL;
+    if (total > 0 && !h_msgs) return LOB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto &a = h->aslot[h->async_calls & 1];
+    const size_t na = (size_t)(c.n_agents > 2 ? c.n_agents : 2);
+    const size_t A = (size_t)c.n_agents, D = (size_t)h->D;
+    const bool want_act = c.n_agents > 0 && c.action_mode == LOB_ACT_HOST;
+    // Zero-copy: when every buffer is page-locked host memory the GPU maps at
+    // the same address, the step reads the messages, offsets and actions and
+    // writes the outputs in host memory itself (over the coherent CPU-GPU
+    // link), so a call costs one launch instead of a chain of copies.
+    const bool zc = (total == 0 || (host_mapped(h, 0, h_msgs + base) && host_mapped(h, 1, h_msgs + h_offsets[n] - 1) &&
+                                    ((uintptr_t)(h_msgs + base) & 15u) == 0)) &&
+                    (!want_act || host_mapped(h, 2, h_actions)) && (!h_obs || !A || host_mapped(h, 3, h_obs)) &&
+                    (!h_rewards || !A || host_mapped(h, 4, h_rewards)) && (!h_done || host_mapped(h, 5, h_done));
+    if (!a.h_off) {
+        if (cudaMallocHost(&a.h_off, ((size_t)n + 1) * 8) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.in_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a.free, cudaEventDisableTiming) != cudaSuccess)
+            return LOB_ENOMEM;
+    }
+    // the step two calls back has used this slot (its offsets, read directly
+    // or through their upload) once it is done
+    if (cudaEventSynchronize(a.free) != cudaSuccess) return LOB_ECUDA;
+    if (zc) {
+        for (int e = 0; e <= n; e++) a.h_off[e] = h_offsets[e] - base;
+        int rc = launch_steps(h, total > 0 ? h_msgs + base : nullptr, a.h_off, 1, 0, 1, want_act ? h_actions : nullptr,
+                              0, A ? h_obs : nullptr, A ? reinterpret_cast<long long *>(h_rewards) : nullptr, h_done,
+                              s, true);
+        if (rc != LOB_OK) return rc;
+        if (cudaEventRecord(a.free, s) != cudaSuccess) return LOB_ECUDA;
+        h->t++;
+        h->async_calls++;
+        return LOB_OK;
+    }
+    if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return LOB_ECUDA;
+    if (!a.d_off) {
+        if (cudaMalloc(&a.d_off, ((size_t)n + 1) * 8) != cudaSuccess || cudaMalloc(&a.d_act, (size_t)n * na * 4) !=
+            cudaSuccess)
+            return LOB_ENOMEM;
+    }
+    if ((size_t)total > a.cap) {
+        if (a.d_msgs) cudaFree(a.d_msgs);
+        a.d_msgs = nullptr;
+        const size_t want = std::max((size_t)total, a.cap * 2);
+        if (cudaMalloc(&a.d_msgs, want * sizeof(lob_msg)) != cudaSuccess) {
+            a.cap = 0;
+            return LOB_ENOMEM;
+        }
+        a.cap = want;
+    }
+    for (int e = 0; e <= n; e++) a.h_off[e] = h_offsets[e] - base;
+    int rc = LOB_OK;
+    rc |= cuda_ok(cudaStreamWaitEvent(h->copy_stream, a.free, 0));
+    if (total > 0)
+        rc |= cuda_ok(cudaMemcpyAsync(a.d_msgs, h_msgs + base, (size_t)total * sizeof(lob_msg), cudaMemcpyHostToDevice,
+                                      h->copy_stream));
+    rc |= cuda_ok(cudaMemcpyAsync(a.d_off, a.h_off, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, h->copy_stream));
+    if (c.n_agents > 0 && c.action_mode == LOB_ACT_HOST)
+        rc |= cuda_ok(cudaMemcpyAsync(a.d_act, h_actions, (size_t)n * c.n_agents * 4, cudaMemcpyHostToDevice,
+                                      h->copy_stream));
+    rc |= cuda_ok(cudaEventRecord(a.in_ready, h->copy_stream));
+    rc |= cuda_ok(cudaStreamWaitEvent(s, a.in_ready, 0));
+    if (rc != LOB_OK) return LOB_ECUDA;
+    rc = launch_steps(h, a.d_msgs, a.d_off, 1, 0, 1, a.d_act, 0, h->d_obs, h->d_rew, h->d_done, s);
+    if (rc != LOB_OK) return rc;
+    if (cudaEventRecord(a.free, s) != cudaSuccess) return LOB_ECUDA;
+    h->t++;
+    h->async_calls++;
+    if (h_obs && A) rc |= cuda_ok(cudaMemcpyAsync(h_obs, h->d_obs, (size_t)n * A * D * 4, cudaMemcpyDeviceToHost, s));
+    if (h_rewards && A) rc |= cuda_ok(cudaMemcpyAsync(h_rewards, h->d_rew, (size_t)n * A * 8, cudaMemcpyDeviceToHost, s));
+    if (h_done) rc |= cuda_ok(cudaMemcpyAsync(h_done, h->d_done, (size_t)n, cudaMemcpyDeviceToHost, s));
+    return rc == LOB_OK ? LOB_OK : LOB_ECUDA;
 }
 
 int64_t lob_book_bytes(const lob_handle *h) { return h ? h->canon_bytes : 0; }

@@ -117,6 +117,7 @@ struct KParams {
     const unsigned char *ep_images;
     const float *ep_obs;
     AgentState *agents;              // several agents per type: [n_envs][n_agents]
+    int msgs_sysmem;                 // messages (and offsets) in page-locked host memory
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -141,6 +142,14 @@ __device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, unsigne
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+// 16-byte asynchronous copies global -> shared through the SM's load path
+// (any address the GPU maps, including page-locked host memory read over the
+// coherent CPU-GPU link), completed per thread by a commit group.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
     unsigned ok;
     asm volatile(
@@ -1102,6 +1111,18 @@ __device__ __forceinline__ int agent_orders_ma(const KParams &p, int t, unsigned
     return __shfl_sync(FULL, ns, 0);
 }
 
+// One message tile (up to TILE records) copied by the warp's lanes, one
+// 32-byte record per lane, as one commit group.
+__device__ __forceinline__ void tile_copy_lanes(DevMsg *dst, const DevMsg *src, int count, int lane) {
+    if (lane < count) {
+        char *d = reinterpret_cast<char *>(dst + lane);
+        const char *g = reinterpret_cast<const char *>(src + lane);
+        cp_async16(d, g);
+        cp_async16(d + 16, g + 16);
+    }
+    cp_async_commit();
+}
+
 // Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
@@ -1127,6 +1148,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     // offsets index of a step's data is the env's window position, or in
     // episode mode (dcur) its episode's first data step plus the step within it.
     const bool ep_mode = XT && p.ep_mode;
+    const bool sysm = XT && p.msgs_sysmem;   // message tiles by lane copies instead of bulk copies
     int ep_start = ep_mode ? st->ep_start : 0;
     long long dcur = ep_mode ? (long long)ep_start + p.t0 % p.T : 0;
     const long long d0 = ep_mode ? dcur : (long long)e * p.off_stride + p.k0;
@@ -1186,7 +1208,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         const unsigned tile0 = pipe.tiles;
         if (ntiles > 0) {
             __syncwarp();
-            if (lane == 0) {
+            if (sysm) {
+                tile_copy_lanes(sm.tile[pipe.tiles & 1], p.msgs + mb, min(TILE, nmsg), lane);
+            } else if (lane == 0) {
                 fence_proxy_async_smem();
                 tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb, (unsigned)min(TILE, nmsg) * 32u,
                              &sm.bar[pipe.tiles & 1]);
@@ -1395,7 +1419,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             } else {
                 const unsigned buf = (tile0 + ch) & 1u;
                 const unsigned phase = ((tile0 + ch) >> 1) & 1u;
-                if (!mbar_wait(&sm.bar[buf], phase, p.wait_budget)) {
+                if (sysm) {
+                    cp_async_wait_all();   // this tile is the only group in flight
+                    __syncwarp();
+                } else if (!mbar_wait(&sm.bar[buf], phase, p.wait_budget)) {
                     c.status |= ST_TIMEOUT;
                     mbar_wait(&sm.bar[buf], phase, p.wait_budget);  // let the copy in flight land
                     timed_out = true;
@@ -1403,7 +1430,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 }
                 if (ch + 1 < ntiles) {
                     __syncwarp();
-                    if (lane == 0) {
+                    if (sysm) {
+                        tile_copy_lanes(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(ch + 1) * TILE,
+                                        min(TILE, nmsg - (ch + 1) * TILE), lane);
+                    } else if (lane == 0) {
                         fence_proxy_async_smem();
                         tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(ch + 1) * TILE,
                                      (unsigned)min(TILE, nmsg - (ch + 1) * TILE) * 32u, &sm.bar[pipe.tiles & 1]);

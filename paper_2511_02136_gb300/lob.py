@@ -48,6 +48,7 @@ EXPORTS = [
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
+    "lob_step_host_async",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
@@ -141,6 +142,7 @@ def _load():
         "lob_observe": (ctypes.c_int, [P, P, P, P, P]),
         "lob_rollout": (ctypes.c_int, [P, I32, P, P, P, P, P]),
         "lob_step_host": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
+        "lob_step_host_async": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
         "lob_book_bytes": (I64, [P]),
         "lob_get_book": (ctypes.c_int, [P, P, P]),
         "lob_get_counters": (ctypes.c_int, [P, P, P]),
@@ -241,6 +243,15 @@ def lob_step_host(h, msgs, offsets, actions, obs, rewards, done, stream=None):
         return None if a is None else a.ctypes.data
     return _check(_load().lob_step_host(h, hp(msgs), hp(offsets), hp(actions), hp(obs), hp(rewards), hp(done),
                                         _stream(stream)), "lob_step_host")
+
+
+def lob_step_host_async(h, msgs, offsets, actions, obs, rewards, done, stream=None):
+    """Pipelined host step: buffers (pinned torch tensors or numpy arrays) must stay
+    untouched, and outputs unread, until `stream` is synchronised."""
+    def hp(a):
+        return None if a is None else _anyp(a)
+    return _check(_load().lob_step_host_async(h, hp(msgs), hp(offsets), hp(actions), hp(obs), hp(rewards),
+                                              hp(done), _stream(stream)), "lob_step_host_async")
 
 
 def lob_book_bytes(h) -> int:

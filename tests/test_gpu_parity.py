@@ -152,6 +152,45 @@ def test_step_host_buffers():
     pr.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_host_async_pipelined(pinned):
+    """The pipelined host step: all steps enqueued back to back, outputs of
+    every step kept in their own host buffers; after one final synchronise
+    every step matches the oracle.  Pinned buffers take the zero-copy path
+    (the kernel reads and writes host memory), pageable ones the staged
+    copies."""
+    import torch
+    n, T = 41, 9
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=70), mbogen.env_seeds(33, n), T)
+    pr = Pair(n, st, cap=100, exec_target=30, action_mode=lob.LOB_ACT_HOST)
+    rng = np.random.default_rng(4)
+    D = pr.env.D
+    pin = (lambda x: x.pin_memory()) if pinned else (lambda x: x)
+    acts = [pin(torch.from_numpy(rng.integers(0, 12, size=(n, 2)).astype(np.int32))) for _ in range(T)]
+    ins, outs = [], []
+    for t in range(T):
+        lo, hi = st.offsets[:, t], st.offsets[:, t + 1]
+        chunk = pin(torch.from_numpy(np.concatenate([st.msgs[lo[e]:hi[e]] for e in range(n)]).view(np.uint8)))
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = np.cumsum(hi - lo)
+        ins.append((chunk, off))
+        outs.append((pin(torch.zeros((n, 2, D), dtype=torch.float32)), pin(torch.zeros((n, 2), dtype=torch.int64)),
+                     pin(torch.zeros(n, dtype=torch.uint8))))
+    stream = torch.cuda.Stream()
+    for t in range(T):
+        lob.lob_step_host_async(pr.env.h, ins[t][0], ins[t][1], acts[t], *outs[t], stream=stream)
+    stream.synchronize()
+    for t in range(T):
+        pr.orc.step(acts[t].numpy())
+        o_obs, o_rew, o_done = pr.orc.observe()
+        np.testing.assert_allclose(outs[t][0].numpy(), o_obs, rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(outs[t][1].numpy(), o_rew)
+        np.testing.assert_array_equal(outs[t][2].numpy(), o_done)
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
+
+
 def test_full_size_1024_envs_1000_steps():
     """The benchmark workload in the benchmark's launch configuration: 1,024
     envs x capacity 100 x 100 messages x 1,000 steps, random policy.  Every
