@@ -81,6 +81,19 @@ typedef struct lob_msg {
     int32_t pad;
 } lob_msg;
 
+/* Compact 16-byte background record: px and qty as above, word = id << 4 |
+ * (side == LOB_SELL) << 3 | type, with ids in [LOB_MSG16_ID_MIN,
+ * LOB_MSG16_ID_MAX] and type 0 for a record whose type or side is invalid
+ * (skipped and counted like any malformed message).  Half the bytes of
+ * lob_msg for the same step results. */
+typedef struct lob_msg16 {
+    int32_t px;
+    int32_t qty;
+    int64_t word;
+} lob_msg16;
+#define LOB_MSG16_ID_MIN (-(1LL << 59))
+#define LOB_MSG16_ID_MAX ((1LL << 59) - 1)
+
 /* 32-byte trade record of the fill log. */
 typedef struct lob_fill {
     int64_t maker_id;   /* resting order */
@@ -173,6 +186,14 @@ int lob_destroy(lob_handle *h);   /* frees device state; synchronises the device
  * the window cursor to 0 without touching env state. */
 int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets,
                       int32_t n_steps, int64_t stride);
+/* The same for a stream of compact 16-byte records (d_msgs 16-byte aligned,
+ * like every bound message buffer: LOB_EINVAL otherwise). */
+int lob_load_messages16(lob_handle *h, const lob_msg16 *d_msgs, const int64_t *d_offsets,
+                        int32_t n_steps, int64_t stride);
+/* Device-side conversion of n records to the compact form.  d_status
+ * (optional, device int32) is set to LOB_EINVAL if an id does not fit (that
+ * record becomes a malformed one). */
+int lob_pack_messages16(const lob_msg *d_src, int64_t n, lob_msg16 *d_dst, int32_t *d_status, void *stream);
 
 /* ---- Episodes over one shared message stream (Sec. 3: the whole data set
  * in one contiguous array, runtime indexing of episode starts, episodes free
@@ -210,6 +231,10 @@ typedef struct lob_start {
 int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
                      const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
                      int64_t n_starts);
+/* Episode mode over a shared stream of compact 16-byte records. */
+int lob_set_episodes16(lob_handle *h, const lob_msg16 *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                       const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
+                       int64_t n_starts);
 /* Device int32 [n_envs]: the first data step of every env's current episode
  * (episode mode; 0 otherwise). */
 int lob_get_episode_starts(lob_handle *h, int32_t *d_out, void *stream);

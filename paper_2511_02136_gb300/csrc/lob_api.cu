@@ -146,7 +146,8 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     // the extended kernel when episode mode, a reward variant or another
     // action space is on
     const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
-                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0;
+                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0 ||
+                     p.msg16 != 0;
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     switch (K) {
@@ -231,6 +232,7 @@ struct lob_handle {
     cudaStream_t copy_stream = nullptr;
     int64_t async_calls = 0;
     const void *mapped_ok[6] = {};   // last host pointers found mapped, per argument
+    bool msg16 = false;   // the bound background stream holds 16-byte compact records
     // several agents per type: per-agent state [n_envs][n_agents]
     AgentState *d_agents = nullptr;
     // episode mode (one shared stream, snapshot table, auto-reset)
@@ -406,20 +408,32 @@ int lob_destroy(lob_handle *h) {
     return LOB_OK;
 }
 
-int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets, int32_t n_steps,
-                      int64_t stride) {
+static int load_messages(lob_handle *h, const void *d_msgs, const int64_t *d_offsets, int32_t n_steps, int64_t stride,
+                         bool msg16) {
     if (!h || !d_offsets || n_steps < 0 || stride < (int64_t)n_steps + 1) return LOB_EINVAL;
+    if (((uintptr_t)d_msgs & 15u) != 0) return LOB_EINVAL;   // bulk copies start on 16-byte boundaries
     if (!d_msgs && n_steps > 0) {
         // an all-empty window may pass a NULL message pointer; offsets still needed
     }
     if (h->ep_mode) h->reset_done = false;   // leaving episode mode: the books need a reset
     h->ep_mode = false;
-    h->msgs = d_msgs;
+    h->msg16 = msg16;
+    h->msgs = static_cast<const lob_msg *>(d_msgs);
     h->offsets = d_offsets;
     h->win_steps = n_steps;
     h->stride = stride;
     h->cursor = 0;
     return LOB_OK;
+}
+
+int lob_load_messages(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_offsets, int32_t n_steps,
+                      int64_t stride) {
+    return load_messages(h, d_msgs, d_offsets, n_steps, stride, false);
+}
+
+int lob_load_messages16(lob_handle *h, const lob_msg16 *d_msgs, const int64_t *d_offsets, int32_t n_steps,
+                        int64_t stride) {
+    return load_messages(h, d_msgs, d_offsets, n_steps, stride, true);
 }
 
 }  // extern "C"
@@ -541,6 +555,23 @@ __global__ void k_get_agents_ma(const AgentState *ag, long long *out, long long 
     out[4 * i + 0] = x.inv; out[4 * i + 1] = x.cash; out[4 * i + 2] = x.pv_prev; out[4 * i + 3] = x.exec_done;
 }
 
+// 32-byte records -> 16-byte compact records; an id outside the 60-bit range
+// sets *status to LOB_EINVAL (that record is written as malformed).
+__global__ void k_pack16(const lob_msg *src, lob_msg16 *dst, long long n, int *status) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const lob_msg m = src[i];
+    const bool valid = m.type >= LOB_ADD && m.type <= LOB_MARKET && (m.side == LOB_BUY || m.side == LOB_SELL);
+    const bool fits = m.oid >= LOB_MSG16_ID_MIN && m.oid <= LOB_MSG16_ID_MAX;
+    if (!fits && status) atomicExch(status, LOB_EINVAL);
+    lob_msg16 r;
+    r.px = m.px;
+    r.qty = m.qty;
+    const unsigned long long code = (valid && fits) ? (unsigned long long)m.type | (m.side == LOB_SELL ? 8ull : 0ull) : 0ull;
+    r.word = (long long)(((unsigned long long)(fits ? m.oid : 0) << 4) | code);
+    dst[i] = r;
+}
+
 // internal blocked layout -> canonical priority-ordered record per env
 __global__ void k_get_book(const unsigned char *books, const long long *book_off, const long long *canon_off,
                            const int *caps, const EnvState *st, unsigned char *out, int n) {
@@ -597,7 +628,8 @@ static const int64_t *step_offsets(const lob_handle *h) { return h->ep_mode ? h-
 
 static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
                         int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
-                        long long *rew, unsigned char *done, cudaStream_t s, bool msgs_sysmem = false) {
+                        long long *rew, unsigned char *done, cudaStream_t s, bool msgs_sysmem = false,
+                        bool msg16 = false) {
     const lob_config &c = h->cfg;
     KParams p;
     memset(&p, 0, sizeof(p));
@@ -619,6 +651,7 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     set_rewards(p, c);
     p.agents = h->d_agents;
     p.msgs_sysmem = msgs_sysmem ? 1 : 0;
+    p.msg16 = msg16 ? 1 : 0;
     if (h->ep_mode) {
         p.ep_mode = 1;
         p.n_starts = h->n_starts;
@@ -661,11 +694,12 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
 
 extern "C" {
 
-int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
-                     const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
-                     int64_t n_starts) {
+static int set_episodes(lob_handle *h, const void *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                        const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side, int64_t n_starts,
+                        bool msg16) {
     if (!h || !d_step_offsets || !h_starts || !h_levels || levels_per_side < 1 || n_starts < 1 ||
-        n_starts > 0x7fffffffLL || n_data_steps < h->cfg.episode_len || !h->uniform_cap)
+        n_starts > 0x7fffffffLL || n_data_steps < h->cfg.episode_len || !h->uniform_cap ||
+        ((uintptr_t)d_msgs & 15u) != 0)
         return LOB_EINVAL;
     const int cap = h->cfg.cap_per_side, T = h->cfg.episode_len;
     const int ls = levels_per_side;
@@ -710,11 +744,24 @@ int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step
     }
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return LOB_ECUDA;
     h->ep_mode = true;
-    h->msgs = d_msgs;
+    h->msg16 = msg16;
+    h->msgs = static_cast<const lob_msg *>(d_msgs);
     h->ep_off = d_step_offsets;
     h->n_data_steps = n_data_steps;
     h->n_starts = (int32_t)n_starts;
     return LOB_OK;
+}
+
+int lob_set_episodes(lob_handle *h, const lob_msg *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                     const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
+                     int64_t n_starts) {
+    return set_episodes(h, d_msgs, d_step_offsets, n_data_steps, h_starts, h_levels, levels_per_side, n_starts, false);
+}
+
+int lob_set_episodes16(lob_handle *h, const lob_msg16 *d_msgs, const int64_t *d_step_offsets, int64_t n_data_steps,
+                       const lob_start *h_starts, const int32_t *h_levels, int32_t levels_per_side,
+                       int64_t n_starts) {
+    return set_episodes(h, d_msgs, d_step_offsets, n_data_steps, h_starts, h_levels, levels_per_side, n_starts, true);
 }
 
 int lob_get_episode_starts(lob_handle *h, int32_t *d_out, void *stream) {
@@ -762,7 +809,7 @@ int lob_step(lob_handle *h, const int32_t *d_actions, void *stream) {
     if (!steps_left(h, 1)) return LOB_ESTATE;
     if (h->cfg.n_agents > 0 && h->cfg.action_mode == LOB_ACT_HOST && !d_actions) return LOB_EINVAL;
     int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, d_actions, 0, h->d_obs, h->d_rew,
-                          h->d_done, (cudaStream_t)stream);
+                          h->d_done, (cudaStream_t)stream, false, h->msg16);
     if (rc != LOB_OK) return rc;
     h->cursor++;
     h->t++;
@@ -777,7 +824,7 @@ int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float 
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, n_steps, d_actions,
                           (long long)h->cfg.n_agents * h->cfg.n_envs, d_obs, reinterpret_cast<long long *>(d_rewards),
-                          d_done, s);
+                          d_done, s, false, h->msg16);
     if (rc != LOB_OK) return rc;
     // keep the last step's outputs for lob_observe
     const size_t n = (size_t)h->cfg.n_envs, A = (size_t)h->cfg.n_agents, D = (size_t)h->D;
@@ -956,6 +1003,13 @@ int lob_step_host_async(lob_handle *h, const lob_msg *h_msgs, const int64_t *h_o
     if (h_rewards && A) rc |= cuda_ok(cudaMemcpyAsync(h_rewards, h->d_rew, (size_t)n * A * 8, cudaMemcpyDeviceToHost, s));
     if (h_done) rc |= cuda_ok(cudaMemcpyAsync(h_done, h->d_done, (size_t)n, cudaMemcpyDeviceToHost, s));
     return rc == LOB_OK ? LOB_OK : LOB_ECUDA;
+}
+
+int lob_pack_messages16(const lob_msg *d_src, int64_t n, lob_msg16 *d_dst, int32_t *d_status, void *stream) {
+    if (n < 0 || (n > 0 && (!d_src || !d_dst))) return LOB_EINVAL;
+    if (n == 0) return LOB_OK;
+    k_pack16<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_src, d_dst, n, d_status);
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 
 int64_t lob_book_bytes(const lob_handle *h) { return h ? h->canon_bytes : 0; }
@@ -1196,7 +1250,7 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
                                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return LOB_ECUDA;
         rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, h->d_act, 0, h->d_obs, h->d_rew,
-                          h->d_done, s);
+                          h->d_done, s, false, h->msg16);
         if (rc != LOB_OK) return rc;
         h->cursor++;
         h->t++;

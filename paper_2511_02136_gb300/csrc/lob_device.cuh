@@ -118,6 +118,7 @@ struct KParams {
     const float *ep_obs;
     AgentState *agents;              // several agents per type: [n_envs][n_agents]
     int msgs_sysmem;                 // messages (and offsets) in page-locked host memory
+    int msg16;                       // background messages are 16-byte compact records
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -1113,12 +1114,12 @@ __device__ __forceinline__ int agent_orders_ma(const KParams &p, int t, unsigned
 
 // One message tile (up to TILE records) copied by the warp's lanes, one
 // 32-byte record per lane, as one commit group.
-__device__ __forceinline__ void tile_copy_lanes(DevMsg *dst, const DevMsg *src, int count, int lane) {
+__device__ __forceinline__ void tile_copy_lanes(void *dst, const void *src, int count, int rec_bytes, int lane) {
     if (lane < count) {
-        char *d = reinterpret_cast<char *>(dst + lane);
-        const char *g = reinterpret_cast<const char *>(src + lane);
+        char *d = reinterpret_cast<char *>(dst) + (long long)lane * rec_bytes;
+        const char *g = reinterpret_cast<const char *>(src) + (long long)lane * rec_bytes;
         cp_async16(d, g);
-        cp_async16(d + 16, g + 16);
+        if (rec_bytes == 32) cp_async16(d + 16, g + 16);
     }
     cp_async_commit();
 }
@@ -1149,6 +1150,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     // episode mode (dcur) its episode's first data step plus the step within it.
     const bool ep_mode = XT && p.ep_mode;
     const bool sysm = XT && p.msgs_sysmem;   // message tiles by lane copies instead of bulk copies
+    const bool m16 = XT && p.msg16;          // compact 16-byte background records
+    const int rec = m16 ? 16 : 32;
+    const char *msg_base = reinterpret_cast<const char *>(p.msgs);
     int ep_start = ep_mode ? st->ep_start : 0;
     long long dcur = ep_mode ? (long long)ep_start + p.t0 % p.T : 0;
     const long long d0 = ep_mode ? dcur : (long long)e * p.off_stride + p.k0;
@@ -1209,10 +1213,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         if (ntiles > 0) {
             __syncwarp();
             if (sysm) {
-                tile_copy_lanes(sm.tile[pipe.tiles & 1], p.msgs + mb, min(TILE, nmsg), lane);
+                tile_copy_lanes(sm.tile[pipe.tiles & 1], msg_base + mb * rec, min(TILE, nmsg), rec, lane);
             } else if (lane == 0) {
                 fence_proxy_async_smem();
-                tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb, (unsigned)min(TILE, nmsg) * 32u,
+                tma_bulk_g2s(sm.tile[pipe.tiles & 1], msg_base + mb * rec, (unsigned)(min(TILE, nmsg) * rec),
                              &sm.bar[pipe.tiles & 1]);
             }
             pipe.tiles++;
@@ -1430,13 +1434,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 }
                 if (ch + 1 < ntiles) {
                     __syncwarp();
+                    const char *src = msg_base + (mb + (long long)(ch + 1) * TILE) * rec;
                     if (sysm) {
-                        tile_copy_lanes(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(ch + 1) * TILE,
-                                        min(TILE, nmsg - (ch + 1) * TILE), lane);
+                        tile_copy_lanes(sm.tile[pipe.tiles & 1], src, min(TILE, nmsg - (ch + 1) * TILE), rec, lane);
                     } else if (lane == 0) {
                         fence_proxy_async_smem();
-                        tma_bulk_g2s(sm.tile[pipe.tiles & 1], p.msgs + mb + (long long)(ch + 1) * TILE,
-                                     (unsigned)min(TILE, nmsg - (ch + 1) * TILE) * 32u, &sm.bar[pipe.tiles & 1]);
+                        tma_bulk_g2s(sm.tile[pipe.tiles & 1], src, (unsigned)(min(TILE, nmsg - (ch + 1) * TILE) * rec),
+                                     &sm.bar[pipe.tiles & 1]);
                     }
                     pipe.tiles++;
                 }
@@ -1444,17 +1448,31 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 cnt_ch = min(TILE, nmsg - ch * TILE);
             }
             const int4 *rp = reinterpret_cast<const int4 *>(base);
-            int4 w0 = rp[0], w1 = rp[1];
+            // a tile of compact records: {px, qty, word = id << 4 | sell << 3 | type}
+            const bool c16 = m16 && ch >= 0;
+            int4 w0 = rp[0], w1 = c16 ? rp[0] : rp[1];
             for (int i = 0; i < cnt_ch; i++) {
-                const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
-                const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                const int key = w1.z;
-                const int px = w1.x;
-                int qty = w1.y;
+                const int4 n0 = c16 ? rp[i + 1] : rp[2 * i + 2], n1 = c16 ? n0 : rp[2 * i + 3];
+                long long oid;
+                int px, qty, type, side;
+                if (c16) {
+                    const long long word = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
+                    px = w0.x;
+                    qty = w0.y;
+                    type = (int)(word & 7);
+                    side = (word & 8) ? -1 : 1;
+                    oid = word >> 4;
+                } else {
+                    oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
+                    const int key = w1.z;
+                    px = w1.x;
+                    qty = w1.y;
+                    type = key & 0xffff;
+                    side = key >> 16;
+                }
                 c.c_msgs += 1;
                 c.c_agent += agent;
                 // one dense dispatch index: (type - 1) * 2 + (side is sell), 8 = malformed
-                const int type = key & 0xffff, side = key >> 16;
                 const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
                                    (qty > 0 || type == LOB_DELETE);
                 const int didx = valid ? ((type - 1) << 1) | (side < 0 ? 1 : 0) : 8;

@@ -48,13 +48,15 @@ EXPORTS = [
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
-    "lob_step_host_async",
+    "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
 LOB_MM_SPREAD_SKEW, LOB_MM_FIXED_QUANT, LOB_MM_DIRECTIONAL = 0, 1, 2
 LOB_INIT_ID = 0x4000000000000000
 START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
+MSG16_DTYPE = np.dtype([("px", "<i4"), ("qty", "<i4"), ("word", "<i8")])
+LOB_MSG16_ID_MIN, LOB_MSG16_ID_MAX = -(1 << 59), (1 << 59) - 1
 POLICY_HIDDEN = 128
 LOB_NOALLOC_MAX_ENVS = 16384
 LOB_MAX_PER_TYPE = 16
@@ -143,6 +145,9 @@ def _load():
         "lob_rollout": (ctypes.c_int, [P, I32, P, P, P, P, P]),
         "lob_step_host": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
         "lob_step_host_async": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
+        "lob_load_messages16": (ctypes.c_int, [P, P, P, I32, I64]),
+        "lob_set_episodes16": (ctypes.c_int, [P, P, P, I64, P, P, I32, I64]),
+        "lob_pack_messages16": (ctypes.c_int, [P, I64, P, P, P]),
         "lob_book_bytes": (I64, [P]),
         "lob_get_book": (ctypes.c_int, [P, P, P]),
         "lob_get_counters": (ctypes.c_int, [P, P, P]),
@@ -328,6 +333,25 @@ def lob_set_episodes(h, msgs_dev, step_offsets_dev, starts, levels):
                                            len(starts)), "lob_set_episodes")
 
 
+def lob_load_messages16(h, msgs_dev, offsets_dev, n_steps, stride):
+    return _check(_load().lob_load_messages16(h, _dp(msgs_dev), _dp(offsets_dev), n_steps, stride),
+                  "lob_load_messages16")
+
+
+def lob_set_episodes16(h, msgs_dev, step_offsets_dev, starts, levels):
+    starts = np.ascontiguousarray(starts, dtype=START_DTYPE)
+    levels = np.ascontiguousarray(levels, dtype=np.int32)
+    n_data = step_offsets_dev.shape[0] - 1
+    return _check(_load().lob_set_episodes16(h, _dp(msgs_dev), _dp(step_offsets_dev), n_data, starts.ctypes.data,
+                                             levels.ctypes.data, levels.shape[2], len(starts)), "lob_set_episodes16")
+
+
+def lob_pack_messages16(src_dev, n, dst_dev, status_dev=None, stream=None):
+    """Device 32-byte records -> 16-byte compact records (status int32 set to LOB_EINVAL on an id out of range)."""
+    return _check(_load().lob_pack_messages16(_dp(src_dev), n, _dp(dst_dev), _dp(status_dev), _stream(stream)),
+                  "lob_pack_messages16")
+
+
 def lob_get_episode_starts(h, out, stream=None):
     return _check(_load().lob_get_episode_starts(h, _dp(out), _stream(stream)), "lob_get_episode_starts")
 
@@ -444,9 +468,14 @@ class LobEnv:
         self._keep = [msgs_dev, offsets_dev]
         lob_load_messages(self.h, msgs_dev, offsets_dev, offsets_dev.shape[1] - 1, offsets_dev.shape[1])
 
-    def set_episodes(self, msgs_dev, step_offsets_dev, starts, levels):
+    def set_episodes(self, msgs_dev, step_offsets_dev, starts, levels, compact=False):
         self._keep = [msgs_dev, step_offsets_dev]
-        lob_set_episodes(self.h, msgs_dev, step_offsets_dev, starts, levels)
+        (lob_set_episodes16 if compact else lob_set_episodes)(self.h, msgs_dev, step_offsets_dev, starts, levels)
+
+    def load_messages16(self, msgs16_dev, offsets_dev):
+        """msgs16_dev: uint8/int64 tensor of 16-byte compact records; offsets_dev int64 [n_envs, n_steps+1]."""
+        self._keep = [msgs16_dev, offsets_dev]
+        lob_load_messages16(self.h, msgs16_dev, offsets_dev, offsets_dev.shape[1] - 1, offsets_dev.shape[1])
 
     def episode_starts(self):
         out = self.torch.zeros(self.n_envs, dtype=self.torch.int32, device=self.dev)

@@ -178,6 +178,25 @@ def generate(model: MessageModel, seeds: np.ndarray, n_steps: int, n_threads: in
 
 
 START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
+MSG16_DTYPE = np.dtype([("px", "<i4"), ("qty", "<i4"), ("word", "<i8")])
+
+
+def pack16(msgs: np.ndarray) -> np.ndarray:
+    """The 16-byte compact encoding of 32-byte records: px, qty and
+    word = id << 4 | (side is sell) << 3 | type, type 0 when the record's type
+    or side is invalid.  Ids must lie in [-2^59, 2^59)."""
+    oid = msgs["oid"].astype(np.int64)
+    if len(oid) and (oid.min() < -(1 << 59) or oid.max() >= (1 << 59)):
+        raise ValueError("order id outside the compact range")
+    t = msgs["type"].astype(np.int64)
+    sd = msgs["side"].astype(np.int64)
+    valid = (t >= 1) & (t <= 4) & ((sd == 1) | (sd == -1))
+    code = np.where(valid, t | np.where(sd == -1, 8, 0), 0)
+    out = np.empty(len(msgs), MSG16_DTYPE)
+    out["px"] = msgs["px"]
+    out["qty"] = msgs["qty"]
+    out["word"] = (oid << 4) | code
+    return out
 
 
 def start_books(seed: int, mids: np.ndarray, start_steps, levels_per_side: int, min_levels: int = 0,

@@ -31,7 +31,7 @@ class Pair:
     def __init__(self, n_envs, st, *, n_agents=2, cap=100, caps=None, top_levels=10, episode_len=None,
                  mm_lot=1, exec_target=500, exec_dir=-1, action_mode=lob.LOB_ACT_RANDOM, start_px=10_000,
                  fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1, rewards=None,
-                 episodes=None, seeds=None, mm_space=0):
+                 episodes=None, seeds=None, mm_space=0, compact=False):
         """episodes: (starts, levels) puts both sides in episode mode over the
         single shared stream st (env 0 of st); seeds then gives the env seeds."""
         import torch
@@ -50,13 +50,15 @@ class Pair:
                                  action_mode=action_mode, trace=(1 if fill_cap else 0) | (2 if snap_cap else 0),
                                  start_px=start_px, n_threads=n_threads, caps=caps, mm_space=mm_space,
                                  **(rewards or {}))
-        self.msgs_d = to_dev(st.msgs) if len(st.msgs) else torch.zeros(32, dtype=torch.uint8, device="cuda")
+        # compact: the GPU reads the 16-byte encoding, the oracle the 32-byte records
+        dev_msgs = mbogen.pack16(st.msgs) if compact else st.msgs
+        self.msgs_d = to_dev(dev_msgs) if len(dev_msgs) else torch.zeros(32, dtype=torch.uint8, device="cuda")
         self.off_d = to_dev(st.offsets)
         if episodes is None:
-            self.env.load_messages(self.msgs_d, self.off_d)
+            (self.env.load_messages16 if compact else self.env.load_messages)(self.msgs_d, self.off_d)
             self.orc.load_messages(st.msgs, st.offsets)
         else:
-            self.env.set_episodes(self.msgs_d, self.off_d[0], *episodes)
+            self.env.set_episodes(self.msgs_d, self.off_d[0], *episodes, compact=compact)
             self.orc.set_episodes(st.msgs, st.offsets[0], *episodes)
         seeds = st.seeds if seeds is None else np.ascontiguousarray(seeds, np.uint64)
         self.seeds_d = to_dev(seeds)

@@ -1,5 +1,6 @@
 """The seeded input generator: determinism, layout and the message model's moments."""
 import numpy as np
+import pytest
 
 from paper_2511_02136_gb300 import mbogen as g
 
@@ -87,3 +88,29 @@ def test_env_caps_choices():
     vals, cnt = np.unique(caps, return_counts=True)
     assert vals.tolist() == [50, 100, 200, 500]
     assert np.all(np.abs(cnt / 4000 - 0.25) < 0.03)
+
+
+def test_pack16_round_trip_and_malformed():
+    """The compact encoding keeps price, size, id, type and side of every valid
+    record; an invalid type or side becomes type 0; ids beyond 60 bits are refused."""
+    st = g.generate(g.MessageModel(msgs_per_step=50), g.env_seeds(3, 4), 5)
+    msgs = st.msgs.copy()
+    msgs["type"][7] = 9
+    msgs["side"][11] = 0
+    msgs["oid"][13] = (1 << 59) - 1
+    p = g.pack16(msgs)
+    assert p.dtype.itemsize == 16
+    w = p["word"].astype(np.int64)
+    typ, sell, oid = w & 7, (w >> 3) & 1, w >> 4
+    ok = np.ones(len(msgs), bool)
+    ok[[7, 11]] = False
+    np.testing.assert_array_equal(p["px"], msgs["px"])
+    np.testing.assert_array_equal(p["qty"], msgs["qty"])
+    np.testing.assert_array_equal(oid, msgs["oid"])
+    np.testing.assert_array_equal(typ[ok], msgs["type"][ok])
+    np.testing.assert_array_equal(np.where(sell[ok] == 1, -1, 1), msgs["side"][ok])
+    assert typ[7] == 0 and typ[11] == 0
+    bad = msgs[:2].copy()
+    bad["oid"][0] = 1 << 59
+    with pytest.raises(ValueError):
+        g.pack16(bad)

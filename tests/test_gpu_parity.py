@@ -513,3 +513,88 @@ def test_checkpoint_resume_bit_identical():
     assert ei.value.code == lob.LOB_EINVAL
     for e in (env, env2, other):
         e.close()
+
+
+def _with_malformed(st):
+    msgs = st.msgs.copy()
+    msgs["type"][5] = 9
+    msgs["side"][17] = 0
+    msgs["qty"][23] = 0 if msgs["type"][23] != 3 else msgs["qty"][23]
+    st.msgs = msgs
+    return st
+
+
+def test_compact_messages_parity():
+    """The GPU reads 16-byte compact records, the oracle the 32-byte originals
+    (malformed ones included): every step's outputs, fills and the final state."""
+    n, T = 37, 12
+    st = _with_malformed(mbogen.generate(mbogen.MessageModel(msgs_per_step=75), mbogen.env_seeds(91, n), T))
+    pr = Pair(n, st, cap=100, exec_target=60, fill_cap=512, compact=True)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    assert pr.env.sync() == lob.LOB_EBADMSG
+    pr.close()
+
+
+def test_compact_messages_rollout_agents_and_episodes():
+    import torch
+    n, T = 30, 10
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=90), mbogen.env_seeds(92, n), T)
+    pr = Pair(n, st, n_agents=6, cap=200, exec_target=40, compact=True)
+    obs = torch.zeros((T, n, 6, pr.env.D), dtype=torch.float32, device="cuda")
+    rew = torch.zeros((T, n, 6), dtype=torch.int64, device="cuda")
+    done = torch.zeros((T, n), dtype=torch.uint8, device="cuda")
+    lob.lob_rollout(pr.env.h, T, None, obs, rew, done)
+    for t in range(T):
+        pr.orc.step()
+        o_obs, o_rew, o_done = pr.orc.observe()
+        np.testing.assert_allclose(obs[t].cpu().numpy(), o_obs, rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(rew[t].cpu().numpy(), o_rew)
+    pr.check_state()
+    pr.check_outputs()
+    pr.close()
+    ds = mbogen.generate(mbogen.MessageModel(msgs_per_step=60), mbogen.env_seeds(93, 1), 30)
+    steps = np.random.default_rng(93).integers(0, 30 - 4 + 1, size=5)
+    starts, levels = mbogen.start_books(93, ds.mids[0], steps, 10)
+    pr = Pair(n, ds, cap=100, episode_len=4, exec_target=30, episodes=(starts, levels),
+              seeds=mbogen.env_seeds(94, n), compact=True)
+    for _ in range(9):
+        pr.step()
+        pr.check_outputs()
+    pr.check_state()
+    pr.close()
+
+
+def test_pack_kernel_matches_packer():
+    import torch
+    from harness import to_dev
+    st = _with_malformed(mbogen.generate(mbogen.MessageModel(msgs_per_step=64), mbogen.env_seeds(95, 8), 6))
+    n = len(st.msgs)
+    src = to_dev(st.msgs)
+    dst = torch.zeros(n * 16, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lob.lob_pack_messages16(src, n, dst, status)
+    assert dst.cpu().numpy().tobytes() == mbogen.pack16(st.msgs).tobytes()
+    assert int(status.item()) == 0
+    big = st.msgs[:4].copy()
+    big["oid"][2] = 1 << 60
+    src = to_dev(big)
+    dst = torch.zeros(4 * 16, dtype=torch.uint8, device="cuda")
+    lob.lob_pack_messages16(src, 4, dst, status)
+    assert int(status.item()) == lob.LOB_EINVAL
+
+
+def test_misaligned_message_buffer_rejected():
+    import torch
+    from harness import to_dev
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=10), mbogen.env_seeds(96, 2), 3)
+    env = lob.LobEnv(2, cap=50, episode_len=3)
+    raw = torch.zeros(len(st.msgs) * 32 + 16, dtype=torch.uint8, device="cuda")
+    off = to_dev(st.offsets)
+    with pytest.raises(lob.LobError) as ei:
+        env.load_messages(raw[8:], off)
+    assert ei.value.code == lob.LOB_EINVAL
+    env.close()
