@@ -563,6 +563,37 @@ def run_workload(args):
                                        "600; one lob_rollout launch per run writing every step's obs, rewards "
                                        "and done flags, inputs resident, 256 MiB written before each run", "value_row": "100 msgs/step, 1 agent per type"},
                 "dtype": "int64", "data": "synthetic"}
+    elif wl == "compact1024":
+        # the benchmark workload stored as 16-byte compact records beside the
+        # 32-byte ones: one 200-step lob_rollout each, inputs resident
+        n, Tr = N_ENVS, 200
+        seeds, st = make_inputs(1, Tr)
+        packed = mbogen.pack16(st.msgs)
+        od = torch.from_numpy(st.offsets).to(dev)
+        sd = torch.from_numpy(seeds.view(np.int64).copy()).to(dev)
+        res = {}
+        for name, arr in (("msg32", st.msgs), ("msg16", packed)):
+            md = torch.from_numpy(arr.view(np.uint8)).to(dev)
+            env = lob.LobEnv(n, cap=CAP, top_levels=L, episode_len=Tr, exec_target=EXEC_TARGET,
+                             action_mode=lob.LOB_ACT_RANDOM)
+            bind = env.load_messages16 if name == "msg16" else env.load_messages
+            times = []
+            for i in range(args.reps):
+                env.reset(sd)
+                bind(md, od)
+                torch.cuda.synchronize()
+                times += _flush_and_time(lambda: lob.lob_rollout(env.h, Tr, None, None, None, None), 1, dev)
+            assert env.sync() == 0
+            msgs = float(env.counters()[:, 0].sum().item())
+            env.close()
+            t = min(times)
+            res[name] = {"msgs_per_s": msgs / t, "seconds": t, "stream_bytes": int(arr.nbytes)}
+            del md
+        line = {"workload": "compact1024", "metric": METRIC, "value": res["msg16"]["msgs_per_s"], "unit": "msgs/s",
+                "msg16": res["msg16"], "msg32": res["msg32"], "n_gpus": 1, "steps": Tr,
+                "config": {"workload": "1024 envs x cap 100 x 100 msgs/step x 200 steps, random policy, one "
+                                       "lob_rollout; the same stream as 16-byte compact and 32-byte records"},
+                "dtype": "int64", "data": "synthetic"}
     elif wl == "stress65536":
         n, T = 65536, args.stress_steps
         seeds = mbogen.env_seeds(4, n)
@@ -604,7 +635,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="envs1024",
-                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "table1", "stress65536"],
+                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "table1", "compact1024",
+                             "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stress-steps", type=int, default=4)

@@ -1124,6 +1124,29 @@ __device__ __forceinline__ void tile_copy_lanes(void *dst, const void *src, int 
     cp_async_commit();
 }
 
+// A tile of compact records {px, qty, word = id << 4 | sell << 3 | type},
+// landed in the upper half of a tile buffer, rewritten in place as 32-byte
+// records (all lanes read before any lane writes).
+__device__ __forceinline__ void widen_tile(DevMsg *tile, int count, int lane) {
+    const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const char *>(tile) + 16 * TILE);
+    int4 w = make_int4(0, 0, 0, 0);
+    if (lane < count) w = src[lane];
+    __syncwarp();
+    if (lane < count) {
+        const long long word = ((long long)(unsigned)w.w << 32) | (unsigned)w.z;
+        DevMsg r;
+        r.ts = 0;
+        r.oid = word >> 4;
+        r.px = w.x;
+        r.qty = w.y;
+        r.type = (short)(word & 7);
+        r.side = (short)((word & 8) ? LOB_SELL : LOB_BUY);
+        r.pad = 0;
+        tile[lane] = r;
+    }
+    __syncwarp();
+}
+
 // Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
@@ -1160,8 +1183,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     long long me = p.offsets[d0 + 1];
 
     Side<K> bid, ask;
-    side_load<K, true>(bid, sm.pool[0], blk, lane);
-    side_load<K, false>(ask, sm.pool[1], blk, lane);
+    if constexpr (!XT) {
+        side_load<K, true>(bid, sm.pool[0], blk, lane);
+        side_load<K, false>(ask, sm.pool[1], blk, lane);
+    }
 
     Ctx c;
     c.ts_next = st->ts_next; c.seq_next = st->seq_next;
@@ -1188,11 +1213,19 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         }
     }
     // live counts arrive with the state: mark occupancy now
-    side_set_count<K>(bid, nb0, lane);
-    side_set_count<K>(ask, na0, lane);
-    __syncwarp();
-    front_refresh<K>(bid, sm.pool[0]);
-    front_refresh<K>(ask, sm.pool[1]);
+    if constexpr (!XT) {
+        side_set_count<K>(bid, nb0, lane);
+        side_set_count<K>(ask, na0, lane);
+        __syncwarp();
+        front_refresh<K>(bid, sm.pool[0]);
+        front_refresh<K>(ask, sm.pool[1]);
+    }
+    // extended kernel: the book is (re)loaded at the top of a step, from the
+    // env's block first and from a snapshot image after an episode reset, so
+    // that the load code appears once
+    const unsigned char *load_src = blk;
+    int load_nb = nb0, load_na = na0;
+    bool need_load = XT;
 
     const bool snap_env = TRACE && p.snaps != nullptr && e == 0;
     long long snap_n = 0;
@@ -1212,14 +1245,28 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         const unsigned tile0 = pipe.tiles;
         if (ntiles > 0) {
             __syncwarp();
+            // compact tiles land in the upper half of the buffer and are widened on arrival
+            char *dst = reinterpret_cast<char *>(sm.tile[pipe.tiles & 1]) + (m16 ? 16 * TILE : 0);
             if (sysm) {
-                tile_copy_lanes(sm.tile[pipe.tiles & 1], msg_base + mb * rec, min(TILE, nmsg), rec, lane);
+                tile_copy_lanes(dst, msg_base + mb * rec, min(TILE, nmsg), rec, lane);
             } else if (lane == 0) {
                 fence_proxy_async_smem();
-                tma_bulk_g2s(sm.tile[pipe.tiles & 1], msg_base + mb * rec, (unsigned)(min(TILE, nmsg) * rec),
-                             &sm.bar[pipe.tiles & 1]);
+                tma_bulk_g2s(dst, msg_base + mb * rec, (unsigned)(min(TILE, nmsg) * rec), &sm.bar[pipe.tiles & 1]);
             }
             pipe.tiles++;
+        }
+        if constexpr (XT) {
+            if (need_load) {
+                __syncwarp();
+                side_load<K, true>(bid, sm.pool[0], load_src, lane);
+                side_load<K, false>(ask, sm.pool[1], load_src, lane);
+                side_set_count<K>(bid, load_nb, lane);
+                side_set_count<K>(ask, load_na, lane);
+                __syncwarp();
+                front_refresh<K>(bid, sm.pool[0]);
+                front_refresh<K>(ask, sm.pool[1]);
+                need_load = false;
+            }
         }
         c.msg_idx = 0;
         c.fill_n = 0;
@@ -1435,44 +1482,32 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 if (ch + 1 < ntiles) {
                     __syncwarp();
                     const char *src = msg_base + (mb + (long long)(ch + 1) * TILE) * rec;
+                    char *dst = reinterpret_cast<char *>(sm.tile[pipe.tiles & 1]) + (m16 ? 16 * TILE : 0);
                     if (sysm) {
-                        tile_copy_lanes(sm.tile[pipe.tiles & 1], src, min(TILE, nmsg - (ch + 1) * TILE), rec, lane);
+                        tile_copy_lanes(dst, src, min(TILE, nmsg - (ch + 1) * TILE), rec, lane);
                     } else if (lane == 0) {
                         fence_proxy_async_smem();
-                        tma_bulk_g2s(sm.tile[pipe.tiles & 1], src, (unsigned)(min(TILE, nmsg - (ch + 1) * TILE) * rec),
+                        tma_bulk_g2s(dst, src, (unsigned)(min(TILE, nmsg - (ch + 1) * TILE) * rec),
                                      &sm.bar[pipe.tiles & 1]);
                     }
                     pipe.tiles++;
                 }
                 base = sm.tile[buf];
                 cnt_ch = min(TILE, nmsg - ch * TILE);
+                if (m16) widen_tile(sm.tile[buf], cnt_ch, lane);
             }
             const int4 *rp = reinterpret_cast<const int4 *>(base);
-            // a tile of compact records: {px, qty, word = id << 4 | sell << 3 | type}
-            const bool c16 = m16 && ch >= 0;
-            int4 w0 = rp[0], w1 = c16 ? rp[0] : rp[1];
+            int4 w0 = rp[0], w1 = rp[1];
             for (int i = 0; i < cnt_ch; i++) {
-                const int4 n0 = c16 ? rp[i + 1] : rp[2 * i + 2], n1 = c16 ? n0 : rp[2 * i + 3];
-                long long oid;
-                int px, qty, type, side;
-                if (c16) {
-                    const long long word = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                    px = w0.x;
-                    qty = w0.y;
-                    type = (int)(word & 7);
-                    side = (word & 8) ? -1 : 1;
-                    oid = word >> 4;
-                } else {
-                    oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                    const int key = w1.z;
-                    px = w1.x;
-                    qty = w1.y;
-                    type = key & 0xffff;
-                    side = key >> 16;
-                }
+                const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
+                const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
+                const int key = w1.z;
+                const int px = w1.x;
+                int qty = w1.y;
                 c.c_msgs += 1;
                 c.c_agent += agent;
                 // one dense dispatch index: (type - 1) * 2 + (side is sell), 8 = malformed
+                const int type = key & 0xffff, side = key >> 16;
                 const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
                                    (qty > 0 || type == LOB_DELETE);
                 const int didx = valid ? ((type - 1) << 1) | (side < 0 ? 1 : 0) : 8;
@@ -1652,17 +1687,14 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         if (TRACE && lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
         if (ep_end) {
-            // the next episode: snapshot book, flat agents, its first data step
+            // the next episode: its snapshot book (loaded at the next step's
+            // top, or copied to the env's block if this launch ends here),
+            // flat agents, its first data step
             const lob_start S = p.ep_starts[ep_j];
-            const unsigned char *img = p.ep_images + (long long)ep_j * p.ep_block;
-            __syncwarp();
-            side_load<K, true>(bid, sm.pool[0], img, lane);
-            side_load<K, false>(ask, sm.pool[1], img, lane);
-            side_set_count<K>(bid, S.n_bid, lane);
-            side_set_count<K>(ask, S.n_ask, lane);
-            __syncwarp();
-            front_refresh<K>(bid, sm.pool[0]);
-            front_refresh<K>(ask, sm.pool[1]);
+            load_src = p.ep_images + (long long)ep_j * p.ep_block;
+            load_nb = S.n_bid;
+            load_na = S.n_ask;
+            need_load = true;
             c.ts_next = S.n_bid + S.n_ask;
             c.seq_next = 0;
             c.inv0 = 0; c.inv1 = 0; c.cash0 = 0; c.cash1 = 0; c.pv0 = 0; c.pv1 = 0; c.exec_done = 0;
@@ -1678,8 +1710,15 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             dcur++;
         }
         if (step + 1 == p.n_steps) {
-            side_store<K, true>(bid, sm.pool[0], blk, lane);
-            side_store<K, false>(ask, sm.pool[1], blk, lane);
+            if (XT && need_load) {
+                // an episode ended with the launch: the env's block becomes the image
+                const int4 *src = reinterpret_cast<const int4 *>(load_src);
+                int4 *dst = reinterpret_cast<int4 *>(blk);
+                for (long long i = lane; i < p.ep_block / 16; i += 32) dst[i] = src[i];
+            } else {
+                side_store<K, true>(bid, sm.pool[0], blk, lane);
+                side_store<K, false>(ask, sm.pool[1], blk, lane);
+            }
         }
     }
 
@@ -1697,7 +1736,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         st->ts_next = c.ts_next; st->seq_next = c.seq_next;
         st->inv[0] = c.inv0; st->inv[1] = c.inv1; st->cash[0] = c.cash0; st->cash[1] = c.cash1;
         st->pv_prev[0] = c.pv0; st->pv_prev[1] = c.pv1; st->exec_done = c.exec_done;
-        st->last_px = c.last_px; st->n[0] = bid.n; st->n[1] = ask.n;
+        st->last_px = c.last_px;
+        st->n[0] = (XT && need_load) ? load_nb : bid.n;
+        st->n[1] = (XT && need_load) ? load_na : ask.n;
         st->t = p.t0 + p.n_steps;
         if (XT) st->ep_start = ep_start;
     }
