@@ -1112,6 +1112,29 @@ __device__ __forceinline__ int agent_orders_ma(const KParams &p, int t, unsigned
     return __shfl_sync(FULL, ns, 0);
 }
 
+// Quotes of the Fixed Quantity (8 options) and directional (3) market-maker
+// spaces (Sec. 4.1.1) around touches bb / ba: {bid, ask, bit 0 = bid quoted,
+// bit 1 = ask quoted}.  Out of line: the benchmark's head never calls it.
+static __device__ __noinline__ int4 mm_other_quotes(int space, int act, int bb, int ba) {
+    int qb = 0, qa = 0, f = 0;
+    if (space == LOB_MM_FIXED_QUANT) {
+        switch (act) {
+            case 1: qb = bb - 2; qa = ba + 2; f = 3; break;
+            case 2: qb = bb - 4; qa = ba + 4; f = 3; break;
+            case 3: qb = bb + 1; qa = ba - 1; f = 3; break;
+            case 4: qb = bb - 2; f = 1; break;
+            case 5: qa = ba + 2; f = 2; break;
+            case 6: qb = bb - 5; qa = ba - 1; f = 3; break;
+            case 7: qb = bb + 1; qa = ba + 5; f = 3; break;
+            default: break;
+        }
+    } else {
+        if (act == 1) { qb = bb; f = 1; }
+        if (act == 2) { qa = ba; f = 2; }
+    }
+    return make_int4(qb, qa, f, 0);
+}
+
 // One message tile (up to TILE records) copied by the warp's lanes, one
 // 32-byte record per lane, as one commit group.
 __device__ __forceinline__ void tile_copy_lanes(void *dst, const void *src, int count, int rec_bytes, int lane) {
@@ -1353,23 +1376,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 }
             } else {
                 // Fixed Quantity (8 options) or directional (3): quotes that may be one-sided
-                bool hb = false, ha = false;
-                long long qb = 0, qa = 0;
-                if (p.mm_space == LOB_MM_FIXED_QUANT) {
-                    switch (act1) {
-                        case 1: qb = bb - 2; qa = ba + 2; hb = ha = true; break;
-                        case 2: qb = bb - 4; qa = ba + 4; hb = ha = true; break;
-                        case 3: qb = bb + 1; qa = ba - 1; hb = ha = true; break;
-                        case 4: qb = bb - 2; hb = true; break;
-                        case 5: qa = ba + 2; ha = true; break;
-                        case 6: qb = bb - 5; qa = ba - 1; hb = ha = true; break;
-                        case 7: qb = bb + 1; qa = ba + 5; hb = ha = true; break;
-                        default: break;
-                    }
-                } else {
-                    if (act1 == 1) { qb = bb; hb = true; }
-                    if (act1 == 2) { qa = ba; ha = true; }
-                }
+                const int4 mq = mm_other_quotes(p.mm_space, act1, (int)bb, (int)ba);
+                const bool hb = (mq.z & 1) != 0, ha = (mq.z & 2) != 0;
+                const long long qb = mq.x, qa = mq.y;
                 // constant array indices only, so the wanted orders stay in registers
                 const int q1s = ha ? LOB_SELL : LOB_BUY;      // a one-sided quote
                 const int q1p = (int)(ha ? qa : qb);
