@@ -251,6 +251,10 @@ struct Side {
     static constexpr unsigned REP = IXB == 8 ? 0x01010101u : 0x00010001u;
     static constexpr unsigned KMASK = K == 32 ? 0xffffffffu : ((1u << K) - 1u);
     static constexpr int RK = REG ? K : 1;
+    // unroll factor of loops over a lane's slots that touch no register array:
+    // for the largest books partial unrolling keeps the kernel's code small
+    // (instruction fetch bounds that class); smaller ones unroll fully
+    static constexpr int SU = K >= 32 ? 4 : K;
     int px[RK];         // price of slot (lane, r) (registers mode only)
     long long id[RK];   // id of slot (lane, r) (registers mode only)
     unsigned occ;       // occupied slots of this lane (bit r)
@@ -561,7 +565,7 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
             pos += __popc(__ballot_sync(FULL, ((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p)));
     } else {
         int cnt = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
         for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(spx<K>(S, P, r, lane), p));
         pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
     }
@@ -627,7 +631,7 @@ template <int K>
 __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type, int p, int qty, long long oid,
                                             Ctx &c, int lane) {
     unsigned m = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++)
         if (((S.occ >> r) & 1u) && spx<K>(S, P, r, lane) == p && sid<K>(S, P, r, lane) == oid) m |= 1u << r;
     const unsigned lanes = __ballot_sync(FULL, m != 0);
@@ -708,7 +712,7 @@ template <int K>
 __device__ __forceinline__ void side_set_count(Side<K> &S, int n, int lane) {
     S.n = n;
     S.occ = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++)
         if (slot_of<K>(lane, r) < n) S.occ |= 1u << r;
 }
@@ -843,7 +847,7 @@ __device__ __forceinline__ unsigned side_carry(const Side<K> &S, const PoolSmem<
                                                const int (&wa)[3], const int (&ws)[3], const int (&wp)[3], int nw,
                                                unsigned (&kept)[3], int lane) {
     unsigned cmask = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++) {
         const int slot = slot_of<K>(lane, r);
         unsigned char flag = 0;
@@ -874,7 +878,7 @@ __device__ __forceinline__ unsigned side_carry(const Side<K> &S, const PoolSmem<
 template <int K>
 __device__ __forceinline__ void side_cancel_set(Side<K> &S, PoolSmem<K> &P, unsigned cmask, Ctx &c, int lane) {
     unsigned vol = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++)
         if ((cmask >> r) & 1u) vol += (unsigned)P.qty[slot_of<K>(lane, r)];
     const int ncan = (int)__reduce_add_sync(FULL, (unsigned)__popc(cmask));
@@ -969,7 +973,7 @@ template <int K>
 __device__ __forceinline__ unsigned side_carry_ma(const Side<K> &S, const PoolSmem<K> &P, unsigned char *cand, int sd,
                                                   AgentSmem &ag, int A, int lane) {
     unsigned cmask = 0;
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++) {
         const int slot = slot_of<K>(lane, r);
         unsigned char flag = 0;
@@ -991,7 +995,7 @@ __device__ __forceinline__ unsigned side_carry_ma(const Side<K> &S, const PoolSm
 // Resting quantity of every agent on one side (shared-memory atomics).
 template <int K>
 __device__ __forceinline__ void side_own_ma(const Side<K> &S, const PoolSmem<K> &P, AgentSmem &ag, int A, int lane) {
-#pragma unroll
+#pragma unroll (Side<K>::SU)
     for (int r = 0; r < K; r++) {
         const long long oid = sid<K>(S, P, r, lane);
         if (((S.occ >> r) & 1u) && oid < 0)
@@ -1520,39 +1524,66 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
                                    (qty > 0 || type == LOB_DELETE);
                 const int didx = valid ? ((type - 1) << 1) | (side < 0 ? 1 : 0) : 8;
-                switch (didx) {
-                    case 0:   // add, buy
-                        c.c_add_vol += qty;
-                        if (ask.n > 0 && px >= ask.fpx)
-                            qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
-                        if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
-                        break;
-                    case 1:   // add, sell
-                        c.c_add_vol += qty;
-                        if (bid.n > 0 && px <= bid.fpx)
-                            qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
-                        if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
-                        break;
-                    case 2:   // partial cancel, buy
-                    case 4:   // delete, buy
+                if constexpr (K >= 32) {
+                    // the largest books: one call site per side for taking
+                    // liquidity and for resting, to keep the kernel's code small
+                    if (didx == 0 || didx == 6) {          // buy: limit add or market
+                        const bool lim = didx == 0;
+                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                        if (!lim || (ask.n > 0 && px >= ask.fpx))
+                            qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], lim, px, qty, oid, LOB_BUY, c, lane);
+                        if (!lim) c.c_mkt_disc += qty;
+                        else if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                    } else if (didx == 1 || didx == 7) {   // sell: limit add or market
+                        const bool lim = didx == 1;
+                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                        if (!lim || (bid.n > 0 && px <= bid.fpx))
+                            qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], lim, px, qty, oid, LOB_SELL, c, lane);
+                        if (!lim) c.c_mkt_disc += qty;
+                        else if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                    } else if (didx == 2 || didx == 4) {
                         side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
-                        break;
-                    case 3:   // partial cancel, sell
-                    case 5:   // delete, sell
+                    } else if (didx == 3 || didx == 5) {
                         side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
-                        break;
-                    case 6:   // market, buy
-                        c.c_mkt_vol += qty;
-                        c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
-                        break;
-                    case 7:   // market, sell
-                        c.c_mkt_vol += qty;
-                        c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
-                        break;
-                    default:
+                    } else {
                         c.c_bad += 1;
                         c.status |= ST_BADMSG;
-                        break;
+                    }
+                } else {
+                    switch (didx) {
+                        case 0:   // add, buy
+                            c.c_add_vol += qty;
+                            if (ask.n > 0 && px >= ask.fpx)
+                                qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
+                            if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                            break;
+                        case 1:   // add, sell
+                            c.c_add_vol += qty;
+                            if (bid.n > 0 && px <= bid.fpx)
+                                qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
+                            if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                            break;
+                        case 2:   // partial cancel, buy
+                        case 4:   // delete, buy
+                            side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
+                            break;
+                        case 3:   // partial cancel, sell
+                        case 5:   // delete, sell
+                            side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+                            break;
+                        case 6:   // market, buy
+                            c.c_mkt_vol += qty;
+                            c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
+                            break;
+                        case 7:   // market, sell
+                            c.c_mkt_vol += qty;
+                            c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
+                            break;
+                        default:
+                            c.c_bad += 1;
+                            c.status |= ST_BADMSG;
+                            break;
+                    }
                 }
                 if (TRACE && snap_env) {
                     __syncwarp();
