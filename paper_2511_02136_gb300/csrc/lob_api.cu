@@ -99,8 +99,6 @@ cudaError_t ensure_optin() {
     return cudaSuccess;
 }
 
-// Launch the step kernel of class K (shared memory opted in by ensure_optin);
-// the warps per block are capped by what one block's shared memory holds.
 // Resident blocks per SM of the wide step kernel, per (class, extended,
 // warps per block); queried once (the launch shape fixes the shared memory).
 int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
@@ -122,6 +120,8 @@ int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
     return c > 0 ? c : 0;
 }
 
+// Launch the step kernel of class K (shared memory opted in by ensure_optin);
+// the warps per block are capped by what one block's shared memory holds.
 cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s,
                      const KParams &p) {
     if (p.n_agents > 2) {

@@ -312,29 +312,6 @@ __device__ __forceinline__ unsigned ix_below(int lim, int lane, int w) {
     return d <= 0 ? 0u : (d >= BPW ? Side<K>::ALLB : ((1u << (IXB * d)) - 1u));
 }
 
-// Insert slot f at position pos; positions >= pos move up by one.
-template <int K>
-__device__ __forceinline__ void ix_insert(Side<K> &S, int pos, int f, int lane) {
-    constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB, EPW = Side<K>::EPW;
-    constexpr unsigned ALLB = Side<K>::ALLB, EMASK = Side<K>::EMASK;
-    const unsigned top = (S.ix[NW - 1] >> (IXB * (BPW - 1))) & EMASK;
-    const unsigned carry = __shfl_up_sync(FULL, top, 1);
-    unsigned shifted[NW];
-#pragma unroll
-    for (int w = 0; w < NW; w++) {
-        const unsigned in = w == 0 ? carry : (S.ix[w - 1] >> (IXB * (BPW - 1)));
-        shifted[w] = ((S.ix[w] << IXB) | in) & ALLB;
-    }
-    const unsigned fb = (unsigned)f * Side<K>::REP;
-#pragma unroll
-    for (int w = 0; w < NW; w++) {
-        const int d = pos - (lane * K + EPW * w);
-        const unsigned keep = ix_below<K>(pos, lane, w);
-        const unsigned fm = (d >= 0 && d < BPW) ? (EMASK << (IXB * d)) : 0u;
-        S.ix[w] = (S.ix[w] & keep) | (fb & fm) | (shifted[w] & ~(keep | fm));
-    }
-}
-
 // Remove position q; positions > q move down by one.
 template <int K>
 __device__ __forceinline__ void ix_remove(Side<K> &S, int q, int lane) {
@@ -369,7 +346,8 @@ __device__ __forceinline__ void ix_removed(const Side<K> &S, int q, int lane, un
     }
 }
 
-// The index words after inserting slot f at position pos.
+// The index words after inserting slot f at position pos (positions >= pos
+// move up by one; the top entry of the last lane falls off).
 template <int K>
 __device__ __forceinline__ void ix_inserted(const Side<K> &S, int pos, int f, int lane, unsigned (&out)[Side<K>::NW]) {
     constexpr int NW = Side<K>::NW, BPW = Side<K>::BPW, IXB = Side<K>::IXB, EPW = Side<K>::EPW;
@@ -439,11 +417,6 @@ struct Ctx {
     int fill_cap;
     AgentSmem *ag;   // several agents per type only
 
-    __device__ __forceinline__ void credit(int who, long long dcash, long long dinv) {
-        if (who == 0) { cash0 += dcash; inv0 += dinv; }
-        else if (who == 1) { cash1 += dcash; inv1 += dinv; }
-        else { bg_cash += dcash; bg_inv += dinv; }
-    }
     __device__ __forceinline__ int owner(long long id) const {
         return (id >= 0 || A == 0) ? 2 : (int)((~id) & 1);
     }
