@@ -1183,10 +1183,6 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     long long me = p.offsets[d0 + 1];
 
     Side<K> bid, ask;
-    if constexpr (!XT) {
-        side_load<K, true>(bid, sm.pool[0], blk, lane);
-        side_load<K, false>(ask, sm.pool[1], blk, lane);
-    }
 
     Ctx c;
     c.ts_next = st->ts_next; c.seq_next = st->seq_next;
@@ -1212,20 +1208,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             agp->act[a] = x.act;
         }
     }
-    // live counts arrive with the state: mark occupancy now
-    if constexpr (!XT) {
-        side_set_count<K>(bid, nb0, lane);
-        side_set_count<K>(ask, na0, lane);
-        __syncwarp();
-        front_refresh<K>(bid, sm.pool[0]);
-        front_refresh<K>(ask, sm.pool[1]);
-    }
-    // extended kernel: the book is (re)loaded at the top of a step, from the
-    // env's block first and from a snapshot image after an episode reset, so
-    // that the load code appears once
+    // The book is loaded at the top of the first step, after its first
+    // message tile is requested (the two fetches overlap), and in episode
+    // mode again after a reset, from the snapshot image; live counts come
+    // with the state.
     const unsigned char *load_src = blk;
     int load_nb = nb0, load_na = na0;
-    bool need_load = XT;
+    bool need_load = true;
 
     const bool snap_env = TRACE && p.snaps != nullptr && e == 0;
     long long snap_n = 0;
@@ -1255,18 +1244,16 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             }
             pipe.tiles++;
         }
-        if constexpr (XT) {
-            if (need_load) {
-                __syncwarp();
-                side_load<K, true>(bid, sm.pool[0], load_src, lane);
-                side_load<K, false>(ask, sm.pool[1], load_src, lane);
-                side_set_count<K>(bid, load_nb, lane);
-                side_set_count<K>(ask, load_na, lane);
-                __syncwarp();
-                front_refresh<K>(bid, sm.pool[0]);
-                front_refresh<K>(ask, sm.pool[1]);
-                need_load = false;
-            }
+        if (need_load) {
+            __syncwarp();
+            side_load<K, true>(bid, sm.pool[0], load_src, lane);
+            side_load<K, false>(ask, sm.pool[1], load_src, lane);
+            side_set_count<K>(bid, load_nb, lane);
+            side_set_count<K>(ask, load_na, lane);
+            __syncwarp();
+            front_refresh<K>(bid, sm.pool[0]);
+            front_refresh<K>(ask, sm.pool[1]);
+            need_load = false;
         }
         c.msg_idx = 0;
         c.fill_n = 0;
