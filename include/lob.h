@@ -282,7 +282,8 @@ typedef struct lob_policy lob_policy;
  * W2 [128][128], b2 [128], W3 [13][128], b3 [13], in that order (row-major,
  * W[out][in]).  0 for an unsupported obs_dim (1..128). */
 int64_t lob_policy_param_count(int32_t obs_dim);
-/* Upload n_agents (1 or 2) consecutive parameter blocks from the host; the
+/* Upload n_agents (1 .. 2 * LOB_MAX_PER_TYPE; every agent its own weights,
+ * Sec. 4.2) consecutive parameter blocks from the host; the
  * library keeps an FP32 copy and a BF16 copy packed for the tensor cores. */
 int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float *h_params, lob_policy **out);
 int lob_policy_destroy(lob_policy *pol);   /* synchronises the device */
@@ -299,9 +300,11 @@ int lob_policy_sync(lob_policy *pol, void *stream);
  * (after lob_reset: the reset observation) and lob_step runs with those
  * actions, all enqueued on `stream` with no host synchronisation, so the
  * sequence can be captured in a CUDA graph.  Per-step outputs (any may be
- * NULL): d_obs [n_steps][n_envs][2][obs_dim] (observation after step i),
- * d_rewards [n_steps][n_envs][2], d_done [n_steps][n_envs], d_actions
- * [n_steps][n_envs][2] (the actions taken at step i). */
+ * NULL): d_obs [n_steps][n_envs][n_agents][obs_dim] (observation after step
+ * i), d_rewards [n_steps][n_envs][n_agents], d_done [n_steps][n_envs],
+ * d_actions [n_steps][n_envs][n_agents] (the actions taken at step i).  The
+ * policy has one network per agent of the handle; the market makers use the
+ * 12-way head. */
 int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
                        int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream);
 

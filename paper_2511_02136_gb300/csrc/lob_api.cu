@@ -1235,18 +1235,18 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
 extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
                                   int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream) {
     if (!h || !pol || n_steps < 1) return LOB_EINVAL;
-    if (h->cfg.n_agents != 2 || h->cfg.action_mode != LOB_ACT_HOST || h->cfg.mm_space != LOB_MM_SPREAD_SKEW)
+    if (h->cfg.n_agents < 2 || h->cfg.action_mode != LOB_ACT_HOST || h->cfg.mm_space != LOB_MM_SPREAD_SKEW)
         return LOB_EINVAL;
-    if (policy_n_agents(pol) != 2 || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
+    if (policy_n_agents(pol) != h->cfg.n_agents || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
     if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
     if (!steps_left(h, n_steps)) return LOB_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D;
+    const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D, A = (size_t)h->cfg.n_agents;
     for (int i = 0; i < n_steps; i++) {
         // the policy acts on the current observation (kept in the handle's buffer)
         int rc = policy_forward_internal(pol, h->d_obs, h->cfg.n_envs, precision, nullptr, nullptr, h->d_act, s);
         if (rc != LOB_OK) return rc;
-        if (d_actions && cudaMemcpyAsync(d_actions + (size_t)i * n * 2, h->d_act, n * 2 * 4,
+        if (d_actions && cudaMemcpyAsync(d_actions + (size_t)i * n * A, h->d_act, n * A * 4,
                                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return LOB_ECUDA;
         rc = launch_steps(h, h->msgs, step_offsets(h), h->stride, h->cursor, 1, h->d_act, 0, h->d_obs, h->d_rew,
@@ -1254,10 +1254,10 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
         if (rc != LOB_OK) return rc;
         h->cursor++;
         h->t++;
-        if (d_obs && cudaMemcpyAsync(d_obs + (size_t)i * n * 2 * D, h->d_obs, n * 2 * D * 4,
+        if (d_obs && cudaMemcpyAsync(d_obs + (size_t)i * n * A * D, h->d_obs, n * A * D * 4,
                                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return LOB_ECUDA;
-        if (d_rewards && cudaMemcpyAsync(d_rewards + (size_t)i * n * 2, h->d_rew, n * 2 * 8,
+        if (d_rewards && cudaMemcpyAsync(d_rewards + (size_t)i * n * A, h->d_rew, n * A * 8,
                                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return LOB_ECUDA;
         if (d_done && cudaMemcpyAsync(d_done + (size_t)i * n, h->d_done, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

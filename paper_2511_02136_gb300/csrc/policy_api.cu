@@ -40,7 +40,8 @@ extern "C" int64_t lob_policy_param_count(int32_t obs_dim) {
 extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float *h_params, lob_policy **out) {
     if (!out) return LOB_EINVAL;
     *out = nullptr;
-    if (n_agents < 1 || n_agents > 2 || !h_params || obs_dim < 5 || (obs_dim - 5) % 4 != 0) return LOB_EINVAL;
+    if (n_agents < 1 || n_agents > 2 * LOB_MAX_PER_TYPE || !h_params || obs_dim < 5 || (obs_dim - 5) % 4 != 0)
+        return LOB_EINVAL;
     if (obs_dim > DMAX) return LOB_ECAPACITY;
     // opt both forward kernels into their shared memory (per device, at creation)
     if (cudaFuncSetAttribute(k_policy_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Bf16Smem)) !=

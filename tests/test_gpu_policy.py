@@ -56,17 +56,17 @@ def test_forward_vs_fp64(prec, tol):
     lob.lob_policy_destroy(pol)
 
 
-def _policy_rollout(n, T, cap, prec, graph=False, seed=3):
+def _policy_rollout(n, T, cap, prec, graph=False, seed=3, A=2):
     import torch
     st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(seed, n), T)
-    pr = Pair(n, st, cap=cap, exec_target=512, action_mode=lob.LOB_ACT_HOST, n_threads=16)
-    params = lob.init_policy_params(5, 2, pr.env.D)
-    pol = lob.lob_policy_create(2, pr.env.D, params)
+    pr = Pair(n, st, n_agents=A, cap=cap, exec_target=512, action_mode=lob.LOB_ACT_HOST, n_threads=16)
+    params = lob.init_policy_params(5, A, pr.env.D)
+    pol = lob.lob_policy_create(A, pr.env.D, params)
     D = pr.env.D
-    obs = torch.zeros((T, n, 2, D), dtype=torch.float32, device="cuda")
-    rew = torch.zeros((T, n, 2), dtype=torch.int64, device="cuda")
+    obs = torch.zeros((T, n, A, D), dtype=torch.float32, device="cuda")
+    rew = torch.zeros((T, n, A), dtype=torch.int64, device="cuda")
     done = torch.zeros((T, n), dtype=torch.uint8, device="cuda")
-    acts = torch.zeros((T, n, 2), dtype=torch.int32, device="cuda")
+    acts = torch.zeros((T, n, A), dtype=torch.int32, device="cuda")
     if graph:
         s = torch.cuda.Stream()
         torch.cuda.synchronize()
@@ -101,6 +101,12 @@ def test_policy_rollout_replayed_into_oracle(prec):
     agree = _policy_rollout(300, 12, 100, prec)
     print(f"greedy agreement with FP64 along the rollout: {agree:.5f}")
     assert agree >= (AGREE_BF16 if prec == lob.LOB_PREC_BF16 else 0.999)
+
+
+def test_policy_rollout_ten_agents_per_type():
+    """20 agents (10 per type, Table 1), each with its own network, BF16 in the loop."""
+    agree = _policy_rollout(150, 8, 100, lob.LOB_PREC_BF16, A=20, seed=7)
+    assert agree >= AGREE_BF16
 
 
 def test_policy_rollout_under_cuda_graph():
