@@ -44,7 +44,7 @@ class OrcConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_envs", "n_agents", "cap", "top_levels", "episode_len", "mm_lot", "exec_target",
         "exec_dir", "action_mode", "trace", "start_px", "n_threads", "reward_mode",
-        "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli", "mm_space")]
+        "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli", "mm_space", "pv_ref")]
 
 
 def build(force: bool = False) -> str:
@@ -120,11 +120,11 @@ class Oracle:
     def __init__(self, n_envs, n_agents=2, cap=100, top_levels=10, episode_len=1000,
                  mm_lot=1, exec_target=500, exec_dir=-1, action_mode=1, trace=0,
                  start_px=10_000, n_threads=1, caps=None, reward_mode=0, spooner_lambda_pct=0,
-                 inv_penalty=0, exec_penalty_milli=0, mm_space=0):
+                 inv_penalty=0, exec_penalty_milli=0, mm_space=0, pv_ref=0):
         self.lib = _load()
         self.cfg = OrcConfig(n_envs, n_agents, cap, top_levels, episode_len, mm_lot,
                              exec_target, exec_dir, action_mode, trace, start_px, n_threads,
-                             reward_mode, spooner_lambda_pct, inv_penalty, exec_penalty_milli, mm_space)
+                             reward_mode, spooner_lambda_pct, inv_penalty, exec_penalty_milli, mm_space, pv_ref)
         self.caps = None if caps is None else np.ascontiguousarray(caps, dtype=np.int32)
         self.h = self.lib.orc_create(ctypes.byref(self.cfg), _ptr(self.caps))
         if not self.h:

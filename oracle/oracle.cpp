@@ -540,9 +540,11 @@ struct Engine {
             write_obs(E, (float)(c.episode_len - (te + 1)) / (float)c.episode_len);
             for (int a = 0; a < A; a++) {
                 Agent &g = E.ag[a];
-                // PV = Q_inv * P_ref + Cash (Eq. 1), P_ref the liquidation touch
+                // PV = Q_inv * P_ref + Cash (Eq. 1), P_ref the liquidation touch,
+                // or the mid price with PV counted in half ticks (2 PV exact)
                 int64_t pref = g.inv > 0 ? bb : g.inv < 0 ? ba : 0;
-                int64_t pv = wadd(wmul(g.inv, pref), g.cash);
+                int64_t pv = c.pv_ref == 1 ? wadd(wmul(g.inv, bb + ba), wmul(2, g.cash))
+                                           : wadd(wmul(g.inv, pref), g.cash);
                 E.rew[a] = wsub(pv, g.pv_prev);
                 g.pv_prev = pv;
                 const bool mm = a >= A / 2;
@@ -570,7 +572,9 @@ struct Engine {
                 if (!mm && c.exec_penalty_milli != 0 && last) {
                     // Table 2: penalty on the part of the task still unfilled at the end
                     const int64_t unfilled = std::max<int64_t>(0, (int64_t)c.exec_target - g.exec_done);
-                    E.rew[a] = wsub(E.rew[a], (wmul(c.exec_penalty_milli, unfilled) + 999) / 1000);  // rounded up
+                    // rounded up; in half ticks with the mid reference
+                    const int64_t milli = wmul(c.exec_penalty_milli, unfilled) * (c.pv_ref == 1 ? 2 : 1);
+                    E.rew[a] = wsub(E.rew[a], (milli + 999) / 1000);
                 }
             }
         }

@@ -49,6 +49,8 @@ typedef struct orc_config {
                              its exact value */
     int32_t mm_space;     /* market maker's action space (Sec. 4.1): 0 the 12-way spread/skew
                              head, 1 Fixed Quantity (8 options), 2 directional trading (3) */
+    int32_t pv_ref;       /* reference price of Eq. 1 (Table 2): 0 the touch one would liquidate
+                             at (best price), 1 the mid price, PV then in half ticks */
 } orc_config;
 
 void   *orc_create(const orc_config *cfg, const int32_t *caps /* [n_envs] or NULL */);

@@ -50,13 +50,15 @@ def wrap(v):
 class BruteEnv:
     def __init__(self, cap, n_agents=0, top_levels=2, episode_len=10, mm_lot=1,
                  exec_target=10, exec_dir=SELL, start_px=10_000, seed=0, action_mode=0,
-                 reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0, mm_space=0):
+                 reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0, mm_space=0,
+                 pv_ref=0):
         self.cap, self.A, self.L, self.T = cap, n_agents, top_levels, episode_len
         self.mm_lot, self.exec_target, self.exec_dir = mm_lot, exec_target, exec_dir
         self.action_mode, self.seed = action_mode, seed
         self.reward_mode, self.lam_pct = reward_mode, spooner_lambda_pct
         self.inv_penalty, self.exec_penalty_milli = inv_penalty, exec_penalty_milli
         self.mm_space = mm_space
+        self.pv_ref = pv_ref     # 0 liquidation touch, 1 mid (PV in half ticks)
         self.orders = {BUY: [], SELL: []}   # dicts: px, qty, id, ts
         self.ts_next = 0
         self.seq_next = 0
@@ -301,6 +303,8 @@ class BruteEnv:
             for a in range(self.A):
                 pref = bb if self.inv[a] > 0 else ba if self.inv[a] < 0 else 0
                 pv = wrap(self.inv[a] * pref + self.cash[a])
+                if self.pv_ref == 1:   # mid reference, in half ticks: twice the exact PV
+                    pv = wrap(int(2 * (self.inv[a] * Fraction(bb + ba, 2) + self.cash[a])))
                 self.rew[a] = wrap(pv - self.pv_prev[a])
                 self.pv_prev[a] = pv
                 if a >= self.P and self.reward_mode:
@@ -309,7 +313,8 @@ class BruteEnv:
                     self.rew[a] -= self.inv_penalty * self.inv[a] ** 2
                 if a < self.P and te + 1 == self.T:
                     unfilled = max(0, self.exec_target - self.exec_done[a])
-                    self.rew[a] = self.rew[a] - self.exec_penalty_milli * unfilled / Fraction(1000)
+                    unit = 2 if self.pv_ref == 1 else 1
+                    self.rew[a] = self.rew[a] - unit * self.exec_penalty_milli * unfilled / Fraction(1000)
                     self.rew[a] = self.rew[a].numerator // self.rew[a].denominator
         self.done = int(te + 1 == self.T)
         self.t += 1

@@ -36,7 +36,7 @@ def test_oracle_matches_brute_reward_variants(seed):
     rng = np.random.default_rng(500 + seed)
     rw = dict(reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=int(rng.integers(0, 101)),
               inv_penalty=int(rng.integers(0, 3)), exec_penalty_milli=int(rng.choice([0, 10, 50, 100, 2500])),
-              mm_space=int(rng.integers(0, 3)))
+              mm_space=int(rng.integers(0, 3)), pv_ref=int(rng.integers(0, 2)))
     _run_against_brute(100 + seed, rw)
 
 
