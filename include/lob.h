@@ -148,8 +148,16 @@ typedef struct lob_config {
      * actions outside it give LOB_EINVAL.  lob_rollout_policy (12 logits)
      * needs LOB_MM_SPREAD_SKEW. */
     int32_t mm_space;
-    int32_t reserved[3];         /* must be zero */
+    /* Reference price P_ref of Eq. 1 (Table 2's value reference price):
+     *   LOB_PV_TOUCH  the touch one would liquidate at (best bid if long, best ask if short)
+     *   LOB_PV_MID    the mid price; PV is then exact in half ticks and the Eq. 1 rewards
+     *                 and the unfilled-task penalty are reported in half ticks x qty */
+    int32_t pv_ref;
+    int32_t reserved[2];         /* must be zero */
 } lob_config;
+
+#define LOB_PV_TOUCH 0
+#define LOB_PV_MID   1
 
 #define LOB_MM_SPREAD_SKEW 0
 #define LOB_MM_FIXED_QUANT 1

@@ -45,6 +45,7 @@ static void set_rewards(KParams &p, const lob_config &c) {
     p.inv_penalty = c.inv_penalty;
     p.exec_pen_milli = c.exec_penalty_milli;
     p.mm_space = c.mm_space;
+    p.pv_ref = c.pv_ref;
 }
 
 size_t warp_smem_bytes(int K) {
@@ -147,7 +148,7 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     // action space is on
     const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
                      p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0 ||
-                     p.msg16 != 0;
+                     p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH;
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     switch (K) {
@@ -305,9 +306,10 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
         return LOB_EINVAL;
     if (c.reward_mode < LOB_REWARD_PV || c.reward_mode > LOB_REWARD_SPOONER || c.spooner_lambda_pct < 0 ||
         c.spooner_lambda_pct > 100 || c.inv_penalty < 0 || c.exec_penalty_milli < 0 ||
-        c.mm_space < LOB_MM_SPREAD_SKEW || c.mm_space > LOB_MM_DIRECTIONAL)
+        c.mm_space < LOB_MM_SPREAD_SKEW || c.mm_space > LOB_MM_DIRECTIONAL || c.pv_ref < LOB_PV_TOUCH ||
+        c.pv_ref > LOB_PV_MID)
         return LOB_EINVAL;
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 2; i++)
         if (c.reserved[i] != 0) return LOB_EINVAL;
     std::vector<int> caps((size_t)c.n_envs);
     for (int e = 0; e < c.n_envs; e++) {

@@ -108,6 +108,7 @@ struct KParams {
     long long inv_penalty;           // rho of the quadratic inventory penalty
     long long exec_pen_milli;        // unfilled-task penalty, thousandths of a tick per unit
     int mm_space;                    // market maker's action space (Sec. 4.1.1)
+    int pv_ref;                      // P_ref of Eq. 1: liquidation touch, or mid (PV in half ticks)
     // episode mode (one shared stream; offsets index data steps): start table,
     // prebuilt book images (ep_block bytes each) and first observations
     int ep_mode;
@@ -1616,13 +1617,15 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 for (int a = lane; a < A; a += 32) {
                     typedef unsigned long long u64;
                     const long long iv = ag.inv[a], cs = ag.cash[a];
-                    const long long pref = iv > 0 ? bb : (iv < 0 ? ba : 0);
-                    const long long pv = (long long)((u64)iv * (u64)pref + (u64)cs);
+                    const bool pvm = p.pv_ref == LOB_PV_MID;   // 2 PV in half ticks
+                    const long long pref = pvm ? s2 : (iv > 0 ? bb : (iv < 0 ? ba : 0));
+                    const long long pv = (long long)((u64)iv * (u64)pref + (u64)cs * (pvm ? 2ull : 1ull));
                     long long r = (long long)((u64)pv - (u64)ag.pv[a]);
                     ag.pv[a] = pv;
                     if (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0) {
-                        const longlong2 rr = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
-                                                             te + 1 == p.T, (long long)p.exec_target - ag.done[a],
+                        const longlong2 rr = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty,
+                                                             p.exec_pen_milli * (pvm ? 2 : 1), te + 1 == p.T,
+                                                             (long long)p.exec_target - ag.done[a],
                                                              sm.rw[0], s2, ag.inv0[a], ag.cash0[a], iv, cs, r, r);
                         r = a < P ? rr.x : rr.y;
                     }
@@ -1633,8 +1636,12 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             // Eq. 1: PV = Q_inv * P_ref + Cash, P_ref the liquidation touch
             const long long pref0 = c.inv0 > 0 ? bb : (c.inv0 < 0 ? ba : 0);
             const long long pref1 = c.inv1 > 0 ? bb : (c.inv1 < 0 ? ba : 0);
-            const long long pv0 = (long long)((unsigned long long)c.inv0 * (unsigned long long)pref0 + (unsigned long long)c.cash0);
-            const long long pv1 = (long long)((unsigned long long)c.inv1 * (unsigned long long)pref1 + (unsigned long long)c.cash1);
+            // with the mid reference, 2 PV = Q_inv (bb + ba) + 2 Cash, exact in half ticks
+            const bool pvm = XT && p.pv_ref == LOB_PV_MID;
+            const long long pv0 = (long long)((unsigned long long)c.inv0 * (unsigned long long)(pvm ? s2 : pref0) +
+                                              (unsigned long long)c.cash0 * (pvm ? 2ull : 1ull));
+            const long long pv1 = (long long)((unsigned long long)c.inv1 * (unsigned long long)(pvm ? s2 : pref1) +
+                                              (unsigned long long)c.cash1 * (pvm ? 2ull : 1ull));
             long long r0 = (long long)((unsigned long long)pv0 - (unsigned long long)c.pv0);
             long long r1 = (long long)((unsigned long long)pv1 - (unsigned long long)c.pv1);
             c.pv0 = pv0; c.pv1 = pv1;
@@ -1672,8 +1679,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             }
             if (lane == 0) {
                 if (XT && (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0)) {
-                    const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty, p.exec_pen_milli,
-                                                        te + 1 == p.T, (long long)p.exec_target - c.exec_done,
+                    const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty,
+                                                        p.exec_pen_milli * (pvm ? 2 : 1), te + 1 == p.T,
+                                                        (long long)p.exec_target - c.exec_done,
                                                         sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
                     r0 = r.x; r1 = r.y;
                 }

@@ -53,6 +53,7 @@ EXPORTS = [
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
 LOB_MM_SPREAD_SKEW, LOB_MM_FIXED_QUANT, LOB_MM_DIRECTIONAL = 0, 1, 2
+LOB_PV_TOUCH, LOB_PV_MID = 0, 1
 LOB_INIT_ID = 0x4000000000000000
 START_DTYPE = np.dtype([("data_step", "<i4"), ("last_px", "<i4"), ("n_bid", "<i4"), ("n_ask", "<i4")])
 MSG16_DTYPE = np.dtype([("px", "<i4"), ("qty", "<i4"), ("word", "<i8")])
@@ -73,8 +74,8 @@ class lob_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_envs", "n_agents", "cap_per_side", "top_levels", "episode_len", "mm_lot",
         "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block",
-        "reward_mode", "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli", "mm_space")] + \
-        [("reserved", ctypes.c_int32 * 3)]
+        "reward_mode", "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli", "mm_space", "pv_ref")] + \
+        [("reserved", ctypes.c_int32 * 2)]
 
 
 class lob_noalloc_args(ctypes.Structure):
@@ -435,12 +436,12 @@ class LobEnv:
     def __init__(self, n_envs, n_agents=2, cap=100, top_levels=10, episode_len=1000, mm_lot=1,
                  exec_target=500, exec_dir=-1, action_mode=LOB_ACT_RANDOM, start_px=10_000,
                  warps_per_block=0, caps=None, reward_mode=0, spooner_lambda_pct=0, inv_penalty=0,
-                 exec_penalty_milli=0, mm_space=0):
+                 exec_penalty_milli=0, mm_space=0, pv_ref=0):
         import torch
         self.torch = torch
         self.cfg = lob_config(n_envs, n_agents, cap, top_levels, episode_len, mm_lot, exec_target,
                               exec_dir, action_mode, 0, start_px, warps_per_block, reward_mode,
-                              spooner_lambda_pct, inv_penalty, exec_penalty_milli, mm_space)
+                              spooner_lambda_pct, inv_penalty, exec_penalty_milli, mm_space, pv_ref)
         self.caps = caps
         self.h = lob_create(self.cfg, caps)
         self.n_envs, self.n_agents = n_envs, n_agents

@@ -56,7 +56,7 @@ def test_agents_per_type_host_actions_variants():
     pr = Pair(n, st, n_agents=2 * P, cap=100, exec_target=50, exec_dir=1, mm_lot=2,
               action_mode=lob.LOB_ACT_HOST, mm_space=lob.LOB_MM_FIXED_QUANT,
               rewards=dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=25, inv_penalty=2,
-                           exec_penalty_milli=300))
+                           exec_penalty_milli=300, pv_ref=lob.LOB_PV_MID))
     for _ in range(T):
         acts = np.concatenate([rng.integers(0, 12, (n, P)), rng.integers(0, 8, (n, P))], axis=1).astype(np.int32)
         pr.step(acts)

@@ -252,7 +252,8 @@ def test_create_rejects_bad_configs():
                              ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 0, lob.LOB_EINVAL),
                              ("action_mode", 7, lob.LOB_EINVAL), ("reward_mode", 3, lob.LOB_EINVAL),
                              ("spooner_lambda_pct", 101, lob.LOB_EINVAL), ("inv_penalty", -1, lob.LOB_EINVAL),
-                             ("exec_penalty_milli", -5, lob.LOB_EINVAL), ("mm_space", 3, lob.LOB_EINVAL)):
+                             ("exec_penalty_milli", -5, lob.LOB_EINVAL), ("mm_space", 3, lob.LOB_EINVAL),
+                             ("pv_ref", 2, lob.LOB_EINVAL)):
         c = lob.lob_config(4, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
         setattr(c, field, val)
         with pytest.raises(lob.LobError) as ei:
@@ -265,6 +266,7 @@ REWARD_CASES = [
     dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=50),
     dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=33, inv_penalty=50, exec_penalty_milli=100),
     dict(reward_mode=lob.LOB_REWARD_PV, inv_penalty=2, exec_penalty_milli=2500),
+    dict(reward_mode=lob.LOB_REWARD_PV, pv_ref=lob.LOB_PV_MID, exec_penalty_milli=100),
 ]
 
 
