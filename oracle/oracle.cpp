@@ -146,6 +146,7 @@ uint32_t lemire(uint64_t x, uint32_t n) {
 const uint64_t TAG_SHUFFLE = 0x5348554646000001ULL;
 const uint64_t TAG_POLICY = 0x504F4C4943590002ULL;
 const uint64_t TAG_EPISODE = 0x4550495344450003ULL;
+const uint64_t TAG_TASKDIR = 0x5441534B44495204ULL;
 const int64_t INIT_ID = 0x4000000000000000LL;   // ids of a snapshot's resting orders
 
 // Number of market-maker actions of each action space (Sec. 4.1.1).
@@ -175,6 +176,7 @@ struct Env {
     bool bad = false;
     int32_t msg_idx = 0;                // processing index within the current step
     int64_t ep_start = 0;               // episode mode: first data step of the current episode
+    int exec_dir = SELL;                // the execution task's side in this episode
     std::vector<unsigned char> *snaps = nullptr;  // env 0 book after every message
 };
 
@@ -248,7 +250,7 @@ struct Engine {
         if (seller != A) { E.ag[seller].sell_q += f; E.ag[seller].sell_n = wadd(E.ag[seller].sell_n, notional); }
         if (A > 0) {
             // the side of the execution task: its owner, if an execution agent, progresses
-            int task_owner = cfg.c.exec_dir == SELL ? seller : buyer;
+            int task_owner = E.exec_dir == SELL ? seller : buyer;
             if (task_owner < A / 2) E.ag[task_owner].exec_done += f;
         }
         E.last_px = maker.px;
@@ -355,6 +357,13 @@ struct Engine {
         E.msg_idx++;
     }
 
+    // The execution task's side in episode k (Table 2: uniformly sampled when
+    // exec_dir is 0): the top bit of a keyed SplitMix64 draw, set -> sell.
+    int task_dir(const Env &E, int64_t k) const {
+        if (cfg.c.exec_dir != 0) return cfg.c.exec_dir;
+        return (draw(E.seed, k, TAG_TASKDIR, 0) >> 63) ? SELL : BUY;
+    }
+
     // Start episode k of env E from its drawn snapshot (episode mode).
     void begin_episode(Env &E, int64_t k) {
         const uint32_t j = lemire(draw(E.seed, k, TAG_EPISODE, 0), (uint32_t)ep_starts.size());
@@ -366,6 +375,7 @@ struct Engine {
         for (Agent &g : E.ag) g = Agent();
         E.last_px = st.last_px;
         E.ep_start = st.data_step;
+        E.exec_dir = task_dir(E, k);
         int64_t idx = 0;
         for (int s = 0; s < 2; s++) {
             Side &side = s == 0 ? E.bids : E.asks;
@@ -404,7 +414,9 @@ struct Engine {
             ob[4 * L + 0] = (float)g.inv;
             ob[4 * L + 1] = (float)g.cash;
             ob[4 * L + 2] = tl;
-            ob[4 * L + 3] = a < A / 2 ? (float)((int64_t)c.exec_target - g.exec_done) : 0.0f;
+            // remaining target; signed by the task's side (+ buy, - sell) when the side is drawn
+            const int64_t rem = (int64_t)c.exec_target - g.exec_done;
+            ob[4 * L + 3] = a < A / 2 ? (float)(c.exec_dir == 0 && E.exec_dir == SELL ? -rem : rem) : 0.0f;
             ob[4 * L + 4] = (float)own_rest[a];
         }
     }
@@ -443,14 +455,14 @@ struct Engine {
                 int64_t q0 = std::max<int64_t>(1, ((int64_t)c.exec_target + c.episode_len - 1) / c.episode_len);
                 int64_t qty = std::min(mult * q0, remaining);
                 int64_t px;
-                if (c.exec_dir == SELL) {
+                if (E.exec_dir == SELL) {
                     const int64_t p4[4] = {bb, ceil_half(bb + ba), ba, ba + 2};
                     px = p4[pi];
                 } else {
                     const int64_t p4[4] = {ba, floor_half(bb + ba), bb, bb - 2};
                     px = p4[pi];
                 }
-                want.push_back({ag, c.exec_dir, (int32_t)px, (int32_t)qty});
+                want.push_back({ag, E.exec_dir, (int32_t)px, (int32_t)qty});
             }
             // market makers (Sec. 4.1.1): quotes of mm_lot around the touch
             for (int ag = P; ag < A; ag++) {
@@ -626,6 +638,7 @@ void orc_reset(void *h, const uint64_t *env_seeds) {
         E.asks.is_bid = false;
         E.seed = env_seeds[e];
         E.last_px = g->cfg.c.start_px;
+        E.exec_dir = g->task_dir(E, 0);
         E.ag.assign((size_t)g->cfg.c.n_agents, Agent());
         E.rew.assign((size_t)g->cfg.c.n_agents, 0);
         E.act.assign((size_t)g->cfg.c.n_agents, 0);

@@ -35,7 +35,7 @@ typedef struct orc_config {
     int32_t episode_len;  /* T */
     int32_t mm_lot;
     int32_t exec_target;
-    int32_t exec_dir;     /* -1 sell task, +1 buy task */
+    int32_t exec_dir;     /* -1 sell task, +1 buy task, 0 drawn per env and episode (Table 2) */
     int32_t action_mode;  /* 0: actions given per step, 1: seeded uniform random policy */
     int32_t trace;        /* bit0: keep the step's fill log; bit1: book snapshot of env 0 after every message */
     int32_t start_px;     /* reference price before the first trade */

@@ -16,6 +16,7 @@ GAMMA = 0x9E3779B97F4A7C15
 TAG_SHUFFLE = 0x5348554646000001
 TAG_POLICY = 0x504F4C4943590002
 TAG_EPISODE = 0x4550495344450003
+TAG_TASKDIR = 0x5441534B44495204
 INIT_ID = 1 << 62
 
 
@@ -53,8 +54,10 @@ class BruteEnv:
                  reward_mode=0, spooner_lambda_pct=0, inv_penalty=0, exec_penalty_milli=0, mm_space=0,
                  pv_ref=0):
         self.cap, self.A, self.L, self.T = cap, n_agents, top_levels, episode_len
-        self.mm_lot, self.exec_target, self.exec_dir = mm_lot, exec_target, exec_dir
+        self.mm_lot, self.exec_target = mm_lot, exec_target
+        self.exec_dir_cfg = exec_dir              # 0: the side is drawn per episode
         self.action_mode, self.seed = action_mode, seed
+        self.exec_dir = self._task_dir(0)
         self.reward_mode, self.lam_pct = reward_mode, spooner_lambda_pct
         self.inv_penalty, self.exec_penalty_milli = inv_penalty, exec_penalty_milli
         self.mm_space = mm_space
@@ -80,10 +83,16 @@ class BruteEnv:
         for a in range(n_agents):
             self.obs[a][4 * top_levels + 2] = 1.0
             if a < n_agents // 2:
-                self.obs[a][4 * top_levels + 3] = float(exec_target)
+                signed = exec_dir == 0 and self.exec_dir == SELL
+                self.obs[a][4 * top_levels + 3] = float(-exec_target if signed else exec_target)
         self.rew = [0] * n_agents
         self.done = 0
         self.acts = [0] * n_agents
+
+    def _task_dir(self, k):
+        if self.exec_dir_cfg != 0:
+            return self.exec_dir_cfg
+        return SELL if keyed_draws(self.seed, k, TAG_TASKDIR, 1)[0] >> 63 else BUY
 
     # -- episodes over one shared stream ----------------------------------------
     def set_episodes(self, msgs, step_offsets, starts, levels):
@@ -102,6 +111,7 @@ class BruteEnv:
         self.exec_done = [0] * self.A
         self.last_px = int(st["last_px"])
         self.ep_start = int(st["data_step"])
+        self.exec_dir = self._task_dir(k)
         idx = 0
         for s, side in enumerate((BUY, SELL)):
             for i in range(int(st["n_bid"] if s == 0 else st["n_ask"])):
@@ -347,7 +357,10 @@ class BruteEnv:
             ob[4 * self.L] = float(self.inv[a])
             ob[4 * self.L + 1] = float(self.cash[a])
             ob[4 * self.L + 2] = time_left
-            ob[4 * self.L + 3] = float(self.exec_target - self.exec_done[a]) if a < self.P else 0.0
+            rem = self.exec_target - self.exec_done[a]
+            if self.exec_dir_cfg == 0 and self.exec_dir == SELL:
+                rem = -rem
+            ob[4 * self.L + 3] = float(rem) if a < self.P else 0.0
             ob[4 * self.L + 4] = float(rest[a])
 
     def _mm_reward(self, a, mid_before, mid_after):

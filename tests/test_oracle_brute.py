@@ -30,6 +30,13 @@ def test_oracle_matches_brute(seed):
     _run_against_brute(seed, {})
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_oracle_matches_brute_drawn_task_side(seed):
+    """Table 2's uniformly sampled task side (exec_dir 0): per env at reset,
+    signed remaining-target observation, both action modes."""
+    _run_against_brute(1200 + seed, {"exec_dir": 0})
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_oracle_matches_brute_reward_variants(seed):
     """Eqs. 3-4 and the Table 2 penalties, against exact fractions in the brute env."""
@@ -53,7 +60,8 @@ def _run_against_brute(seed, rw):
     host = seed % 2 == 0
     kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)),
               exec_target=int(rng.integers(5, 60)), exec_dir=int(rng.choice([-1, 1])),
-              start_px=10_000, **rw)
+              start_px=10_000)
+    kw.update(rw)
     o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
     o.reset(seeds)
     o.load_messages(st.msgs, st.offsets)
@@ -112,6 +120,8 @@ def test_oracle_matches_brute_episodes(seed):
               exec_target=int(rng.integers(5, 40)), exec_dir=int(rng.choice([-1, 1])), start_px=10_000,
               reward_mode=int(rng.integers(0, 3)), spooner_lambda_pct=30, inv_penalty=int(rng.integers(0, 2)),
               exec_penalty_milli=int(rng.choice([0, 100])), mm_space=seed % 3)
+    if seed % 2:
+        kw["exec_dir"] = 0      # the task side drawn per episode
     seeds = mbogen.env_seeds(3000 + seed, n_env)
     o = oracle.Oracle(n_env, n_agents=2, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
     o.set_episodes(st.msgs, st.offsets[0], starts, levels)

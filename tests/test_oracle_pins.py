@@ -541,3 +541,19 @@ def test_episodes_counters_accumulate_and_books_restart():
         assert _book_rows(o) == first
         assert o.counters()[0][oracle.COUNTER_NAMES.index("msgs")] >= (ep + 1) * msgs_per_episode
         assert o.agents()[0].tolist() == [[0, 0, 0, 0], [0, 0, 0, 0]]
+
+
+def test_drawn_task_side_at_reset():
+    """exec_dir 0 (Table 2: task side uniformly sampled): each env's side is the
+    top bit of a keyed SplitMix64 draw (set -> sell), seen as the sign of the
+    remaining-target observation; both sides occur about equally often."""
+    import brute_lob
+    n, L = 400, 3
+    seeds = mbogen.env_seeds(11, n)
+    o = oracle.Oracle(n, n_agents=2, cap=8, top_levels=L, episode_len=5, exec_target=50, exec_dir=0)
+    o.reset(seeds)
+    rem = o.observe()[0][:, 0, 4 * L + 3]
+    want = np.array([-50.0 if brute_lob.keyed_draws(int(s), 0, brute_lob.TAG_TASKDIR, 1)[0] >> 63 else 50.0
+                     for s in seeds], np.float32)
+    np.testing.assert_array_equal(rem, want)
+    assert 150 < int((want < 0).sum()) < 250
