@@ -116,7 +116,10 @@ typedef struct lob_config {
     int32_t episode_len;   /* T steps per episode, >= 1 */
     int32_t mm_lot;        /* market maker's quote size, >= 1 */
     int32_t exec_target;   /* execution task size, >= 0 */
-    int32_t exec_dir;      /* LOB_SELL or LOB_BUY: side of the execution task */
+    int32_t exec_dir;      /* LOB_SELL or LOB_BUY: side of the execution task; 0 = drawn per env and
+                              episode (Table 2: uniformly sampled) from the top bit of a SplitMix64
+                              draw keyed (seed, episode, LOB_TAG_TASKDIR), set -> sell; the
+                              remaining-target observation is then signed (+ buy, - sell) */
     int32_t action_mode;   /* LOB_ACT_HOST or LOB_ACT_RANDOM */
     int32_t trace;         /* bit0: fill log; bit1: env 0 book snapshot after every message */
     int32_t start_px;      /* reference price before the first trade (e.g. 10000) */
@@ -231,6 +234,7 @@ int lob_pack_messages16(const lob_msg *d_src, int64_t n, lob_msg16 *d_dst, int32
  * before the next step.  LOB_EINVAL on a table that breaks the rules above. */
 #define LOB_INIT_ID 0x4000000000000000LL
 #define LOB_TAG_EPISODE 0x4550495344450003ULL
+#define LOB_TAG_TASKDIR 0x5441534B44495204ULL
 typedef struct lob_start {
     int32_t data_step;
     int32_t last_px;

@@ -148,7 +148,7 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     // action space is on
     const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
                      p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0 ||
-                     p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH;
+                     p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH || p.exec_dir == 0;
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     switch (K) {
@@ -300,7 +300,7 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     if (c.n_envs < 1 || c.n_agents < 0 || c.n_agents % 2 != 0 || c.n_agents > 2 * LOB_MAX_PER_TYPE ||
         c.top_levels < 1 || c.top_levels > LMAX ||
         c.episode_len < 1 || c.mm_lot < 1 || c.exec_target < 0 ||
-        (c.exec_dir != LOB_SELL && c.exec_dir != LOB_BUY) ||
+        (c.exec_dir != LOB_SELL && c.exec_dir != LOB_BUY && c.exec_dir != 0) ||
         (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace < 0 || c.trace > 3 ||
         c.warps_per_block < 0 || c.warps_per_block > 8)
         return LOB_EINVAL;
@@ -443,18 +443,22 @@ int lob_load_messages16(lob_handle *h, const lob_msg16 *d_msgs, const int64_t *d
 // zero the state of every env
 __global__ void k_reset(EnvState *st, long long *cnt, unsigned long long *seeds_dst,
                         const unsigned long long *seeds_src, int n, int start_px, float *obs, int A, int D,
-                        int L, int exec_target) {
+                        int L, int exec_target, int exec_dir) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
+    // the task's side: configured, or drawn (then signed into the remaining target)
+    const int dir = exec_dir != 0 ? exec_dir : drawn_task_side(seeds_src[e], 0);
+    const long long rem = (exec_dir == 0 && dir == LOB_SELL) ? -(long long)exec_target : exec_target;
     for (int a = 0; a < A; a++) {
         float *o = obs + ((long long)e * A + a) * D;
         for (int f = 0; f < D; f++) o[f] = 0.0f;
         o[4 * L + 2] = 1.0f;                                   // time left T / T
-        if (a < (A >> 1)) o[4 * L + 3] = __ll2float_rn(exec_target);  // remaining target (execution agents)
+        if (a < (A >> 1)) o[4 * L + 3] = __ll2float_rn(rem);  // remaining target (execution agents)
     }
     EnvState z;
     memset(&z, 0, sizeof(z));
     z.last_px = start_px;
+    z.exec_dir = dir;
     st[e] = z;
     for (int i = 0; i < LOB_NCOUNTERS; i++) cnt[(long long)e * LOB_NCOUNTERS + i] = 0;
     seeds_dst[e] = seeds_src[e];
@@ -520,15 +524,21 @@ __global__ void k_ep_obs(const lob_start *starts, const int *levels, int ls, int
 __global__ void k_reset_ep(EnvState *st, long long *cnt, unsigned long long *seeds_dst,
                            const unsigned long long *seeds_src, int n, unsigned char *books,
                            const long long *book_off, const unsigned char *images, long long block,
-                           const lob_start *starts, int n_starts, const float *ep_obs, float *obs, int A, int D) {
+                           const lob_start *starts, int n_starts, const float *ep_obs, float *obs, int A, int D,
+                           int L, int exec_dir) {
     const int e = blockIdx.x;
     if (e >= n) return;
     const unsigned long long seed = seeds_src[e];
     const unsigned j = bounded(sm_mix(step_key(seed, 0, LOB_TAG_EPISODE) + GAMMA), (unsigned)n_starts);
+    const int dir = exec_dir != 0 ? exec_dir : drawn_task_side(seed, 0);
+    const bool flip = exec_dir == 0 && dir == LOB_SELL;   // a drawn sell task: negative remaining target
     const int4 *src = reinterpret_cast<const int4 *>(images + (long long)j * block);
     int4 *dst = reinterpret_cast<int4 *>(books + book_off[e]);
     for (long long i = threadIdx.x; i < block / 16; i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i < A * D; i += blockDim.x) obs[(long long)e * A * D + i] = ep_obs[(long long)j * A * D + i];
+    for (int i = threadIdx.x; i < A * D; i += blockDim.x) {
+        const float v = ep_obs[(long long)j * A * D + i];
+        obs[(long long)e * A * D + i] = (flip && i % D == 4 * L + 3 && i / D < (A >> 1)) ? -v : v;
+    }
     if (threadIdx.x < LOB_NCOUNTERS) cnt[(long long)e * LOB_NCOUNTERS + threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         const lob_start S = starts[j];
@@ -539,6 +549,7 @@ __global__ void k_reset_ep(EnvState *st, long long *cnt, unsigned long long *see
         z.n[0] = S.n_bid;
         z.n[1] = S.n_ask;
         z.ep_start = S.data_step;
+        z.exec_dir = dir;
         st[e] = z;
         seeds_dst[e] = seed;
     }
@@ -782,7 +793,8 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
         k_reset_ep<<<n, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                      reinterpret_cast<const unsigned long long *>(d_env_seeds), n, h->d_books,
                                      h->d_book_off, h->d_ep_images, h->uni_block, h->d_ep_starts, h->n_starts,
-                                     h->d_ep_obs, h->d_obs, h->cfg.n_agents, h->D);
+                                     h->d_ep_obs, h->d_obs, h->cfg.n_agents, h->D, h->cfg.top_levels,
+                                     h->cfg.exec_dir);
         h->launches++;
         if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
         if (h->d_agents &&
@@ -798,7 +810,7 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
     k_reset<<<(n + 127) / 128, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                              reinterpret_cast<const unsigned long long *>(d_env_seeds), n,
                                              h->cfg.start_px, h->d_obs, h->cfg.n_agents, h->D, h->cfg.top_levels,
-                                             h->cfg.exec_target);
+                                             h->cfg.exec_target, h->cfg.exec_dir);
     h->launches++;
     if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
     h->t = 0;

@@ -54,7 +54,8 @@ struct __align__(16) EnvState {
     int act[2];
     int t;
     int ep_start;          // episode mode: first data step of the current episode
-    int pad[7];
+    int exec_dir;          // the execution task's side in this episode (drawn when configured 0)
+    int pad[6];
 };
 static_assert(sizeof(EnvState) == 128, "env state");
 
@@ -186,8 +187,15 @@ __device__ __forceinline__ unsigned long long step_key(unsigned long long seed, 
                                                       unsigned long long tag) {
     return sm_mix(sm_mix(seed ^ tag) + GAMMA * (unsigned long long)(t + 1));
 }
+// The execution task's side of an env in episode k when it is drawn (Table 2:
+// uniformly sampled): the top bit of a keyed SplitMix64 draw, set -> sell.
+constexpr unsigned long long TAG_TASKDIR = 0x5441534B44495204ull;
+__device__ __forceinline__ int drawn_task_side(unsigned long long seed, long long k);
 __device__ __forceinline__ unsigned bounded(unsigned long long x, unsigned n) {
     return (unsigned)(((unsigned long long)(unsigned)(x >> 32) * n) >> 32);
+}
+__device__ __forceinline__ int drawn_task_side(unsigned long long seed, long long k) {
+    return (sm_mix(step_key(seed, k, TAG_TASKDIR) + GAMMA) >> 63) ? LOB_SELL : LOB_BUY;
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -1014,7 +1022,7 @@ __device__ __forceinline__ void agent_wants_ma(const KParams &p, int e, int t, i
                     const long long s2 = bb + ba;
                     const long long fl = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
                     const long long ce = s2 <= 0 ? -((-s2) / 2) : (s2 + 1) / 2;
-                    if (p.exec_dir == LOB_SELL) {
+                    if (c.exec_dir == LOB_SELL) {
                         apx = pi == 0 ? bb : pi == 1 ? ce : pi == 2 ? ba : ba + 2;
                         aq = (int)qty;
                     } else {
@@ -1193,7 +1201,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     c.exec_done = st->exec_done;
     c.last_px = st->last_px;
     const int nb0 = st->n[0], na0 = st->n[1];
-    c.A = A; c.exec_dir = p.exec_dir;
+    c.A = A;
+    c.exec_dir = (XT && p.exec_dir == 0) ? st->exec_dir : p.exec_dir;
     c.c_msgs = cnt[0]; c.c_agent = cnt[1]; c.c_fills = cnt[2]; c.c_fill_vol = cnt[3];
     c.c_add_vol = cnt[4]; c.c_mkt_vol = cnt[5]; c.c_mkt_disc = cnt[6]; c.c_cancel_vol = cnt[7];
     c.c_cancel_miss = cnt[8]; c.c_drop_vol = cnt[9]; c.c_drop_cnt = cnt[10]; c.c_evict_vol = cnt[11];
@@ -1319,9 +1328,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 const long long fl = s2 >= 0 ? s2 / 2 : -((-s2 + 1) / 2);
                 const long long ce = s2 <= 0 ? -((-s2) / 2) : (s2 + 1) / 2;
                 long long wpx;
-                if (p.exec_dir == LOB_SELL) wpx = pi == 0 ? bb : pi == 1 ? ce : pi == 2 ? ba : ba + 2;
+                if (c.exec_dir == LOB_SELL) wpx = pi == 0 ? bb : pi == 1 ? ce : pi == 2 ? ba : ba + 2;
                 else wpx = pi == 0 ? ba : pi == 1 ? fl : pi == 2 ? bb : bb - 2;
-                wa[0] = 0; ws[0] = p.exec_dir; wp[0] = (int)wpx; wq[0] = qty;
+                wa[0] = 0; ws[0] = c.exec_dir; wp[0] = (int)wpx; wq[0] = qty;
                 nw = 1;
             }
             if (!XT || p.mm_space == LOB_MM_SPREAD_SKEW) {
@@ -1565,6 +1574,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         const bool ep_end = ep_mode && te + 1 == p.T;
         const unsigned ep_j =
             ep_end ? bounded(sm_mix(step_key(seed, t / p.T + 1, LOB_TAG_EPISODE) + GAMMA), (unsigned)p.n_starts) : 0u;
+        // a drawn task side is signed into the remaining-target observation
+        // (+ buy, - sell); the next episode draws its own side
+        const bool side_drawn = XT && p.exec_dir == 0;
+        const int ep_dir = (ep_end && side_drawn) ? drawn_task_side(seed, t / p.T + 1) : c.exec_dir;
         __syncwarp();
         const long long obs_base = ((long long)step * p.n_envs + e);
         if (A > 0) {
@@ -1594,7 +1607,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 float *ob = p.obs ? p.obs + obs_base * A * D : nullptr;
                 if (ob && ep_end) {
                     const float *src = p.ep_obs + (long long)ep_j * A * D;
-                    for (int i = lane; i < A * D; i += 32) ob[i] = src[i];
+                    const bool flip = side_drawn && ep_dir == LOB_SELL;
+                    for (int i = lane; i < A * D; i += 32)
+                        ob[i] = (flip && i % D == 4 * L + 3 && i / D < P) ? -src[i] : src[i];
                 } else if (ob) {
                     for (int idx = lane; idx < 4 * L; idx += 32) {
                         const int sd = idx >= 2 * L ? 1 : 0;
@@ -1607,8 +1622,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                     }
                     for (int i = lane; i < 5 * A; i += 32) {
                         const int a = i / 5, g = i - 5 * a;
+                        const long long rem = a < P ? (long long)p.exec_target - ag.done[a] : 0;
                         const long long x = g == 0 ? ag.inv[a] : g == 1 ? ag.cash[a]
-                                          : g == 3 ? (a < P ? (long long)p.exec_target - ag.done[a] : 0) : ag.own[a];
+                                          : g == 3 ? ((side_drawn && c.exec_dir == LOB_SELL) ? -rem : rem) : ag.own[a];
                         ob[a * D + 4 * L + g] = g == 2 ? tl : __ll2float_rn(x);
                     }
                 }
@@ -1651,7 +1667,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             float *ob = p.obs ? p.obs + obs_base * A * D : nullptr;
             if (ob && ep_end) {
                 const float *src = p.ep_obs + (long long)ep_j * A * D;
-                for (int i = lane; i < A * D; i += 32) ob[i] = src[i];
+                const bool flip = side_drawn && ep_dir == LOB_SELL;
+                for (int i = lane; i < A * D; i += 32) ob[i] = (flip && i == 4 * L + 3) ? -src[i] : src[i];
             } else if (ob) {
                 // level entries: the same for both agents
                 for (int idx = lane; idx < 4 * L; idx += 32) {
@@ -1670,7 +1687,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                     const int g = lane - 5 * a;
                     const long long iv = a == 0 ? c.inv0 : c.inv1;
                     const long long cs = a == 0 ? c.cash0 : c.cash1;
-                    const long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    if (side_drawn && c.exec_dir == LOB_SELL) rem = -rem;
                     const long long own = a == 0 ? own0 : own1;
                     const long long x = g == 0 ? iv : g == 1 ? cs : g == 3 ? rem : own;
                     const float v = g == 2 ? tl : __ll2float_rn(x);
@@ -1707,6 +1725,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             c.seq_next = 0;
             c.inv0 = 0; c.inv1 = 0; c.cash0 = 0; c.cash1 = 0; c.pv0 = 0; c.pv1 = 0; c.exec_done = 0;
             c.last_px = S.last_px;
+            c.exec_dir = ep_dir;
             if constexpr (MA) {
                 __syncwarp();
                 for (int a = lane; a < A; a += 32) { agp->inv[a] = 0; agp->cash[a] = 0; agp->pv[a] = 0; agp->done[a] = 0; }
@@ -1749,6 +1768,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         st->n[1] = (XT && need_load) ? load_na : ask.n;
         st->t = p.t0 + p.n_steps;
         if (XT) st->ep_start = ep_start;
+        if (XT) st->exec_dir = c.exec_dir;
     }
     if constexpr (MA) {
         __syncwarp();

@@ -249,7 +249,7 @@ def test_create_rejects_bad_configs():
     lob.lob_destroy(h)
     for field, val, code in (("n_envs", 0, lob.LOB_EINVAL), ("n_agents", 1, lob.LOB_EINVAL),
                              ("cap_per_side", lob.LOB_MAX_CAP + 1, lob.LOB_ECAPACITY),
-                             ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 0, lob.LOB_EINVAL),
+                             ("top_levels", 65, lob.LOB_EINVAL), ("exec_dir", 2, lob.LOB_EINVAL),
                              ("action_mode", 7, lob.LOB_EINVAL), ("reward_mode", 3, lob.LOB_EINVAL),
                              ("spooner_lambda_pct", 101, lob.LOB_EINVAL), ("inv_penalty", -1, lob.LOB_EINVAL),
                              ("exec_penalty_milli", -5, lob.LOB_EINVAL), ("mm_space", 3, lob.LOB_EINVAL),
