@@ -9,10 +9,14 @@
 //
 // k_policy_bf16: BF16 operands on the 5th-generation tensor cores
 // (tcgen05.mma, kind::f16, FP32 accumulation in tensor memory).  One CTA of
-// 128 threads handles 128 envs of one agent: the three layers are M=128
+// 256 threads handles 128 envs of one agent: the three layers are M=128
 // GEMMs (N = 128, 128, 16) whose operands sit in shared memory in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix);
-// thread t owns TMEM lane t (env row t) for the bias + tanh epilogues.
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix).
+// The agent's packed weights arrive by bulk copy while the threads stage
+// the observation tile with coalesced loads; in the bias + tanh epilogues
+// warp w reads TMEM lanes 32 (w mod 4) .. +31 (env rows) and column half
+// w / 4, with the tensor-core-era tanh.approx (its error, below 2^-10.9
+// relative, is under the BF16 rounding of the activations that follows).
 // k_policy_fp32: the same forward with FP32 FMAs on the CUDA cores.
 #pragma once
 #include <cstdint>
@@ -25,6 +29,7 @@ constexpr int H = 128;        // hidden width
 constexpr int NOUT = 13;      // 12 logits + value
 constexpr int NA = 12;        // actions
 constexpr int DMAX = 128;     // max observation length (padded to a multiple of 16)
+constexpr int PT = 256;       // threads per CTA of the BF16 forward
 
 // Input scale of feature f of an observation with L levels per side.
 __host__ __device__ inline float obs_scale(int f, int L) {
@@ -102,6 +107,19 @@ __device__ __forceinline__ void pbar_init(unsigned long long *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// One arrival that expects `bytes` of bulk-copy data, then the copies.
+__device__ __forceinline__ void pbar_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                     "r"(s_u32(dst)), "l"(src), "r"(bytes), "r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ bool pbar_wait(unsigned long long *bar, unsigned phase, long long budget) {
     const long long t0 = clock64();
     for (;;) {
@@ -139,7 +157,8 @@ struct __align__(128) Bf16Smem {
     unsigned char x[128 * DMAX * 2];  // [128 x Dp]
     unsigned char h[128 * H * 2];     // [128 x 128], h1 then h2
     float b1[H], b2[H], b3[16];
-    unsigned long long bar;
+    unsigned long long bar;    // MMA completion
+    unsigned long long wbar;   // weight bulk copies
     unsigned tmem_base;
 };
 
@@ -160,7 +179,7 @@ __device__ __forceinline__ void write_outputs(const PolicyParams &p, int env, in
     if (p.actions) p.actions[r] = best;
 }
 
-__global__ void __launch_bounds__(128) k_policy_bf16(const PolicyParams p) {
+__global__ void __launch_bounds__(PT) k_policy_bf16(const PolicyParams p) {
     extern __shared__ __align__(1024) unsigned char praw[];
     Bf16Smem &sm = *reinterpret_cast<Bf16Smem *>(praw);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -168,31 +187,44 @@ __global__ void __launch_bounds__(128) k_policy_bf16(const PolicyParams p) {
     const int row0 = blockIdx.x * 128;
     const int Dp = p.Dp;
     if (warp == 0) tm_alloc(&sm.tmem_base, 128);
-    if (tid == 0) pbar_init(&sm.bar);
-    // weights of agent a (already bf16 in core layout) and biases
+    if (tid == 0) {
+        pbar_init(&sm.bar);
+        pbar_init(&sm.wbar);
+        // weights of agent a, already bf16 in core layout: three bulk copies
+        const unsigned char *src = p.wpack + (long long)a * p.wpack_stride;
+        const unsigned n1 = (unsigned)(H * Dp * 2), n2 = H * H * 2, n3 = 16 * H * 2;
+        pbar_expect(&sm.wbar, n1 + n2 + n3);
+        bulk_g2s(sm.w1, src, n1, &sm.wbar);
+        bulk_g2s(sm.w2, src + n1, n2, &sm.wbar);
+        bulk_g2s(sm.w3, src + n1 + n2, n3, &sm.wbar);
+    }
     {
-        const int4 *src = reinterpret_cast<const int4 *>(p.wpack + (long long)a * p.wpack_stride);
-        const int n1 = H * Dp * 2 / 16, n2 = H * H * 2 / 16, n3 = 16 * H * 2 / 16;
-        for (int i = tid; i < n1; i += 128) reinterpret_cast<int4 *>(sm.w1)[i] = src[i];
-        for (int i = tid; i < n2; i += 128) reinterpret_cast<int4 *>(sm.w2)[i] = src[n1 + i];
-        for (int i = tid; i < n3; i += 128) reinterpret_cast<int4 *>(sm.w3)[i] = src[n1 + n2 + i];
         const float *wf = p.wf32 + (long long)a * p.wf32_stride;
         const float *b1 = wf + H * p.D, *b2 = b1 + H + H * H, *b3 = b2 + H + NOUT * H;
-        sm.b1[tid] = b1[tid];
-        sm.b2[tid] = b2[tid];
+        if (tid < H) sm.b1[tid] = b1[tid];
+        else sm.b2[tid - H] = b2[tid - H];
         if (tid < 16) sm.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
     }
-    // X tile: row tid = env row0 + tid, scaled, bf16, zero-padded
+    // X tile [128 x Dp]: element i = (row, k) row-major, consecutive threads on
+    // consecutive features (coalesced), eight loads in flight per thread
     {
-        const int env = row0 + tid;
-        const float *o = p.obs + ((long long)env * p.A + a) * p.D;
-        for (int k = 0; k < Dp; k += 2) {
-            float v0 = 0.0f, v1 = 0.0f;
-            if (env < p.n_envs) {
-                if (k < p.D) v0 = o[k] * obs_scale(k, p.L);
-                if (k + 1 < p.D) v1 = o[k + 1] * obs_scale(k + 1, p.L);
+        const int nx = 128 * Dp;
+        for (int base = 0; base < nx; base += 8 * PT) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int i = base + u * PT + tid;
+                const int r = i / Dp, k = i - r * Dp;
+                const int env = row0 + r;
+                v[u] = (i < nx && env < p.n_envs && k < p.D)
+                           ? p.obs[((long long)env * p.A + a) * p.D + k] * obs_scale(k, p.L) : 0.0f;
             }
-            *reinterpret_cast<__nv_bfloat162 *>(sm.x + cm_off(tid, k, Dp)) = __floats2bfloat162_rn(v0, v1);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int i = base + u * PT + tid;
+                const int r = i / Dp, k = i - r * Dp;
+                if (i < nx) *reinterpret_cast<__nv_bfloat16 *>(sm.x + cm_off(r, k, Dp)) = __float2bfloat16_rn(v[u]);
+            }
         }
     }
     fence_async_smem();
@@ -200,9 +232,20 @@ __global__ void __launch_bounds__(128) k_policy_bf16(const PolicyParams p) {
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = sm.tmem_base;
-    const unsigned lane_addr = tmem + ((unsigned)(warp * 32) << 16);
+    const int row = 32 * (warp & 3) + (tid & 31);   // TMEM lane = env row
+    const int half = warp >> 2;                     // column half of the epilogues
+    const unsigned lane_addr = tmem + ((unsigned)(32 * (warp & 3)) << 16);
     bool ok = true;
     unsigned phase = 0;
+    // the weights, before the first MMA reads them
+    {
+        const bool landed = pbar_wait(&sm.wbar, 0, p.wait_budget);
+        if (__syncthreads_or(!landed)) {
+            ok = false;
+            if (tid == 0) atomicOr(p.status, 4);
+            pbar_wait(&sm.wbar, 0, p.wait_budget);   // let the copies in flight land
+        }
+    }
     // ---- three layers
     for (int layer = 0; layer < 3 && ok; layer++) {
         if (tid == 0) {
@@ -229,27 +272,33 @@ __global__ void __launch_bounds__(128) k_policy_bf16(const PolicyParams p) {
         tc_fence_after();
         if (layer < 2) {
             const float *bias = layer == 0 ? sm.b1 : sm.b2;
-            for (int c0 = 0; c0 < H; c0 += 32) {
+#pragma unroll
+            for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
                 float v[32];
                 tm_ld32(lane_addr + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const float t0 = tanhf(v[j] + bias[c0 + j]);
-                    const float t1 = tanhf(v[j + 1] + bias[c0 + j + 1]);
-                    *reinterpret_cast<__nv_bfloat162 *>(sm.h + cm_off(tid, c0 + j, H)) = __floats2bfloat162_rn(t0, t1);
+                for (int j = 0; j < 32; j += 8) {
+                    unsigned w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const __nv_bfloat162 t = __floats2bfloat162_rn(tanh_approx(v[j + 2 * q] + bias[c0 + j + 2 * q]),
+                                                                       tanh_approx(v[j + 2 * q + 1] + bias[c0 + j + 2 * q + 1]));
+                        w[q] = *reinterpret_cast<const unsigned *>(&t);
+                    }
+                    *reinterpret_cast<uint4 *>(sm.h + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
-        } else {
+        } else if (half == 0) {
             float v[32];
             tm_ld32(lane_addr, v);
             float y[16];
 #pragma unroll
             for (int j = 0; j < 16; j++) y[j] = v[j] + sm.b3[j];
-            write_outputs(p, row0 + tid, a, y);
+            write_outputs(p, row0 + row, a, y);
         }
     }
     tc_fence_before();

@@ -128,7 +128,7 @@ int policy_forward_internal(lob_policy *pol, const float *d_obs, int32_t n_envs,
     pp.wait_budget = 2000000000LL;
     if (precision == LOB_PREC_BF16) {
         dim3 grid((n_envs + 127) / 128, pol->A);
-        k_policy_bf16<<<grid, 128, sizeof(Bf16Smem), s>>>(pp);
+        k_policy_bf16<<<grid, PT, sizeof(Bf16Smem), s>>>(pp);
     } else {
         dim3 grid((n_envs + 63) / 64, pol->A);
         k_policy_fp32<<<grid, 64, sizeof(F32Smem), s>>>(pp);

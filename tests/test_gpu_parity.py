@@ -82,6 +82,31 @@ def test_tiny_capacities_every_branch(seed):
     pr.close()
 
 
+@pytest.mark.parametrize("L", [1, 64])
+def test_pool_boundary_capacities_filled(L):
+    """Capacities at and beside every pool size (32 K slots per side for
+    K = 1 .. 32, up to the 1,024 maximum), an add-heavy mix over a wide price
+    band that fills every side to capacity (no free slot left, evictions and
+    drops), and the fewest / most observation levels."""
+    caps = np.array([32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023, 1024], np.int32)
+    n, T = len(caps), 10
+    model = mbogen.MessageModel(mix_add=0.88, mix_partial=0.03, mix_delete=0.03, mix_market=0.06,
+                                price_p=0.05, msgs_per_step=600)
+    st = mbogen.generate(model, mbogen.env_seeds(300 + L, n), T)
+    pr = Pair(n, st, caps=caps, cap=1024, top_levels=L, exec_target=200, fill_cap=2048)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    full = [e for e in range(n) if max(pr.orc.book(e)[0]) == caps[e]]
+    assert len(full) == n, f"sides at capacity only for envs {full}"
+    cnt = pr.orc.counters()
+    assert (cnt[:, 12] > 0).all() and (cnt[:, 10] > 0).all()   # evictions and drops everywhere
+    assert pr.env.sync() == 0
+    pr.close()
+
+
 def test_uneven_caps_and_poisson_counts():
     """Capacities from 20 to 1,000 (every capacity class) and
     M_t ~ Poisson(lambda_env), including empty steps."""
