@@ -205,25 +205,30 @@ __global__ void __launch_bounds__(PT) k_policy_bf16(const PolicyParams p) {
         else sm.b2[tid - H] = b2[tid - H];
         if (tid < 16) sm.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
     }
-    // X tile [128 x Dp]: element i = (row, k) row-major, consecutive threads on
-    // consecutive features (coalesced), eight loads in flight per thread
+    // X tile [128 x Dp]: warp w stages rows w, w + 8, ..., its lanes along the
+    // features (coalesced); all of a thread's loads are in flight at once
     {
-        const int nx = 128 * Dp;
-        for (int base = 0; base < nx; base += 8 * PT) {
-            float v[8];
+        constexpr int RPW = 128 / (PT / 32);   // rows per warp
+        const int lane = tid & 31;
+        float v[DMAX / 32][RPW];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int i = base + u * PT + tid;
-                const int r = i / Dp, k = i - r * Dp;
-                const int env = row0 + r;
-                v[u] = (i < nx && env < p.n_envs && k < p.D)
-                           ? p.obs[((long long)env * p.A + a) * p.D + k] * obs_scale(k, p.L) : 0.0f;
+        for (int c = 0; c < DMAX / 32; c++) {
+            const int k = 32 * c + lane;
+#pragma unroll
+            for (int j = 0; j < RPW; j++) {
+                const int env = row0 + warp + (PT / 32) * j;
+                v[c][j] = (k < p.D && env < p.n_envs)
+                              ? p.obs[((long long)env * p.A + a) * p.D + k] * obs_scale(k, p.L) : 0.0f;
             }
+        }
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int i = base + u * PT + tid;
-                const int r = i / Dp, k = i - r * Dp;
-                if (i < nx) *reinterpret_cast<__nv_bfloat16 *>(sm.x + cm_off(r, k, Dp)) = __float2bfloat16_rn(v[u]);
+        for (int c = 0; c < DMAX / 32; c++) {
+            const int k = 32 * c + lane;
+            if (k < Dp) {
+#pragma unroll
+                for (int j = 0; j < RPW; j++)
+                    *reinterpret_cast<__nv_bfloat16 *>(sm.x + cm_off(warp + (PT / 32) * j, k, Dp)) =
+                        __float2bfloat16_rn(v[c][j]);
             }
         }
     }
