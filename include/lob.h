@@ -372,8 +372,18 @@ int lob_set_trace(lob_handle *h, lob_fill *d_fills, int32_t fill_cap, int32_t *d
  * status (first error seen: LOB_EBADMSG, LOB_EINVAL or LOB_ETIMEOUT). */
 int lob_sync(lob_handle *h, void *stream);
 /* Launch-shape control used by the autotuner: warps per block for the step
- * kernels (1..32) and whether they take envs from a work queue. */
+ * kernels (1..8) and whether they take envs from a work queue. */
 int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
+/* Failure-detection hook.  `cycles` bounds every wait of the step kernels on
+ * a message tile, in SM cycles (0 = the default, about one second).  hold = 1
+ * makes the next step or rollout launch leave each env's first message tile
+ * unrequested (device-resident messages only), so that the wait for it runs
+ * out: the launch stops every env at that point, its outputs and env state
+ * are not written (counters may have advanced), and lob_sync reports
+ * LOB_ETIMEOUT.  The hold applies to that one launch; continue with lob_reset
+ * (or lob_load of a checkpoint).  Returns LOB_EINVAL for cycles < 0 or hold
+ * not 0/1. */
+int lob_debug_wait(lob_handle *h, int64_t cycles, int32_t hold);
 /* ---- Checkpoint / resume of every env (books, per-env scalars, counters,
  * seeds, the last step's outputs, the step t and the window cursor).  The
  * bound message window is not part of it: bind the same window before
@@ -415,7 +425,10 @@ int64_t lob_kernel_launches(const lob_handle *h);
  * lob_step in persistent mode) on caller-owned state:
  *   cfg           uniform capacity cap_per_side, trace must be 0,
  *                 warps_per_block 0..8 (0 = 4, fewer where a block's shared
- *                 memory cannot hold that many books); n_envs <= LOB_NOALLOC_MAX_ENVS
+ *                 memory cannot hold that many books); n_envs <= LOB_NOALLOC_MAX_ENVS;
+ *                 n_agents 0 or 2 with the defaults of every other option
+ *                 (LOB_REWARD_PV, no penalties, LOB_MM_SPREAD_SKEW, LOB_PV_TOUCH,
+ *                 exec_dir LOB_SELL or LOB_BUY), else LOB_EINVAL
  *   d_books       n_envs book blocks, each 48*S bytes rounded up to a multiple
  *                 of 256, S = the smallest power of two >= max(cap, 32)
  *   d_env_state   n_envs * 128 bytes of per-env scalars (opaque)

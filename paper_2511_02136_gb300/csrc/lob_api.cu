@@ -208,6 +208,8 @@ struct lob_handle {
     // launch shape
     int wpb = 4;
     int persistent = 0;
+    long long wait_budget = 0;   // 0: the default bound
+    int hold_first = 0;          // failure-detection test hook (next launch only)
     int n_sm = 0;
     int64_t launches = 0;
     // per-class streams: several capacity classes run concurrently (fork/join
@@ -659,7 +661,10 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     p.fill_counts = (c.trace & 1) ? h->d_fill_counts : nullptr;
     p.snaps = (c.trace & 2) ? h->d_snaps : nullptr; p.snap_cap = h->snap_cap;
     p.snap_count = (c.trace & 2) ? reinterpret_cast<long long *>(h->d_snap_count) : nullptr;
-    p.wait_budget = DEFAULT_WAIT_BUDGET;
+    p.wait_budget = h->wait_budget > 0 ? h->wait_budget : DEFAULT_WAIT_BUDGET;
+    p.drain_budget = DEFAULT_WAIT_BUDGET;
+    p.hold_first = h->hold_first;
+    h->hold_first = 0;   // one launch only
     p.exec_q0 = exec_lot(c);
     set_rewards(p, c);
     p.agents = h->d_agents;
@@ -1115,6 +1120,13 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
     return LOB_OK;
 }
 
+int lob_debug_wait(lob_handle *h, int64_t cycles, int32_t hold) {
+    if (!h || cycles < 0 || (hold != 0 && hold != 1)) return LOB_EINVAL;
+    h->wait_budget = cycles;
+    h->hold_first = hold;
+    return LOB_OK;
+}
+
 int64_t lob_kernel_launches(const lob_handle *h) { return h ? h->launches : 0; }
 
 int lob_set_env_costs(lob_handle *h, const float *h_cost) {
@@ -1185,6 +1197,11 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
         (c.action_mode != LOB_ACT_HOST && c.action_mode != LOB_ACT_RANDOM) || c.trace != 0 ||
         c.warps_per_block < 0 || c.warps_per_block > 8 || c.cap_per_side < 1)
         return LOB_EINVAL;
+    // the plain kernel only: the PV reward, no penalties, the 12-way market
+    // maker, the touch as value reference, a fixed task side
+    if (c.reward_mode != LOB_REWARD_PV || c.inv_penalty != 0 || c.exec_penalty_milli != 0 ||
+        c.mm_space != LOB_MM_SPREAD_SKEW || c.pv_ref != LOB_PV_TOUCH)
+        return LOB_EINVAL;
     if (c.n_envs > LOB_NOALLOC_MAX_ENVS || c.cap_per_side > LOB_MAX_CAP) return LOB_ECAPACITY;
     if (!a->d_books || !a->d_env_state || !a->d_counters || !a->d_env_seeds || !a->d_offsets || !a->d_status ||
         a->k < 0 || a->stride < (int64_t)a->k + 2 || a->t < 0 || a->t >= c.episode_len)
@@ -1239,6 +1256,7 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     p.n_list = n;
     p.queue = reinterpret_cast<int *>(scratch);
     p.wait_budget = DEFAULT_WAIT_BUDGET;
+    p.drain_budget = DEFAULT_WAIT_BUDGET;
     p.exec_q0 = exec_lot(c);
     set_rewards(p, c);
     const int wpb = c.warps_per_block > 0 ? c.warps_per_block : 4;

@@ -99,7 +99,9 @@ struct KParams {
     const int *env_list;   // NULL: env = list position (identity)
     int n_list;
     int *queue;
-    long long wait_budget;
+    long long wait_budget;      // bound of a wait on a message tile (SM cycles)
+    long long drain_budget;     // bound of the wait for a copy in flight after a timeout
+    int hold_first;             // test hook: the launch's first tile per env is never requested
     // uniform layout: when uni_cap > 0 every env has capacity uni_cap and its
     // book block at env * uni_block; book_off / caps are not read
     int uni_cap;
@@ -1242,13 +1244,16 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         const int nmsg = (int)(me - mb);
         const int ntiles = (nmsg + TILE - 1) / TILE;
         const unsigned tile0 = pipe.tiles;
+        // failure-detection test hook: the launch's first tile is not requested,
+        // so the wait for it runs out (bulk-copy path only)
+        const bool held = p.hold_first && step == 0 && !sysm;
         if (ntiles > 0) {
             __syncwarp();
             // compact tiles land in the upper half of the buffer and are widened on arrival
             char *dst = reinterpret_cast<char *>(sm.tile[pipe.tiles & 1]) + (m16 ? 16 * TILE : 0);
             if (sysm) {
                 tile_copy_lanes(dst, msg_base + mb * rec, min(TILE, nmsg), rec, lane);
-            } else if (lane == 0) {
+            } else if (lane == 0 && !held) {
                 fence_proxy_async_smem();
                 tma_bulk_g2s(dst, msg_base + mb * rec, (unsigned)(min(TILE, nmsg) * rec), &sm.bar[pipe.tiles & 1]);
             }
@@ -1458,7 +1463,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                     __syncwarp();
                 } else if (!mbar_wait(&sm.bar[buf], phase, p.wait_budget)) {
                     c.status |= ST_TIMEOUT;
-                    mbar_wait(&sm.bar[buf], phase, p.wait_budget);  // let the copy in flight land
+                    if (!(held && ch == 0))
+                        mbar_wait(&sm.bar[buf], phase, p.drain_budget);  // let the copy in flight land
                     timed_out = true;
                     break;
                 }

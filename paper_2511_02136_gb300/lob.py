@@ -44,7 +44,7 @@ EXPORTS = [
     "lob_obs_dim", "lob_create", "lob_destroy", "lob_load_messages", "lob_reset", "lob_step",
     "lob_observe", "lob_rollout", "lob_step_host", "lob_book_bytes", "lob_get_book",
     "lob_get_counters", "lob_get_agents", "lob_get_env_misc", "lob_get_actions", "lob_set_trace",
-    "lob_sync", "lob_set_launch", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
+    "lob_sync", "lob_set_launch", "lob_debug_wait", "lob_kernel_launches", "lob_strerror", "lob_step_noalloc",
     "lob_policy_param_count", "lob_policy_create", "lob_policy_destroy", "lob_policy_forward",
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
@@ -158,6 +158,7 @@ def _load():
         "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
         "lob_sync": (ctypes.c_int, [P, P]),
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
+        "lob_debug_wait": (ctypes.c_int, [P, ctypes.c_int64, I32]),
         "lob_kernel_launches": (I64, [P]),
         "lob_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lob_step_noalloc": (ctypes.c_int, [ctypes.POINTER(lob_noalloc_args), P]),
@@ -296,6 +297,12 @@ def lob_sync(h, stream=None):
 
 def lob_set_launch(h, warps_per_block, persistent):
     return _check(_load().lob_set_launch(h, warps_per_block, persistent), "lob_set_launch")
+
+
+def lob_debug_wait(h, cycles, hold):
+    """Failure-detection hook: wait bound in SM cycles (0 = default) and, with
+    hold=1, the next launch's first message tile left unrequested."""
+    return _check(_load().lob_debug_wait(h, cycles, hold), "lob_debug_wait")
 
 
 def lob_set_env_costs(h, costs=None):

@@ -82,3 +82,24 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(lob.LobError) as ei:
         lob.lob_step_noalloc(args)
     assert ei.value.code == lob.LOB_ECAPACITY
+
+
+def test_noalloc_rejects_extended_options():
+    """The allocation-free step runs the plain kernel only: every extended
+    option (reward variants, penalties, other market-maker spaces, the mid as
+    value reference, a drawn task side) is refused, not ignored."""
+    import torch
+    lob.build()
+    dummy = torch.zeros(64, dtype=torch.int64, device="cuda")
+    p = dummy.data_ptr()
+    for field, val in (("reward_mode", lob.LOB_REWARD_SPOONER), ("inv_penalty", 1), ("exec_penalty_milli", 10),
+                       ("mm_space", lob.LOB_MM_DIRECTIONAL), ("pv_ref", lob.LOB_PV_MID), ("exec_dir", 0),
+                       ("n_agents", 4)):
+        cfg = lob.lob_config(8, 2, 100, 10, 4, 1, 50, -1, 1, 0, 10_000, 0)
+        setattr(cfg, field, val)
+        args = lob.lob_noalloc_args(cfg=lob.ctypes.pointer(cfg), d_books=p, d_env_state=p, d_counters=p,
+                                    d_env_seeds=p, d_msgs=p, d_offsets=p, stride=5, k=0, t=0, d_actions=None,
+                                    d_obs=None, d_rewards=None, d_done=None, d_status=p)
+        with pytest.raises(lob.LobError) as ei:
+            lob.lob_step_noalloc(args)
+        assert ei.value.code == lob.LOB_EINVAL, field
