@@ -387,10 +387,10 @@ __device__ __forceinline__ int ix_find(const Side<K> &S, int s, int lane) {
         const unsigned key = (unsigned)s * Side<K>::REP;
         const unsigned eq = IXB == 8 ? __vcmpeq4(S.ix[w], key) : __vcmpeq2(S.ix[w], key);
         const unsigned m = eq & ix_below<K>(S.n, lane, w);
-        if (m) local = EPW * w + (__ffs(m) - 1) / IXB;
+        if (m) local = EPW * w + (31 - __clz(m)) / IXB;   // s occurs once: any set bit of its entry
     }
     const unsigned lanes = __ballot_sync(FULL, local >= 0);
-    const int L = __ffs(lanes) - 1;
+    const int L = 31 - __clz(lanes);
     return __shfl_sync(FULL, lane * K + local, L);
 }
 
@@ -476,18 +476,22 @@ __device__ __forceinline__ void do_fill(Ctx &c, int px, int f, long long maker_i
         }
         return;
     }
-    const int om = c.owner(maker_id), ot = c.owner(taker_id);
-    const int buyer = taker_side == LOB_BUY ? ot : om;
-    const int seller = taker_side == LOB_BUY ? om : ot;
-    const long long notional = (long long)((unsigned long long)(long long)px * (unsigned long long)(long long)f);
-    const long long ff = f;
-    c.cash0 += (buyer == 0 ? -notional : 0) + (seller == 0 ? notional : 0);
-    c.inv0 += (buyer == 0 ? ff : 0) - (seller == 0 ? ff : 0);
-    c.cash1 += (buyer == 1 ? -notional : 0) + (seller == 1 ? notional : 0);
-    c.inv1 += (buyer == 1 ? ff : 0) - (seller == 1 ? ff : 0);
-    c.bg_cash += (buyer == 2 ? -notional : 0) + (seller == 2 ? notional : 0);
-    c.bg_inv += (buyer == 2 ? ff : 0) - (seller == 2 ? ff : 0);
-    c.exec_done += (c.A > 0 && (c.exec_dir == LOB_SELL ? seller : buyer) == 0) ? ff : 0;
+    // Only agent ids are negative, so a fill between two background orders
+    // (the common case) moves nothing tracked per owner and skips this
+    // block; the background's totals are the negated agents' totals over the
+    // step (every notional and quantity changes hands), settled once per step.
+    if ((maker_id | taker_id) < 0 && c.A > 0) {
+        const int om = c.owner(maker_id), ot = c.owner(taker_id);
+        const int buyer = taker_side == LOB_BUY ? ot : om;
+        const int seller = taker_side == LOB_BUY ? om : ot;
+        const long long notional = (long long)((unsigned long long)(long long)px * (unsigned long long)(long long)f);
+        const long long ff = f;
+        c.cash0 += (buyer == 0 ? -notional : 0) + (seller == 0 ? notional : 0);
+        c.inv0 += (buyer == 0 ? ff : 0) - (seller == 0 ? ff : 0);
+        c.cash1 += (buyer == 1 ? -notional : 0) + (seller == 1 ? notional : 0);
+        c.inv1 += (buyer == 1 ? ff : 0) - (seller == 1 ? ff : 0);
+        c.exec_done += ((c.exec_dir == LOB_SELL ? seller : buyer) == 0) ? ff : 0;
+    }
     c.last_px = px;
     c.c_fills += 1;
     c.c_fill_vol += f;
@@ -540,7 +544,8 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
     const int vic_q = P.qty[vic];
     const unsigned fr = ~S.occ & Side<K>::KMASK;
     const unsigned flanes = __ballot_sync(FULL, fr != 0);
-    const int free_slot = __shfl_sync(FULL, slot_of<K>(lane, __ffs(fr) - 1), __ffs(flanes) - 1);
+    // any free slot will do: the highest set bits (one instruction each)
+    const int free_slot = __shfl_sync(FULL, slot_of<K>(lane, 31 - __clz(fr)), 31 - __clz(flanes));
     int pos;
     if constexpr (Side<K>::REG) {
         pos = 0;
@@ -556,10 +561,12 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
     const bool full = S.n >= cap;
     const bool ins = !(full && pos >= S.n);   // a full side keeps only strictly better prices
     const bool ev = full && ins;
-    c.c_drop_vol += ins ? 0 : q;
-    c.c_drop_cnt += ins ? 0 : 1;
-    c.c_evict_vol += ev ? vic_q : 0;
-    c.c_evict_cnt += ev ? 1 : 0;
+    if (full) {   // the capacity counters move only on a full side
+        c.c_drop_vol += ins ? 0 : q;
+        c.c_drop_cnt += ins ? 0 : 1;
+        c.c_evict_vol += ev ? vic_q : 0;
+        c.c_evict_cnt += ev ? 1 : 0;
+    }
     const int f = full ? vic : free_slot;
     const int fl = slot_lane<K>(f), fr_ = slot_r<K>(f);
     if (ins && lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
@@ -625,9 +632,9 @@ __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type
     }
     const bool dup = __popc(lanes) > 1 || __ballot_sync(FULL, __popc(m) > 1) != 0;
     int s;
-    if (!dup) {
-        const int L = __ffs(lanes) - 1;
-        s = __shfl_sync(FULL, slot_of<K>(lane, __ffs(m) - 1), L);
+    if (!dup) {   // the single match: its lane and register by their highest set bits
+        const int L = 31 - __clz(lanes);
+        s = __shfl_sync(FULL, slot_of<K>(lane, 31 - __clz(m)), L);
     } else {
         s = first_dup_slot<K>(S, P, p, oid, lane);
     }
@@ -1273,6 +1280,9 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         c.msg_idx = 0;
         c.fill_n = 0;
         snap_n = 0;
+        // the pair's totals at the step start (the background settles against them)
+        typedef unsigned long long u64;
+        const u64 pair_cash0 = (u64)c.cash0 + (u64)c.cash1, pair_inv0 = (u64)c.inv0 + (u64)c.inv1;
 
         // ---- 1-3. action conversion, carry-over cancels, shuffle
         int act0 = 0, act1 = 0, ns = 0;
@@ -1526,39 +1536,30 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                         c.status |= ST_BADMSG;
                     }
                 } else {
-                    switch (didx) {
-                        case 0:   // add, buy
-                            c.c_add_vol += qty;
+                    // uniform branches in order of frequency: adds, cancels, market orders
+                    if (didx < 2) {
+                        c.c_add_vol += qty;
+                        if (didx == 0) {
                             if (ask.n > 0 && px >= ask.fpx)
                                 qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
                             if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
-                            break;
-                        case 1:   // add, sell
-                            c.c_add_vol += qty;
+                        } else {
                             if (bid.n > 0 && px <= bid.fpx)
                                 qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
                             if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
-                            break;
-                        case 2:   // partial cancel, buy
-                        case 4:   // delete, buy
-                            side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
-                            break;
-                        case 3:   // partial cancel, sell
-                        case 5:   // delete, sell
-                            side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
-                            break;
-                        case 6:   // market, buy
-                            c.c_mkt_vol += qty;
+                        }
+                    } else if (didx < 6) {
+                        if ((didx & 1) == 0) side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
+                        else side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+                    } else if (didx < 8) {
+                        c.c_mkt_vol += qty;
+                        if (didx == 6)
                             c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
-                            break;
-                        case 7:   // market, sell
-                            c.c_mkt_vol += qty;
+                        else
                             c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
-                            break;
-                        default:
-                            c.c_bad += 1;
-                            c.status |= ST_BADMSG;
-                            break;
+                    } else {
+                        c.c_bad += 1;
+                        c.status |= ST_BADMSG;
                     }
                 }
                 if (TRACE && snap_env) {
@@ -1572,6 +1573,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             }
         }
         if (timed_out) break;
+        if constexpr (!MA) {   // the background gained what the pair lost this step
+            c.bg_cash = (long long)((u64)c.bg_cash - ((u64)c.cash0 + (u64)c.cash1 - pair_cash0));
+            c.bg_inv = (long long)((u64)c.bg_inv - ((u64)c.inv0 + (u64)c.inv1 - pair_inv0));
+        }
 
         // ---- 5. step outcomes (and, after the last step, the book write-back)
         // Episode mode: after the episode's last step the env starts the next
@@ -1831,6 +1836,15 @@ __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
 }
 template <int K, bool TRACE, bool EXT, bool MA = false>
 __global__ void __launch_bounds__(256, 1) k_env_steps_wide(const KParams p) {
+    env_steps_body<K, TRACE, EXT, MA>(p);
+}
+// A fixed register budget of NREG per thread, for launches of several waves
+// where resident warps per SM set the throughput: e.g. 168 keeps three 4-warp
+// blocks resident (3 x 128 threads x 168 registers fit the 64 K register
+// file), where ptxas left to itself may take a few registers more and leave
+// room for two.
+template <int K, bool TRACE, bool EXT, bool MA, int NREG>
+__global__ void __maxnreg__(NREG) k_env_steps_nreg(const KParams p) {
     env_steps_body<K, TRACE, EXT, MA>(p);
 }
 

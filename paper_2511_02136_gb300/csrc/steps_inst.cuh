@@ -24,7 +24,10 @@ struct StepLaunch {
             else k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
         } else {
             if (ext && wide) k_env_steps_wide<KK, false, true><<<blocks, threads, smem, s>>>(p);
-            else if (ext) k_env_steps<KK, false, true><<<blocks, threads, smem, s>>>(p);
+            else if (ext) {
+                if constexpr (KK == 4) k_env_steps_nreg<KK, false, true, false, 168><<<blocks, threads, smem, s>>>(p);
+                else k_env_steps<KK, false, true><<<blocks, threads, smem, s>>>(p);
+            }
             else if (wide) k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
             else k_env_steps<KK, false, false><<<blocks, threads, smem, s>>>(p);
         }
@@ -37,7 +40,11 @@ struct StepLaunch {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, true>, A, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, false>, A, b);
         if constexpr (!ALWAYS_WIDE) {
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, true>, A, b);
+            if constexpr (KK == 4) {
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_nreg<KK, false, true, false, 168>, A, b);
+            } else {
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, true>, A, b);
+            }
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, false>, A, b);
         }
         return e;

@@ -107,6 +107,24 @@ def test_pool_boundary_capacities_filled(L):
     pr.close()
 
 
+def test_extended_kernel_default_budget_many_envs():
+    """Enough envs (1,600 per class at capacities 50 and 100) that the host
+    launches the extended kernel in its default register budget rather than
+    the one-wave wide budget; reward variants on, every env checked."""
+    n, T = 3200, 3
+    caps = np.where(np.arange(n) % 2 == 0, 50, 100).astype(np.int32)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=50), mbogen.env_seeds(160, n), T)
+    pr = Pair(n, st, caps=caps, cap=100, exec_target=40, n_threads=os.cpu_count() or 1,
+              rewards=dict(reward_mode=lob.LOB_REWARD_SPOONER, spooner_lambda_pct=30, inv_penalty=1,
+                           exec_penalty_milli=100))
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
+
+
 def test_uneven_caps_and_poisson_counts():
     """Capacities from 20 to 1,000 (every capacity class) and
     M_t ~ Poisson(lambda_env), including empty steps."""
