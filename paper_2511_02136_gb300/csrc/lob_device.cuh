@@ -1496,6 +1496,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 if (m16) widen_tile(sm.tile[buf], cnt_ch, lane);
             }
             const int4 *rp = reinterpret_cast<const int4 *>(base);
+            c.c_msgs += cnt_ch;                 // a started chunk is always finished
+            c.c_agent += agent ? cnt_ch : 0;
             int4 w0 = rp[0], w1 = rp[1];
             for (int i = 0; i < cnt_ch; i++) {
                 const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
@@ -1503,8 +1505,6 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 const int key = w1.z;
                 const int px = w1.x;
                 int qty = w1.y;
-                c.c_msgs += 1;
-                c.c_agent += agent;
                 // one dense dispatch index: (type - 1) * 2 + (side is sell), 8 = malformed
                 const int type = key & 0xffff, side = key >> 16;
                 const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
