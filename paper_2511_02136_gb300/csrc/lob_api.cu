@@ -151,13 +151,15 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
                      p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH || p.exec_dir == 0;
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
+    KParams q = p;
+    q.book_prefetch = wide ? 1 : 0;   // every env starts at once: fetch the books early
     switch (K) {
-        case 1: return launch_steps_1(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
-        case 2: return launch_steps_2(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
-        case 4: return launch_steps_4(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
-        case 8: return launch_steps_8(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
-        case 16: return launch_steps_16(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
-        default: return launch_steps_32(trace, ext, wide, blocks, 32 * wpb, smem, s, p);
+        case 1: return launch_steps_1(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
+        case 2: return launch_steps_2(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
+        case 4: return launch_steps_4(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
+        case 8: return launch_steps_8(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
+        case 16: return launch_steps_16(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
+        default: return launch_steps_32(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
     }
 }
 

@@ -102,6 +102,7 @@ struct KParams {
     long long wait_budget;      // bound of a wait on a message tile (SM cycles)
     long long drain_budget;     // bound of the wait for a copy in flight after a timeout
     int hold_first;             // test hook: the launch's first tile per env is never requested
+    int book_prefetch;          // one-wave launches: each env's book block is requested into L2 at entry
     // uniform layout: when uni_cap > 0 every env has capacity uni_cap and its
     // book block at env * uni_block; book_off / caps are not read
     int uni_cap;
@@ -1182,6 +1183,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     const bool uni = p.uni_cap > 0;
     const int cap = uni ? p.uni_cap : p.caps[e];
     unsigned char *blk = p.books + (uni ? (long long)e * p.uni_block : p.book_off[e]);
+    // one-wave launches: the env's book block heads for L2 while the offsets
+    // and the env state are read, so the first book load finds it there
+    if (p.book_prefetch && lane == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blk), "r"((unsigned)(48 * 32 * K)) : "memory");
     const int A = p.n_agents;
     const unsigned long long seed = p.seeds[e];
     long long *cnt = p.counters + (long long)e * LOB_NCOUNTERS;
