@@ -170,7 +170,7 @@ typedef struct lob_config {
 #define LOB_REWARD_BUYSELL 1
 #define LOB_REWARD_SPOONER 2
 
-#define LOB_MAX_CAP 1024   /* per-side capacity supported by this build */
+#define LOB_MAX_CAP 1024   /* largest per-side capacity the library supports */
 
 typedef struct lob_handle lob_handle;
 
