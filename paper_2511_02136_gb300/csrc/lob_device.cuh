@@ -234,6 +234,10 @@ static_assert(offsetof(WarpSmem<1>, tile) == 0 && offsetof(WarpSmem<32>, tile) =
 // array: the step's agent orders (3 per agent pair at most, plus the record
 // read ahead), the agents' running state and the step's wanted orders.
 constexpr int AMSG_MA = 3 * LOB_MAX_PER_TYPE + 1;
+// the message loop keeps a chunk's dispatch indices in the carry-over flags'
+// space: a tile or the agents' orders, plus the one-ahead read
+static_assert(sizeof(WarpSmem<1>::cand) >= AMSG_MA + 1 && sizeof(WarpSmem<1>::cand) >= TILE + 1,
+              "dispatch indices fit the carry-over flags");
 struct __align__(16) AgentSmem {
     DevMsg amsg[AMSG_MA];
     long long inv[AMAX], cash[AMAX], pv[AMAX], done[AMAX];
@@ -1503,18 +1507,28 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             const int4 *rp = reinterpret_cast<const int4 *>(base);
             c.c_msgs += cnt_ch;                 // a started chunk is always finished
             c.c_agent += agent ? cnt_ch : 0;
+            // each record's dense dispatch index, (type - 1) * 2 + (side is sell)
+            // or 8 = malformed, decoded one record per lane into a byte array
+            // (the carry-over flags' space, free during the message loop and
+            // rewritten by the next step's carry-over), off the serial chain
+            unsigned char *dx = &sm.cand[0][0];
+            for (int r = lane; r < cnt_ch; r += 32) {   // a tile, or up to 3 orders per agent
+                const int4 w = rp[2 * r + 1];
+                const int ty = w.z & 0xffff, sd = w.z >> 16;
+                const bool ok = ty >= LOB_ADD && ty <= LOB_MARKET && (sd == 1 || sd == -1) && (w.y > 0 || ty == LOB_DELETE);
+                dx[r] = (unsigned char)(ok ? ((ty - 1) << 1) | (sd < 0 ? 1 : 0) : 8);
+            }
+            __syncwarp();
             int4 w0 = rp[0], w1 = rp[1];
+            int dcur = dx[0];
             for (int i = 0; i < cnt_ch; i++) {
                 const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
+                const int dnext = dx[i + 1];   // read one ahead, like the record (stays in this warp's space)
                 const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                const int key = w1.z;
                 const int px = w1.x;
                 int qty = w1.y;
-                // one dense dispatch index: (type - 1) * 2 + (side is sell), 8 = malformed
-                const int type = key & 0xffff, side = key >> 16;
-                const bool valid = type >= LOB_ADD && type <= LOB_MARKET && (side == 1 || side == -1) &&
-                                   (qty > 0 || type == LOB_DELETE);
-                const int didx = valid ? ((type - 1) << 1) | (side < 0 ? 1 : 0) : 8;
+                const int didx = dcur;
+                const int type = (didx >> 1) + 1;   // cancels: LOB_PARTIAL or LOB_DELETE
                 if constexpr (K >= 32) {
                     // the largest books: one call site per side for taking
                     // liquidity and for resting, to keep the kernel's code small
@@ -1575,6 +1589,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 c.msg_idx++;
                 w0 = n0;
                 w1 = n1;
+                dcur = dnext;
             }
         }
         if (timed_out) break;
