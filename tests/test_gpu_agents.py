@@ -177,3 +177,20 @@ def test_agents_per_type_config_limits():
     env.step(bad)
     assert env.sync() == lob.LOB_EINVAL
     env.close()
+
+
+def test_most_agents_smallest_books():
+    """The largest agent count (16 per type, up to 48 agent orders a step) on
+    the smallest capacity class: the agents' chunk is the longest and the
+    per-warp buffers the smallest."""
+    n, T = 12, 10
+    P = lob.LOB_MAX_PER_TYPE
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=40), mbogen.env_seeds(170, n), T)
+    pr = Pair(n, st, n_agents=2 * P, cap=20, exec_target=50, fill_cap=512)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
