@@ -29,6 +29,7 @@ _DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.c
 _OBJDIR = os.path.join(_PKG, "_build")
 _lock = threading.Lock()
 _lib = None
+_lib_path = None
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -128,8 +129,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 def _load():
-    global _lib
+    global _lib, _lib_path
     if _lib is not None:
+        # one library per process: handles, streams and device state belong to it
+        if os.path.abspath(LIB_PATH) != _lib_path:
+            raise RuntimeError(f"liblob.so already loaded from {_lib_path}; "
+                               f"LIB_PATH now names {LIB_PATH}: use one process per library")
         return _lib
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"liblob.so is not built ({LIB_PATH}); call paper_2511_02136_gb300.lob.build()")
@@ -180,6 +185,7 @@ def _load():
         fn.restype = res
         fn.argtypes = args
     _lib = lib
+    _lib_path = os.path.abspath(LIB_PATH)
     return lib
 
 

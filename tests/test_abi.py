@@ -42,3 +42,22 @@ def test_built_for_sm103a_only():
     for cmd in [lob.nvcc_cmd("x.so")] + [lob.nvcc_cmd("x.o", src=s) for s in lob._SOURCES]:
         assert "arch=compute_103a,code=sm_103a" in cmd
         assert sum(1 for c in cmd if c == "-gencode") == 1
+
+
+def test_one_library_per_process():
+    """Pointing the binding at another library after the first load raises
+    instead of silently calling the library already loaded."""
+    lob.build()
+    lob._load()
+    old = lob.LIB_PATH
+    try:
+        lob.LIB_PATH = old + ".other.so"
+        try:
+            lob._load()
+        except RuntimeError as e:
+            assert "one process per library" in str(e)
+        else:
+            raise AssertionError("a second library path was accepted")
+    finally:
+        lob.LIB_PATH = old
+    assert lob._load() is not None
