@@ -51,6 +51,8 @@ extern "C" {
 #define LOB_ECAPACITY  (-5)  /* a size exceeds what the handle or build supports */
 #define LOB_EBADMSG    (-6)  /* a message with unknown type/side or non-positive size (skipped) */
 #define LOB_ESTATE     (-7)  /* call out of order (no messages bound, window exhausted) */
+#define LOB_ECHECK     (-8)  /* checked build only (compiled with LOB_CHECKED): an index bound
+                                or a book invariant failed on the device */
 
 /* message types and sides (LOBSTER-style event codes) */
 #define LOB_ADD     1

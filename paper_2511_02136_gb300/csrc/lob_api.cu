@@ -293,6 +293,7 @@ const char *lob_strerror(int code) {
         case LOB_ECAPACITY: return "size exceeds supported capacity";
         case LOB_EBADMSG: return "malformed message (skipped)";
         case LOB_ESTATE: return "call out of order";
+        case LOB_ECHECK: return "checked build: an index bound or book invariant failed";
         default: return "unknown status";
     }
 }
@@ -1110,6 +1111,7 @@ int lob_sync(lob_handle *h, void *stream) {
     if (cudaMemcpy(&st, h->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LOB_ECUDA;
     if (st) cudaMemset(h->d_status, 0, 4);
     if (st & ST_TIMEOUT) return LOB_ETIMEOUT;
+    if (st & ST_CHECK) return LOB_ECHECK;
     if (st & ST_BADACT) return LOB_EINVAL;
     if (st & ST_BADMSG) return LOB_EBADMSG;
     return LOB_OK;

@@ -34,7 +34,23 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int TILE = 32;        // messages per staged tile
 constexpr int LMAX = 64;        // max observation levels per side
 constexpr int SMAX = 256;       // max pool slots per side (byte-wide index)
-constexpr int ST_BADMSG = 1, ST_BADACT = 2, ST_TIMEOUT = 4;
+constexpr int ST_BADMSG = 1, ST_BADACT = 2, ST_TIMEOUT = 4, ST_CHECK = 8;
+
+// Checked build (-DLOB_CHECKED, compute-sanitizer being unavailable): every
+// slot number and position taken from the priority index is bounds-checked
+// before it addresses shared memory, and each step ends with a check of both
+// books' invariants; a violation records ST_CHECK (the index is clamped into
+// range) instead of faulting.  The regular build compiles none of it.
+#ifdef LOB_CHECKED
+__device__ __forceinline__ int lob_chk(int x, int hi, int &st) {
+    if ((unsigned)x < (unsigned)hi) return x;
+    st |= ST_CHECK;
+    return 0;
+}
+#define LOB_CHK(x, hi, st) lob_chk((x), (hi), (st))
+#else
+#define LOB_CHK(x, hi, st) (x)
+#endif
 
 struct DevMsg {
     long long ts, oid;
@@ -416,6 +432,46 @@ __device__ __forceinline__ void front_refresh(Side<K> &S, const PoolSmem<K> &P) 
     }
 }
 
+#ifdef LOB_CHECKED
+// Checked build: one side's invariants after a step -- live count within the
+// capacity and equal to the occupied slots; positions 0..n-1 name occupied
+// slots in priority order (better price first, earlier stamp first at a
+// price), each with a positive quantity; register copies and the cached front
+// order agree with shared memory.  Warp-uniform result.
+template <int K, bool BID>
+__device__ bool book_ok(const Side<K> &S, const PoolSmem<K> &P, int cap, int lane) {
+    const int n = S.n;
+    const int occ_n = (int)__reduce_add_sync(FULL, (unsigned)__popc(S.occ & Side<K>::KMASK));
+    bool ok = n >= 0 && n <= cap && n <= 32 * K && occ_n == n;
+    const int last = min(ix_ent<K>(S, K - 1), 32 * K - 1);
+    int ppx = __shfl_up_sync(FULL, P.px[last], 1);
+    long long pts = __shfl_up_sync(FULL, P.ts[last], 1);
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        const int q = lane * K + j;
+        const int s = ix_ent<K>(S, j);
+        const bool in_range = s < 32 * K;
+        const int ss = in_range ? s : 0;
+        const unsigned o = __shfl_sync(FULL, S.occ, slot_lane<K>(ss));
+        const bool occupied = (o >> slot_r<K>(ss)) & 1u;
+        const int px = P.px[ss];
+        const long long ts = P.ts[ss];
+        const bool order = q == 0 || (BID ? (ppx > px || (ppx == px && pts < ts)) : (ppx < px || (ppx == px && pts < ts)));
+        if (q < n) ok = ok && in_range && occupied && order && P.qty[ss] > 0;
+        if constexpr (Side<K>::REG) {
+            if ((S.occ >> j) & 1u) ok = ok && S.px[j] == P.px[slot_of<K>(lane, j)] && S.id[j] == P.id[slot_of<K>(lane, j)];
+        }
+        ppx = px;
+        pts = ts;
+    }
+    if (n > 0) {
+        const int f = min(slot_at<K>(S, 0), 32 * K - 1);
+        ok = ok && f == S.fslot && P.px[f] == S.fpx && P.qty[f] == S.fqty && P.id[f] == S.fid;
+    }
+    return __all_sync(FULL, ok);
+}
+#endif
+
 // ---------------------------------------------------------------- env context
 // Warp-uniform per-env scalars of the running step.
 struct Ctx {
@@ -516,7 +572,7 @@ __device__ __forceinline__ int side_take(Side<K> &O, PoolSmem<K> &P, bool has_li
                                          long long taker_id, int taker_side, Ctx &c, int lane) {
     while (q > 0 && O.n > 0 && (!has_limit || at_least<RBID>(O.fpx, limit))) {
         // the order behind the front, fetched before we know whether it is needed
-        const int s1 = slot_at<K>(O, 1);
+        const int s1 = LOB_CHK(slot_at<K>(O, 1), 32 * K, c.status);
         const int npx = P.px[s1], nqt = P.qty[s1];
         const long long nid = P.id[s1];
         unsigned popped[Side<K>::NW];
@@ -545,7 +601,7 @@ template <int K, bool BID>
 __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, int p, int q, long long oid,
                                           Ctx &c, int lane) {
     // independent of p: the worst order (evicted if the side is full) and a free slot
-    const int vic = slot_at<K>(S, S.n > 0 ? S.n - 1 : 0);
+    const int vic = LOB_CHK(slot_at<K>(S, S.n > 0 ? S.n - 1 : 0), 32 * K, c.status);
     const int vic_q = P.qty[vic];
     const unsigned fr = ~S.occ & Side<K>::KMASK;
     const unsigned flanes = __ballot_sync(FULL, fr != 0);
@@ -572,7 +628,7 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
         c.c_evict_vol += ev ? vic_q : 0;
         c.c_evict_cnt += ev ? 1 : 0;
     }
-    const int f = full ? vic : free_slot;
+    const int f = full ? vic : LOB_CHK(free_slot, 32 * K, c.status);
     const int fl = slot_lane<K>(f), fr_ = slot_r<K>(f);
     if (ins && lane == fl) S.occ |= 1u << fr_;   // a reused victim slot stays occupied
     if constexpr (Side<K>::REG) {
@@ -596,8 +652,8 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
 
 // Remove slot s (any position) and fix the front if it was there.
 template <int K>
-__device__ __forceinline__ void side_remove_slot(Side<K> &S, PoolSmem<K> &P, int s, int lane) {
-    const int q = ix_find<K>(S, s, lane);
+__device__ __forceinline__ void side_remove_slot(Side<K> &S, PoolSmem<K> &P, int s, int lane, int &st) {
+    const int q = LOB_CHK(ix_find<K>(S, s, lane), S.n, st);
     slot_clear<K>(S, s, lane);
     ix_remove<K>(S, q, lane);
     S.n--;
@@ -643,11 +699,12 @@ __device__ __forceinline__ void side_cancel(Side<K> &S, PoolSmem<K> &P, int type
     } else {
         s = first_dup_slot<K>(S, P, p, oid, lane);
     }
+    s = LOB_CHK(s, 32 * K, c.status);
     const int q0 = P.qty[s];
     const int cut = type == LOB_PARTIAL ? min(qty, q0) : q0;
     c.c_cancel_vol += cut;
     if (q0 - cut == 0) {
-        side_remove_slot<K>(S, P, s, lane);
+        side_remove_slot<K>(S, P, s, lane, c.status);
     } else {
         P.qty[s] = q0 - cut;   // same value from every lane
         if (s == S.fslot) S.fqty = q0 - cut;
@@ -889,7 +946,7 @@ __device__ __forceinline__ void side_cancel_set(Side<K> &S, PoolSmem<K> &P, unsi
         const int L = __ffs(lanes) - 1;
         const int s = __shfl_sync(FULL, slot_of<K>(lane, __ffs(cmask) - 1), L);
         if (lane == L) cmask &= cmask - 1;
-        side_remove_slot<K>(S, P, s, lane);
+        side_remove_slot<K>(S, P, s, lane, c.status);
     }
 }
 
@@ -909,7 +966,7 @@ __device__ __forceinline__ void side_agent_cancels(Side<K> &S, PoolSmem<K> &P, u
         if (lanes == 0) break;
         const int L = __ffs(lanes) - 1;
         const int q = L * K + __shfl_sync(FULL, first, L);
-        const int s = slot_at<K>(S, q);
+        const int s = LOB_CHK(slot_at<K>(S, q), 32 * K, c.status);
         c.c_msgs += 1;
         c.c_agent += 1;
         c.c_cancel_vol += P.qty[s];
@@ -1593,6 +1650,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             }
         }
         if (timed_out) break;
+#ifdef LOB_CHECKED
+        {
+            bool ok = book_ok<K, true>(bid, sm.pool[0], cap, lane) && book_ok<K, false>(ask, sm.pool[1], cap, lane);
+            if (bid.n > 0 && ask.n > 0 && bid.fpx >= ask.fpx) ok = false;   // never crossed after a message
+            if (!ok) c.status |= ST_CHECK;
+        }
+#endif
         if constexpr (!MA) {   // the background gained what the pair lost this step
             c.bg_cash = (long long)((u64)c.bg_cash - ((u64)c.cash0 + (u64)c.cash1 - pair_cash0));
             c.bg_inv = (long long)((u64)c.bg_inv - ((u64)c.inv0 + (u64)c.inv1 - pair_inv0));

@@ -19,7 +19,11 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_PKG)
 _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
-LIB_PATH = os.path.join(_PKG, "liblob.so")
+# LOB_CHECKED=1 in the environment selects the checked build (index bounds and
+# book invariants verified on the device, reported as LOB_ECHECK), built and
+# loaded as liblob_checked.so
+CHECKED = os.environ.get("LOB_CHECKED") == "1"
+LIB_PATH = os.path.join(_PKG, "liblob_checked.so" if CHECKED else "liblob.so")
 _SOURCES = [os.path.join(_CSRC, n) for n in
             ["lob_api.cu", "policy_api.cu"] + [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)] +
             [f"steps_ma_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
@@ -33,8 +37,8 @@ _lib_path = None
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-LOB_OK, LOB_EINVAL, LOB_ENOMEM, LOB_ECUDA, LOB_ETIMEOUT, LOB_ECAPACITY, LOB_EBADMSG, LOB_ESTATE = \
-    0, -1, -2, -3, -4, -5, -6, -7
+LOB_OK, LOB_EINVAL, LOB_ENOMEM, LOB_ECUDA, LOB_ETIMEOUT, LOB_ECAPACITY, LOB_EBADMSG, LOB_ESTATE, LOB_ECHECK = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
 LOB_ACT_HOST, LOB_ACT_RANDOM = 0, 1
 LOB_NCOUNTERS = 16
 LOB_MAX_CAP = 1024
@@ -98,7 +102,8 @@ def _stale(target, deps):
 
 def nvcc_cmd(out_path, extra=(), src=None):
     """Compile command of one translation unit (all of them for the shared object when src is None)."""
-    base = ["nvcc", "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-Xcompiler", "-fPIC", "-I", _INC]
+    base = ["nvcc", "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-Xcompiler", "-fPIC", "-I", _INC] + \
+        (["-DLOB_CHECKED"] if CHECKED else [])
     if src is None:
         return base + ["-shared", "-o", out_path] + list(extra) + _SOURCES
     return base + ["-c", "-o", out_path] + list(extra) + [src]

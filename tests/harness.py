@@ -138,4 +138,6 @@ class Pair:
         np.testing.assert_array_equal(got.view(np.uint8), want[:k].view(np.uint8))
 
     def close(self):
+        if lob.CHECKED:   # checked build: no index bound or book invariant may have failed
+            assert self.env.sync() != lob.LOB_ECHECK, "checked build: device invariant failed"
         self.env.close()
