@@ -371,7 +371,8 @@ int lob_set_trace(lob_handle *h, lob_fill *d_fills, int32_t fill_cap, int32_t *d
                   void *d_snaps, int64_t snap_cap, int64_t *d_snap_count);
 
 /* Wait for the handle's work on `stream`, then return and clear the device
- * status (first error seen: LOB_EBADMSG, LOB_EINVAL or LOB_ETIMEOUT). */
+ * status: LOB_ETIMEOUT, else LOB_ECHECK (checked build), else LOB_EINVAL (an
+ * invalid action), else LOB_EBADMSG (a malformed message), else LOB_OK. */
 int lob_sync(lob_handle *h, void *stream);
 /* Launch-shape control used by the autotuner: warps per block for the step
  * kernels (1..8) and whether they take envs from a work queue. */
