@@ -35,16 +35,36 @@ def apply(h, choice: Choice, costs=None):
     lob.lob_set_env_costs(h, costs if (choice.longest_first and costs is not None) else None)
 
 
-def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=None, key=None):
-    """`run()` performs one timed unit of work on the current stream (it must
-    reset/rebind whatever it consumes); returns the fastest Choice."""
+def _event_timer(run, repeats):
+    """Best of `repeats` CUDA-event timings of run() after one warm-up (ms)."""
     import torch
+    run()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=None, key=None,
+         timer=None, applier=None):
+    """`run()` performs one timed unit of work on the current stream (it must
+    reset/rebind whatever it consumes); returns the fastest Choice.  `timer`
+    (run, repeats) -> ms and `applier` (h, choice, costs) default to CUDA
+    events and the C ABI."""
+    timer = timer or _event_timer
+    applier = applier or apply
     if cache and key and os.path.exists(cache):
         with open(cache) as f:
             got = json.load(f).get(key)
         if got:
             ch = Choice(**got)
-            apply(h, ch, costs)
+            applier(h, ch, costs)
             return ch
     results = []
     orders = (False, True) if costs is not None else (False,)
@@ -53,21 +73,11 @@ def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=Non
             if lf and not pers:
                 continue          # the order only matters to the work queue
             ch = Choice(wpb, pers, lf, 0.0)
-            apply(h, ch, costs)
-            run()                  # warm-up
-            torch.cuda.synchronize()
-            best = float("inf")
-            for _ in range(repeats):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                run()
-                b.record()
-                torch.cuda.synchronize()
-                best = min(best, a.elapsed_time(b))
-            ch.ms = best
+            applier(h, ch, costs)
+            ch.ms = timer(run, repeats)
             results.append(ch)
     win = min(results, key=lambda c: c.ms)
-    apply(h, win, costs)
+    applier(h, win, costs)
     if cache and key:
         data = {}
         if os.path.exists(cache):

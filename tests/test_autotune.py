@@ -1,0 +1,63 @@
+"""The launch-shape autotuner's search and cache (host logic, no GPU): a fake
+timer stands in for the CUDA-event timing of each applied shape."""
+import json
+
+from paper_2511_02136_gb300 import autotune
+
+
+def _fake(times):
+    state = {"cur": None, "applied": [], "timed": 0}
+
+    def applier(h, ch, costs):
+        state["cur"] = (ch.warps_per_block, ch.persistent, ch.longest_first)
+        state["applied"].append(state["cur"])
+
+    def timer(run, repeats):
+        state["timed"] += 1
+        return times[state["cur"]]
+    return state, applier, timer
+
+
+def _times():
+    t = {}
+    for wpb in (1, 2, 4, 8):
+        for pers in (0, 1):
+            for lf in (False, True):
+                t[(wpb, pers, lf)] = 10.0 + wpb + pers + (0.5 if lf else 0.0)
+    t[(4, 1, True)] = 3.0      # the fastest shape
+    t[(2, 0, True)] = 1.0      # never a candidate: the order only matters to the work queue
+    return t
+
+
+def test_picks_fastest_and_skips_order_without_queue(tmp_path):
+    state, applier, timer = _fake(_times())
+    win = autotune.tune(None, lambda: None, costs=[1.0], timer=timer, applier=applier)
+    assert (win.warps_per_block, win.persistent, win.longest_first) == (4, 1, True)
+    assert win.ms == 3.0
+    # 8 shapes in natural order, 4 work-queue shapes also longest first
+    assert state["timed"] == 12
+    assert all(not (lf and not pers) for _, pers, lf in state["applied"])
+    assert state["applied"][-1] == (4, 1, True)          # the winner is left applied
+
+
+def test_without_costs_no_longest_first():
+    state, applier, timer = _fake(_times())
+    win = autotune.tune(None, lambda: None, costs=None, timer=timer, applier=applier)
+    assert not win.longest_first and state["timed"] == 8
+    assert (win.warps_per_block, win.persistent) == (1, 0)
+
+
+def test_cache_round_trip(tmp_path):
+    cache = str(tmp_path / "tune.json")
+    state, applier, timer = _fake(_times())
+    win = autotune.tune(None, lambda: None, costs=[1.0], timer=timer, applier=applier, cache=cache, key="k1")
+    assert json.load(open(cache))["k1"]["warps_per_block"] == 4
+    state2, applier2, timer2 = _fake(_times())
+    again = autotune.tune(None, lambda: None, costs=[1.0], timer=timer2, applier=applier2, cache=cache, key="k1")
+    assert again == win and state2["timed"] == 0 and state2["applied"] == [(4, 1, True)]
+
+
+def test_signature_is_order_independent():
+    a = autotune.signature(8, {100: 3, 50: 5}, 99.6, 500)
+    b = autotune.signature(8, {50: 5, 100: 3}, 100.4, 500)
+    assert a == b
