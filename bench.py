@@ -250,7 +250,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                         "kernel": "k_env_steps<4>", "alg_bytes_per_launch": alg_bytes,
+                         "kernel": "k_env_steps_wide<4> (plain, one wave)", "alg_bytes_per_launch": alg_bytes,
                          "mean_live_slots_per_env": live},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
             "wall_s": t_wall,
