@@ -171,6 +171,8 @@ def test_oracle_matches_brute_agents_per_type(seed):
     kw = dict(top_levels=3, episode_len=T, mm_lot=int(rng.integers(1, 4)), exec_target=int(rng.integers(5, 40)),
               exec_dir=int(rng.choice([-1, 1])), start_px=10_000, mm_space=space,
               reward_mode=seed % 3, spooner_lambda_pct=60, inv_penalty=seed % 2, exec_penalty_milli=100)
+    if seed % 3 == 1:
+        kw["exec_dir"] = 0      # the task side drawn per env, shared by its execution agents
     o = oracle.Oracle(n_env, n_agents=A, cap=cap, action_mode=0 if host else 1, trace=1, **kw)
     o.reset(seeds)
     o.load_messages(st.msgs, st.offsets)
