@@ -1,0 +1,61 @@
+"""Argument validation of the C ABI that happens before any CUDA call, so it
+runs without a GPU: each bad configuration or argument gets its documented
+code (include/lob.h)."""
+import numpy as np
+import pytest
+
+from paper_2511_02136_gb300 import lob
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lob.build()
+
+
+def _cfg(**kw):
+    c = lob.lob_config(8, 2, 100, 10, 10, 1, 10, -1, 1, 0, 10000, 0)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+@pytest.mark.parametrize("field,val,code", [
+    ("n_envs", 0, lob.LOB_EINVAL), ("n_agents", 3, lob.LOB_EINVAL),
+    ("n_agents", 2 * lob.LOB_MAX_PER_TYPE + 2, lob.LOB_EINVAL),
+    ("cap_per_side", 0, lob.LOB_EINVAL), ("cap_per_side", lob.LOB_MAX_CAP + 1, lob.LOB_ECAPACITY),
+    ("top_levels", 0, lob.LOB_EINVAL), ("top_levels", 65, lob.LOB_EINVAL),
+    ("episode_len", 0, lob.LOB_EINVAL), ("mm_lot", 0, lob.LOB_EINVAL), ("exec_target", -1, lob.LOB_EINVAL),
+    ("exec_dir", 2, lob.LOB_EINVAL), ("action_mode", 7, lob.LOB_EINVAL), ("trace", 4, lob.LOB_EINVAL),
+    ("warps_per_block", 9, lob.LOB_EINVAL), ("reward_mode", 3, lob.LOB_EINVAL),
+    ("spooner_lambda_pct", 101, lob.LOB_EINVAL), ("inv_penalty", -1, lob.LOB_EINVAL),
+    ("exec_penalty_milli", -5, lob.LOB_EINVAL), ("mm_space", 3, lob.LOB_EINVAL), ("pv_ref", 2, lob.LOB_EINVAL),
+])
+def test_create_rejects_before_touching_the_device(field, val, code):
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_create(_cfg(**{field: val}))
+    assert ei.value.code == code
+
+
+def test_per_env_capacities_checked():
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_create(_cfg(), caps=np.array([100] * 7 + [lob.LOB_MAX_CAP + 1], np.int32))
+    assert ei.value.code == lob.LOB_ECAPACITY
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_create(_cfg(), caps=np.array([100] * 7 + [0], np.int32))
+    assert ei.value.code == lob.LOB_EINVAL
+
+
+def test_null_handles_and_bad_hooks():
+    for call in (lambda: lob.lob_set_launch(None, 4, 0), lambda: lob.lob_debug_wait(None, 0, 0)):
+        with pytest.raises(lob.LobError) as ei:
+            call()
+        assert ei.value.code == lob.LOB_EINVAL
+
+
+def test_policy_create_validates_shapes():
+    n = lob.lob_policy_param_count(45)
+    for agents, dim, code in ((0, 45, lob.LOB_EINVAL), (2 * lob.LOB_MAX_PER_TYPE + 1, 45, lob.LOB_EINVAL),
+                              (2, 46, lob.LOB_EINVAL), (2, 133, lob.LOB_ECAPACITY)):
+        with pytest.raises(lob.LobError) as ei:
+            lob.lob_policy_create(agents, dim, np.zeros((max(agents, 1), max(n, 1)), np.float32))
+        assert ei.value.code == code
