@@ -97,25 +97,34 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        text = self.f.read()
         os.unlink(self.f.name)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_rows(text)
+
+
+def parse_clock_rows(text):
+    """Median SM clock, max clock and active slowdown reasons from nvidia-smi
+    CSV rows (index, clocks.sm, clocks.max.sm, power, active mask, then the
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown and sw_power_cap
+    flags); None without a valid sample."""
+    rows = [r.split(",") for r in text.strip().splitlines() if r.strip()]
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        if len(r) < 9:
+            continue
+        try:
+            sm.append(float(r[1]))
+            mx = float(r[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, r[5:9]):
+            if v.strip().lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def _traffic_record():

@@ -1,0 +1,32 @@
+"""Host-side pieces of the benchmark: clock-sample parsing and the peak source."""
+import json
+import os
+
+import bench
+
+
+def test_clock_rows_median_max_and_reasons():
+    text = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1300.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, 1980, 2070, 1390.0, 0x8, Active, Not Active, Not Active, Active",
+    ])
+    c = bench.parse_clock_rows(text)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2055 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_rows_empty():
+    assert bench.parse_clock_rows("") is None
+    assert bench.parse_clock_rows("0, N/A, N/A, N/A, N/A, N/A, N/A, N/A, N/A") is None
+
+
+def test_peak_is_the_measured_copy_bandwidth():
+    peak, kind = bench._peaks()
+    p = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        assert kind == "measured" and peak == float(json.load(open(p))["hbm_gbs"])
+    else:
+        assert kind == "fallback" and peak == 6800.0
