@@ -14,11 +14,12 @@
  *      records the trades (Sec. 4, "Processing by JAX-LOB");
  *   5. rewards, termination flags and observations are computed (Sec. 4,
  *      "Calculate step outcomes"; portfolio value per Eq. 1).
- * Agent 0 is the order-execution agent (Sec. 4.1.2, 12 discrete actions:
- * four reference prices x {1, 2, 5} lots); agent 1 is the market maker
- * (Sec. 4.1.1, 12 discrete actions: one lot at the best bid/ask -/+ {0,1,2}
- * ticks, or one tick into the spread on either side).  With n_agents = 0 the
- * library is a plain market-replay engine.
+ * With n_agents = 2P, agents 0..P-1 are order-execution agents (Sec. 4.1.2,
+ * 12 discrete actions: four reference prices x {1, 2, 5} lots) and agents
+ * P..2P-1 market makers (Sec. 4.1.1; by default 12 discrete actions: one lot
+ * at the best bid/ask -/+ {0,1,2} ticks, or one tick into the spread on either
+ * side).  The benchmark pair is P = 1.  With n_agents = 0 the library is a
+ * plain market-replay engine.
  *
  * Conventions (every entry point):
  *   - returns LOB_OK (0) or a negative LOB_E* code; lob_strerror() names it;
@@ -29,8 +30,9 @@
  *     device work is enqueued on it and the call returns without waiting,
  *     except where a function says it synchronises;
  *   - errors found on the device (a malformed message, an invalid action, a
- *     bounded wait that expired) are recorded in the handle's status word and
- *     returned by the next lob_sync() or lob_get_status();
+ *     bounded wait that expired, a failed check of the checked build) are
+ *     recorded in the handle's status word and returned by the next
+ *     lob_sync();
  *   - a handle is not thread-safe; handles are independent of each other.
  */
 #ifndef LOB_H
