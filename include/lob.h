@@ -363,6 +363,11 @@ int lob_get_agents(lob_handle *h, int64_t *d_out, void *stream);
 int lob_get_env_misc(lob_handle *h, int64_t *d_out, void *stream);
 /* d_out int32 [n_envs][n_agents]: the actions used in the last step. */
 int lob_get_actions(lob_handle *h, int32_t *d_out, void *stream);
+/* Statistics for byte accounting (no counterpart in the paper): adds the
+ * number of resting orders of every env, bids plus asks, to the int64 at
+ * d_acc (device, caller-owned, not cleared), on the stream, without a host
+ * synchronisation; one small kernel.  LOB_EINVAL for a NULL argument. */
+int lob_live_orders(lob_handle *h, int64_t *d_acc, void *stream);
 
 /* Trace buffers (caller-owned, device): fill log of the last step for every
  * env, d_fills [n_envs][fill_cap] with d_fill_counts int32 [n_envs] (counts
@@ -435,20 +440,24 @@ int64_t lob_kernel_launches(const lob_handle *h);
  *                 (LOB_REWARD_PV, no penalties, LOB_MM_SPREAD_SKEW, LOB_PV_TOUCH,
  *                 exec_dir LOB_SELL or LOB_BUY), else LOB_EINVAL
  *   d_books       n_envs book blocks, each 48*S bytes rounded up to a multiple
- *                 of 256, S = the smallest power of two >= max(cap, 32)
- *   d_env_state   n_envs * 128 bytes of per-env scalars (opaque)
+ *                 of 256, S = the smallest power of two >= max(cap, 32);
+ *                 256-byte aligned.  At t == 0 their contents are ignored
+ *                 (any bytes will do); afterwards they are the library's.
+ *   d_env_state   n_envs * 128 bytes of per-env scalars (opaque), 16-byte aligned
  *   d_counters    int64 [n_envs][LOB_NCOUNTERS]
  *   d_env_seeds   uint64 [n_envs]
  *   d_msgs, d_offsets, stride, k   as lob_load_messages: this step uses
- *                 window step k
+ *                 window step k; d_msgs 16-byte aligned
  *   t             episode step; t == 0 first resets every env (empty books,
  *                 zero agents and counters), as lob_reset does
  *   d_actions     int32 [n_envs][2] in LOB_ACT_HOST mode, else ignored
  *   d_obs, d_rewards, d_done   outputs as lob_observe (any may be NULL)
  *   d_status      int32, OR-ed with 1 (malformed message), 2 (invalid action),
  *                 4 (bounded wait expired); the caller clears it
- * Returns LOB_EINVAL for a bad argument, LOB_ECAPACITY when n_envs or the
- * capacity exceeds the limits above, LOB_ECUDA if a CUDA call fails. */
+ * Returns LOB_EINVAL for a bad argument (including a pointer off the
+ * alignment stated above, refused before anything is launched), LOB_ECAPACITY
+ * when n_envs or the capacity exceeds the limits above, LOB_ECUDA if a CUDA
+ * call fails. */
 #define LOB_NOALLOC_MAX_ENVS 16384
 typedef struct lob_noalloc_args {
     const lob_config *cfg;

@@ -48,14 +48,16 @@ static void set_rewards(KParams &p, const lob_config &c) {
     p.pv_ref = c.pv_ref;
 }
 
+// Shared memory of one warp (env): its WarpSmem plus, for the register-pool
+// classes, its price-ladder block.
 size_t warp_smem_bytes(int K) {
     switch (K) {
-        case 1: return sizeof(WarpSmem<1>);
-        case 2: return sizeof(WarpSmem<2>);
-        case 4: return sizeof(WarpSmem<4>);
-        case 8: return sizeof(WarpSmem<8>);
-        case 16: return sizeof(WarpSmem<16>);
-        default: return sizeof(WarpSmem<32>);
+        case 1: return sizeof(WarpSmem<1>) + ladder_bytes<1>();
+        case 2: return sizeof(WarpSmem<2>) + ladder_bytes<2>();
+        case 4: return sizeof(WarpSmem<4>) + ladder_bytes<4>();
+        case 8: return sizeof(WarpSmem<8>) + ladder_bytes<8>();
+        case 16: return sizeof(WarpSmem<16>) + ladder_bytes<16>();
+        default: return sizeof(WarpSmem<32>) + ladder_bytes<32>();
     }
 }
 
@@ -620,6 +622,23 @@ __global__ void k_get_book(const unsigned char *books, const long long *book_off
     }
 }
 
+// Resting orders of all envs (both sides) added to *acc: a block-wide sum,
+// then one atomic per block.
+__global__ void k_live_orders(const EnvState *st, int n, long long *acc) {
+    long long v = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        v += (long long)st[e].n[0] + st[e].n[1];
+    v = warp_sum(v);
+    __shared__ long long part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        atomicAdd(reinterpret_cast<unsigned long long *>(acc), (unsigned long long)t);
+    }
+}
+
 __global__ void k_get_agents(const EnvState *st, long long *out, int n, int A, int misc) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -1076,6 +1095,15 @@ int lob_get_env_misc(lob_handle *h, int64_t *d_out, void *stream) {
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 
+int lob_live_orders(lob_handle *h, int64_t *d_acc, void *stream) {
+    if (!h || !d_acc) return LOB_EINVAL;
+    const int n = h->cfg.n_envs;
+    const int blocks = std::min((n + 255) / 256, 4 * std::max(h->n_sm, 1));
+    k_live_orders<<<blocks, 256, 0, (cudaStream_t)stream>>>(h->d_state, n, reinterpret_cast<long long *>(d_acc));
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
 int lob_get_actions(lob_handle *h, int32_t *d_out, void *stream) {
     if (!h || !d_out) return LOB_EINVAL;
     if (h->cfg.n_agents == 0) return LOB_OK;
@@ -1176,7 +1204,7 @@ static int g_noalloc_n_sm[NOALLOC_MAX_DEVICES];
 
 // Per-call preparation of the scratch tables (and the episode reset at t = 0).
 __global__ void k_noalloc_prepare(unsigned char *scratch, int n, int cap, long long block_bytes, int reset,
-                                  EnvState *st, long long *cnt, int start_px) {
+                                  EnvState *st, long long *cnt, int start_px, int exec_dir) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e == 0) *reinterpret_cast<int *>(scratch) = 0;   // the work queue starts at zero every call
     if (e >= n) return;
@@ -1187,6 +1215,7 @@ __global__ void k_noalloc_prepare(unsigned char *scratch, int n, int cap, long l
         EnvState z;
         memset(&z, 0, sizeof(z));
         z.last_px = start_px;
+        z.exec_dir = exec_dir;   // the configured task side, as lob_reset stores it
         st[e] = z;
         for (int i = 0; i < LOB_NCOUNTERS; i++) cnt[(long long)e * LOB_NCOUNTERS + i] = 0;
     }
@@ -1211,6 +1240,12 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
         a->k < 0 || a->stride < (int64_t)a->k + 2 || a->t < 0 || a->t >= c.episode_len)
         return LOB_EINVAL;
     if (c.n_agents == 2 && c.action_mode == LOB_ACT_HOST && !a->d_actions) return LOB_EINVAL;
+    // the kernel stages messages with bulk copies (16-byte boundaries), reads
+    // the env state with 16-byte vector loads and each book block with 16-byte
+    // vectors from 256-byte block boundaries: refuse what it could not read
+    if (((uintptr_t)a->d_msgs & 15u) != 0 || ((uintptr_t)a->d_env_state & 15u) != 0 ||
+        ((uintptr_t)a->d_books & 255u) != 0)
+        return LOB_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LOB_ECUDA;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LOB_ECAPACITY;
@@ -1231,7 +1266,8 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     k_noalloc_prepare<<<(n + 127) / 128, 128, 0, s>>>(scratch, n, c.cap_per_side, block_bytes, a->t == 0 ? 1 : 0,
                                                        reinterpret_cast<EnvState *>(a->d_env_state),
-                                                       reinterpret_cast<long long *>(a->d_counters), c.start_px);
+                                                       reinterpret_cast<long long *>(a->d_counters), c.start_px,
+                                                       c.exec_dir);
     if (cudaGetLastError() != cudaSuccess) return LOB_ECUDA;
 
     KParams p;

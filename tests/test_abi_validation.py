@@ -59,3 +59,48 @@ def test_policy_create_validates_shapes():
         with pytest.raises(lob.LobError) as ei:
             lob.lob_policy_create(agents, dim, np.zeros((max(agents, 1), max(n, 1)), np.float32))
         assert ei.value.code == code
+
+
+class _DefaultStream:
+    """The legacy default stream, named without asking torch (no GPU here)."""
+    cuda_stream = None
+
+
+def _noalloc_args(cfg, **ptrs):
+    """Arguments of lob_step_noalloc with fake, suitably aligned device
+    addresses: every case below is refused before any CUDA call."""
+    base = dict(d_books=0x100000, d_env_state=0x200000, d_counters=0x300000, d_env_seeds=0x400000,
+                d_msgs=0x500000, d_offsets=0x600000, d_status=0x700000)
+    base.update(ptrs)
+    return lob.lob_noalloc_args(cfg=lob.ctypes.pointer(cfg), stride=5, k=0, t=0, d_actions=None, d_obs=None,
+                                d_rewards=None, d_done=None, **base)
+
+
+@pytest.mark.parametrize("field,val", [
+    ("reward_mode", lob.LOB_REWARD_SPOONER), ("inv_penalty", 1), ("exec_penalty_milli", 10),
+    ("mm_space", lob.LOB_MM_DIRECTIONAL), ("pv_ref", lob.LOB_PV_MID), ("exec_dir", 0), ("n_agents", 4)])
+def test_noalloc_rejects_extended_options(field, val):
+    """The allocation-free step runs the plain kernel only: every extended
+    option is refused, not ignored."""
+    cfg = _cfg()
+    setattr(cfg, field, val)
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_step_noalloc(_noalloc_args(cfg), _DefaultStream)
+    assert ei.value.code == lob.LOB_EINVAL, field
+
+
+@pytest.mark.parametrize("ptr,addr", [
+    ("d_msgs", 0x500008), ("d_env_state", 0x200008), ("d_books", 0x100010), ("d_books", 0x100080)])
+def test_noalloc_rejects_misaligned_buffers(ptr, addr):
+    """Messages and env state must sit on 16-byte boundaries and book blocks on
+    256-byte ones (bulk copies and vector accesses): a misaligned pointer is an
+    argument error on the host, never a launch."""
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_step_noalloc(_noalloc_args(_cfg(), **{ptr: addr}), _DefaultStream)
+    assert ei.value.code == lob.LOB_EINVAL
+
+
+def test_noalloc_rejects_oversize_on_the_host():
+    with pytest.raises(lob.LobError) as ei:
+        lob.lob_step_noalloc(_noalloc_args(_cfg(n_envs=lob.LOB_NOALLOC_MAX_ENVS + 1)), _DefaultStream)
+    assert ei.value.code == lob.LOB_ECAPACITY
