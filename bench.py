@@ -145,6 +145,24 @@ def _traffic_record():
     return float(rec["dram_bytes_per_launch"])
 
 
+def bench_config(world):
+    """The workload description both arms print (the GPU arm and the oracle arm)."""
+    return {"workload": WORKLOAD, "n_envs": N_ENVS, "cap_per_side": CAP, "msgs_per_step": M,
+            "episode_len": T, "top_levels": L, "global_batch": N_ENVS * world,
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "256 MiB buffer written between timed steps (outside the events)",
+            "timing": "CUDA events per step on the launching stream, summed"}
+
+
+def alg_bytes_per_env_step(live_orders, D):
+    """Algorithmic bytes of one env-step: the step's messages, the book's live
+    orders loaded and stored (24 bytes each way), the env state and counters
+    read and written, seed and offsets read, observations and rewards of both
+    agents and the done flag written.  live_orders = resting orders at the
+    load plus those at the store (both sides)."""
+    return M * 32 + 24 * live_orders + 2 * 128 + 2 * 16 * 8 + 8 + 16 + 2 * (4 * D + 8) + 1
+
+
 def make_inputs(seed, gen_steps=T):
     from paper_2511_02136_gb300 import mbogen
     seeds = mbogen.env_seeds(seed, N_ENVS)
@@ -198,8 +216,11 @@ def run_gpu(args):
         return int(env.counters()[:, 0].sum().item())
 
     msgs_total = -msgs_so_far()           # counters restart at every reset
-    launches0 = lob.lob_kernel_launches(env.h)
-    live_slots = []
+    # resting orders at every timed step's load and store, summed on the
+    # device (one small kernel after each step, outside the events), read once
+    live_acc = torch.zeros(1, dtype=torch.int64, device=dev)
+    lob.lob_live_orders(env.h, live_acc)       # the first timed step's load
+    launches = 0
     clk = Clocks(local)
     t_wall0 = time.perf_counter()
     for i in range(K):
@@ -209,17 +230,21 @@ def run_gpu(args):
             env.load_messages(msgs_d, off_d)
             state["t"] = 0
         flush.fill_(i)
+        l0 = lob.lob_kernel_launches(env.h)
         ev[i][0].record(stream)
         env.step()
         ev[i][1].record(stream)
+        launches += lob.lob_kernel_launches(env.h) - l0
         state["t"] += 1
-        if i % 97 == 0:
-            live_slots.append(env.books_live())
+        # this step's store and (unless it is the last) the next step's load
+        lob.lob_live_orders(env.h, live_acc)
+        if i + 1 < K:
+            lob.lob_live_orders(env.h, live_acc)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
     msgs_total += msgs_so_far()
-    launches = lob.lob_kernel_launches(env.h) - launches0
+    live_sum = int(live_acc.item())       # sum over the K steps of (orders at load + orders at store)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     rc = env.sync()
     if rc != 0:
@@ -228,13 +253,11 @@ def run_gpu(args):
     total_s, msgs_total = aggregate_over_ranks(total_s, msgs_total, dev)
     env_steps = K * N_ENVS * world
     value = msgs_total / total_s
-    # algorithmic bytes per launch (one launch per step): messages, book
-    # load + store of the live slots, per-env scalars, counters, seed,
-    # offsets, observations, rewards, done
-    live = float(np.mean(live_slots))
+    # algorithmic bytes per launch (one launch per step), with the live
+    # orders averaged over every timed step's load and store
     D = env.D
-    per_env = (M * 32 + 2 * 24 * live + 2 * 128 + 2 * 16 * 8 + 8 + 16 + 2 * (4 * D + 8) + 1)
-    alg_bytes = per_env * N_ENVS
+    live_ls = live_sum / (K * N_ENVS)      # per env-step: orders loaded + orders stored
+    alg_bytes = alg_bytes_per_env_step(live_ls, D) * N_ENVS
     peak, peak_kind = _peaks()
     mean_step_s = total_s / K
     achieved = alg_bytes / mean_step_s / 1e9
@@ -251,16 +274,13 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * mean_step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "env_steps_per_s": env_steps / total_s,
-            "config": {"workload": WORKLOAD, "n_envs": N_ENVS, "cap_per_side": CAP, "msgs_per_step": M,
-                       "episode_len": T, "top_levels": L, "global_batch": N_ENVS * world,
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "timing": "CUDA events per step on the launching stream, summed"},
+            "config": bench_config(world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                          "kernel": "k_env_steps_wide<4> (plain, one wave)", "alg_bytes_per_launch": alg_bytes,
-                         "mean_live_slots_per_env": live},
+                         "mean_live_orders_per_env": live_ls / 2,
+                         "live_orders_from": f"every timed step's load and store ({K} steps)"},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
             "wall_s": t_wall,
         }
@@ -374,7 +394,7 @@ def run_reference(args):
            "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "env_steps_per_s": K * N_ENVS / el,
-           "config": {"workload": WORKLOAD, "n_envs": N_ENVS, "cap_per_side": CAP, "msgs_per_step": M},
+           "config": bench_config(world),
            "cpu_baseline": {"value": value, "unit": "msgs/s", "cores": n_threads, "kind": "oracle",
                             "sample": f"all {N_ENVS} envs, steps {t}..{t + K - 1} of one episode"},
            "e2e": {"value": value, "unit": "msgs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

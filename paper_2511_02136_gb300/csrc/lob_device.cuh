@@ -265,6 +265,11 @@ struct __align__(16) AgentSmem {
 };
 static_assert(sizeof(AgentSmem) % 16 == 0, "agent block keeps 16-byte alignment");
 
+// A 128-bit bitmap as two words (the price ladder's non-empty levels).
+struct Bm128 {
+    unsigned long long lo, hi;
+};
+
 // ---------------------------------------------------------------- book side
 // Pool slot s of a side belongs to one lane, which scans it in its register
 // index r:  K <= 8: s = lane*K + r, with the slot's price and id kept in
@@ -294,6 +299,10 @@ struct Side {
     int n;              // live orders (warp-uniform)
     int fpx, fqty, fslot;  // front order (position 0), valid when n > 0
     long long fid;
+    // price-ladder form (lob_ladder.cuh): bitmap of non-empty levels and the
+    // worst resting price, warp-uniform, valid when n > 0
+    Bm128 bm;
+    int wpx;
 };
 
 template <int K> __device__ __forceinline__ int slot_of(int lane, int r) {
@@ -1227,6 +1236,79 @@ __device__ __forceinline__ void widen_tile(DevMsg *tile, int count, int lane) {
     __syncwarp();
 }
 
+}  // namespace lobk
+#include "lob_ladder.cuh"
+namespace lobk {
+static_assert(LW == 128, "Side<K>::bm holds the ladder bitmap");
+
+// Book operations in the env's current form: the price ladder while `lad`
+// holds (LADC: the instance has a ladder), else the sorted index.
+template <int K, bool RBID, bool TRACE, bool MA, bool LADC>
+__device__ __forceinline__ int book_take(Side<K> &O, PoolSmem<K> &P, LadBlock<K> *lb, bool lad, bool has_limit,
+                                         int limit, int q, long long taker_id, int taker_side, Ctx &c, int lane) {
+    if constexpr (LADC) {
+        if (lad) return lad_take<K, RBID, TRACE, MA>(O, P, lb->s[RBID ? 0 : 1], has_limit, limit, q, taker_id,
+                                                     taker_side, c, lane);
+    }
+    return side_take<K, RBID, TRACE, MA>(O, P, has_limit, limit, q, taker_id, taker_side, c, lane);
+}
+// Rest on side S (BID: bids); O is the other side.  An order the ladder
+// cannot hold converts the env to the sorted index first.
+template <int K, bool BID, bool LADC>
+__device__ __forceinline__ void book_rest(Side<K> &S, Side<K> &O, PoolSmem<K> &P, LadBlock<K> *lb, bool &lad, int cap,
+                                          int p, int q, long long oid, Ctx &c, int lane) {
+    if constexpr (LADC) {
+        if (lad) {
+            if (lad_rest<K, BID>(S, P, lb->s[BID ? 0 : 1], cap, p, q, oid, c, lane)) return;
+            lad_to_index<K, BID>(S, lb->s[BID ? 0 : 1], lb->inv, lane);
+            lad_to_index<K, !BID>(O, lb->s[BID ? 1 : 0], lb->inv, lane);
+            lad = false;
+        }
+    }
+    side_rest<K, BID>(S, P, cap, p, q, oid, c, lane);
+}
+template <int K, bool BID, bool LADC>
+__device__ __forceinline__ void book_cancel(Side<K> &S, PoolSmem<K> &P, LadBlock<K> *lb, bool lad, int type, int p,
+                                            int qty, long long oid, Ctx &c, int lane) {
+    if constexpr (LADC) {
+        if (lad) {
+            lad_cancel<K, BID>(S, P, lb->s[BID ? 0 : 1], type, p, qty, oid, c, lane);
+            return;
+        }
+    }
+    side_cancel<K>(S, P, type, p, qty, oid, c, lane);
+}
+template <int K, bool BID, bool LADC>
+__device__ __forceinline__ void book_cancel_set(Side<K> &S, PoolSmem<K> &P, LadBlock<K> *lb, bool lad,
+                                                unsigned cmask, Ctx &c, int lane) {
+    if constexpr (LADC) {
+        if (lad) {
+            lad_cancel_set<K, BID>(S, P, lb->s[BID ? 0 : 1], cmask, c, lane);
+            return;
+        }
+    }
+    side_cancel_set<K>(S, P, cmask, c, lane);
+}
+template <int K, bool BID, bool LADC>
+__device__ __forceinline__ int book_levels(const Side<K> &S, const PoolSmem<K> &P, LadBlock<K> *lb, bool lad, int L,
+                                           int *lvl_px, long long *lvl_q, long long &own0, long long &own1, int lane) {
+    if constexpr (LADC) {
+        if (lad) return lad_levels<K, BID>(S, P, lb->s[BID ? 0 : 1], L, lvl_px, lvl_q, own0, own1, lane);
+    }
+    return side_levels<K>(S, P, L, lvl_px, lvl_q, own0, own1, lane);
+}
+template <int K, bool BID, bool LADC>
+__device__ __forceinline__ void book_store(const Side<K> &S, const PoolSmem<K> &P, LadBlock<K> *lb, bool lad,
+                                           unsigned char *blk, int lane) {
+    if constexpr (LADC) {
+        if (lad) {
+            lad_store<K, BID>(S, P, lb->s[BID ? 0 : 1], lb->inv, blk, lane);
+            return;
+        }
+    }
+    side_store<K, BID>(S, P, blk, lane);
+}
+
 // Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
@@ -1238,8 +1320,13 @@ struct MsgPipe {
 // one is set.  MA (which implies EXT) runs 2P agents with their state in the
 // warp's agent block agp; without it the agents are the benchmark pair.
 template <int K, bool TRACE, bool EXT, bool MA>
-__device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp, MsgPipe &pipe, int lane) {
+__device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp, LadBlock<K> *lb, MsgPipe &pipe,
+                        int lane) {
     constexpr bool XT = EXT || MA;
+    // the price-ladder form for every untraced instance of the register-pool
+    // classes (traces record the book after every message in the sorted form)
+    constexpr bool LADC = !TRACE && ladder_class<K>();
+    bool lad = false;
     EnvState *st = p.st + e;
     const bool uni = p.uni_cap > 0;
     const int cap = uni ? p.uni_cap : p.caps[e];
@@ -1341,6 +1428,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             __syncwarp();
             front_refresh<K>(bid, sm.pool[0]);
             front_refresh<K>(ask, sm.pool[1]);
+            if constexpr (LADC) {
+                const bool okb = lad_build<K, true>(bid, sm.pool[0], lb->s[0], lane);
+                const bool oka = lad_build<K, false>(ask, sm.pool[1], lb->s[1], lane);
+                lad = okb && oka;   // else both sides keep the sorted index of the load
+            }
             need_load = false;
         }
         c.msg_idx = 0;
@@ -1372,8 +1464,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                                           snap_n, snap_bytes);
                 }
             } else {
-                side_cancel_set<K>(bid, sm.pool[0], cm_b, c, lane);
-                side_cancel_set<K>(ask, sm.pool[1], cm_a, c, lane);
+                book_cancel_set<K, true, LADC>(bid, sm.pool[0], lb, lad, cm_b, c, lane);
+                book_cancel_set<K, false, LADC>(ask, sm.pool[1], lb, lad, cm_a, c, lane);
             }
             ns = agent_orders_ma(p, t, seed, ag, c, lane);
             c.seq_next += ns;
@@ -1468,8 +1560,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                                           snap_n, snap_bytes);
                 }
             } else {
-                side_cancel_set<K>(bid, sm.pool[0], cm_b, c, lane);
-                side_cancel_set<K>(ask, sm.pool[1], cm_a, c, lane);
+                book_cancel_set<K, true, LADC>(bid, sm.pool[0], lb, lad, cm_b, c, lane);
+                book_cancel_set<K, false, LADC>(ask, sm.pool[1], lb, lad, cm_a, c, lane);
             }
             // orders to send (wanted minus kept), Fisher-Yates shuffled
             int sa[3] = {0, 0, 0}, ss[3] = {0, 0, 0}, sp[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
@@ -1617,22 +1709,26 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                         c.c_add_vol += qty;
                         if (didx == 0) {
                             if (ask.n > 0 && px >= ask.fpx)
-                                qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
-                            if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                                qty = book_take<K, false, TRACE, MA, LADC>(ask, sm.pool[1], lb, lad, true, px, qty, oid,
+                                                                          LOB_BUY, c, lane);
+                            if (qty > 0) book_rest<K, true, LADC>(bid, ask, sm.pool[0], lb, lad, cap, px, qty, oid, c, lane);
                         } else {
                             if (bid.n > 0 && px <= bid.fpx)
-                                qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
-                            if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                                qty = book_take<K, true, TRACE, MA, LADC>(bid, sm.pool[0], lb, lad, true, px, qty, oid,
+                                                                         LOB_SELL, c, lane);
+                            if (qty > 0) book_rest<K, false, LADC>(ask, bid, sm.pool[1], lb, lad, cap, px, qty, oid, c, lane);
                         }
                     } else if (didx < 6) {
-                        if ((didx & 1) == 0) side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
-                        else side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+                        if ((didx & 1) == 0) book_cancel<K, true, LADC>(bid, sm.pool[0], lb, lad, type, px, qty, oid, c, lane);
+                        else book_cancel<K, false, LADC>(ask, sm.pool[1], lb, lad, type, px, qty, oid, c, lane);
                     } else if (didx < 8) {
                         c.c_mkt_vol += qty;
                         if (didx == 6)
-                            c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
+                            c.c_mkt_disc += book_take<K, false, TRACE, MA, LADC>(ask, sm.pool[1], lb, lad, false, 0, qty,
+                                                                                 oid, LOB_BUY, c, lane);
                         else
-                            c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
+                            c.c_mkt_disc += book_take<K, true, TRACE, MA, LADC>(bid, sm.pool[0], lb, lad, false, 0, qty,
+                                                                                oid, LOB_SELL, c, lane);
                     } else {
                         c.c_bad += 1;
                         c.status |= ST_BADMSG;
@@ -1652,7 +1748,14 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         if (timed_out) break;
 #ifdef LOB_CHECKED
         {
-            bool ok = book_ok<K, true>(bid, sm.pool[0], cap, lane) && book_ok<K, false>(ask, sm.pool[1], cap, lane);
+            bool ok;
+            if constexpr (LADC) {
+                ok = lad ? (lad_ok<K, true>(bid, sm.pool[0], lb->s[0], lb->inv, cap, lane) &&
+                            lad_ok<K, false>(ask, sm.pool[1], lb->s[1], lb->inv, cap, lane))
+                         : (book_ok<K, true>(bid, sm.pool[0], cap, lane) && book_ok<K, false>(ask, sm.pool[1], cap, lane));
+            } else {
+                ok = book_ok<K, true>(bid, sm.pool[0], cap, lane) && book_ok<K, false>(ask, sm.pool[1], cap, lane);
+            }
             if (bid.n > 0 && ask.n > 0 && bid.fpx >= ask.fpx) ok = false;   // never crossed after a message
             if (!ok) c.status |= ST_CHECK;
         }
@@ -1683,8 +1786,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             }
             __syncwarp();
             long long own0 = 0, own1 = 0;
-            const int nlb = side_levels<K>(bid, sm.pool[0], L, sm.lvl_px[0], sm.lvl_q[0], own0, own1, lane);
-            const int nla = side_levels<K>(ask, sm.pool[1], L, sm.lvl_px[1], sm.lvl_q[1], own0, own1, lane);
+            const int nlb = book_levels<K, true, LADC>(bid, sm.pool[0], lb, lad, L, sm.lvl_px[0], sm.lvl_q[0], own0, own1, lane);
+            const int nla = book_levels<K, false, LADC>(ask, sm.pool[1], lb, lad, L, sm.lvl_px[1], sm.lvl_q[1], own0, own1, lane);
             const long long bb = bid.n ? bid.fpx : c.last_px;
             const long long ba = ask.n ? ask.fpx : c.last_px;
             const long long s2 = bb + ba;
@@ -1838,8 +1941,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 int4 *dst = reinterpret_cast<int4 *>(blk);
                 for (long long i = lane; i < p.ep_block / 16; i += 32) dst[i] = src[i];
             } else {
-                side_store<K, true>(bid, sm.pool[0], blk, lane);
-                side_store<K, false>(ask, sm.pool[1], blk, lane);
+                book_store<K, true, LADC>(bid, sm.pool[0], lb, lad, blk, lane);
+                book_store<K, false, LADC>(ask, sm.pool[1], lb, lad, blk, lane);
             }
         }
     }
@@ -1884,9 +1987,13 @@ __device__ __forceinline__ void env_steps_body(const KParams &p) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WarpSmem<K> &sm = reinterpret_cast<WarpSmem<K> *>(smem_raw)[wib];
-    // several agents: the warp's agent block follows the block's WarpSmem array
-    AgentSmem *agp = MA ? reinterpret_cast<AgentSmem *>(smem_raw + (blockDim.x >> 5) * sizeof(WarpSmem<K>)) + wib
-                        : nullptr;
+    // after the block's WarpSmem array: the warps' ladder blocks (register-pool
+    // classes), then (several agents) the warps' agent blocks
+    const int nw = blockDim.x >> 5;
+    unsigned char *after = smem_raw + nw * sizeof(WarpSmem<K>);
+    LadBlock<K> *lb = ladder_class<K>() ? reinterpret_cast<LadBlock<K> *>(after) + wib : nullptr;
+    after += nw * ladder_bytes<K>();
+    AgentSmem *agp = MA ? reinterpret_cast<AgentSmem *>(after) + wib : nullptr;
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -1896,14 +2003,14 @@ __device__ __forceinline__ void env_steps_body(const KParams &p) {
     MsgPipe pipe{0u};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, pipe, lane);
+        if (w < p.n_list) run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, pipe, lane);
+            run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
         }
     }
 }

@@ -54,6 +54,7 @@ EXPORTS = [
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
     "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
+    "lob_live_orders",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
@@ -165,6 +166,7 @@ def _load():
         "lob_get_agents": (ctypes.c_int, [P, P, P]),
         "lob_get_env_misc": (ctypes.c_int, [P, P, P]),
         "lob_get_actions": (ctypes.c_int, [P, P, P]),
+        "lob_live_orders": (ctypes.c_int, [P, P, P]),
         "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
         "lob_sync": (ctypes.c_int, [P, P]),
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
@@ -294,6 +296,11 @@ def lob_get_env_misc(h, out, stream=None):
 
 def lob_get_actions(h, out, stream=None):
     return _check(_load().lob_get_actions(h, _dp(out), _stream(stream)), "lob_get_actions")
+
+
+def lob_live_orders(h, acc, stream=None):
+    """Adds the resting orders of every env (bids + asks) to the int64 device scalar acc."""
+    return _check(_load().lob_live_orders(h, _dp(acc), _stream(stream)), "lob_live_orders")
 
 
 def lob_set_trace(h, fills=None, fill_cap=0, fill_counts=None, snaps=None, snap_cap=0, snap_count=None):

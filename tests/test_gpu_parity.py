@@ -643,3 +643,52 @@ def test_misaligned_message_buffer_rejected():
         env.load_messages(raw[8:], off)
     assert ei.value.code == lob.LOB_EINVAL
     env.close()
+
+
+@pytest.mark.parametrize("price_p,cap", [(0.02, 100), (0.05, 200), (0.1, 100), (0.05, 8)])
+def test_wide_price_spans_leave_the_ladder(price_p, cap):
+    """Add prices spread over hundreds of ticks: many sides come to span more
+    than the step kernel's 128-tick price ladder, so envs switch to the
+    sorted-index form in the middle of a step (and later steps start in it
+    when the loaded book is already that wide), while others stay on the
+    ladder.  Every step must still match the oracle."""
+    n, T = 33, 12
+    model = mbogen.MessageModel(price_p=price_p, msgs_per_step=80)
+    st = mbogen.generate(model, mbogen.env_seeds(300 + int(price_p * 100) + cap, n), T)
+    pr = Pair(n, st, cap=cap, exec_target=100, fill_cap=512)
+    for _ in range(T):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+    pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_ladder_window_edge_by_hand(side):
+    """One env, no agents: orders at 127 ticks from the best still fit the
+    ladder; one at 128 ticks converts the env to the sorted form in the middle
+    of the step; a sweep, cancels and rests follow in both forms.  The book and
+    fills after every step equal the oracle's."""
+    from conftest import single_env_stream
+    import types
+    s = side
+    far, edge = 10_000 - s * 127, 10_000 - s * 128
+    steps = [
+        # type, side, px, qty, oid
+        [(1, s, 10_000, 5, 1), (1, s, far, 5, 2), (1, s, 10_000 - s * 60, 7, 3), (1, s, far, 2, 4)],
+        [(1, s, edge, 3, 5), (1, s, 10_000 - s * 5, 4, 6), (2, s, far, 1, 2), (3, s, 10_000, 0, 1)],
+        [(4, -s, 0, 20, 7), (1, s, 10_000 - s * 3, 9, 8), (1, -s, 10_000 + s * 50, 6, 9)],
+        [(1, -s, edge, 30, 10), (1, s, 10_000, 2, 11)],
+    ]
+    msgs, off = single_env_stream(steps)
+    st = types.SimpleNamespace(msgs=msgs, offsets=off, seeds=np.array([5], np.uint64))
+    pr = Pair(1, st, n_agents=0, cap=100, fill_cap=64)
+    for _ in range(len(steps)):
+        pr.step()
+        pr.check_outputs()
+        pr.check_fills()
+        pr.check_state()
+    assert pr.env.sync() == 0
+    pr.close()
