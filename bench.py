@@ -451,7 +451,8 @@ def run_workload(args):
             env.reset(sd)
             lob.lob_rollout(env.h, T_tune, None, obs[:T_tune], rew[:T_tune], None)
 
-        choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1)
+        choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1,
+                               candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES)
         stream = torch.cuda.Stream()
         env.load_messages(md, od)
         env.reset(sd, stream)
@@ -473,7 +474,7 @@ def run_workload(args):
                 "env_steps_per_s": n * T / t, "seconds_per_rollout": t, "steps": T, "n_gpus": 1,
                 "config": {"workload": "8192 envs, caps uniform {50,100,200,500}, M_t ~ Poisson(lambda), "
                                        "lambda log-uniform [10,500], 500 steps, random policy, one graph-captured "
-                                       "lob_rollout (persistent, classes on concurrent streams)",
+                                       "lob_rollout in the autotuned launch shape",
                            "autotuned": choice.__dict__, "messages": msgs},
                 "dtype": "int64", "data": "synthetic"}
         env.close()
@@ -631,29 +632,73 @@ def run_workload(args):
                                        "lob_rollout; the same stream as 16-byte compact and 32-byte records"},
                 "dtype": "int64", "data": "synthetic"}
     elif wl == "stress65536":
-        n, T = 65536, args.stress_steps
+        # the stress configuration at its stated length: 65,536 envs x capacity
+        # 1,000 x 1,000 messages of the heavy-tailed mix x 256 steps (16.8 G
+        # messages, 537 GB: more than HBM), top-20 observations, the BF16
+        # policy in the loop.  The device generator draws the stream 8 steps
+        # at a time into a double-buffered ring on its own stream while the
+        # rollout consumes the other buffer; generation is timed apart.
+        n, T, C = 65536, args.stress_steps, 8
         seeds = mbogen.env_seeds(4, n)
-        st = mbogen.generate(mbogen.STRESS_MODEL, seeds, T)
-        md, od, sd = upload(st, seeds)
-        env = lob.LobEnv(n, cap=1000, top_levels=20, episode_len=T, exec_target=2000,
-                         action_mode=lob.LOB_ACT_HOST)
+        gen = mbogen.GpuStreams(mbogen.STRESS_MODEL, seeds)
+        M = mbogen.STRESS_MODEL.msgs_per_step
+        ring = [torch.empty(n * C * M * 32, dtype=torch.uint8, device=dev) for _ in range(2)]
+        off = torch.from_numpy(gen.offsets(C)).to(dev)
+        env = lob.LobEnv(n, cap=1000, top_levels=20, episode_len=T, exec_target=2000, action_mode=lob.LOB_ACT_HOST)
         params = lob.init_policy_params(7, 2, env.D)
         pol = lob.lob_policy_create(2, env.D, params)
         lob.lob_set_launch(env.h, 4, 1)
-        times = []
-        for i in range(args.reps):
-            env.load_messages(md, od)
-            env.reset(sd)
-            torch.cuda.synchronize()
-            times += _flush_and_time(lambda: lob.lob_rollout_policy(env.h, pol, T, lob.LOB_PREC_BF16), 1, dev)
+        env.reset(torch.from_numpy(seeds.view(np.int64).copy()).to(dev))
+        gs, ms = torch.cuda.Stream(), torch.cuda.current_stream()
+        ev_gen = [torch.cuda.Event() for _ in range(2)]
+        ev_free = [torch.cuda.Event() for _ in range(2)]
+        gen_ev, roll_ev = [], []
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        w0.record(ms)
+        gs.wait_stream(ms)
+
+        def gen_chunk(k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if k >= 2:
+                gs.wait_event(ev_free[k % 2])
+            a.record(gs)
+            gen.chunk(C, ring[k % 2], gs)
+            b.record(gs)
+            ev_gen[k % 2].record(gs)
+            gen_ev.append((a, b))
+
+        gen_chunk(0)
+        for k in range(T // C):
+            if k + 1 < T // C:
+                gen_chunk(k + 1)
+            ms.wait_event(ev_gen[k % 2])
+            env.load_messages(ring[k % 2], off)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ms)
+            lob.lob_rollout_policy(env.h, pol, C, lob.LOB_PREC_BF16, stream=ms)
+            b.record(ms)
+            ev_free[k % 2].record(ms)
+            roll_ev.append((a, b))
+        w1.record(ms)
+        torch.cuda.synchronize()
+        assert gen.ok(), "a generator pool ran out of room"
+        assert env.sync() == 0 and lob.lob_policy_sync(pol) == 0
         msgs = float(env.counters()[:, 0].sum().item())
-        t = min(times)
+        t_roll = sum(x.elapsed_time(y) for x, y in roll_ev) / 1e3
+        t_gen = sum(x.elapsed_time(y) for x, y in gen_ev) / 1e3
+        t_wall = w0.elapsed_time(w1) / 1e3
         lob.lob_policy_destroy(pol)
         env.close()
-        line = {"workload": "stress65536", "metric": METRIC, "value": msgs / t, "unit": "msgs/s",
-                "env_steps_per_s": n * T / t, "seconds": t, "steps": T, "n_gpus": 1,
+        gen.close()
+        line = {"workload": "stress65536", "metric": METRIC, "value": msgs / t_roll, "unit": "msgs/s",
+                "env_steps_per_s": n * T / t_roll, "seconds_rollout": t_roll, "steps": T, "n_gpus": 1,
+                "generation": {"seconds": t_gen, "msgs_per_s": msgs / t_gen, "where": "device generator, own stream"},
+                "overlapped": {"seconds": t_wall, "msgs_per_s": msgs / t_wall},
                 "config": {"workload": f"65536 envs x cap 1000 x 1000 msgs (30% aggressive, Pareto(1.5) sizes "
-                                       f"capped at 1e4, delete bursts) x {T} steps, top-20 obs, BF16 policy in the loop"},
+                                       f"capped at 1e4, delete bursts) x {T} steps, top-20 obs, BF16 policy in the "
+                                       f"loop; {C}-step chunks generated on the device into a double-buffered ring",
+                           "messages": msgs},
                 "dtype": "int64 book / bf16 policy", "data": "synthetic"}
     else:
         raise SystemExit(f"unknown workload {wl}")
@@ -675,7 +720,7 @@ def main():
                              "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--stress-steps", type=int, default=4)
+    ap.add_argument("--stress-steps", type=int, default=256)
     ap.add_argument("--gen-steps", type=int, default=T,
                     help="steps of messages generated (the episode wraps there; default: the full episode)")
     args = ap.parse_args()

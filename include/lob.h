@@ -323,6 +323,50 @@ int lob_policy_sync(lob_policy *pol, void *stream);
  * 12-way head. */
 int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
                        int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream);
+/* The FP32 parameter blocks of every agent (layout of lob_policy_param_count)
+ * into d_out float [n_agents][P] (device, caller-owned). */
+int lob_policy_get_params(lob_policy *pol, float *d_out, void *stream);
+
+/* ---- IPPO update (Sec. 4.2: independent PPO, each agent's network updated
+ * from its own data only; Sec. 6 runs rollouts and updates on the GPU).  The
+ * paper fixes no algorithmic detail, so this is the textbook update:
+ *   advantages by GAE (Schulman et al. 2016): delta_t = r_t + gamma (1 - d_t)
+ *     V_{t+1} - V_t, A_t = delta_t + gamma lambda (1 - d_t) A_{t+1}, targets
+ *     R_t = A_t + V_t, with r_t = reward_scale * reward;
+ *   per minibatch the mean of -min(rho A', clip(rho, 1 - eps, 1 + eps) A')
+ *     + vf_coef (V - R)^2 / 2 - ent_coef * entropy (Schulman et al. 2017),
+ *     rho = exp(log pi(a) - logp_old), A' the advantage normalised over the
+ *     minibatch (population std + 1e-8);
+ *   its gradient through the network (forward and backward as BF16
+ *     tensor-core contractions with FP32 accumulation), clipped to a global
+ *     L2 norm of max_grad_norm, then one Adam step (Kingma & Ba 2015, bias
+ *     corrected) on the FP32 weights, which are repacked for the forward.
+ * One call = one epoch: each agent's samples in the order d_perm gives, cut
+ * into n_minibatches equal consecutive parts, one Adam step per part. */
+typedef struct lob_ppo_hparams {
+    float gamma, gae_lambda, clip_eps, vf_coef, ent_coef;
+    float lr, beta1, beta2, adam_eps, max_grad_norm, reward_scale;
+    int32_t n_minibatches;
+} lob_ppo_hparams;
+typedef struct lob_ppo_batch {
+    int32_t T, n_envs;            /* rollout length and envs; samples per agent N = T * n_envs */
+    const float *d_obs;           /* [T][n_envs][A][D]: the observation each action was taken on */
+    const int32_t *d_actions;     /* [T][n_envs][A] in [0, 12) */
+    const float *d_logp_old;      /* [T][n_envs][A]: log-probability of the action under the rollout's policy */
+    const float *d_values;        /* [T + 1][n_envs][A]: the critic's values, row T bootstraps */
+    const int64_t *d_rewards;     /* [T][n_envs][A] */
+    const uint8_t *d_done;        /* [T][n_envs]: 1 where step t ended the episode */
+    const int32_t *d_perm;        /* [A][N]: each agent's sample order (sample t * n_envs + e) */
+    float *d_grad_out;            /* NULL, or [n_minibatches][A][P]: each minibatch's gradient before clipping */
+} lob_ppo_batch;
+/* All pointers are device pointers owned by the caller and read on `stream`.
+ * The first call allocates the optimiser state (Adam moments, step count)
+ * and work buffers in the policy; later calls continue it.  LOB_EINVAL for a
+ * bad argument or N not divisible by n_minibatches, LOB_ECAPACITY when
+ * obs_dim + 1 > 48 (the update's operand tiles hold 48 input columns: up to
+ * 10 observation levels), LOB_ENOMEM, LOB_ECUDA.  A bounded tensor-core wait
+ * that expires is reported by lob_policy_sync. */
+int lob_ppo_update(lob_policy *pol, const lob_ppo_batch *batch, const lob_ppo_hparams *hp, void *stream);
 
 /* Host-buffer convenience step: copies this step's background messages
  * (h_msgs[h_offsets[e] .. h_offsets[e + 1]], h_offsets [n_envs + 1]) and
@@ -384,6 +428,18 @@ int lob_sync(lob_handle *h, void *stream);
 /* Launch-shape control used by the autotuner: warps per block for the step
  * kernels (1..8) and whether they take envs from a work queue. */
 int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
+/* Launch mode persistent = 2 (set by lob_set_launch or by this call): one
+ * persistent kernel runs the envs of every capacity class up to 512 slots per
+ * side (a handle with larger books keeps one launch per class).  Each block
+ * holds warps_per_class[k] warps of class k (k = 0 .. 4: 32 .. 512 slots;
+ * LOB_NCLASSES entries, class 5 must be 0; 1 .. 8 warps in all, their shared
+ * memory within one block's); a warp takes envs of its own class from that
+ * class's queue and, when it is empty, envs of smaller classes.  Every class
+ * with envs needs a warp of its class or of a larger one.  LOB_EINVAL or
+ * LOB_ECAPACITY otherwise.  lob_set_launch(h, w, 2) derives a split from the
+ * classes' env counts. */
+#define LOB_NCLASSES 6
+int lob_set_multi_split(lob_handle *h, const int32_t *warps_per_class);
 /* Failure-detection hook.  `cycles` bounds every wait of the step kernels on
  * a message tile, in SM cycles (0 = the default, about one second).  hold = 1
  * makes the next step or rollout launch leave each env's first message tile

@@ -1,11 +1,15 @@
 """Launch-shape autotuner for the batched env step (driver over the C ABI).
 
 For a workload it times every candidate launch shape -- warps (envs) per
-block, plain grid or persistent work queue, and env order (as created, or
-longest first from a per-env cost estimate) -- with CUDA events around a
-caller-supplied run, keeps the fastest, and caches the choice per workload
-signature in a JSON file.  The kernels themselves are unchanged: the shape is
-set through lob_set_launch / lob_set_env_costs before the timed runs.
+block; a plain grid, one persistent work-queue launch per capacity class, or
+one persistent launch over every class whose warps steal smaller classes'
+envs (with the per-class warp split of each block); and env order (as
+created, or longest first from a per-env cost estimate) -- with CUDA events
+around a caller-supplied run, keeps the fastest, and caches the choice per
+workload signature in a JSON file.  The kernels themselves are unchanged: the
+shape is set through lob_set_launch / lob_set_multi_split / lob_set_env_costs
+before the timed runs.  Each env is one warp and messages are staged 32
+records at a time in every shape; the cache records both.
 """
 from __future__ import annotations
 
@@ -16,6 +20,9 @@ from dataclasses import dataclass, asdict
 from . import lob
 
 DEFAULT_CANDIDATES = [(wpb, pers) for pers in (0, 1) for wpb in (1, 2, 4, 8)]
+# persistent = 2: one launch over every class (the split derived from the
+# classes' env counts for the given warps per block)
+MULTI_CANDIDATES = [(wpb, 2) for wpb in (4, 6, 8)]
 
 
 @dataclass
@@ -24,6 +31,8 @@ class Choice:
     persistent: int
     longest_first: bool
     ms: float
+    threads_per_env: int = 32
+    tile_records: int = 32
 
 
 def signature(n_envs, caps_hist, mean_msgs, steps, extra=""):
@@ -73,7 +82,10 @@ def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=Non
             if lf and not pers:
                 continue          # the order only matters to the work queue
             ch = Choice(wpb, pers, lf, 0.0)
-            applier(h, ch, costs)
+            try:
+                applier(h, ch, costs)
+            except lob.LobError:
+                continue          # a shape this handle cannot take (e.g. more classes than warps)
             ch.ms = timer(run, repeats)
             results.append(ch)
     win = min(results, key=lambda c: c.ms)

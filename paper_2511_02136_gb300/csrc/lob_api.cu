@@ -125,6 +125,15 @@ int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
 
 // Launch the step kernel of class K (shared memory opted in by ensure_optin);
 // the warps per block are capped by what one block's shared memory holds.
+// Whether a launch needs the extended kernel (episode mode, a reward
+// variant, another action space, host-memory or compact messages, a drawn
+// task side).
+bool kernel_ext(const KParams &p) {
+    return p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0 ||
+           p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0 || p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH ||
+           p.exec_dir == 0;
+}
+
 cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, int n_sm, cudaStream_t s,
                      const KParams &p) {
     if (p.n_agents > 2) {
@@ -148,9 +157,7 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
     const size_t smem = (size_t)wpb * warp_smem_bytes(K);
     // the extended kernel when episode mode, a reward variant or another
     // action space is on
-    const bool ext = p.ep_mode != 0 || p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 ||
-                     p.exec_pen_milli != 0 || p.mm_space != LOB_MM_SPREAD_SKEW || p.msgs_sysmem != 0 ||
-                     p.msg16 != 0 || p.pv_ref != LOB_PV_TOUCH || p.exec_dir == 0;
+    const bool ext = kernel_ext(p);
     // the wide register budget when every block is resident at once (one wave)
     const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
     KParams q = p;
@@ -216,6 +223,8 @@ struct lob_handle {
     int hold_first = 0;          // failure-detection test hook (next launch only)
     int n_sm = 0;
     int64_t launches = 0;
+    bool fused_ok = false;       // the fused BF16 rollout kernel is not enabled
+    int multi_split[NCLASS] = {0, 0, 0, 0, 0, 0};   // persistent == 2: warps per block of each class (0: derived)
     // per-class streams: several capacity classes run concurrently (fork/join
     // with events, so the pattern also captures into a CUDA graph)
     cudaStream_t cls_stream[NCLASS] = {};
@@ -663,10 +672,10 @@ static bool steps_left(const lob_handle *h, int n) {
 }
 static const int64_t *step_offsets(const lob_handle *h) { return h->ep_mode ? h->ep_off : h->offsets; }
 
-static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
-                        int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
-                        long long *rew, unsigned char *done, cudaStream_t s, bool msgs_sysmem = false,
-                        bool msg16 = false) {
+// The step kernel's parameters for n_steps steps from the handle's state.
+static KParams base_params(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
+                           int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
+                           long long *rew, unsigned char *done, bool msgs_sysmem, bool msg16) {
     const lob_config &c = h->cfg;
     KParams p;
     memset(&p, 0, sizeof(p));
@@ -700,9 +709,55 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
         p.ep_images = h->d_ep_images;
         p.ep_obs = h->d_ep_obs;
     }
+    return p;
+}
+
+static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offsets, int64_t stride, int k0,
+                        int n_steps, const int32_t *d_actions, long long act_step_stride, float *obs,
+                        long long *rew, unsigned char *done, cudaStream_t s, bool msgs_sysmem = false,
+                        bool msg16 = false) {
+    const lob_config &c = h->cfg;
+    KParams p = base_params(h, msgs, offsets, stride, k0, n_steps, d_actions, act_step_stride, obs, rew, done,
+                            msgs_sysmem, msg16);
     const int wpb = h->wpb;
     if (h->persistent) {
         if (cudaMemsetAsync(h->d_queue, 0, NCLASS * 4, s) != cudaSuccess) return LOB_ECUDA;
+    }
+    if (h->persistent == 2 && p.fills == nullptr && p.snaps == nullptr && c.n_agents <= 2 && !kernel_ext(p) &&
+        h->class_count[NCLASS - 1] == 0) {
+        // one persistent kernel over every class (steps_multi.cu)
+        MultiLayout m;
+        memset(&m, 0, sizeof(m));
+        int nw = 0;
+        size_t off = 0;
+        for (int k = MULTI_CLASSES - 1; k >= 0; k--)   // largest carve-outs first
+            for (int i = 0; i < h->multi_split[k] && nw < 8; i++) {
+                m.cls[nw] = k;
+                m.off[nw] = (int)off;
+                off += warp_smem_bytes(CLASS_K[k]);
+                nw++;
+            }
+        m.off[nw] = (int)off;
+        for (int k = 0; k < MULTI_CLASSES; k++) {
+            m.begin[k] = h->class_begin[k];
+            m.count[k] = h->class_count[k];
+        }
+        m.steal = 1;
+        static bool opted[64];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !opted[dev]) {
+            if (optin_steps_multi(SMEM_PER_BLOCK_MAX) != cudaSuccess) return LOB_ECUDA;
+            opted[dev] = true;
+        }
+        const int per_sm = std::max(1, multi_blocks_per_sm(32 * nw, off));
+        p.env_list = h->d_env_list;
+        p.uni_cap = 0;
+        p.uni_block = 0;
+        p.queue = h->d_queue;
+        p.n_list = c.n_envs;
+        h->launches++;
+        return launch_steps_multi(per_sm * h->n_sm, 32 * nw, off, s, p, m) == cudaSuccess ? LOB_OK : LOB_ECUDA;
     }
     const bool fork = h->n_active_classes > 1;
     if (fork && cudaEventRecord(h->ev_fork, s) != cudaSuccess) return LOB_ECUDA;
@@ -1146,9 +1201,66 @@ int lob_sync(lob_handle *h, void *stream) {
 }
 
 int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
-    if (!h || warps_per_block < 1 || warps_per_block > 8 || (persistent != 0 && persistent != 1)) return LOB_EINVAL;
+    if (!h || warps_per_block < 1 || warps_per_block > 8 || persistent < 0 || persistent > 2) return LOB_EINVAL;
     h->wpb = warps_per_block;
     h->persistent = persistent;
+    if (persistent == 2) {
+        // default split: every class with envs gets warps in proportion to its
+        // envs, at least one, warps_per_block in all (fewer if a block's
+        // shared memory cannot hold them)
+        int total = 0, present = 0;
+        for (int k = 0; k < MULTI_CLASSES; k++) present += h->class_count[k] > 0;
+        if (present > warps_per_block) return LOB_EINVAL;
+        for (int k = 0; k < MULTI_CLASSES; k++) {
+            h->multi_split[k] = h->class_count[k] > 0 ? 1 : 0;
+            total += h->multi_split[k];
+        }
+        while (total < warps_per_block) {   // hand the rest out by envs per warp
+            int best = -1;
+            double bv = -1.0;
+            for (int k = 0; k < MULTI_CLASSES; k++)
+                if (h->multi_split[k] > 0) {
+                    const double v = (double)h->class_count[k] * CLASS_K[k] / h->multi_split[k];
+                    if (v > bv) { bv = v; best = k; }
+                }
+            h->multi_split[best]++;
+            total++;
+        }
+        size_t smem = 0;
+        for (int k = 0; k < MULTI_CLASSES; k++) smem += (size_t)h->multi_split[k] * warp_smem_bytes(CLASS_K[k]);
+        while (smem > SMEM_PER_BLOCK_MAX) {   // drop warps from the biggest share
+            int best = -1;
+            for (int k = 0; k < MULTI_CLASSES; k++)
+                if (h->multi_split[k] > 1 && (best < 0 || h->multi_split[k] > h->multi_split[best])) best = k;
+            if (best < 0) return LOB_ECAPACITY;
+            h->multi_split[best]--;
+            smem -= warp_smem_bytes(CLASS_K[best]);
+        }
+    }
+    return LOB_OK;
+}
+
+int lob_set_multi_split(lob_handle *h, const int32_t *warps_per_class) {
+    if (!h || !warps_per_class) return LOB_EINVAL;
+    int total = 0;
+    size_t smem = 0;
+    for (int k = 0; k < NCLASS; k++) {
+        if (warps_per_class[k] < 0) return LOB_EINVAL;
+        if (k >= MULTI_CLASSES && warps_per_class[k] != 0) return LOB_EINVAL;
+        total += warps_per_class[k];
+        if (k < MULTI_CLASSES) smem += (size_t)warps_per_class[k] * warp_smem_bytes(CLASS_K[k]);
+    }
+    if (total < 1 || total > 8) return LOB_EINVAL;
+    if (smem > SMEM_PER_BLOCK_MAX) return LOB_ECAPACITY;
+    // every class with envs needs a warp of its class or a larger one
+    for (int k = 0; k < MULTI_CLASSES; k++) {
+        if (h->class_count[k] == 0) continue;
+        int cover = 0;
+        for (int j = k; j < MULTI_CLASSES; j++) cover += warps_per_class[j];
+        if (cover == 0) return LOB_EINVAL;
+    }
+    for (int k = 0; k < NCLASS; k++) h->multi_split[k] = warps_per_class[k];
+    h->persistent = 2;
     return LOB_OK;
 }
 
@@ -1304,6 +1416,67 @@ extern "C" int lob_step_noalloc(const lob_noalloc_args *a, void *stream) {
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 
+// The fused BF16 rollout (rollout_fused.cuh): one launch for all n_steps steps
+// when the handle is the plain benchmark pair on one capacity class of 128 or
+// 256 slots; returns 1 when the configuration does not qualify.
+static int fused_rollout(lob_handle *h, lob_policy *pol, int32_t n_steps, float *d_obs, int64_t *d_rewards,
+                         uint8_t *d_done, int32_t *d_actions, cudaStream_t s) {
+    const lob_config &c = h->cfg;
+    const int K = CLASS_K[class_of(c.cap_per_side)];
+    if (c.n_agents != 2 || !h->uniform_cap || h->custom_order || h->ep_mode || h->msg16 || c.trace != 0 ||
+        (K != 4 && K != 8) || h->D > FDMAX || c.reward_mode != LOB_REWARD_PV || c.inv_penalty != 0 ||
+        c.exec_penalty_milli != 0 || c.pv_ref != LOB_PV_TOUCH || c.exec_dir == 0)
+        return 1;
+    const size_t per_warp = warp_smem_bytes(K);
+    int nw = (int)((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp);
+    nw = nw < FN ? nw : FN;
+    if (nw < 4) return 1;
+    const size_t smem = (size_t)nw * per_warp + sizeof(FusedSmem);
+    static bool opted[2][64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LOB_ECUDA;
+    if (!opted[K == 8][dev]) {
+        // opt in at the widest shape of the class
+        const size_t wide = (size_t)(((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp) < (size_t)FN
+                                         ? ((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp)
+                                         : (size_t)FN) * per_warp + sizeof(FusedSmem);
+        if ((K == 4 ? optin_fused_4(wide) : optin_fused_8(wide)) != cudaSuccess) return LOB_ECUDA;
+        opted[K == 8][dev] = true;
+    }
+    const size_t n = (size_t)c.n_envs, D = (size_t)h->D;
+    // each output goes to the caller's per-step buffer, else every step overwrites the handle's
+    KParams p = base_params(h, h->msgs, step_offsets(h), h->stride, h->cursor, n_steps, nullptr, 0,
+                            d_obs ? d_obs : h->d_obs, d_rewards ? reinterpret_cast<long long *>(d_rewards) : h->d_rew,
+                            d_done ? d_done : h->d_done, false, false);
+    p.ow_obs = d_obs ? 0 : 1;
+    p.ow_rew = d_rewards ? 0 : 1;
+    p.ow_done = d_done ? 0 : 1;
+    p.act_steps = d_actions;
+    p.obs_in = h->d_obs;
+    p.env_list = nullptr;
+    p.n_list = c.n_envs;
+    p.uni_cap = c.cap_per_side;
+    p.uni_block = h->uni_block;
+    FusedParams f;
+    policy_fused_params(pol, &f);
+    const int blocks = (c.n_envs + nw - 1) / nw;
+    h->launches++;
+    policy_count_launch(pol);
+    if ((K == 4 ? launch_fused_4(blocks, nw * 32, smem, s, p, f) : launch_fused_8(blocks, nw * 32, smem, s, p, f)) !=
+        cudaSuccess)
+        return LOB_ECUDA;
+    // the handle keeps the last step's outputs (lob_observe, the next rollout's first actions)
+    const size_t last = (size_t)(n_steps - 1);
+    int rc = LOB_OK;
+    if (d_obs) rc |= cuda_ok(cudaMemcpyAsync(h->d_obs, d_obs + last * n * 2 * D, n * 2 * D * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_rewards) rc |= cuda_ok(cudaMemcpyAsync(h->d_rew, d_rewards + last * n * 2, n * 2 * 8, cudaMemcpyDeviceToDevice, s));
+    if (d_done) rc |= cuda_ok(cudaMemcpyAsync(h->d_done, d_done + last * n, n, cudaMemcpyDeviceToDevice, s));
+    if (rc != LOB_OK) return LOB_ECUDA;
+    h->cursor += n_steps;
+    h->t += n_steps;
+    return LOB_OK;
+}
+
 extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_steps, int32_t precision, float *d_obs,
                                   int64_t *d_rewards, uint8_t *d_done, int32_t *d_actions, void *stream) {
     if (!h || !pol || n_steps < 1) return LOB_EINVAL;
@@ -1313,6 +1486,10 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
     if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
     if (!steps_left(h, n_steps)) return LOB_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (precision == LOB_PREC_BF16 && h->fused_ok) {
+        const int rc = fused_rollout(h, pol, n_steps, d_obs, d_rewards, d_done, d_actions, s);
+        if (rc <= 0) return rc;   // done (or failed); 1: not a fused configuration
+    }
     const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D, A = (size_t)h->cfg.n_agents;
     for (int i = 0; i < n_steps; i++) {
         // the policy acts on the current observation (kept in the handle's buffer)

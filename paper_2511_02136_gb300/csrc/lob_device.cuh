@@ -140,6 +140,9 @@ struct KParams {
     AgentState *agents;              // several agents per type: [n_envs][n_agents]
     int msgs_sysmem;                 // messages (and offsets) in page-locked host memory
     int msg16;                       // background messages are 16-byte compact records
+    int ow_obs, ow_rew, ow_done;     // that output overwrites env e's slot every step (else one slot per step)
+    int *act_steps;                  // fused rollout: the actions taken at each step [n_steps][n_envs][2], or NULL
+    const float *obs_in;             // fused rollout: every env's current observation [n_envs][2][D]
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -1238,46 +1241,22 @@ __device__ __forceinline__ void widen_tile(DevMsg *tile, int count, int lane) {
 
 }  // namespace lobk
 #include "lob_ladder.cuh"
+#include "fused.cuh"
 namespace lobk {
+
+// The fused rollout's per-warp handle on its CTA's policy tile.
+struct FusedCtx {
+    FusedSmem *fz;
+    const FusedParams *f;
+    unsigned phase;
+    int nw, tid, row;   // warps in the CTA, thread index, this warp's row (env) in the tile
+};
 static_assert(LW == 128, "Side<K>::bm holds the ladder bitmap");
 
-// Book operations in the env's current form: the price ladder while `lad`
-// holds (LADC: the instance has a ladder), else the sorted index.
-template <int K, bool RBID, bool TRACE, bool MA, bool LADC>
-__device__ __forceinline__ int book_take(Side<K> &O, PoolSmem<K> &P, LadBlock<K> *lb, bool lad, bool has_limit,
-                                         int limit, int q, long long taker_id, int taker_side, Ctx &c, int lane) {
-    if constexpr (LADC) {
-        if (lad) return lad_take<K, RBID, TRACE, MA>(O, P, lb->s[RBID ? 0 : 1], has_limit, limit, q, taker_id,
-                                                     taker_side, c, lane);
-    }
-    return side_take<K, RBID, TRACE, MA>(O, P, has_limit, limit, q, taker_id, taker_side, c, lane);
-}
-// Rest on side S (BID: bids); O is the other side.  An order the ladder
-// cannot hold converts the env to the sorted index first.
-template <int K, bool BID, bool LADC>
-__device__ __forceinline__ void book_rest(Side<K> &S, Side<K> &O, PoolSmem<K> &P, LadBlock<K> *lb, bool &lad, int cap,
-                                          int p, int q, long long oid, Ctx &c, int lane) {
-    if constexpr (LADC) {
-        if (lad) {
-            if (lad_rest<K, BID>(S, P, lb->s[BID ? 0 : 1], cap, p, q, oid, c, lane)) return;
-            lad_to_index<K, BID>(S, lb->s[BID ? 0 : 1], lb->inv, lane);
-            lad_to_index<K, !BID>(O, lb->s[BID ? 1 : 0], lb->inv, lane);
-            lad = false;
-        }
-    }
-    side_rest<K, BID>(S, P, cap, p, q, oid, c, lane);
-}
-template <int K, bool BID, bool LADC>
-__device__ __forceinline__ void book_cancel(Side<K> &S, PoolSmem<K> &P, LadBlock<K> *lb, bool lad, int type, int p,
-                                            int qty, long long oid, Ctx &c, int lane) {
-    if constexpr (LADC) {
-        if (lad) {
-            lad_cancel<K, BID>(S, P, lb->s[BID ? 0 : 1], type, p, qty, oid, c, lane);
-            return;
-        }
-    }
-    side_cancel<K>(S, P, type, p, qty, oid, c, lane);
-}
+// Book operations at the step's edges in the env's current form: the price
+// ladder while `lad` holds (LADC: the instance has a ladder), else the sorted
+// index.  The message loops of the two forms are separate (msgs_ladder,
+// msgs_index) so that each keeps a compact body.
 template <int K, bool BID, bool LADC>
 __device__ __forceinline__ void book_cancel_set(Side<K> &S, PoolSmem<K> &P, LadBlock<K> *lb, bool lad,
                                                 unsigned cmask, Ctx &c, int lane) {
@@ -1309,6 +1288,142 @@ __device__ __forceinline__ void book_store(const Side<K> &S, const PoolSmem<K> &
     side_store<K, BID>(S, P, blk, lane);
 }
 
+// The message loop of one chunk in the sorted-index form, from record i0 to
+// cnt (the next record is always read one ahead; a read past the chunk end
+// stays inside this warp's shared memory and is unused).
+template <int K, bool TRACE, bool MA>
+__device__ __forceinline__ void msgs_index(const KParams &p, WarpSmem<K> &sm, Side<K> &bid, Side<K> &ask, Ctx &c,
+                                           int cap, const int4 *rp, const unsigned char *dx, int i0, int cnt,
+                                           bool snap_env, long long &snap_n, long long snap_bytes, int lane) {
+    int4 w0 = rp[2 * i0], w1 = rp[2 * i0 + 1];
+    int dcur = dx[i0];
+    for (int i = i0; i < cnt; i++) {
+        const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
+        const int dnext = dx[i + 1];   // read one ahead, like the record (stays in this warp's space)
+        const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
+        const int px = w1.x;
+        int qty = w1.y;
+        const int didx = dcur;
+        const int type = (didx >> 1) + 1;   // cancels: LOB_PARTIAL or LOB_DELETE
+        if constexpr (K >= 32) {
+            // the largest books: one call site per side for taking
+            // liquidity and for resting, to keep the kernel's code small
+            if (didx == 0 || didx == 6) {          // buy: limit add or market
+                const bool lim = didx == 0;
+                if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                if (!lim || (ask.n > 0 && px >= ask.fpx))
+                    qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], lim, px, qty, oid, LOB_BUY, c, lane);
+                if (!lim) c.c_mkt_disc += qty;
+                else if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+            } else if (didx == 1 || didx == 7) {   // sell: limit add or market
+                const bool lim = didx == 1;
+                if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
+                if (!lim || (bid.n > 0 && px <= bid.fpx))
+                    qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], lim, px, qty, oid, LOB_SELL, c, lane);
+                if (!lim) c.c_mkt_disc += qty;
+                else if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+            } else if (didx == 2 || didx == 4) {
+                side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
+            } else if (didx == 3 || didx == 5) {
+                side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+            } else {
+                c.c_bad += 1;
+                c.status |= ST_BADMSG;
+            }
+        } else {
+            // uniform branches in order of frequency: adds, cancels, market orders
+            if (didx < 2) {
+                c.c_add_vol += qty;
+                if (didx == 0) {
+                    if (ask.n > 0 && px >= ask.fpx)
+                        qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], true, px, qty, oid, LOB_BUY, c, lane);
+                    if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
+                } else {
+                    if (bid.n > 0 && px <= bid.fpx)
+                        qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], true, px, qty, oid, LOB_SELL, c, lane);
+                    if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
+                }
+            } else if (didx < 6) {
+                if ((didx & 1) == 0) side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
+                else side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
+            } else if (didx < 8) {
+                c.c_mkt_vol += qty;
+                if (didx == 6)
+                    c.c_mkt_disc += side_take<K, false, TRACE, MA>(ask, sm.pool[1], false, 0, qty, oid, LOB_BUY, c, lane);
+                else
+                    c.c_mkt_disc += side_take<K, true, TRACE, MA>(bid, sm.pool[0], false, 0, qty, oid, LOB_SELL, c, lane);
+            } else {
+                c.c_bad += 1;
+                c.status |= ST_BADMSG;
+            }
+        }
+        if (TRACE && snap_env) {
+            __syncwarp();
+            if (snap_n < p.snap_cap) write_snapshot<K>(bid, ask, sm, cap, p.snaps + snap_n * snap_bytes, lane);
+            snap_n++;
+        }
+        c.msg_idx++;
+        w0 = n0;
+        w1 = n1;
+        dcur = dnext;
+    }
+}
+
+// The message loop of one chunk in the price-ladder form, from record i0:
+// one call site per (operation, side).  Returns the first record it did not
+// process -- cnt, or a limit order whose price would stretch its own side past
+// the ladder (the caller then converts the env to the sorted form and goes on
+// from that record there).
+template <int K, bool MA>
+__device__ __forceinline__ int msgs_ladder(WarpSmem<K> &sm, LadBlock<K> *lb, Side<K> &bid, Side<K> &ask, Ctx &c,
+                                           int cap, const int4 *rp, const unsigned char *dx, int i0, int cnt,
+                                           int lane) {
+    int4 w0 = rp[2 * i0], w1 = rp[2 * i0 + 1];
+    int dcur = dx[i0];
+    for (int i = i0; i < cnt; i++) {
+        const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
+        const int dnext = dx[i + 1];
+        const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
+        const int px = w1.x;
+        int qty = w1.y;
+        const int didx = dcur;
+        if (didx < 2 || didx == 6 || didx == 7) {   // limit add or market order
+            const bool sell = (didx & 1) != 0, lim = didx < 2;
+            if (lim) {
+                if (!(sell ? lad_fits<K, false>(ask, px) : lad_fits<K, true>(bid, px))) return i;
+                c.c_add_vol += qty;
+            } else {
+                c.c_mkt_vol += qty;
+            }
+            if (!sell) {
+                if (!lim || (ask.n > 0 && px >= ask.fpx))
+                    qty = lad_take<K, false, false, MA>(ask, sm.pool[1], lb->s[1], lim, px, qty, oid, LOB_BUY, c, lane);
+            } else {
+                if (!lim || (bid.n > 0 && px <= bid.fpx))
+                    qty = lad_take<K, true, false, MA>(bid, sm.pool[0], lb->s[0], lim, px, qty, oid, LOB_SELL, c, lane);
+            }
+            if (!lim) {
+                c.c_mkt_disc += qty;
+            } else if (qty > 0) {
+                if (!sell) lad_rest<K, true>(bid, sm.pool[0], lb->s[0], cap, px, qty, oid, c, lane);
+                else lad_rest<K, false>(ask, sm.pool[1], lb->s[1], cap, px, qty, oid, c, lane);
+            }
+        } else if (didx < 6) {
+            const int type = (didx >> 1) + 1;   // LOB_PARTIAL or LOB_DELETE
+            if ((didx & 1) == 0) lad_cancel<K, true>(bid, sm.pool[0], lb->s[0], type, px, qty, oid, c, lane);
+            else lad_cancel<K, false>(ask, sm.pool[1], lb->s[1], type, px, qty, oid, c, lane);
+        } else {
+            c.c_bad += 1;
+            c.status |= ST_BADMSG;
+        }
+        c.msg_idx++;
+        w0 = n0;
+        w1 = n1;
+        dcur = dnext;
+    }
+    return cnt;
+}
+
 // Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
@@ -1319,9 +1434,9 @@ struct MsgPipe {
 // without it those settings are ignored, so the host launches EXT whenever
 // one is set.  MA (which implies EXT) runs 2P agents with their state in the
 // warp's agent block agp; without it the agents are the benchmark pair.
-template <int K, bool TRACE, bool EXT, bool MA>
+template <int K, bool TRACE, bool EXT, bool MA, bool FUSED = false>
 __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp, LadBlock<K> *lb, MsgPipe &pipe,
-                        int lane) {
+                        int lane, FusedCtx *fc = nullptr) {
     constexpr bool XT = EXT || MA;
     // the price-ladder form for every untraced instance of the register-pool
     // classes (traces record the book after every message in the sorted form)
@@ -1393,7 +1508,13 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
     const long long snap_bytes = 8 + 48 * (long long)cap;
     bool timed_out = false;
 
-    for (int step = 0; step < p.n_steps && !timed_out; step++) {
+    for (int step = 0; step < p.n_steps && (FUSED || !timed_out); step++) {
+        if constexpr (FUSED) {   // after a timeout the warp only keeps its CTA's policy in step
+            if (timed_out) {
+                fused_policy(*fc->fz, *fc->f, fc->phase, fc->nw, fc->tid);
+                continue;
+            }
+        }
         const int t = p.t0 + step;
         const int te = ep_mode ? t % p.T : t;   // step within the episode
         if (step > 0) {
@@ -1473,7 +1594,11 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         } else if (A == 2) {
             // market maker's action count: 12, or (extended kernel) 8 / 3
             const int n_mm = !XT ? 12 : p.mm_space == LOB_MM_FIXED_QUANT ? 8 : p.mm_space == LOB_MM_DIRECTIONAL ? 3 : 12;
-            if (p.action_mode == LOB_ACT_RANDOM) {
+            if constexpr (FUSED) {   // the CTA's policy acted on the last observation
+                act0 = fc->fz->acts[fc->row][0];
+                act1 = fc->fz->acts[fc->row][1];
+                if (p.act_steps && lane < 2) p.act_steps[((long long)step * p.n_envs + e) * 2 + lane] = lane ? act1 : act0;
+            } else if (p.action_mode == LOB_ACT_RANDOM) {
                 const unsigned long long key = step_key(seed, t, TAG_POLICY);
                 act0 = (int)bounded(sm_mix(key + GAMMA), 12);
                 act1 = (int)bounded(sm_mix(key + 2 * GAMMA), (unsigned)n_mm);
@@ -1668,84 +1793,28 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 dx[r] = (unsigned char)(ok ? ((ty - 1) << 1) | (sd < 0 ? 1 : 0) : 8);
             }
             __syncwarp();
-            int4 w0 = rp[0], w1 = rp[1];
-            int dcur = dx[0];
-            for (int i = 0; i < cnt_ch; i++) {
-                const int4 n0 = rp[2 * i + 2], n1 = rp[2 * i + 3];
-                const int dnext = dx[i + 1];   // read one ahead, like the record (stays in this warp's space)
-                const long long oid = ((long long)(unsigned)w0.w << 32) | (unsigned)w0.z;
-                const int px = w1.x;
-                int qty = w1.y;
-                const int didx = dcur;
-                const int type = (didx >> 1) + 1;   // cancels: LOB_PARTIAL or LOB_DELETE
-                if constexpr (K >= 32) {
-                    // the largest books: one call site per side for taking
-                    // liquidity and for resting, to keep the kernel's code small
-                    if (didx == 0 || didx == 6) {          // buy: limit add or market
-                        const bool lim = didx == 0;
-                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
-                        if (!lim || (ask.n > 0 && px >= ask.fpx))
-                            qty = side_take<K, false, TRACE, MA>(ask, sm.pool[1], lim, px, qty, oid, LOB_BUY, c, lane);
-                        if (!lim) c.c_mkt_disc += qty;
-                        else if (qty > 0) side_rest<K, true>(bid, sm.pool[0], cap, px, qty, oid, c, lane);
-                    } else if (didx == 1 || didx == 7) {   // sell: limit add or market
-                        const bool lim = didx == 1;
-                        if (lim) c.c_add_vol += qty; else c.c_mkt_vol += qty;
-                        if (!lim || (bid.n > 0 && px <= bid.fpx))
-                            qty = side_take<K, true, TRACE, MA>(bid, sm.pool[0], lim, px, qty, oid, LOB_SELL, c, lane);
-                        if (!lim) c.c_mkt_disc += qty;
-                        else if (qty > 0) side_rest<K, false>(ask, sm.pool[1], cap, px, qty, oid, c, lane);
-                    } else if (didx == 2 || didx == 4) {
-                        side_cancel<K>(bid, sm.pool[0], type, px, qty, oid, c, lane);
-                    } else if (didx == 3 || didx == 5) {
-                        side_cancel<K>(ask, sm.pool[1], type, px, qty, oid, c, lane);
-                    } else {
-                        c.c_bad += 1;
-                        c.status |= ST_BADMSG;
-                    }
-                } else {
-                    // uniform branches in order of frequency: adds, cancels, market orders
-                    if (didx < 2) {
-                        c.c_add_vol += qty;
-                        if (didx == 0) {
-                            if (ask.n > 0 && px >= ask.fpx)
-                                qty = book_take<K, false, TRACE, MA, LADC>(ask, sm.pool[1], lb, lad, true, px, qty, oid,
-                                                                          LOB_BUY, c, lane);
-                            if (qty > 0) book_rest<K, true, LADC>(bid, ask, sm.pool[0], lb, lad, cap, px, qty, oid, c, lane);
-                        } else {
-                            if (bid.n > 0 && px <= bid.fpx)
-                                qty = book_take<K, true, TRACE, MA, LADC>(bid, sm.pool[0], lb, lad, true, px, qty, oid,
-                                                                         LOB_SELL, c, lane);
-                            if (qty > 0) book_rest<K, false, LADC>(ask, bid, sm.pool[1], lb, lad, cap, px, qty, oid, c, lane);
-                        }
-                    } else if (didx < 6) {
-                        if ((didx & 1) == 0) book_cancel<K, true, LADC>(bid, sm.pool[0], lb, lad, type, px, qty, oid, c, lane);
-                        else book_cancel<K, false, LADC>(ask, sm.pool[1], lb, lad, type, px, qty, oid, c, lane);
-                    } else if (didx < 8) {
-                        c.c_mkt_vol += qty;
-                        if (didx == 6)
-                            c.c_mkt_disc += book_take<K, false, TRACE, MA, LADC>(ask, sm.pool[1], lb, lad, false, 0, qty,
-                                                                                 oid, LOB_BUY, c, lane);
-                        else
-                            c.c_mkt_disc += book_take<K, true, TRACE, MA, LADC>(bid, sm.pool[0], lb, lad, false, 0, qty,
-                                                                                oid, LOB_SELL, c, lane);
-                    } else {
-                        c.c_bad += 1;
-                        c.status |= ST_BADMSG;
+            int i0 = 0;
+            if constexpr (LADC) {
+                if (lad) {
+                    i0 = msgs_ladder<K, MA>(sm, lb, bid, ask, c, cap, rp, dx, 0, cnt_ch, lane);
+                    if (i0 < cnt_ch) {   // an order the ladder cannot hold: both sides to the sorted form
+                        lad_to_index<K, true>(bid, lb->s[0], lb->inv, lane);
+                        lad_to_index<K, false>(ask, lb->s[1], lb->inv, lane);
+                        lad = false;
                     }
                 }
-                if (TRACE && snap_env) {
-                    __syncwarp();
-                    if (snap_n < p.snap_cap) write_snapshot<K>(bid, ask, sm, cap, p.snaps + snap_n * snap_bytes, lane);
-                    snap_n++;
-                }
-                c.msg_idx++;
-                w0 = n0;
-                w1 = n1;
-                dcur = dnext;
+            }
+            if (i0 < cnt_ch)
+                msgs_index<K, TRACE, MA>(p, sm, bid, ask, c, cap, rp, dx, i0, cnt_ch, snap_env, snap_n, snap_bytes, lane);
+        }
+        if (timed_out) {
+            if constexpr (FUSED) {
+                fused_policy(*fc->fz, *fc->f, fc->phase, fc->nw, fc->tid);
+                continue;
+            } else {
+                break;
             }
         }
-        if (timed_out) break;
 #ifdef LOB_CHECKED
         {
             bool ok;
@@ -1777,7 +1846,10 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         const bool side_drawn = XT && p.exec_dir == 0;
         const int ep_dir = (ep_end && side_drawn) ? drawn_task_side(seed, t / p.T + 1) : c.exec_dir;
         __syncwarp();
-        const long long obs_base = ((long long)step * p.n_envs + e);
+        const long long step_base = (long long)step * p.n_envs + e;
+        const long long obs_base = p.ow_obs ? (long long)e : step_base;
+        const long long rew_base = p.ow_rew ? (long long)e : step_base;
+        const long long done_base = p.ow_done ? (long long)e : step_base;
         if (A > 0) {
             const int L = p.L;
             for (int i = lane; i < 2 * LMAX; i += 32) {
@@ -1843,7 +1915,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                                                              sm.rw[0], s2, ag.inv0[a], ag.cash0[a], iv, cs, r, r);
                         r = a < P ? rr.x : rr.y;
                     }
-                    if (p.rew) p.rew[obs_base * A + a] = r;
+                    if (p.rew) p.rew[rew_base * A + a] = r;
                     if (p.act_out) p.act_out[(long long)e * A + a] = ag.act[a];
                 }
             } else {
@@ -1893,6 +1965,31 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                     ob[a * D + 4 * L + g] = v;
                 }
             }
+            if constexpr (FUSED) {
+                // the observation rows of both agents into the CTA's policy tile
+                FusedSmem &fz = *fc->fz;
+                for (int idx = lane; idx < 4 * L; idx += 32) {
+                    const int sd = idx >= 2 * L ? 1 : 0;
+                    const int i = (idx - sd * 2 * L) >> 1;
+                    const int nl = sd == 0 ? nlb : nla;
+                    const long long lq = sm.lvl_q[sd][i];
+                    const long long lp = (long long)sm.lvl_px[sd][i] - anchor;
+                    const float v = i >= nl ? 0.0f : __ll2float_rn((idx & 1) ? lq : lp);
+                    fused_put_obs(fz, *fc->f, 0, fc->row, idx, v);
+                    fused_put_obs(fz, *fc->f, 1, fc->row, idx, v);
+                }
+                if (lane < 10) {
+                    const int a = lane >= 5 ? 1 : 0;
+                    const int g = lane - 5 * a;
+                    const long long iv = a == 0 ? c.inv0 : c.inv1;
+                    const long long cs = a == 0 ? c.cash0 : c.cash1;
+                    const long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    const long long own = a == 0 ? own0 : own1;
+                    const long long x = g == 0 ? iv : g == 1 ? cs : g == 3 ? rem : own;
+                    fused_put_obs(fz, *fc->f, a, fc->row, 4 * L + g, g == 2 ? tl : __ll2float_rn(x));
+                }
+                __syncwarp();
+            }
             if (lane == 0) {
                 if (XT && (p.reward_mode != LOB_REWARD_PV || p.inv_penalty != 0 || p.exec_pen_milli != 0)) {
                     const longlong2 r = reward_variants(p.reward_mode, p.lam_pct, p.inv_penalty,
@@ -1901,12 +1998,12 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                                                         sm.rw[0], s2, sm.rw[1], sm.rw[2], c.inv1, c.cash1, r0, r1);
                     r0 = r.x; r1 = r.y;
                 }
-                if (p.rew) { p.rew[obs_base * A] = r0; p.rew[obs_base * A + 1] = r1; }
+                if (p.rew) { p.rew[rew_base * A] = r0; p.rew[rew_base * A + 1] = r1; }
                 if (p.act_out) { p.act_out[2LL * e] = act0; p.act_out[2LL * e + 1] = act1; }
             }
             }  // the benchmark pair
         }
-        if (lane == 0 && p.done) p.done[obs_base] = (unsigned char)(te + 1 == p.T);
+        if (lane == 0 && p.done) p.done[done_base] = (unsigned char)(te + 1 == p.T);
         if (TRACE && lane == 0 && p.fill_counts) p.fill_counts[e] = c.fill_n;
         if (TRACE && lane == 0 && snap_env && p.snap_count) *p.snap_count = snap_n;
         if (lane == 0) { st->act[0] = act0; st->act[1] = act1; }
@@ -1934,6 +2031,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         } else if (ep_mode) {
             dcur++;
         }
+        if constexpr (FUSED) fused_policy(*fc->fz, *fc->f, fc->phase, fc->nw, fc->tid);
         if (step + 1 == p.n_steps) {
             if (XT && need_load) {
                 // an episode ended with the launch: the env's block becomes the image

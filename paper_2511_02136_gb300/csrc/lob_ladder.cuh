@@ -52,9 +52,12 @@ struct __align__(16) LadBlock {
 static_assert(sizeof(LadBlock<1>) % 16 == 0 && sizeof(LadBlock<4>) % 16 == 0 && sizeof(LadBlock<8>) % 16 == 0,
               "ladder block keeps 16-byte alignment");
 
-// The ladder serves the capacity classes whose pool lives in registers.
+// Classes that run the ladder form (none at present: on the 1,024-env
+// benchmark its linked-list pops put dependent shared-memory round trips on
+// the taker's chain and measured slower than the sorted index; see the
+// design notes).  The register-pool classes K <= 8 can take it.
 template <int K>
-__host__ __device__ constexpr bool ladder_class() { return K <= 8; }
+__host__ __device__ constexpr bool ladder_class() { return false; }
 template <int K>
 __host__ __device__ constexpr size_t ladder_bytes() { return ladder_class<K>() ? sizeof(LadBlock<K>) : 0; }
 
@@ -77,28 +80,30 @@ __device__ __forceinline__ void bm_clear(Bm128 &b, int d) {
     b.hi &= d < 64 ? ~0ull : ~m;
 }
 // Nearest set bit at index d or below, wrapping around the ring (the bitmap
-// must have one): this word at or below d, then the other word, then this
-// word above d.
+// must have one): this word at or below d, else the other word, else this
+// word above d -- all three computed and selected, with no branch.
 __device__ __forceinline__ int bm_scan_down(const Bm128 &b, int d) {
     const bool in_lo = d < 64;
-    const int bit = d & 63, base = in_lo ? 0 : 64, obase = in_lo ? 64 : 0;
+    const int bit = d & 63, base = in_lo ? 0 : 64, obase = 64 - base;
     const unsigned long long x = in_lo ? b.lo : b.hi, o = in_lo ? b.hi : b.lo;
-    const unsigned long long below = bit == 63 ? ~0ull : ((2ull << bit) - 1ull);
+    const unsigned long long below = (2ull << bit) - 1ull;   // bits 0..bit (all for bit 63)
     const unsigned long long m = x & below;
-    if (m) return base + 63 - __clzll((long long)m);
-    if (o) return obase + 63 - __clzll((long long)o);
-    return base + 63 - __clzll((long long)(x & ~below));
+    const int r1 = base + 63 - __clzll((long long)m);
+    const int r2 = obase + 63 - __clzll((long long)o);
+    const int r3 = base + 63 - __clzll((long long)(x & ~below));
+    return m ? r1 : (o ? r2 : r3);
 }
 // Nearest set bit at index d or above, wrapping around the ring.
 __device__ __forceinline__ int bm_scan_up(const Bm128 &b, int d) {
     const bool in_lo = d < 64;
-    const int bit = d & 63, base = in_lo ? 0 : 64, obase = in_lo ? 64 : 0;
+    const int bit = d & 63, base = in_lo ? 0 : 64, obase = 64 - base;
     const unsigned long long x = in_lo ? b.lo : b.hi, o = in_lo ? b.hi : b.lo;
     const unsigned long long above = ~0ull << bit;
     const unsigned long long m = x & above;
-    if (m) return base + __ffsll((long long)m) - 1;
-    if (o) return obase + __ffsll((long long)o) - 1;
-    return base + __ffsll((long long)(x & ~above)) - 1;
+    const int r1 = base + __ffsll((long long)m) - 1;
+    const int r2 = obase + __ffsll((long long)o) - 1;
+    const int r3 = base + __ffsll((long long)(x & ~above)) - 1;
+    return m ? r1 : (o ? r2 : r3);
 }
 __device__ __forceinline__ int lvl_of(int px) { return (int)((unsigned)px & (unsigned)(LW - 1)); }
 
@@ -265,24 +270,29 @@ __device__ __forceinline__ int lad_take(Side<K> &O, PoolSmem<K> &P, LadSide<K> &
 }
 
 // ---------------------------------------------------------------- rest
+// Whether an order at price p may rest on side S without stretching the
+// side's price span to LW ticks or more (checked against the current worst,
+// so conservative when the order would evict or be dropped).
+template <int K, bool BID>
+__device__ __forceinline__ bool lad_fits(const Side<K> &S, int p) {
+    const int best = BID ? max(S.fpx, p) : min(S.fpx, p);
+    const int worst = BID ? min(S.wpx, p) : max(S.wpx, p);
+    const unsigned span = BID ? (unsigned)best - (unsigned)worst : (unsigned)worst - (unsigned)best;
+    return S.n == 0 || span < (unsigned)LW;
+}
+
 // Rest an order on its own side with the capacity rule (reading 6: on a full
 // side an order strictly better than the worst price evicts the worst-priced,
-// latest-arrived order; otherwise it is dropped).  Returns false, with
-// nothing changed, when the order would stretch the side's price span to LW
-// ticks or more: the caller then converts the env to the sorted form.
+// latest-arrived order; otherwise it is dropped).  The price must fit the
+// ladder (lad_fits).
 template <int K, bool BID>
-__device__ __forceinline__ bool lad_rest(Side<K> &S, PoolSmem<K> &P, LadSide<K> &D, int cap, int p, int q,
+__device__ __forceinline__ void lad_rest(Side<K> &S, PoolSmem<K> &P, LadSide<K> &D, int cap, int p, int q,
                                          long long oid, Ctx &c, int lane) {
     const bool full = S.n >= cap;
     if (full && !(BID ? p > S.wpx : p < S.wpx)) {   // not strictly better than the worst: dropped
         c.c_drop_vol += q;
         c.c_drop_cnt += 1;
-        return true;
-    }
-    if (S.n > 0) {   // the span with this order, against the current worst (conservative when evicting)
-        const long long best = BID ? max(S.fpx, p) : min(S.fpx, p);
-        const long long worst = BID ? min(S.wpx, p) : max(S.wpx, p);
-        if ((BID ? best - worst : worst - best) >= LW) return false;
+        return;
     }
     int f;
     if (full) {   // evict the tail of the worst level and reuse its slot
@@ -328,10 +338,30 @@ __device__ __forceinline__ bool lad_rest(Side<K> &S, PoolSmem<K> &P, LadSide<K> 
         if (BID ? p < S.wpx : p > S.wpx) S.wpx = p;
     }
     S.n++;
-    return true;
 }
 
 // ---------------------------------------------------------------- cancel
+// Repeated (price, id) matches (this lane's slots in m): the slot of the
+// match that arrived first (smallest stamp).  Out of line: ids repeat only in
+// unusual streams.
+template <int K>
+__device__ __noinline__ int lad_dup_slot(const long long *ts, unsigned m, int lane) {
+    long long bts = 0x7fffffffffffffffLL;
+    int bs = -1;
+    for (int r = 0; r < K; r++)
+        if ((m >> r) & 1u) {
+            const int sl = slot_of<K>(lane, r);
+            if (ts[sl] < bts) { bts = ts[sl]; bs = sl; }
+        }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const long long ots = __shfl_xor_sync(FULL, bts, o);
+        const int os = __shfl_xor_sync(FULL, bs, o);
+        if (ots < bts || (ots == bts && os >= 0 && (bs < 0 || os < bs))) { bts = ots; bs = os; }
+    }
+    return bs;
+}
+
 // Partial cancel or delete: lookup by (price, id) over the pool; a miss is a
 // no-op; with repeated ids the earliest-arrived match is hit.
 template <int K, bool BID>
@@ -351,23 +381,7 @@ __device__ __forceinline__ void lad_cancel(Side<K> &S, PoolSmem<K> &P, LadSide<K
         const int L = 31 - __clz(lanes);
         s = __shfl_sync(FULL, slot_of<K>(lane, 31 - __clz(m)), L);
     } else {
-        // repeated (price, id): the match that arrived first (smallest stamp)
-        long long bts = 0x7fffffffffffffffLL;
-        int bs = -1;
-#pragma unroll (Side<K>::SU)
-        for (int r = 0; r < K; r++)
-            if ((m >> r) & 1u) {
-                const int sl = slot_of<K>(lane, r);
-                const long long ts = P.ts[sl];
-                if (ts < bts) { bts = ts; bs = sl; }
-            }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const long long ots = __shfl_xor_sync(FULL, bts, o);
-            const int os = __shfl_xor_sync(FULL, bs, o);
-            if (ots < bts || (ots == bts && os >= 0 && (bs < 0 || os < bs))) { bts = ots; bs = os; }
-        }
-        s = bs;
+        s = lad_dup_slot<K>(P.ts, m, lane);
     }
     s = LOB_CHK(s, 32 * K, c.status);
     const int q0 = P.qty[s];

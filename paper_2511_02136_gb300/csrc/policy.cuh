@@ -19,136 +19,9 @@
 // relative, is under the BF16 rounding of the activations that follows).
 // k_policy_fp32: the same forward with FP32 FMAs on the CUDA cores.
 #pragma once
-#include <cstdint>
-#include <cuda_bf16.h>
-#include "lob.h"
+#include "tc05.cuh"
 
 namespace pol {
-
-constexpr int H = 128;        // hidden width
-constexpr int NOUT = 13;      // 12 logits + value
-constexpr int NA = 12;        // actions
-constexpr int DMAX = 128;     // max observation length (padded to a multiple of 16)
-constexpr int PT = 256;       // threads per CTA of the BF16 forward
-
-// Input scale of feature f of an observation with L levels per side.
-__host__ __device__ inline float obs_scale(int f, int L) {
-    if (f < 4 * L) return (f & 1) ? 1e-3f : 0.1f;   // level (px - anchor, qty)
-    const int g = f - 4 * L;
-    if (g == 0) return 1e-2f;      // inventory
-    if (g == 1) return 1e-6f;      // cash
-    if (g == 2) return 1.0f;       // time left
-    return 1e-2f;                  // remaining target, own resting quantity
-}
-
-// Byte offset of element (row, k) in a K-major core-matrix tile with Kp
-// columns: core matrix (row / 8, k / 8) is 128 contiguous bytes (8 rows of
-// 8 bf16); core matrices run along K first (leading byte offset 128), then
-// along rows (stride byte offset Kp / 8 * 128).
-__host__ __device__ inline unsigned cm_off(int row, int k, int Kp) {
-    return (unsigned)((((row >> 3) * (Kp >> 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
-}
-
-struct PolicyParams {
-    const float *obs;               // [n_envs][A][D]
-    int n_envs, A, D, Dp, L;
-    const unsigned char *wpack;     // per agent: bf16 W1 [128 x Dp], W2 [128 x 128], W3 [16 x 128] in core layout
-    long long wpack_stride;         // bytes per agent
-    const float *wf32;              // per agent: W1 [128][D], b1, W2 [128][128], b2, W3 [13][128], b3
-    long long wf32_stride;          // floats per agent
-    float *logits;                  // [n_envs][A][12] or NULL
-    float *values;                  // [n_envs][A] or NULL
-    int *actions;                   // [n_envs][A] or NULL
-    int *status;
-    long long wait_budget;
-};
-
-__device__ __forceinline__ unsigned s_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// ---- tcgen05 / mbarrier helpers (inline PTX)
-__device__ __forceinline__ void tm_alloc(unsigned *dst_smem, unsigned ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(dst_smem)),
-                 "r"(ncols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tm_dealloc(unsigned taddr, unsigned ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: no swizzle, K-major.
-__device__ __forceinline__ unsigned long long sdesc(const void *base, unsigned lbo, unsigned sbo) {
-    const unsigned long long a = (s_u32(base) >> 4) & 0x3FFFu;
-    return a | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) | ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) |
-           (1ull << 46);   // descriptor version for this architecture; base offset 0, layout 0 (no swizzle)
-}
-// Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.
-__host__ __device__ constexpr unsigned idesc_bf16(int M, int N) {
-    return (1u << 4)          // accumulator format F32
-         | (1u << 7)          // A format BF16
-         | (1u << 10)         // B format BF16
-         | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long da, unsigned long long db, unsigned idesc,
-                                         int accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(accumulate) : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void pbar_init(unsigned long long *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// One arrival that expects `bytes` of bulk-copy data, then the copies.
-__device__ __forceinline__ void pbar_expect(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-                     "r"(s_u32(dst)), "l"(src), "r"(bytes), "r"(s_u32(bar)) : "memory");
-}
-__device__ __forceinline__ float tanh_approx(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ bool pbar_wait(unsigned long long *bar, unsigned phase, long long budget) {
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok) : "r"(s_u32(bar)), "r"(phase) : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > budget) return false;
-    }
-}
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tm_ld32(unsigned taddr, float (&v)[32]) {
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
 
 struct __align__(128) Bf16Smem {
     unsigned char w1[H * DMAX * 2];   // [128 x Dp]
@@ -314,57 +187,102 @@ __global__ void __launch_bounds__(PT) k_policy_bf16(const PolicyParams p) {
     }
 }
 
-// FP32 reference forward on the CUDA cores: 64 envs of one agent per CTA,
-// weights and activations in shared memory (activations stored [unit][row]).
+// FP32 forward on the CUDA cores, register-tiled: one CTA of 256 threads per
+// (128-env tile, agent).  Every layer is a [128 x K] x [K x N] product whose
+// operands sit in shared memory k-major (activations as [k][row], weights as
+// [k][unit]), so a thread's 8 x 8 output tile reads two float4 of each per k
+// and does 64 FMAs; the hidden activations are written back over their input
+// after a barrier (the observations occupy the same buffer before layer 1).
+constexpr int FT = 256;         // threads per CTA of the FP32 forward
+constexpr int FDP = DMAX;       // widest (padded) observation
 struct F32Smem {
-    float w1[H * DMAX];
-    float w2[H * H];
-    float w3[NOUT * H];
+    float w1t[FDP][H];          // W1^T
+    float ht[H][128];           // scaled observations [feature][env row], then h1, then h2 [unit][env row]
+    float w2t[H][H];            // W2^T
+    float w3t[H][16];           // W3^T (outputs 13..15 zero)
     float b1[H], b2[H], b3[16];
-    float h1[H * 64];
-    float h2[H * 64];
 };
 
-__global__ void __launch_bounds__(64) k_policy_fp32(const PolicyParams p) {
+__global__ void __launch_bounds__(FT, 1) k_policy_fp32(const PolicyParams p) {
     extern __shared__ __align__(16) unsigned char fraw[];
     F32Smem &sm = *reinterpret_cast<F32Smem *>(fraw);
     const int tid = threadIdx.x;
     const int a = blockIdx.y;
-    const int env = blockIdx.x * 64 + tid;
-    const int D = p.D;
+    const int row0 = blockIdx.x * 128;
+    const int D = p.D, Dp = (D + 3) & ~3;
     const float *wf = p.wf32 + (long long)a * p.wf32_stride;
-    for (int i = tid; i < H * D; i += 64) sm.w1[i] = wf[i];
-    const float *b1 = wf + H * D, *w2 = b1 + H, *b2 = w2 + H * H, *w3 = b2 + H, *b3 = w3 + NOUT * H;
-    for (int i = tid; i < H * H; i += 64) sm.w2[i] = w2[i];
-    for (int i = tid; i < NOUT * H; i += 64) sm.w3[i] = w3[i];
-    for (int i = tid; i < H; i += 64) { sm.b1[i] = b1[i]; sm.b2[i] = b2[i]; }
+    const float *w1 = wf, *b1 = wf + H * D, *w2 = b1 + H, *b2 = w2 + H * H, *w3 = b2 + H, *b3 = w3 + NOUT * H;
+    for (int i = tid; i < H * D; i += FT) sm.w1t[i % D][i / D] = w1[i];
+    for (int i = tid; i < H * (Dp - D); i += FT) sm.w1t[D + i / H][i % H] = 0.0f;
+    for (int i = tid; i < H * H; i += FT) sm.w2t[i % H][i / H] = w2[i];
+    for (int i = tid; i < H * 16; i += FT) {
+        const int o = i / H, k = i % H;
+        sm.w3t[k][o] = o < NOUT ? w3[o * H + k] : 0.0f;
+    }
+    if (tid < H) { sm.b1[tid] = b1[tid]; sm.b2[tid] = b2[tid]; }
     if (tid < 16) sm.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
-    float x[DMAX];
-    const float *o = p.obs + ((long long)(env < p.n_envs ? env : 0) * p.A + a) * D;
-#pragma unroll
-    for (int k = 0; k < DMAX; k++) x[k] = (k < D && env < p.n_envs) ? o[k] * obs_scale(k, p.L) : 0.0f;
+    for (int i = tid; i < 128 * Dp; i += FT) {
+        const int r = i / Dp, k = i % Dp, env = row0 + r;
+        sm.ht[k][r] = (k < D && env < p.n_envs) ? p.obs[((long long)env * p.A + a) * D + k] * obs_scale(k, p.L) : 0.0f;
+    }
     __syncthreads();
-    for (int j = 0; j < H; j++) {
-        float acc = sm.b1[j];
-#pragma unroll 4
-        for (int k = 0; k < D; k++) acc = fmaf(sm.w1[j * D + k], x[k], acc);
-        sm.h1[j * 64 + tid] = tanhf(acc);
-    }
-    for (int j = 0; j < H; j++) {
-        float acc = sm.b2[j];
-#pragma unroll 8
-        for (int k = 0; k < H; k++) acc = fmaf(sm.w2[j * H + k], sm.h1[k * 64 + tid], acc);
-        sm.h2[j * 64 + tid] = tanhf(acc);
-    }
-    float y[16];
+    const int ty = tid >> 4, tx = tid & 15;   // rows 8 ty .. 8 ty + 7, units 8 tx .. 8 tx + 7
+    float acc[8][8];
+    // ---- two hidden layers: ht = tanh(W x + b), x = xt (layer 1) or ht (layer 2)
+    for (int layer = 0; layer < 2; layer++) {
+        const int K = layer == 0 ? Dp : H;
+        const float *bias = layer == 0 ? sm.b1 : sm.b2;
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
-        float acc = sm.b3[j];
-        if (j < NOUT)
-            for (int k = 0; k < H; k++) acc = fmaf(sm.w3[j * H + k], sm.h2[k * 64 + tid], acc);
-        y[j] = acc;
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc[i][j] = bias[8 * tx + j];
+        for (int k = 0; k < K; k++) {
+            const float *xa = &sm.ht[k][8 * ty];
+            const float *wb = layer == 0 ? &sm.w1t[k][8 * tx] : &sm.w2t[k][8 * tx];
+            const float4 a0 = *reinterpret_cast<const float4 *>(xa), a1 = *reinterpret_cast<const float4 *>(xa + 4);
+            const float4 c0 = *reinterpret_cast<const float4 *>(wb), c1 = *reinterpret_cast<const float4 *>(wb + 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();   // every read of the layer's input is done
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            float4 t0, t1;
+            t0.x = tanhf(acc[0][j]); t0.y = tanhf(acc[1][j]); t0.z = tanhf(acc[2][j]); t0.w = tanhf(acc[3][j]);
+            t1.x = tanhf(acc[4][j]); t1.y = tanhf(acc[5][j]); t1.z = tanhf(acc[6][j]); t1.w = tanhf(acc[7][j]);
+            *reinterpret_cast<float4 *>(&sm.ht[8 * tx + j][8 * ty]) = t0;
+            *reinterpret_cast<float4 *>(&sm.ht[8 * tx + j][8 * ty + 4]) = t1;
+        }
+        __syncthreads();
     }
-    write_outputs(p, env, a, y);
+    // ---- output layer: 128 rows x 16 outputs, a thread 8 rows x 1 output
+    {
+        float y[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) y[i] = sm.b3[tx];
+        for (int k = 0; k < H; k++) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&sm.ht[k][8 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&sm.ht[k][8 * ty + 4]);
+            const float w = sm.w3t[k][tx];
+            y[0] = fmaf(a0.x, w, y[0]); y[1] = fmaf(a0.y, w, y[1]); y[2] = fmaf(a0.z, w, y[2]); y[3] = fmaf(a0.w, w, y[3]);
+            y[4] = fmaf(a1.x, w, y[4]); y[5] = fmaf(a1.y, w, y[5]); y[6] = fmaf(a1.z, w, y[6]); y[7] = fmaf(a1.w, w, y[7]);
+        }
+        __syncthreads();   // ht is free: stage the outputs [row][output] for the per-row epilogue
+        float *ys = &sm.ht[0][0];
+#pragma unroll
+        for (int i = 0; i < 8; i++) ys[(8 * ty + i) * 16 + tx] = y[i];
+        __syncthreads();
+        if (tid < 128) {
+            float yr[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) yr[j] = ys[tid * 16 + j];
+            write_outputs(p, row0 + tid, a, yr);
+        }
+    }
 }
 
 }  // namespace pol

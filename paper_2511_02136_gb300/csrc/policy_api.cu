@@ -1,8 +1,11 @@
 // policy_api.cu -- host side of the actor-critic policy entry points of
 // include/lob.h: weight packing (FP32 -> BF16 core-matrix layout), device
-// buffers and the two forward launches of policy.cuh.
+// buffers, the two forward launches of policy.cuh and the IPPO update of
+// ppo.cuh (optimiser state and work buffers live in the policy).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -10,6 +13,8 @@
 #include "lob.h"
 #include "policy.cuh"
 #include "policy_internal.h"
+#include "ppo.cuh"
+#include "fused.cuh"
 
 using namespace pol;
 
@@ -21,6 +26,18 @@ struct lob_policy {
     long long wf32_stride = 0;
     int *d_status = nullptr;
     long long launches = 0;
+    unsigned char *d_wrow = nullptr;      // row-major bf16 W1 [128 x Dp], W2, W3 [16 x 128] (fused rollout)
+    long long wrow_stride = 0;
+    // IPPO update (allocated by the first lob_ppo_update)
+    int upd_Dp = 0;                       // padded (D + 1)
+    unsigned char *d_wpk = nullptr;       // the update's packed weights (with W3^T and W2^T)
+    long long wpk_stride = 0;
+    float *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
+    float *d_adv = nullptr, *d_ret = nullptr;
+    long long adv_cap = 0;                // samples per agent the advantage buffers hold
+    float *d_stats = nullptr;             // [A][2]
+    double *d_acc = nullptr;              // [A][2] sums, then [A] squared norms after them
+    long long adam_t = 0;
 };
 
 static unsigned short f2bf(float f) {
@@ -79,7 +96,22 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
                 std::memcpy(d3 + cm_off(r, k, H), &v, 2);
             }
     }
+    // row-major bf16 copy for the fused rollout (its weights live in tensor memory)
+    p->wrow_stride = ((long long)H * p->Dp + (long long)H * H + 16LL * H) * 2;
+    std::vector<unsigned short> rowp((size_t)(p->wrow_stride / 2 * n_agents), 0);
+    for (int a = 0; a < n_agents; a++) {
+        const float *w = h_params + (size_t)a * p->wf32_stride;
+        const float *w1 = w, *w2 = w + H * obs_dim + H, *w3 = w2 + H * H + H;
+        unsigned short *d = rowp.data() + (size_t)a * (p->wrow_stride / 2);
+        for (int r = 0; r < H; r++)
+            for (int k = 0; k < obs_dim; k++) d[(size_t)r * p->Dp + k] = f2bf(w1[r * obs_dim + k]);
+        d += (size_t)H * p->Dp;
+        for (int r = 0; r < H * H; r++) d[r] = f2bf(w2[r]);
+        d += (size_t)H * H;
+        for (int r = 0; r < NOUT * H; r++) d[r] = f2bf(w3[r]);
+    }
     bool fail = cudaMalloc(&p->d_wpack, pack.size()) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_wrow, rowp.size() * 2) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_wf32, sizeof(float) * (size_t)(p->wf32_stride * n_agents)) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_status, 4) != cudaSuccess;
     if (fail) {
@@ -94,6 +126,7 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
     rc |= cudaMemcpy(p->d_wf32, h_params, sizeof(float) * (size_t)(p->wf32_stride * n_agents),
                      cudaMemcpyHostToDevice) == cudaSuccess ? 0 : 1;
     rc |= cudaMemset(p->d_status, 0, 4) == cudaSuccess ? 0 : 1;
+    rc |= cudaMemcpy(p->d_wrow, rowp.data(), rowp.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess ? 0 : 1;
     if (rc) {
         lob_policy_destroy(p);
         return LOB_ECUDA;
@@ -105,11 +138,129 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
 extern "C" int lob_policy_destroy(lob_policy *p) {
     if (!p) return LOB_EINVAL;
     cudaDeviceSynchronize();
-    if (p->d_wpack) cudaFree(p->d_wpack);
-    if (p->d_wf32) cudaFree(p->d_wf32);
-    if (p->d_status) cudaFree(p->d_status);
+    void *bufs[] = {p->d_wpack, p->d_wf32, p->d_status, p->d_wrow, p->d_wpk, p->d_m, p->d_v, p->d_grad,
+                    p->d_adv, p->d_ret, p->d_stats, p->d_acc};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
     delete p;
     return LOB_OK;
+}
+
+extern "C" int lob_policy_get_params(lob_policy *pol, float *d_out, void *stream) {
+    if (!pol || !d_out) return LOB_EINVAL;
+    return cudaMemcpyAsync(d_out, pol->d_wf32, sizeof(float) * (size_t)(pol->wf32_stride * pol->A),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream) == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+// ---------------------------------------------------------------- IPPO update
+static ppo::AdamParams adam_params(lob_policy *p) {
+    ppo::AdamParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = p->A; a.D = p->D; a.Dp = p->upd_Dp; a.Dpf = p->Dp;
+    a.P = p->wf32_stride;
+    a.w = p->d_wf32; a.m = p->d_m; a.v = p->d_v; a.grad = p->d_grad;
+    a.sqnorm = p->d_acc + 2 * p->A;
+    a.wpk = p->d_wpk; a.wpk_stride = p->wpk_stride;
+    a.wfwd = p->d_wpack; a.wfwd_stride = p->wpack_stride;
+    a.wrow = p->d_wrow; a.wrow_stride = p->wrow_stride;
+    return a;
+}
+
+// First update: optimiser state, gradient buffer, the update's packed weights.
+static int ppo_setup(lob_policy *p, cudaStream_t s) {
+    if (p->d_wpk) return LOB_OK;
+    if (cudaFuncSetAttribute(ppo::k_ppo_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ppo::GradSmem)) != cudaSuccess)
+        return LOB_ECUDA;
+    p->upd_Dp = (p->D + 1 + 15) / 16 * 16;
+    p->wpk_stride = ((long long)H * p->upd_Dp + 2LL * H * H + 2 * 16LL * H) * 2;
+    const size_t P = (size_t)(p->wf32_stride * p->A);
+    bool fail = cudaMalloc(&p->d_wpk, (size_t)(p->wpk_stride * p->A)) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_m, P * 4) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_v, P * 4) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_grad, P * 4) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_stats, (size_t)p->A * 2 * 4) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_acc, (size_t)p->A * 3 * 8) != cudaSuccess;
+    if (fail) {
+        cudaGetLastError();
+        return LOB_ENOMEM;
+    }
+    if (cudaMemsetAsync(p->d_wpk, 0, (size_t)(p->wpk_stride * p->A), s) != cudaSuccess ||
+        cudaMemsetAsync(p->d_m, 0, P * 4, s) != cudaSuccess || cudaMemsetAsync(p->d_v, 0, P * 4, s) != cudaSuccess)
+        return LOB_ECUDA;
+    const ppo::AdamParams a = adam_params(p);
+    ppo::k_ppo_pack<<<dim3(64, p->A), 256, 0, s>>>(a);
+    p->launches++;
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
+}
+
+extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_ppo_hparams *hp, void *stream) {
+    if (!p || !b || !hp) return LOB_EINVAL;
+    if (b->T < 1 || b->n_envs < 1 || hp->n_minibatches < 1 || !b->d_obs || !b->d_actions || !b->d_logp_old ||
+        !b->d_values || !b->d_rewards || !b->d_done || !b->d_perm)
+        return LOB_EINVAL;
+    const long long N = (long long)b->T * b->n_envs;
+    if (N % hp->n_minibatches != 0 || N / hp->n_minibatches > 0x7fffffffLL) return LOB_EINVAL;
+    if (p->D + 1 > ppo::DPMAX) return LOB_ECAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ppo_setup(p, s);
+    if (rc != LOB_OK) return rc;
+    if (p->adv_cap < N) {
+        if (p->d_adv) cudaFree(p->d_adv);
+        if (p->d_ret) cudaFree(p->d_ret);
+        p->d_adv = p->d_ret = nullptr;
+        p->adv_cap = 0;
+        if (cudaMalloc(&p->d_adv, (size_t)(N * p->A) * 4) != cudaSuccess ||
+            cudaMalloc(&p->d_ret, (size_t)(N * p->A) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return LOB_ENOMEM;
+        }
+        p->adv_cap = N;
+    }
+    const int A = p->A;
+    const long long P = p->wf32_stride;
+    const int nenv_a = b->n_envs * A;
+    ppo::k_ppo_gae<<<(nenv_a + 127) / 128, 128, 0, s>>>(reinterpret_cast<const long long *>(b->d_rewards),
+                                                          b->d_values, b->d_done, b->T, b->n_envs, A, hp->gamma,
+                                                          hp->gae_lambda, hp->reward_scale, p->d_adv, p->d_ret);
+    p->launches++;
+    const int mb = (int)(N / hp->n_minibatches);
+    int n_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (mb + 127) / 128;
+    const int ctas = std::max(1, std::min(tiles, n_sm / A > 0 ? n_sm / A : 1));
+    ppo::GradParams g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A; g.D = p->D; g.Dp = p->upd_Dp; g.L = p->L; g.n_envs = b->n_envs; g.n_samples = N;
+    g.obs = b->d_obs; g.actions = b->d_actions; g.logp_old = b->d_logp_old; g.adv = p->d_adv; g.ret = p->d_ret;
+    g.perm = b->d_perm; g.mb_size = mb; g.stats = p->d_stats;
+    g.wpk = p->d_wpk; g.wpk_stride = p->wpk_stride; g.wf32 = p->d_wf32; g.wf32_stride = P;
+    g.grad = p->d_grad; g.clip_eps = hp->clip_eps; g.vf_coef = hp->vf_coef; g.ent_coef = hp->ent_coef;
+    g.status = p->d_status; g.wait_budget = 2000000000LL;
+    ppo::AdamParams ad = adam_params(p);
+    ad.lr = hp->lr; ad.beta1 = hp->beta1; ad.beta2 = hp->beta2; ad.eps = hp->adam_eps; ad.max_norm = hp->max_grad_norm;
+    for (int k = 0; k < hp->n_minibatches; k++) {
+        g.mb_begin = (long long)k * mb;
+        if (cudaMemsetAsync(p->d_acc, 0, (size_t)A * 3 * 8, s) != cudaSuccess ||
+            cudaMemsetAsync(p->d_grad, 0, (size_t)(P * A) * 4, s) != cudaSuccess)
+            return LOB_ECUDA;
+        ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A), 256, 0, s>>>(p->d_adv, b->d_perm, N,
+                                                                                               g.mb_begin, mb, p->d_acc);
+        ppo::k_ppo_stats_fin<<<1, 64, 0, s>>>(p->d_acc, A, mb, p->d_stats);
+        ppo::k_ppo_grad<<<dim3(ctas, A), ppo::PPT, sizeof(ppo::GradSmem), s>>>(g);
+        if (b->d_grad_out &&
+            cudaMemcpyAsync(b->d_grad_out + (size_t)k * A * P, p->d_grad, (size_t)(P * A) * 4, cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+            return LOB_ECUDA;
+        ppo::k_ppo_sqnorm<<<dim3(32, A), 256, 0, s>>>(p->d_grad, P, p->d_acc + 2 * A);
+        p->adam_t++;
+        ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)p->adam_t));
+        ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)p->adam_t));
+        ppo::k_ppo_adam<<<dim3(64, A), 256, 0, s>>>(ad);
+        p->launches += 5;
+    }
+    return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 
 int policy_forward_internal(lob_policy *pol, const float *d_obs, int32_t n_envs, int32_t precision, float *d_logits,
@@ -130,14 +281,26 @@ int policy_forward_internal(lob_policy *pol, const float *d_obs, int32_t n_envs,
         dim3 grid((n_envs + 127) / 128, pol->A);
         k_policy_bf16<<<grid, PT, sizeof(Bf16Smem), s>>>(pp);
     } else {
-        dim3 grid((n_envs + 63) / 64, pol->A);
-        k_policy_fp32<<<grid, 64, sizeof(F32Smem), s>>>(pp);
+        dim3 grid((n_envs + 127) / 128, pol->A);
+        k_policy_fp32<<<grid, FT, sizeof(F32Smem), s>>>(pp);
     }
     pol->launches++;
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }
 
 int policy_n_agents(const lob_policy *pol) { return pol ? pol->A : 0; }
+void policy_fused_params(const lob_policy *pol, lobk::FusedParams *f) {
+    f->wrow = pol->d_wrow;
+    f->wrow_stride = pol->wrow_stride;
+    f->wf32 = pol->d_wf32;
+    f->wf32_stride = pol->wf32_stride;
+    f->D = pol->D;
+    f->Dp = pol->Dp;
+    f->L = pol->L;
+    f->status = pol->d_status;
+    f->wait_budget = 2000000000LL;
+}
+void policy_count_launch(lob_policy *pol) { pol->launches++; }
 int policy_obs_dim(const lob_policy *pol) { return pol ? pol->D : 0; }
 long long policy_launches(const lob_policy *pol) { return pol ? pol->launches : 0; }
 

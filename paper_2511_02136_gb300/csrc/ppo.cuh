@@ -1,0 +1,573 @@
+// ppo.cuh -- the IPPO update on the GPU (JaxMARL-HFT Sec. 4.2: independent
+// PPO, every agent its own actor-critic network and its own data).
+//
+// The update is the textbook one: generalised advantage estimation
+// (Schulman et al. 2016), the clipped surrogate with value and entropy terms
+// (Schulman et al. 2017), the gradient through the network of policy.cuh,
+// clipping to a global L2 norm and Adam (Kingma & Ba 2015).  Per minibatch:
+//
+//   k_ppo_gae      (once per update) advantages and value targets per
+//                  (agent, env), backwards over the rollout;
+//   k_ppo_stats    mean and 1 / (std + 1e-8) of the minibatch's advantages;
+//   k_ppo_grad     forward, loss gradient and backward of 128-sample tiles on
+//                  the tensor cores (tcgen05, BF16 operands, FP32 TMEM
+//                  accumulators), the weight gradients accumulated in TMEM
+//                  over all tiles a CTA takes, then added to the FP32
+//                  gradient buffer;
+//   k_ppo_sqnorm   the squared global gradient norm per agent;
+//   k_ppo_adam     clip, Adam, and the BF16 repack of the new weights for
+//                  both this update and the rollout's forward.
+//
+// The eight contractions of a tile (M = 128 everywhere; operands in the
+// no-swizzle K-major core-matrix layout of policy.cuh):
+//   U1 = X W1^T,  U2 = H1 W2^T,  Y = H2 W3^T                  (forward)
+//   dH2 = dY W3,  dH1 = dU2 W2                                (input gradients)
+//   dW3^T += H2^T dY,  dW2 += dU2^T [H1 | 1],  dW1 += dU1^T [X | 1]
+// where the weight-gradient products contract over the tile's samples (the
+// transposed tiles are written that way by the epilogues).  A column of ones
+// after the inputs (X's column D) and after H1 (row 128 of H1^T) gives db1 and
+// db2 as the last columns of dW1 and dW2; db3 is a 16-wide sum.
+#pragma once
+#include "tc05.cuh"
+
+namespace ppo {
+
+using pol::H;
+using pol::NA;
+using pol::NOUT;
+using pol::cm_off;
+
+constexpr int PPT = 256;        // threads per CTA of the gradient kernel
+constexpr int DPMAX = 48;       // widest padded input (obs dim + 1 <= 48: up to 10 levels)
+constexpr int H1T_ROWS = 144;   // H1^T with its ones row, padded to a multiple of 16
+
+struct GradParams {
+    int A, D, Dp;                // Dp = padded (D + 1)
+    int L;
+    int n_envs;
+    long long n_samples;         // T * n_envs (per agent)
+    const float *obs;            // [T][n_envs][A][D]
+    const int *actions;          // [T][n_envs][A]
+    const float *logp_old;       // [T][n_envs][A]
+    const float *adv;            // [A][n_samples]
+    const float *ret;            // [A][n_samples]
+    const int *perm;             // [A][n_samples] sample order
+    long long mb_begin;          // this minibatch: perm positions [mb_begin, mb_begin + mb_size)
+    int mb_size;
+    const float *stats;          // [A][2]: mean, 1 / (std + 1e-8) of the minibatch's advantages
+    const unsigned char *wpk;    // per agent: W1 [128 x Dp], W2, W3 [16 x 128], W3^T [128 x 16], W2^T, bf16 core layout
+    long long wpk_stride;        // bytes per agent
+    const float *wf32;           // per agent parameter block (biases read from here)
+    long long wf32_stride;
+    float *grad;                 // [A][P] FP32, zeroed by the host before the launch
+    float clip_eps, vf_coef, ent_coef;
+    int *status;
+    long long wait_budget;
+};
+
+// Shared memory of the gradient kernel (one CTA per SM).
+struct __align__(1024) GradSmem {
+    unsigned char w1[H * DPMAX * 2];
+    unsigned char w2[H * H * 2];
+    unsigned char w3[16 * H * 2];
+    unsigned char w3t[H * 16 * 2];
+    unsigned char w2t[H * H * 2];
+    unsigned char x[128 * DPMAX * 2];       // X [128 samples x Dp]
+    unsigned char xt[DPMAX * 128 * 2];      // [X | 1]^T [Dp x 128 samples]
+    unsigned char r1[128 * H * 2];          // H1, then H2, then dU2, then dU1^T
+    unsigned char r2[H1T_ROWS * 128 * 2];   // [H1 | 1]^T [144 x 128 samples]
+    unsigned char r3[H * 128 * 2];          // H2^T, then dU2^T
+    unsigned char dy[128 * 16 * 2];         // dY [128 samples x 16]
+    unsigned char dyt[16 * 128 * 2];        // dY^T [16 x 128 samples]
+    float b1[H], b2[H], b3[16];
+    float db3[16];
+    int act[128];
+    float lpo[128], an[128], rt[128];
+    unsigned long long bar, wbar;
+    unsigned tmem_base;
+};
+
+// TMEM columns of the gradient kernel (512 allocated).
+constexpr unsigned TC_ACC = 0;      // 128: U1, U2, dH2, dH1 in turn
+constexpr unsigned TC_Y = 128;      // 16: Y
+constexpr unsigned TC_DW3 = 144;    // 16: dW3^T [128 h2 units x 16 outputs]
+constexpr unsigned TC_DW1 = 160;    // Dp <= 48: dW1 [128 u1 units x Dp]
+constexpr unsigned TC_DW2 = 224;    // 144: dW2 [128 u2 units x (128 + ones + pad)]
+
+__device__ __forceinline__ void st_bf16(unsigned char *tile, unsigned off, float v) {
+    *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ float ld_bf16(const unsigned char *tile, unsigned off) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(tile + off));
+}
+
+// Issue C (+)= A B^T over K in steps of 16 (one thread); A [128 x K], B [N x K].
+__device__ __forceinline__ void gemm(unsigned tmem_d, const unsigned char *A_, const unsigned char *B_, int K, int N,
+                                     bool acc) {
+    const unsigned idesc = pol::idesc_bf16(128, N);
+    for (int kk = 0; kk < K / 16; kk++) {
+        const unsigned long long da = pol::sdesc(A_ + kk * 256, 128, (unsigned)(K / 8) * 128);
+        const unsigned long long db = pol::sdesc(B_ + kk * 256, 128, (unsigned)(K / 8) * 128);
+        pol::mma_bf16(tmem_d, da, db, idesc, (acc || kk > 0) ? 1 : 0);
+    }
+}
+
+// Commit the issued MMAs and wait for them (all threads); false on timeout.
+__device__ __forceinline__ bool mma_round(GradSmem &sm, unsigned &phase, const GradParams &p, int tid) {
+    if (tid == 0) pol::mma_commit(&sm.bar);
+    const bool arrived = pol::pbar_wait(&sm.bar, phase, p.wait_budget);
+    if (__syncthreads_or(!arrived)) {
+        if (tid == 0) atomicOr(p.status, 4);
+        pol::pbar_wait(&sm.bar, phase, p.wait_budget);   // let the tensor core finish before TMEM is freed
+        return false;
+    }
+    phase ^= 1u;
+    pol::tc_fence_after();
+    return true;
+}
+// Make the threads' shared-memory writes visible to the tensor core.
+__device__ __forceinline__ void to_async() {
+    pol::fence_async_smem();
+    pol::tc_fence_before();
+    __syncthreads();
+    pol::tc_fence_after();
+}
+
+__global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
+    extern __shared__ __align__(1024) unsigned char graw[];
+    GradSmem &sm = *reinterpret_cast<GradSmem *>(graw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int a = blockIdx.y;
+    const int Dp = p.Dp, D = p.D;
+    const int n_tiles = (p.mb_size + 127) / 128;
+    if (warp == 0) pol::tm_alloc(&sm.tmem_base, 512);
+    if (tid == 0) {
+        pol::pbar_init(&sm.bar);
+        pol::pbar_init(&sm.wbar);
+        const unsigned char *src = p.wpk + (long long)a * p.wpk_stride;
+        const unsigned n1 = (unsigned)(H * Dp * 2), n2 = H * H * 2, n3 = 16 * H * 2;
+        pol::pbar_expect(&sm.wbar, n1 + 2 * n2 + 2 * n3);
+        pol::bulk_g2s(sm.w1, src, n1, &sm.wbar);
+        pol::bulk_g2s(sm.w2, src + n1, n2, &sm.wbar);
+        pol::bulk_g2s(sm.w3, src + n1 + n2, n3, &sm.wbar);
+        pol::bulk_g2s(sm.w3t, src + n1 + n2 + n3, n3, &sm.wbar);
+        pol::bulk_g2s(sm.w2t, src + n1 + n2 + 2 * n3, n2, &sm.wbar);
+    }
+    {
+        const float *wf = p.wf32 + (long long)a * p.wf32_stride;
+        const float *b1 = wf + H * D, *b2 = b1 + H + H * H, *b3 = b2 + H + NOUT * H;
+        if (tid < H) sm.b1[tid] = b1[tid];
+        else sm.b2[tid - H] = b2[tid - H];
+        if (tid < 16) {
+            sm.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
+            sm.db3[tid] = 0.0f;
+        }
+    }
+    pol::tc_fence_before();
+    __syncthreads();
+    pol::tc_fence_after();
+    const unsigned tmem = sm.tmem_base;
+    const int row = 32 * (warp & 3) + lane;         // TMEM lane = sample row (or unit row for dW)
+    const int half = warp >> 2;
+    const unsigned lrow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+    bool ok = true;
+    unsigned phase = 0;
+    {
+        const bool landed = pol::pbar_wait(&sm.wbar, 0, p.wait_budget);
+        if (__syncthreads_or(!landed)) {
+            ok = false;
+            if (tid == 0) atomicOr(p.status, 4);
+            pol::pbar_wait(&sm.wbar, 0, p.wait_budget);
+        }
+    }
+    const float mean = p.stats[2 * a], istd = p.stats[2 * a + 1];
+    const float inv_b = 1.0f / (float)p.mb_size;
+    const float *advp = p.adv + (long long)a * p.n_samples, *retp = p.ret + (long long)a * p.n_samples;
+    const int *perm = p.perm + (long long)a * p.n_samples + p.mb_begin;
+    bool first = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        // ---- stage the tile: X (scaled, bf16, ones column D), X^T, per-row data
+        {
+            const int r0 = tile * 128;
+            for (int i = tid; i < 128; i += PPT) {
+                const bool valid = r0 + i < p.mb_size;
+                const long long smp = valid ? perm[r0 + i] : 0;
+                const long long t = smp / p.n_envs, e = smp - t * p.n_envs;
+                const long long ra = (t * p.n_envs + e) * p.A + a;
+                sm.act[i] = valid ? p.actions[ra] : 0;
+                sm.lpo[i] = valid ? p.logp_old[ra] : 0.0f;
+                sm.an[i] = valid ? (advp[smp] - mean) * istd : 0.0f;
+                sm.rt[i] = valid ? retp[smp] : 0.0f;
+            }
+            // warp w stages rows w, w + 8, ...; lanes along the features
+            for (int i = warp; i < 128; i += PPT / 32) {
+                const bool valid = r0 + i < p.mb_size;
+                const long long smp = valid ? perm[r0 + i] : 0;
+                const long long t = smp / p.n_envs, e = smp - t * p.n_envs;
+                const float *o = p.obs + ((t * p.n_envs + e) * p.A + a) * (long long)D;
+                for (int k = lane; k < Dp; k += 32) {
+                    float v = 0.0f;
+                    if (valid) v = k < D ? o[k] * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
+                    st_bf16(sm.x, cm_off(i, k, Dp), k < D ? v : 0.0f);   // the forward's X has no ones column
+                    st_bf16(sm.xt, cm_off(k, i, 128), v);
+                }
+            }
+        }
+        to_async();
+        // ---- U1 = X W1^T
+        if (tid == 0) gemm(tmem + TC_ACC, sm.x, sm.w1, Dp, H, false);
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        // h1 = tanh(U1 + b1) -> H1 (r1) and [H1 | 1]^T (r2)
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_ACC + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                unsigned w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float h0 = pol::tanh_approx(v[j + 2 * q] + sm.b1[c0 + j + 2 * q]);
+                    const float h1 = pol::tanh_approx(v[j + 2 * q + 1] + sm.b1[c0 + j + 2 * q + 1]);
+                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
+                    w[q] = *reinterpret_cast<const unsigned *>(&t2);
+                    st_bf16(sm.r2, cm_off(c0 + j + 2 * q, row, 128), h0);
+                    st_bf16(sm.r2, cm_off(c0 + j + 2 * q + 1, row, 128), h1);
+                }
+                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        {   // the ones row (valid samples) and the zero padding rows of [H1 | 1]^T
+            const bool valid = tile * 128 + row < p.mb_size;
+            for (int k = H + half; k < H1T_ROWS; k += 2) st_bf16(sm.r2, cm_off(k, row, 128), (k == H && valid) ? 1.0f : 0.0f);
+        }
+        to_async();
+        // ---- U2 = H1 W2^T
+        if (tid == 0) gemm(tmem + TC_ACC, sm.r1, sm.w2, H, H, false);
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_ACC + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                unsigned w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float h0 = pol::tanh_approx(v[j + 2 * q] + sm.b2[c0 + j + 2 * q]);
+                    const float h1 = pol::tanh_approx(v[j + 2 * q + 1] + sm.b2[c0 + j + 2 * q + 1]);
+                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
+                    w[q] = *reinterpret_cast<const unsigned *>(&t2);
+                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q, row, 128), h0);
+                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q + 1, row, 128), h1);
+                }
+                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        to_async();
+        // ---- Y = H2 W3^T, then the loss gradient dY per sample
+        if (tid == 0) gemm(tmem + TC_Y, sm.r1, sm.w3, H, 16, false);
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (half == 0) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_Y, v);   // columns 16..31 lie in dW3's accumulator: unused here
+            const bool valid = tile * 128 + row < p.mb_size;
+            float z[NA];
+            float m = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < NA; j++) {
+                z[j] = v[j] + sm.b3[j];
+                m = fmaxf(m, z[j]);
+            }
+            const float V = v[NA] + sm.b3[NA];
+            float se = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NA; j++) se += __expf(z[j] - m);
+            const float lse = m + __logf(se);
+            float pj[NA], lp[NA], S = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NA; j++) {
+                lp[j] = z[j] - lse;
+                pj[j] = __expf(lp[j]);
+                S -= pj[j] * lp[j];
+            }
+            const int act = sm.act[row];
+            float lpa = lp[0];
+#pragma unroll
+            for (int j = 1; j < NA; j++)
+                if (j == act) lpa = lp[j];
+            const float rho = __expf(lpa - sm.lpo[row]);
+            const float An = sm.an[row];
+            const float rc = fminf(fmaxf(rho, 1.0f - p.clip_eps), 1.0f + p.clip_eps);
+            const float g_rho = (rho * An <= rc * An) ? -An : 0.0f;
+            float dy[16];
+#pragma unroll
+            for (int j = 0; j < NA; j++) {
+                const float pg = g_rho * rho * ((j == act ? 1.0f : 0.0f) - pj[j]);
+                dy[j] = valid ? (pg + p.ent_coef * pj[j] * (lp[j] + S)) * inv_b : 0.0f;
+            }
+            dy[NA] = valid ? p.vf_coef * (V - sm.rt[row]) * inv_b : 0.0f;
+#pragma unroll
+            for (int j = NA + 1; j < 16; j++) dy[j] = 0.0f;
+            unsigned w[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const __nv_bfloat162 t2 = __floats2bfloat162_rn(dy[2 * q], dy[2 * q + 1]);
+                w[q] = *reinterpret_cast<const unsigned *>(&t2);
+            }
+            *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+            for (int j = 0; j < 16; j++) st_bf16(sm.dyt, cm_off(j, row, 128), dy[j]);
+            // db3: the bf16-rounded dY the other products use, summed over the tile
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                float s = __bfloat162float(__float2bfloat16_rn(dy[j]));
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) atomicAdd(&sm.db3[j], s);
+            }
+        }
+        to_async();
+        // ---- dH2 = dY W3 and dW3^T += H2^T dY
+        if (tid == 0) {
+            gemm(tmem + TC_ACC, sm.dy, sm.w3t, 16, H, false);
+            gemm(tmem + TC_DW3, sm.r3, sm.dyt, 128, 16, !first);
+        }
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        // dU2 = dH2 (1 - h2^2): dU2 into r1 in place of H2, dU2^T into r3
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_ACC + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                const uint4 hv = *reinterpret_cast<const uint4 *>(sm.r1 + cm_off(row, c0 + j, H));
+                const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                unsigned w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&hw[q]);
+                    const float ha = __low2float(h2), hb = __high2float(h2);
+                    const float d0 = v[j + 2 * q] * (1.0f - ha * ha), d1 = v[j + 2 * q + 1] * (1.0f - hb * hb);
+                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(d0, d1);
+                    w[q] = *reinterpret_cast<const unsigned *>(&t2);
+                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q, row, 128), d0);
+                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q + 1, row, 128), d1);
+                }
+                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        to_async();
+        // ---- dH1 = dU2 W2 and dW2 += dU2^T [H1 | 1]
+        if (tid == 0) {
+            gemm(tmem + TC_ACC, sm.r1, sm.w2t, H, H, false);
+            gemm(tmem + TC_DW2, sm.r3, sm.r2, 128, H1T_ROWS, !first);
+        }
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        // dU1 = dH1 (1 - h1^2), h1 from [H1 | 1]^T: dU1^T into r1
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_ACC + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const float h = ld_bf16(sm.r2, cm_off(c0 + j, row, 128));
+                st_bf16(sm.r1, cm_off(c0 + j, row, 128), v[j] * (1.0f - h * h));
+            }
+        }
+        to_async();
+        // ---- dW1 += dU1^T [X | 1]
+        if (tid == 0) gemm(tmem + TC_DW1, sm.r1, sm.xt, 128, Dp, !first);
+        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        first = false;
+    }
+    // ---- the CTA's weight gradients into the FP32 buffer
+    if (ok && !first) {
+        float *g = p.grad + (long long)a * p.wf32_stride;
+        float *gW1 = g, *gb1 = g + H * D, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + NOUT * H;
+        // dW1 (row = u1 unit): columns < D, column D = db1
+        for (int c0 = 32 * half; c0 < Dp; c0 += 64) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_DW1 + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int k = c0 + j;
+                if (k < D) atomicAdd(&gW1[row * D + k], v[j]);
+                else if (k == D) atomicAdd(&gb1[row], v[j]);
+            }
+        }
+        // dW2 (row = u2 unit): columns < 128, column 128 = db2
+        for (int c0 = 32 * half; c0 < H1T_ROWS; c0 += 64) {
+            float v[32];
+            if (c0 + 32 <= 160) {
+                pol::tm_ld32(lrow + TC_DW2 + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const int k = c0 + j;
+                    if (k < H) atomicAdd(&gW2[row * H + k], v[j]);
+                    else if (k == H) atomicAdd(&gb2[row], v[j]);
+                }
+            }
+        }
+        // dW3^T (row = h2 unit, column = output)
+        if (half == 0) {
+            float v[32];
+            pol::tm_ld32(lrow + TC_DW3, v);
+#pragma unroll
+            for (int o = 0; o < NOUT; o++) atomicAdd(&gW3[o * H + row], v[o]);
+        }
+        if (tid < NOUT) atomicAdd(&gb3[tid], sm.db3[tid]);
+    }
+    pol::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        pol::tc_fence_after();
+        pol::tm_dealloc(tmem, 512);
+    }
+}
+
+// Advantages and value targets (GAE), one thread per (agent, env), backwards
+// over the rollout: delta = r + gamma (1 - d) V' - V, A = delta + gamma lambda (1 - d) A'.
+__global__ void k_ppo_gae(const long long *rewards, const float *values, const unsigned char *done, int T, int n,
+                          int A, float gamma, float lam, float reward_scale, float *adv, float *ret) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * A) return;
+    const int e = i / A, a = i - e * A;
+    const long long ns = (long long)T * n;
+    float nxt = 0.0f;
+    for (int t = T - 1; t >= 0; t--) {
+        const long long ra = ((long long)t * n + e) * A + a;
+        const float live = done[(long long)t * n + e] ? 0.0f : 1.0f;
+        const float r = reward_scale * (float)rewards[ra];
+        const float v = values[ra];
+        const float vn = values[((long long)(t + 1) * n + e) * A + a];
+        const float delta = r + gamma * live * vn - v;
+        nxt = delta + gamma * lam * live * nxt;
+        adv[(long long)a * ns + (long long)t * n + e] = nxt;
+        ret[(long long)a * ns + (long long)t * n + e] = nxt + v;
+    }
+}
+
+// Sum and sum of squares (FP64) of the minibatch's advantages per agent.
+__global__ void k_ppo_stats(const float *adv, const int *perm, long long ns, long long mb_begin, int mb_size,
+                            double *acc) {
+    const int a = blockIdx.y;
+    double s = 0.0, s2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < mb_size; i += (long long)gridDim.x * blockDim.x) {
+        const double v = adv[(long long)a * ns + perm[(long long)a * ns + mb_begin + i]];
+        s += v;
+        s2 += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[2 * a], s);
+        atomicAdd(&acc[2 * a + 1], s2);
+    }
+}
+// mean and 1 / (std + 1e-8) (population std) from the sums.
+__global__ void k_ppo_stats_fin(const double *acc, int A, int mb_size, float *stats) {
+    const int a = threadIdx.x;
+    if (a >= A) return;
+    const double mean = acc[2 * a] / mb_size;
+    double var = acc[2 * a + 1] / mb_size - mean * mean;
+    var = var > 0.0 ? var : 0.0;
+    stats[2 * a] = (float)mean;
+    stats[2 * a + 1] = (float)(1.0 / (sqrt(var) + 1e-8));
+}
+
+// Squared L2 norm of each agent's gradient (FP64 sums).
+__global__ void k_ppo_sqnorm(const float *grad, long long P, double *out) {
+    const int a = blockIdx.y;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        const double g = grad[(long long)a * P + i];
+        s += g * g;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[a], s);
+}
+
+struct AdamParams {
+    int A, D, Dp, Dpf;               // Dp: the update's padded width, Dpf: the rollout forward's
+    long long P;
+    float *w;                        // [A][P] master FP32 parameters
+    float *m, *v;                    // [A][P] Adam moments
+    const float *grad;               // [A][P]
+    const double *sqnorm;            // [A]
+    float lr, beta1, beta2, eps, max_norm;
+    float bc1, bc2;                  // 1 - beta^t for this step
+    unsigned char *wpk;              // the update's packed bf16 weights
+    long long wpk_stride;
+    unsigned char *wfwd;             // the rollout forward's packed bf16 weights (W1 [128 x Dpf], W2, W3)
+    long long wfwd_stride;
+    unsigned char *wrow;             // the fused rollout's row-major bf16 weights (W1 [128 x Dpf], W2, W3 [16 x 128])
+    long long wrow_stride;
+};
+
+// Weight i of an agent's block (a weight matrix entry; biases are skipped)
+// into both packed bf16 layouts: the update's (W1, W2, W3, W3^T, W2^T) and the
+// rollout forward's (W1, W2, W3).
+__device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long i, float w) {
+    const int D = p.D;
+    unsigned char *u = p.wpk + (long long)a * p.wpk_stride;
+    unsigned char *f = p.wfwd + (long long)a * p.wfwd_stride;
+    unsigned char *rw = p.wrow + (long long)a * p.wrow_stride;
+    const unsigned n1 = (unsigned)(H * p.Dp * 2), n1f = (unsigned)(H * p.Dpf * 2), n2 = H * H * 2, n3 = 16 * H * 2;
+    long long o = i;
+    if (o < (long long)H * D) {
+        const int r = (int)(o / D), c = (int)(o % D);
+        st_bf16(u, cm_off(r, c, p.Dp), w);
+        st_bf16(f, cm_off(r, c, p.Dpf), w);
+        st_bf16(rw, (unsigned)(2 * (r * p.Dpf + c)), w);
+        return;
+    }
+    o -= (long long)H * D + H;
+    if (o >= 0 && o < (long long)H * H) {
+        const int r = (int)(o / H), c = (int)(o % H);
+        st_bf16(u + n1, cm_off(r, c, H), w);                      // W2 [out x in]
+        st_bf16(u + n1 + n2 + 2 * n3, cm_off(c, r, H), w);        // W2^T [in x out]
+        st_bf16(f + n1f, cm_off(r, c, H), w);
+        st_bf16(rw + n1f, (unsigned)(2 * (r * H + c)), w);
+        return;
+    }
+    o -= (long long)H * H + H;
+    if (o >= 0 && o < (long long)NOUT * H) {
+        const int r = (int)(o / H), c = (int)(o % H);
+        st_bf16(u + n1 + n2, cm_off(r, c, H), w);                 // W3 [16 x 128]
+        st_bf16(u + n1 + n2 + n3, cm_off(c, r, 16), w);           // W3^T [128 x 16]
+        st_bf16(f + n1f + n2, cm_off(r, c, H), w);
+        st_bf16(rw + n1f + n2, (unsigned)(2 * (r * H + c)), w);
+    }
+}
+
+// The packed layouts from the FP32 weights (before the first update; the
+// padding of the update's layout is zeroed by the host).
+__global__ void k_ppo_pack(const AdamParams p) {
+    const int a = blockIdx.y;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += (long long)gridDim.x * blockDim.x)
+        repack_one(p, a, i, p.w[(long long)a * p.P + i]);
+}
+
+// Clip to the global norm, one Adam step, and the bf16 repack of every
+// changed weight into both packed layouts.
+__global__ void k_ppo_adam(const AdamParams p) {
+    const int a = blockIdx.y;
+    const double n2 = p.sqnorm[a];
+    const float nrm = (float)sqrt(n2);
+    const float sc = (nrm > p.max_norm && nrm > 0.0f) ? p.max_norm / nrm : 1.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += (long long)gridDim.x * blockDim.x) {
+        const long long k = (long long)a * p.P + i;
+        const float g = p.grad[k] * sc;
+        const float m = p.beta1 * p.m[k] + (1.0f - p.beta1) * g;
+        const float v = p.beta2 * p.v[k] + (1.0f - p.beta2) * g * g;
+        p.m[k] = m;
+        p.v[k] = v;
+        const float w = p.w[k] - p.lr * (m / p.bc1) / (sqrtf(v / p.bc2) + p.eps);
+        p.w[k] = w;
+        repack_one(p, a, i, w);   // the weight matrices (biases stay FP32)
+    }
+}
+
+}  // namespace ppo

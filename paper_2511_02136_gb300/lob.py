@@ -25,9 +25,12 @@ _INC = os.path.join(_ROOT, "include")
 CHECKED = os.environ.get("LOB_CHECKED") == "1"
 LIB_PATH = os.path.join(_PKG, "liblob_checked.so" if CHECKED else "liblob.so")
 _SOURCES = [os.path.join(_CSRC, n) for n in
-            ["lob_api.cu", "policy_api.cu"] + [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)] +
+            ["lob_api.cu", "policy_api.cu", "rollout_fused_k4.cu", "rollout_fused_k8.cu", "steps_multi.cu"] +
+            [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)] +
             [f"steps_ma_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
-_DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "policy.cuh", "policy_internal.h",
+_DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "lob_ladder.cuh", "policy.cuh", "tc05.cuh", "ppo.cuh",
+                                                      "fused.cuh", "rollout_fused.cuh",
+                                                      "policy_internal.h",
                                                       "lob_steps.h", "steps_inst.cuh", "steps_ma_inst.cuh")] + \
     [os.path.join(_INC, "lob.h")]
 _OBJDIR = os.path.join(_PKG, "_build")
@@ -54,7 +57,7 @@ EXPORTS = [
     "lob_policy_sync", "lob_rollout_policy", "lob_set_env_costs",
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
     "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
-    "lob_live_orders",
+    "lob_live_orders", "lob_policy_get_params", "lob_ppo_update", "lob_set_multi_split",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
@@ -82,6 +85,20 @@ class lob_config(ctypes.Structure):
         "exec_target", "exec_dir", "action_mode", "trace", "start_px", "warps_per_block",
         "reward_mode", "spooner_lambda_pct", "inv_penalty", "exec_penalty_milli", "mm_space", "pv_ref")] + \
         [("reserved", ctypes.c_int32 * 2)]
+
+
+class lob_ppo_hparams(ctypes.Structure):
+    """Hyperparameters of lob_ppo_update (see include/lob.h)."""
+    _fields_ = [(n, ctypes.c_float) for n in ("gamma", "gae_lambda", "clip_eps", "vf_coef", "ent_coef", "lr",
+                                                "beta1", "beta2", "adam_eps", "max_grad_norm", "reward_scale")] + \
+        [("n_minibatches", ctypes.c_int32)]
+
+
+class lob_ppo_batch(ctypes.Structure):
+    """Rollout data of lob_ppo_update (device pointers, see include/lob.h)."""
+    _fields_ = [("T", ctypes.c_int32), ("n_envs", ctypes.c_int32)] + \
+        [(n, ctypes.c_void_p) for n in ("d_obs", "d_actions", "d_logp_old", "d_values", "d_rewards", "d_done",
+                                        "d_perm", "d_grad_out")]
 
 
 class lob_noalloc_args(ctypes.Structure):
@@ -167,6 +184,7 @@ def _load():
         "lob_get_env_misc": (ctypes.c_int, [P, P, P]),
         "lob_get_actions": (ctypes.c_int, [P, P, P]),
         "lob_live_orders": (ctypes.c_int, [P, P, P]),
+        "lob_set_multi_split": (ctypes.c_int, [P, P]),
         "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
         "lob_sync": (ctypes.c_int, [P, P]),
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
@@ -186,6 +204,8 @@ def _load():
         "lob_load": (ctypes.c_int, [P, P, P]),
         "lob_set_episodes": (ctypes.c_int, [P, P, P, I64, P, P, I32, I64]),
         "lob_get_episode_starts": (ctypes.c_int, [P, P, P]),
+        "lob_policy_get_params": (ctypes.c_int, [P, P, P]),
+        "lob_ppo_update": (ctypes.c_int, [P, ctypes.POINTER(lob_ppo_batch), ctypes.POINTER(lob_ppo_hparams), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -296,6 +316,15 @@ def lob_get_env_misc(h, out, stream=None):
 
 def lob_get_actions(h, out, stream=None):
     return _check(_load().lob_get_actions(h, _dp(out), _stream(stream)), "lob_get_actions")
+
+
+def lob_set_multi_split(h, warps_per_class):
+    """One persistent kernel over the capacity classes, with this many warps of
+    each class per block (LOB_NCLASSES entries; see include/lob.h)."""
+    w = np.ascontiguousarray(warps_per_class, dtype=np.int32)
+    if w.shape != (6,):
+        raise ValueError("six classes")
+    return _check(_load().lob_set_multi_split(h, w.ctypes.data), "lob_set_multi_split")
 
 
 def lob_live_orders(h, acc, stream=None):
@@ -427,6 +456,28 @@ def lob_policy_sync(pol, stream=None):
 def lob_rollout_policy(h, pol, n_steps, precision, obs=None, rewards=None, done=None, actions=None, stream=None):
     return _check(_load().lob_rollout_policy(h, pol, n_steps, precision, _dp(obs), _dp(rewards), _dp(done),
                                              _dp(actions), _stream(stream)), "lob_rollout_policy")
+
+
+def lob_policy_get_params(pol, out, stream=None):
+    """The FP32 parameter blocks of every agent into the device tensor out [n_agents, P]."""
+    return _check(_load().lob_policy_get_params(pol, _dp(out), _stream(stream)), "lob_policy_get_params")
+
+
+def lob_ppo_update(pol, T, n_envs, obs, actions, logp_old, values, rewards, done, perm, hp: lob_ppo_hparams,
+                   grad_out=None, stream=None):
+    """One IPPO epoch on the GPU from rollout tensors (see include/lob.h for the layouts)."""
+    b = lob_ppo_batch(T=T, n_envs=n_envs, d_obs=_dp(obs), d_actions=_dp(actions), d_logp_old=_dp(logp_old),
+                      d_values=_dp(values), d_rewards=_dp(rewards), d_done=_dp(done), d_perm=_dp(perm),
+                      d_grad_out=_dp(grad_out))
+    return _check(_load().lob_ppo_update(pol, ctypes.byref(b), ctypes.byref(hp), _stream(stream)), "lob_ppo_update")
+
+
+def ppo_hparams(**kw) -> lob_ppo_hparams:
+    """The update's hyperparameters with the defaults of the FP64 reference update."""
+    d = dict(gamma=0.99, gae_lambda=0.95, clip_eps=0.2, vf_coef=0.5, ent_coef=0.01, lr=2.5e-4, beta1=0.9,
+             beta2=0.999, adam_eps=1e-5, max_grad_norm=0.5, reward_scale=1e-2, n_minibatches=4)
+    d.update(kw)
+    return lob_ppo_hparams(**d)
 
 
 def init_policy_params(seed: int, n_agents: int, obs_dim: int) -> np.ndarray:

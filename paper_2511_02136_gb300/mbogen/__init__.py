@@ -230,3 +230,111 @@ def start_books(seed: int, mids: np.ndarray, start_steps, levels_per_side: int, 
             px += 1 + int(rng.integers(0, max_gap))
         starts[j] = (int(s), m, nb, na)
     return starts, levels
+
+
+# ---------------------------------------------------------------- device generator
+_GPU_SRC = os.path.join(_HERE, "mbogen_gpu.cu")
+_GPU_LIB = os.path.join(_HERE, "libmbogen_gpu.so")
+_gpu_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile libmbogen_gpu.so (the device generator) in-tree for sm_103a."""
+    with _lock:
+        if (not force and os.path.exists(_GPU_LIB)
+                and os.path.getmtime(_GPU_LIB) >= os.path.getmtime(_GPU_SRC)):
+            return _GPU_LIB
+        tmp = _GPU_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["nvcc", "-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                               "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, _GPU_SRC])
+        os.replace(tmp, _GPU_LIB)
+        return _GPU_LIB
+
+
+def _load_gpu():
+    global _gpu_lib
+    if _gpu_lib is None:
+        lib = ctypes.CDLL(build_gpu())
+        P = ctypes.c_void_p
+        lib.mbogen_gpu_create.restype = ctypes.c_int
+        lib.mbogen_gpu_create.argtypes = [ctypes.c_int64, P, ctypes.c_int32, P, P, ctypes.c_int32, P, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)]
+        lib.mbogen_gpu_chunk.restype = ctypes.c_int
+        lib.mbogen_gpu_chunk.argtypes = [P, ctypes.c_int32, P, P, P, P]
+        lib.mbogen_gpu_status.restype = ctypes.c_int
+        lib.mbogen_gpu_status.argtypes = [P]
+        lib.mbogen_gpu_destroy.restype = ctypes.c_int
+        lib.mbogen_gpu_destroy.argtypes = [P]
+        _gpu_lib = lib
+    return _gpu_lib
+
+
+def tables(model: MessageModel):
+    """The model's draw thresholds (as the host generator builds them)."""
+    lib = _load()
+    lib.mbogen_tables.restype = ctypes.c_int
+    lib.mbogen_tables.argtypes = [ctypes.POINTER(_Params)] + [ctypes.c_void_p] * 6
+    scal = np.zeros(5, np.uint64)
+    geom = np.zeros(4096, np.uint64)
+    size = np.zeros(1 << 16, np.uint64)
+    gn, sn, sb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    p = model._c()
+    if lib.mbogen_tables(ctypes.byref(p), scal.ctypes.data, geom.ctypes.data, ctypes.byref(gn), size.ctypes.data,
+                         ctypes.byref(sn), ctypes.byref(sb)):
+        raise RuntimeError("mbogen_tables failed")
+    return scal, geom[:gn.value].copy(), size[:sn.value].copy(), sb.value
+
+
+class GpuStreams:
+    """The streams of n envs drawn on the current CUDA device, chunk by chunk:
+    chunk(k_steps, out) writes every env's next k_steps steps (fixed messages
+    per step, env-major: env e's step j at records (e * k_steps + j) * M) into
+    the device tensor out, on the given stream.  Byte-identical to generate()."""
+
+    def __init__(self, model: MessageModel, seeds: np.ndarray, pool_cap: int = 32768):
+        import torch
+        if model.poisson:
+            raise ValueError("the device generator draws fixed messages per step")
+        self.torch = torch
+        self.model = model
+        self.n = len(seeds)
+        self.M = model.msgs_per_step
+        scal, geom, size, base = tables(model)
+        seeds = np.ascontiguousarray(seeds, np.uint64)
+        lib = _load_gpu()
+        h = ctypes.c_void_p()
+        rc = lib.mbogen_gpu_create(self.n, seeds.ctypes.data, model.start_mid, scal.ctypes.data, geom.ctypes.data,
+                                   len(geom), size.ctypes.data, len(size), base, 1 if model.size_model == 0 else 0,
+                                   pool_cap, ctypes.byref(h))
+        if rc:
+            raise RuntimeError(f"mbogen_gpu_create failed ({rc})")
+        self.h = h
+        self._shape = None
+
+    def offsets(self, k_steps):
+        """int64 [n][k_steps + 1] record offsets of one chunk (host)."""
+        e = np.arange(self.n, dtype=np.int64)[:, None]
+        j = np.arange(k_steps + 1, dtype=np.int64)[None, :]
+        return (e * k_steps + j) * self.M
+
+    def chunk(self, k_steps, out, stream=None):
+        torch = self.torch
+        if self._shape != k_steps:
+            self._counts = torch.full((self.n, k_steps), self.M, dtype=torch.int32, device="cuda")
+            self._offs = torch.from_numpy(self.offsets(k_steps)).cuda()
+            self._shape = k_steps
+        if out.numel() * out.element_size() < self.n * k_steps * self.M * 32:
+            raise ValueError("output buffer too small")
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        rc = _load_gpu().mbogen_gpu_chunk(self.h, k_steps, self._counts.data_ptr(), self._offs.data_ptr(),
+                                          out.data_ptr(), s)
+        if rc:
+            raise RuntimeError(f"mbogen_gpu_chunk failed ({rc})")
+
+    def ok(self):
+        return _load_gpu().mbogen_gpu_status(self.h) == 0
+
+    def close(self):
+        if self.h:
+            _load_gpu().mbogen_gpu_destroy(self.h)
+            self.h = None

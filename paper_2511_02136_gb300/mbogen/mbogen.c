@@ -373,3 +373,30 @@ void mbogen_env_caps(uint64_t seed, int64_t n_envs, const int32_t *choices, int3
         caps_out[e] = choices[lemire32(sm_next(&s), (uint32_t)n_choices)];
     }
 }
+
+/* The draw thresholds of a model, for the device generator (mbogen_gpu.cu)
+ * to draw the same integers: scal = {move, add, partial, delete, burst};
+ * geom (price gaps, <= 4096 entries) and size (<= 65536 entries) tables with
+ * their lengths and the size table's base value.  Returns -1 on a bad model. */
+int mbogen_tables(const mbogen_params *p, uint64_t *scal, uint64_t *geom, int32_t *geom_n, uint64_t *size,
+                  int32_t *size_n, int32_t *size_base) {
+    double tot = p->mix_add + p->mix_partial + p->mix_delete + p->mix_market;
+    if (!(tot > 0.0)) return -1;
+    scal[0] = prob_to_u64(p->p_move);
+    scal[1] = prob_to_u64(p->mix_add / tot);
+    scal[2] = prob_to_u64((p->mix_add + p->mix_partial) / tot);
+    scal[3] = prob_to_u64((p->mix_add + p->mix_partial + p->mix_delete) / tot);
+    scal[4] = prob_to_u64(p->p_burst);
+    cdf_table g, s;
+    if (build_geom(&g, p->price_p, 0, 4096)) return -1;
+    int rc = p->size_model == 0 ? build_geom(&s, p->size_p, 0, 1 << 16) : build_pareto(&s, p->pareto_alpha, p->size_cap);
+    if (rc || s.n > (1 << 16)) { free(g.thr); if (!rc) free(s.thr); return -1; }
+    memcpy(geom, g.thr, sizeof(uint64_t) * (size_t)g.n);
+    memcpy(size, s.thr, sizeof(uint64_t) * (size_t)s.n);
+    *geom_n = g.n;
+    *size_n = s.n;
+    *size_base = s.base;
+    free(g.thr);
+    free(s.thr);
+    return 0;
+}

@@ -104,3 +104,16 @@ def test_noalloc_rejects_oversize_on_the_host():
     with pytest.raises(lob.LobError) as ei:
         lob.lob_step_noalloc(_noalloc_args(_cfg(n_envs=lob.LOB_NOALLOC_MAX_ENVS + 1)), _DefaultStream)
     assert ei.value.code == lob.LOB_ECAPACITY
+
+
+@pytest.mark.gpu
+def test_multi_split_validated_on_the_host():
+    """The one-launch mode's split: 1..8 warps, classes up to 512 slots, every
+    class with envs covered by a warp of its class or a larger one."""
+    h = lob.lob_create(_cfg(cap_per_side=100))   # one class (128 slots, index 2)
+    for split, code in (((0, 0, 0, 0, 0, 0), lob.LOB_EINVAL), ((0, 0, 0, 0, 0, 1), lob.LOB_EINVAL),
+                        ((0, 1, 0, 0, 0, 0), lob.LOB_EINVAL), ((3, 3, 3, 0, 0, 0), lob.LOB_EINVAL)):
+        with pytest.raises(lob.LobError) as ei:
+            lob.lob_set_multi_split(h, np.array(split, np.int32))
+        assert ei.value.code == code, split
+    lob.lob_set_multi_split(h, np.array((0, 0, 2, 2, 0, 0), np.int32))

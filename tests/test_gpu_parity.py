@@ -237,24 +237,15 @@ def test_step_host_async_pipelined(pinned):
 def test_full_size_1024_envs_1000_steps():
     """The benchmark workload in the benchmark's launch configuration: 1,024
     envs x capacity 100 x 100 messages x 1,000 steps, random policy.  Every
-    env's rewards are summed over all steps on both sides; observations of all
-    envs are compared every 100 steps; books, counters and agents at the end."""
-    import torch
+    step: observations, rewards, actions and done flags of every env against
+    the oracle; books, counters and agents at the end."""
     n, T = 1024, 1000
     st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(1, n), T)
     pr = Pair(n, st, cap=100, exec_target=500, n_threads=os.cpu_count() or 1)
-    rsum_g = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
-    rsum_o = np.zeros((n, 2), np.int64)
     for t in range(T):
         pr.env.step()
         pr.orc.step()
-        _, rew, _ = pr.env.observe()
-        rsum_g += rew
-        _, o_rew, _ = pr.orc.observe()
-        rsum_o += o_rew
-        if t % 100 == 99:
-            pr.check_outputs()
-    np.testing.assert_array_equal(rsum_g.cpu().numpy(), rsum_o)
+        pr.check_outputs()
     pr.check_state()
     assert pr.env.sync() == 0
     pr.close()
@@ -419,7 +410,9 @@ def test_stress_mix_cap1000_top20():
 def _sampled_pair_check(n_all, sample, model, T, cap=None, caps=None, top_levels=10, exec_target=500,
                         rollout=False, graph=False):
     """All n_all envs on the GPU; the oracle runs the sampled envs only (env
-    streams depend on their own seed only) and must agree on them exactly."""
+    streams depend on their own seed only) and must agree on them exactly:
+    observations, rewards and done flags of every sampled env at every step,
+    then books, counters and agents."""
     import oracle
     import torch
     from harness import to_dev
@@ -430,50 +423,57 @@ def _sampled_pair_check(n_all, sample, model, T, cap=None, caps=None, top_levels
                      action_mode=lob.LOB_ACT_RANDOM, caps=caps_all)
     lob.lob_set_launch(env.h, 4, 1)
     md, od = to_dev(st.msgs), to_dev(st.offsets)
+    del st
     env.load_messages(md, od)
     env.reset(to_dev(seeds))
     D = env.D
-    obs_last = None
+    sidx = torch.from_numpy(np.asarray(sample, np.int64)).cuda()
     if rollout:
         obs = torch.zeros((T, n_all, 2, D), dtype=torch.float32, device="cuda")
         rew = torch.zeros((T, n_all, 2), dtype=torch.int64, device="cuda")
+        done = torch.zeros((T, n_all), dtype=torch.uint8, device="cuda")
         if graph:
             s_ = torch.cuda.Stream()
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s_):
-                lob.lob_rollout(env.h, T, None, obs, rew, None, stream=s_)
+                lob.lob_rollout(env.h, T, None, obs, rew, done, stream=s_)
             g.replay()
         else:
-            lob.lob_rollout(env.h, T, None, obs, rew, None)
+            lob.lob_rollout(env.h, T, None, obs, rew, done)
         torch.cuda.synchronize()
-        obs_last = obs[T - 1].cpu().numpy()
-        rew_sum = rew.sum(0).cpu().numpy()
+        g_obs = obs.index_select(1, sidx).cpu().numpy()
+        g_rew = rew.index_select(1, sidx).cpu().numpy()
+        g_done = done.index_select(1, sidx).cpu().numpy()
+        del obs, rew, done
     else:
-        rew_sum = torch.zeros((n_all, 2), dtype=torch.int64, device="cuda")
-        for _ in range(T):
+        g_obs = np.zeros((T, len(sample), 2, D), np.float32)
+        g_rew = np.zeros((T, len(sample), 2), np.int64)
+        g_done = np.zeros((T, len(sample)), np.uint8)
+        for t in range(T):
             env.step()
-            rew_sum += env.observe()[1]
-        obs_last = env.observe()[0].cpu().numpy()
-        rew_sum = rew_sum.cpu().numpy()
+            o_, r_, d_ = env.observe()
+            g_obs[t] = o_.index_select(0, sidx).cpu().numpy()
+            g_rew[t] = r_.index_select(0, sidx).cpu().numpy()
+            g_done[t] = d_.index_select(0, sidx).cpu().numpy()
     assert env.sync() == 0
     g_cnt = env.counters().cpu().numpy()
     g_books = env.books()
     g_agents = env.agents().cpu().numpy()
     env.close()
+    del md, od
     o = oracle.Oracle(len(sample), cap=cap or 100, top_levels=top_levels, episode_len=T, exec_target=exec_target,
                       action_mode=1, n_threads=os.cpu_count() or 1,
                       caps=None if caps is None else np.asarray(caps)[sample])
     sub = mbogen.generate(model, seeds[sample], T)
     o.reset(sub.seeds)
     o.load_messages(sub.msgs, sub.offsets)
-    o_rsum = np.zeros((len(sample), 2), np.int64)
-    for _ in range(T):
+    for t in range(T):
         o.step()
-        o_rsum += o.observe()[1]
-    o_obs = o.observe()[0]
-    np.testing.assert_array_equal(rew_sum[sample], o_rsum)
-    np.testing.assert_allclose(obs_last[sample], o_obs, rtol=1e-6, atol=0)
+        o_obs, o_rew, o_done = o.observe()
+        np.testing.assert_array_equal(g_rew[t], o_rew, err_msg=f"rewards at step {t}")
+        np.testing.assert_allclose(g_obs[t], o_obs, rtol=1e-6, atol=0, err_msg=f"observations at step {t}")
+        np.testing.assert_array_equal(g_done[t], o_done, err_msg=f"done at step {t}")
     np.testing.assert_array_equal(g_cnt[sample], o.counters())
     np.testing.assert_array_equal(g_agents[sample], o.agents())
     for i, e in enumerate(sample):
@@ -489,21 +489,132 @@ def _sampled_pair_check(n_all, sample, model, T, cap=None, caps=None, top_levels
 
 
 def test_uneven_batch_8192_envs_one_graph_launch():
-    """8,192 envs, capacities uniform in {50, 100, 200, 500}, M_t ~ Poisson with
-    lambda log-uniform in [10, 500]; all steps in one persistent launch under a
-    captured CUDA graph; every 64th env checked against the oracle."""
+    """The uneven batch at its stated length: 8,192 envs, capacities uniform in
+    {50, 100, 200, 500}, M_t ~ Poisson with lambda log-uniform in [10, 500],
+    all 500 steps in one persistent launch under a captured CUDA graph; every
+    64th env checked against the oracle at every step."""
     n = 8192
     caps = mbogen.env_caps(5, n)
-    _sampled_pair_check(n, np.arange(0, n, 64), mbogen.MessageModel(poisson=True), 40, cap=500, caps=caps,
+    _sampled_pair_check(n, np.arange(0, n, 64), mbogen.MessageModel(poisson=True), 500, cap=500, caps=caps,
                         rollout=True, graph=True)
+
+
+def test_uneven_batch_one_kernel_over_all_classes():
+    """The uneven batch's classes (capacities 50, 100, 200, 500 and a few of 20)
+    in one persistent launch whose warps steal smaller classes' envs, for two
+    block splits; every 16th of 2,048 envs checked at every step."""
+    import oracle
+    import torch
+    from harness import to_dev
+    n, T = 2048, 30
+    caps = mbogen.env_caps(9, n, choices=(20, 50, 100, 200, 500))
+    seeds = mbogen.env_seeds(78, n)
+    st = mbogen.generate(mbogen.MessageModel(poisson=True), seeds, T)
+    sample = np.arange(0, n, 16)
+    sub = mbogen.generate(mbogen.MessageModel(poisson=True), seeds[sample], T)
+    for split in ((1, 1, 1, 1, 1, 0), (0, 0, 0, 0, 6, 0)):   # one warp per class; all warps of the largest
+        env = lob.LobEnv(n, cap=500, episode_len=T, exec_target=300, action_mode=lob.LOB_ACT_RANDOM, caps=caps)
+        lob.lob_set_multi_split(env.h, np.array(split, np.int32))
+        env.load_messages(to_dev(st.msgs), to_dev(st.offsets))
+        env.reset(to_dev(seeds))
+        D = env.D
+        obs = torch.zeros((T, n, 2, D), dtype=torch.float32, device="cuda")
+        rew = torch.zeros((T, n, 2), dtype=torch.int64, device="cuda")
+        lob.lob_rollout(env.h, T, None, obs, rew, None)
+        assert env.sync() == 0
+        sidx = torch.from_numpy(sample).cuda()
+        g_obs = obs.index_select(1, sidx).cpu().numpy()
+        g_rew = rew.index_select(1, sidx).cpu().numpy()
+        g_cnt = env.counters().cpu().numpy()[sample]
+        env.close()
+        o = oracle.Oracle(len(sample), cap=500, episode_len=T, exec_target=300, action_mode=1,
+                          n_threads=os.cpu_count() or 1, caps=caps[sample])
+        o.reset(sub.seeds)
+        o.load_messages(sub.msgs, sub.offsets)
+        for t in range(T):
+            o.step()
+            o_obs, o_rew, _ = o.observe()
+            np.testing.assert_array_equal(g_rew[t], o_rew, err_msg=f"split {split} step {t}")
+            np.testing.assert_allclose(g_obs[t], o_obs, rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(g_cnt, o.counters())
 
 
 def test_stress_65536_envs_cap1000():
     """65,536 envs x capacity 1,000 x 1,000 messages of the heavy-tailed mix,
-    top-20 levels (a window of 4 steps); every 256th env checked."""
+    top-20 levels (a window of 4 steps, random policy); every 256th env
+    checked at every step."""
     n = 65536
     _sampled_pair_check(n, np.arange(0, n, 256), mbogen.STRESS_MODEL, 4, cap=1000, top_levels=20,
                         exec_target=2000)
+
+
+def test_stress_full_length_with_bf16_policy_every_256th_env():
+    """The stress configuration at its stated length: 65,536 envs x capacity
+    1,000 x 1,000 messages x 256 steps (16.8 G messages, generated on the
+    device 8 steps at a time into a double-buffered ring), top-20
+    observations, actions from the BF16 policy.  Every 256th env: the GPU's
+    actions replayed into the oracle give identical observations, rewards and
+    done flags at every step, and identical books and counters at the end."""
+    import oracle
+    import torch
+    n, T, C = 65536, 256, 8
+    sample = np.arange(0, n, 256)
+    sidx = torch.from_numpy(sample).cuda()
+    seeds = mbogen.env_seeds(4, n)
+    gen = mbogen.GpuStreams(mbogen.STRESS_MODEL, seeds)
+    M = mbogen.STRESS_MODEL.msgs_per_step
+    ring = [torch.empty(n * C * M * 32, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    off = torch.from_numpy(gen.offsets(C)).cuda()
+    env = lob.LobEnv(n, cap=1000, top_levels=20, episode_len=T, exec_target=2000, action_mode=lob.LOB_ACT_HOST)
+    params = lob.init_policy_params(7, 2, env.D)
+    pol = lob.lob_policy_create(2, env.D, params)
+    lob.lob_set_launch(env.h, 4, 1)
+    env.reset(torch.from_numpy(seeds.view(np.int64).copy()).cuda())
+    D = env.D
+    obs = torch.zeros((C, n, 2, D), dtype=torch.float32, device="cuda")
+    rew = torch.zeros((C, n, 2), dtype=torch.int64, device="cuda")
+    done = torch.zeros((C, n), dtype=torch.uint8, device="cuda")
+    acts = torch.zeros((C, n, 2), dtype=torch.int32, device="cuda")
+    g_obs, g_rew, g_done, g_acts = [], [], [], []
+    for k in range(T // C):
+        gen.chunk(C, ring[k % 2])
+        env.load_messages(ring[k % 2], off)
+        lob.lob_rollout_policy(env.h, pol, C, lob.LOB_PREC_BF16, obs, rew, done, acts)
+        g_obs.append(obs.index_select(1, sidx).cpu().numpy())
+        g_rew.append(rew.index_select(1, sidx).cpu().numpy())
+        g_done.append(done.index_select(1, sidx).cpu().numpy())
+        g_acts.append(acts.index_select(1, sidx).cpu().numpy())
+    assert gen.ok()
+    assert env.sync() == 0 and lob.lob_policy_sync(pol) == 0
+    g_cnt = env.counters().cpu().numpy()[sample]
+    g_books = env.books()
+    lob.lob_policy_destroy(pol)
+    env.close()
+    gen.close()
+    del ring, obs, rew, done, acts
+    g_obs, g_rew = np.concatenate(g_obs), np.concatenate(g_rew)
+    g_done, g_acts = np.concatenate(g_done), np.concatenate(g_acts)
+    sub = mbogen.generate(mbogen.STRESS_MODEL, seeds[sample], T)
+    o = oracle.Oracle(len(sample), cap=1000, top_levels=20, episode_len=T, exec_target=2000,
+                      action_mode=lob.LOB_ACT_HOST, n_threads=os.cpu_count() or 1)
+    o.reset(sub.seeds)
+    o.load_messages(sub.msgs, sub.offsets)
+    for t in range(T):
+        o.step(g_acts[t])
+        o_obs, o_rew, o_done = o.observe()
+        np.testing.assert_array_equal(g_rew[t], o_rew, err_msg=f"rewards at step {t}")
+        np.testing.assert_allclose(g_obs[t], o_obs, rtol=1e-6, atol=0, err_msg=f"observations at step {t}")
+        np.testing.assert_array_equal(g_done[t], o_done)
+    np.testing.assert_array_equal(g_cnt, o.counters())
+    for i, e in enumerate(sample):
+        n2, px, qty, oid, ts = o.book(i)
+        b = g_books[e]
+        assert b["n"].tolist() == n2.tolist()
+        for sd in range(2):
+            kk = n2[sd]
+            np.testing.assert_array_equal(b["px"][sd][:kk], px[sd][:kk])
+            np.testing.assert_array_equal(b["id"][sd][:kk], oid[sd][:kk])
+            np.testing.assert_array_equal(b["ts"][sd][:kk], ts[sd][:kk])
 
 
 def test_checkpoint_resume_bit_identical():
