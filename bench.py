@@ -37,6 +37,13 @@ METRIC = "MBO messages/sec and env-steps/sec on 1 GB300 (bit-exact vs oracle); %
 WORKLOAD = "1024 envs x cap 100/side x 100 msgs/step, 1000-step episodes, 2 agents (exec 500-lot sell + MM), random policy, top-10 obs"
 
 
+def set_envs(n):
+    """The same workload at another env count (the 16,384-env secondary line)."""
+    global N_ENVS, WORKLOAD
+    WORKLOAD = WORKLOAD.replace(f"{N_ENVS} envs", f"{n} envs", 1)
+    N_ENVS = n
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -72,22 +79,104 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+class _NvmlPci(__import__("ctypes").Structure):
+    import ctypes as _c
+    _fields_ = [("busIdLegacy", _c.c_char * 16), ("domain", _c.c_uint), ("bus", _c.c_uint),
+                ("device", _c.c_uint), ("pciDeviceId", _c.c_uint), ("pciSubSystemId", _c.c_uint),
+                ("busId", _c.c_char * 32)]
+
+
+# NVML clock-event reason bits (nvml.h) reported by name
+_REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region.
+
+    NVML (read-only queries through ctypes) is polled about every 0.5 ms from a
+    thread, so even a timed region of a millisecond or two gets samples; the
+    device is matched to the CUDA device by PCI address.  Without NVML it falls
+    back to nvidia-smi at 200 ms (which sees nothing of a short region)."""
 
     def __init__(self, gpu_index):
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        import ctypes
+        import threading
+        self.rows, self.p, self.nv, self.t_in = [], None, None, None
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.p = None
+            import torch
+            pr = torch.cuda.get_device_properties(gpu_index)
+            want = (int(pr.pci_domain_id), int(pr.pci_bus_id), int(pr.pci_device_id))
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            cnt = ctypes.c_uint(0)
+            nv.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+            self.dev = None
+            for i in range(cnt.value):
+                d = ctypes.c_void_p()
+                info = _NvmlPci()
+                if nv.nvmlDeviceGetHandleByIndex_v2(i, ctypes.byref(d)) == 0 and \
+                        nv.nvmlDeviceGetPciInfo_v3(d, ctypes.byref(info)) == 0 and \
+                        (info.domain, info.bus, info.device) == want:
+                    self.dev = d
+            if self.dev is None:
+                raise OSError("no NVML device at the CUDA device's PCI address")
+            self.nv = nv
+            mx = ctypes.c_uint(0)
+            nv.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx))   # 1 = NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+            self.stop_flag = threading.Event()
+            self.first = threading.Event()
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+            self.first.wait(2.0)
+        except Exception:
+            self.nv = None
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            try:
+                self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            except OSError:
+                self.p = None
+
+    def _poll(self):
+        import ctypes
+        mhz, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            ok = self.nv.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(mhz)) == 0
+            if self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.dev, ctypes.byref(rs)) != 0:
+                self.nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.dev, ctypes.byref(rs))
+            if ok:
+                self.rows.append((time.perf_counter(), float(mhz.value), int(rs.value)))
+            self.first.set()
+            time.sleep(0.0005)
+
+    def enter(self):
+        """Marks the start of the timed region."""
+        self.t_in = time.perf_counter()
 
     def stop(self):
+        if self.nv is not None:
+            t_out = time.perf_counter()
+            self.stop_flag.set()
+            self.th.join(timeout=5)
+            t_in = self.t_in if self.t_in is not None else 0.0
+            inside = [r for r in self.rows if t_in <= r[0] <= t_out]
+            where = "inside the timed region"
+            if not inside and self.rows:   # a region shorter than one poll: the samples bracketing it
+                before = [r for r in self.rows if r[0] < t_in][-1:]
+                after = [r for r in self.rows if r[0] > t_out][:1]
+                inside, where = before + after, "the polls bracketing the timed region"
+            if not inside:
+                return None
+            reasons = sorted({nm for _, _, m in inside for b, nm in _REASON_BITS.items() if m & b})
+            return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(inside), "source": f"NVML, {where}"}
         if self.p is None:
             return None
         self.p.terminate()
@@ -222,6 +311,7 @@ def run_gpu(args):
     lob.lob_live_orders(env.h, live_acc)       # the first timed step's load
     launches = 0
     clk = Clocks(local)
+    clk.enter()
     t_wall0 = time.perf_counter()
     for i in range(K):
         if state["t"] >= gen:             # end of the generated window: bank its messages, reset (untimed)
@@ -261,7 +351,7 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     mean_step_s = total_s / K
     achieved = alg_bytes / mean_step_s / 1e9
-    traffic = _traffic_record()
+    traffic = _traffic_record() if N_ENVS == 1024 else None   # the record is of the 1,024-env launch
 
     e2e = run_e2e(args, env, st, seeds_d) if rank == 0 else None
     cpu = None
@@ -278,7 +368,9 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                         "kernel": "k_env_steps_wide<4> (plain, one wave)", "alg_bytes_per_launch": alg_bytes,
+                         "kernel": "k_env_steps<4> (plain; " + ("wide register budget, one wave)" if N_ENVS <= 1024
+                                                                     else "default register budget, several waves)"),
+                         "alg_bytes_per_launch": alg_bytes,
                          "mean_live_orders_per_env": live_ls / 2,
                          "live_orders_from": f"every timed step's load and store ({K} steps)"},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
@@ -479,7 +571,7 @@ def run_workload(args):
                 "dtype": "int64", "data": "synthetic"}
         env.close()
     elif wl == "policy4096":
-        n, T = 4096, 128
+        n, T = args.policy_envs, args.policy_steps
         seeds = mbogen.env_seeds(3, n)
         st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), seeds, T)
         md, od, sd = upload(st, seeds)
@@ -488,7 +580,8 @@ def run_workload(args):
         pol = lob.lob_policy_create(2, env.D, params)
         acts = torch.zeros((T, n, 2), dtype=torch.int32, device=dev)
         res = {}
-        for prec, name in ((lob.LOB_PREC_BF16, "bf16"), (lob.LOB_PREC_FP32, "fp32")):
+        for prec, name in ((lob.LOB_PREC_BF16_FUSED, "bf16_fused"), (lob.LOB_PREC_BF16, "bf16"),
+                           (lob.LOB_PREC_FP32, "fp32")):
             stream = torch.cuda.Stream()
             env.load_messages(md, od)
             env.reset(sd)
@@ -505,6 +598,8 @@ def run_workload(args):
             msgs = float(env.counters()[:, 0].sum().item())
             t = min(times)
             res[name] = {"msgs_per_s": msgs / t, "env_steps_per_s": n * T / t, "seconds_per_rollout": t}
+            if prec == lob.LOB_PREC_BF16_FUSED:
+                continue   # its forward runs inside the step kernel
             # policy forward alone on the final observations
             ob = torch.zeros((n, 2, env.D), dtype=torch.float32, device=dev)
             lob.lob_observe(env.h, ob)
@@ -512,10 +607,29 @@ def run_workload(args):
             res[name]["policy_forward_us"] = 1e6 * float(np.median(pt))
         lob.lob_policy_destroy(pol)
         env.close()
-        line = {"workload": "policy4096", "metric": METRIC, "value": res["bf16"]["msgs_per_s"], "unit": "msgs/s",
-                "env_steps_per_s": res["bf16"]["env_steps_per_s"], "bf16": res["bf16"], "fp32": res["fp32"],
-                "config": {"workload": "4096 envs x cap 200 x 100 msgs x 128 steps, per-agent MLP 45-128-128-13 "
-                                       "(tanh) in the loop, one graph-captured lob_rollout_policy"},
+        # the same rollout without a network: the seeded random policy inside the step kernel
+        env = lob.LobEnv(n, cap=200, episode_len=T, exec_target=512, action_mode=lob.LOB_ACT_RANDOM)
+        times = []
+        for i in range(args.reps):
+            env.load_messages(md, od)
+            env.reset(sd)
+            torch.cuda.synchronize()
+            times += _flush_and_time(lambda: lob.lob_rollout(env.h, T, None, None, None, None), 1, dev)
+        msgs = float(env.counters()[:, 0].sum().item())
+        t = min(times)
+        res["no_policy"] = {"msgs_per_s": msgs / t, "env_steps_per_s": n * T / t, "seconds_per_rollout": t,
+                            "what": "lob_rollout with the seeded random policy (no network)"}
+        env.close()
+        head = res["bf16_fused"]
+        head["step_time_vs_no_policy"] = head["seconds_per_rollout"] / t
+        line = {"workload": "policy4096" if (n, T) == (4096, 128) else f"policy{n}x{T}", "metric": METRIC, "value": head["msgs_per_s"], "unit": "msgs/s",
+                "env_steps_per_s": head["env_steps_per_s"], "bf16_fused": head, "bf16": res["bf16"],
+                "fp32": res["fp32"], "no_policy": res["no_policy"],
+                "config": {"workload": f"{n} envs x cap 200 x 100 msgs x {T} steps, per-agent MLP 45-128-128-13 "
+                                       "(tanh) in the loop, one graph-captured lob_rollout_policy; value: the "
+                                       "forward inside the step kernel (one launch per rollout); bf16: batched "
+                                       "tcgen05 forward between step launches; fp32: register-tiled CUDA-core "
+                                       "forward between step launches"},
                 "dtype": "int64 book / bf16 policy", "data": "synthetic", "n_gpus": 1, "steps": T}
     elif wl == "episodes4096":
         # Table 2's training setup on one shared stream: 64-step episodes
@@ -716,19 +830,23 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="envs1024",
-                    choices=["envs1024", "uneven8192", "policy4096", "episodes4096", "table1", "compact1024",
-                             "stress65536"],
+                    choices=["envs1024", "envs16384", "uneven8192", "policy4096", "episodes4096", "table1",
+                             "compact1024", "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stress-steps", type=int, default=256)
+    ap.add_argument("--policy-envs", type=int, default=4096, help="policy4096: envs (a smaller case for profiling)")
+    ap.add_argument("--policy-steps", type=int, default=128, help="policy4096: rollout steps")
     ap.add_argument("--gen-steps", type=int, default=T,
                     help="steps of messages generated (the episode wraps there; default: the full episode)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "envs16384":
+        set_envs(16384)   # the step kernel over several waves: its own roofline line
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload != "envs1024":
+    elif args.workload not in ("envs1024", "envs16384"):
         run_workload(args)
     else:
         run_gpu(args)

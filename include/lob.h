@@ -293,6 +293,15 @@ int lob_rollout(lob_handle *h, int32_t n_steps, const int32_t *d_actions, float 
 #define LOB_POLICY_HIDDEN 128
 #define LOB_PREC_FP32 0   /* FP32 FMAs on the CUDA cores */
 #define LOB_PREC_BF16 1   /* BF16 operands, FP32 accumulation, tcgen05 tensor cores */
+/* lob_rollout_policy only: the BF16 forward inside the step kernel, one
+ * launch for the whole rollout (observations and actions stay on chip).
+ * It takes the two-agent benchmark configuration on one capacity class of
+ * 65..256 slots per side, obs_dim <= 48, the PV reward with the touch
+ * reference and no penalties, a fixed task side (exec_dir +1 or -1), no
+ * trace, no episode mode; anything else is LOB_EINVAL.  Its actions equal LOB_PREC_BF16's wherever the two forwards
+ * round alike (the hidden layers are the same BF16 products; the head sums
+ * in another order). */
+#define LOB_PREC_BF16_FUSED 2
 typedef struct lob_policy lob_policy;
 /* Floats per agent in the parameter block: W1 [128][obs_dim], b1 [128],
  * W2 [128][128], b2 [128], W3 [13][128], b3 [13], in that order (row-major,

@@ -223,7 +223,6 @@ struct lob_handle {
     int hold_first = 0;          // failure-detection test hook (next launch only)
     int n_sm = 0;
     int64_t launches = 0;
-    bool fused_ok = false;       // the fused BF16 rollout kernel is not enabled
     int multi_split[NCLASS] = {0, 0, 0, 0, 0, 0};   // persistent == 2: warps per block of each class (0: derived)
     // per-class streams: several capacity classes run concurrently (fork/join
     // with events, so the pattern also captures into a CUDA graph)
@@ -408,7 +407,9 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
         }
     }
     rc |= cuda_ok(cudaMemset(h->d_status, 0, 4));
-    rc |= cuda_ok(cudaMemset(h->d_obs, 0, n * (size_t)(A * h->D) * 4 + 0));
+    rc |= cuda_ok(cudaMemset(h->d_obs, 0, n * (size_t)(A * h->D) * 4));
+    rc |= cuda_ok(cudaMemset(h->d_rew, 0, n * (size_t)A * 8 + (A == 0)));
+    rc |= cuda_ok(cudaMemset(h->d_done, 0, n));
     if (rc != LOB_OK) {
         free_all(h);
         delete h;
@@ -871,6 +872,11 @@ int lob_reset(lob_handle *h, const uint64_t *d_env_seeds, void *stream) {
     if (!h || !d_env_seeds) return LOB_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->cfg.n_envs;
+    // a fresh episode has earned nothing and is not done (the reset observation's reward and flag)
+    if ((h->cfg.n_agents > 0 &&
+         cudaMemsetAsync(h->d_rew, 0, (size_t)n * h->cfg.n_agents * 8, s) != cudaSuccess) ||
+        cudaMemsetAsync(h->d_done, 0, (size_t)n, s) != cudaSuccess)
+        return LOB_ECUDA;
     if (h->ep_mode) {
         k_reset_ep<<<n, 128, 0, s>>>(h->d_state, h->d_counters, h->d_seeds,
                                      reinterpret_cast<const unsigned long long *>(d_env_seeds), n, h->d_books,
@@ -1424,23 +1430,27 @@ static int fused_rollout(lob_handle *h, lob_policy *pol, int32_t n_steps, float 
     const lob_config &c = h->cfg;
     const int K = CLASS_K[class_of(c.cap_per_side)];
     if (c.n_agents != 2 || !h->uniform_cap || h->custom_order || h->ep_mode || h->msg16 || c.trace != 0 ||
-        (K != 4 && K != 8) || h->D > FDMAX || c.reward_mode != LOB_REWARD_PV || c.inv_penalty != 0 ||
+        (K != 4 && K != 8) || (h->D + 15) / 16 * 16 > FDMAX || c.reward_mode != LOB_REWARD_PV || c.inv_penalty != 0 ||
         c.exec_penalty_milli != 0 || c.pv_ref != LOB_PV_TOUCH || c.exec_dir == 0)
         return 1;
     const size_t per_warp = warp_smem_bytes(K);
-    int nw = (int)((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp);
-    nw = nw < FN ? nw : FN;
-    if (nw < 4) return 1;
+    const int nw_fit = (int)((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp);
+    const int nw_max = nw_fit < FWMAX ? nw_fit : FWMAX;
+    if (nw_max < 4) return 1;
+    // one CTA per SM (its tiles take half the shared memory): as few waves as
+    // the widest CTA allows, then the envs spread evenly over every SM of them
+    const long long slots = (long long)h->n_sm * nw_max;
+    const long long waves = (c.n_envs + slots - 1) / slots;
+    int nw = (int)((c.n_envs + waves * h->n_sm - 1) / (waves * h->n_sm));
+    nw = nw < 4 ? 4 : (nw > nw_max ? nw_max : nw);
     const size_t smem = (size_t)nw * per_warp + sizeof(FusedSmem);
     static bool opted[2][64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LOB_ECUDA;
     if (!opted[K == 8][dev]) {
         // opt in at the widest shape of the class
-        const size_t wide = (size_t)(((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp) < (size_t)FN
-                                         ? ((SMEM_PER_BLOCK_MAX - sizeof(FusedSmem)) / per_warp)
-                                         : (size_t)FN) * per_warp + sizeof(FusedSmem);
-        if ((K == 4 ? optin_fused_4(wide) : optin_fused_8(wide)) != cudaSuccess) return LOB_ECUDA;
+        const size_t widest = (size_t)nw_max * per_warp + sizeof(FusedSmem);
+        if ((K == 4 ? optin_fused_4(widest) : optin_fused_8(widest)) != cudaSuccess) return LOB_ECUDA;
         opted[K == 8][dev] = true;
     }
     const size_t n = (size_t)c.n_envs, D = (size_t)h->D;
@@ -1448,6 +1458,7 @@ static int fused_rollout(lob_handle *h, lob_policy *pol, int32_t n_steps, float 
     KParams p = base_params(h, h->msgs, step_offsets(h), h->stride, h->cursor, n_steps, nullptr, 0,
                             d_obs ? d_obs : h->d_obs, d_rewards ? reinterpret_cast<long long *>(d_rewards) : h->d_rew,
                             d_done ? d_done : h->d_done, false, false);
+    if (kernel_ext(p)) return 1;   // the fused kernel is built on the plain step only
     p.ow_obs = d_obs ? 0 : 1;
     p.ow_rew = d_rewards ? 0 : 1;
     p.ow_done = d_done ? 0 : 1;
@@ -1483,12 +1494,12 @@ extern "C" int lob_rollout_policy(lob_handle *h, lob_policy *pol, int32_t n_step
     if (h->cfg.n_agents < 2 || h->cfg.action_mode != LOB_ACT_HOST || h->cfg.mm_space != LOB_MM_SPREAD_SKEW)
         return LOB_EINVAL;
     if (policy_n_agents(pol) != h->cfg.n_agents || policy_obs_dim(pol) != h->D) return LOB_EINVAL;
-    if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16) return LOB_EINVAL;
+    if (precision != LOB_PREC_FP32 && precision != LOB_PREC_BF16 && precision != LOB_PREC_BF16_FUSED) return LOB_EINVAL;
     if (!steps_left(h, n_steps)) return LOB_ESTATE;
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == LOB_PREC_BF16 && h->fused_ok) {
+    if (precision == LOB_PREC_BF16_FUSED) {
         const int rc = fused_rollout(h, pol, n_steps, d_obs, d_rewards, d_done, d_actions, s);
-        if (rc <= 0) return rc;   // done (or failed); 1: not a fused configuration
+        return rc == 1 ? LOB_EINVAL : rc;   // 1: not a configuration of the fused kernel
     }
     const size_t n = (size_t)h->cfg.n_envs, D = (size_t)h->D, A = (size_t)h->cfg.n_agents;
     for (int i = 0; i < n_steps; i++) {

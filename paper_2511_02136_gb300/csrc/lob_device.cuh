@@ -1983,7 +1983,8 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                     const int g = lane - 5 * a;
                     const long long iv = a == 0 ? c.inv0 : c.inv1;
                     const long long cs = a == 0 ? c.cash0 : c.cash1;
-                    const long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    long long rem = a == 0 ? (long long)p.exec_target - c.exec_done : 0;
+                    if (side_drawn && c.exec_dir == LOB_SELL) rem = -rem;
                     const long long own = a == 0 ? own0 : own1;
                     const long long x = g == 0 ? iv : g == 1 ? cs : g == 3 ? rem : own;
                     fused_put_obs(fz, *fc->f, a, fc->row, 4 * L + g, g == 2 ? tl : __ll2float_rn(x));

@@ -26,8 +26,6 @@ struct lob_policy {
     long long wf32_stride = 0;
     int *d_status = nullptr;
     long long launches = 0;
-    unsigned char *d_wrow = nullptr;      // row-major bf16 W1 [128 x Dp], W2, W3 [16 x 128] (fused rollout)
-    long long wrow_stride = 0;
     // IPPO update (allocated by the first lob_ppo_update)
     int upd_Dp = 0;                       // padded (D + 1)
     unsigned char *d_wpk = nullptr;       // the update's packed weights (with W3^T and W2^T)
@@ -96,22 +94,7 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
                 std::memcpy(d3 + cm_off(r, k, H), &v, 2);
             }
     }
-    // row-major bf16 copy for the fused rollout (its weights live in tensor memory)
-    p->wrow_stride = ((long long)H * p->Dp + (long long)H * H + 16LL * H) * 2;
-    std::vector<unsigned short> rowp((size_t)(p->wrow_stride / 2 * n_agents), 0);
-    for (int a = 0; a < n_agents; a++) {
-        const float *w = h_params + (size_t)a * p->wf32_stride;
-        const float *w1 = w, *w2 = w + H * obs_dim + H, *w3 = w2 + H * H + H;
-        unsigned short *d = rowp.data() + (size_t)a * (p->wrow_stride / 2);
-        for (int r = 0; r < H; r++)
-            for (int k = 0; k < obs_dim; k++) d[(size_t)r * p->Dp + k] = f2bf(w1[r * obs_dim + k]);
-        d += (size_t)H * p->Dp;
-        for (int r = 0; r < H * H; r++) d[r] = f2bf(w2[r]);
-        d += (size_t)H * H;
-        for (int r = 0; r < NOUT * H; r++) d[r] = f2bf(w3[r]);
-    }
     bool fail = cudaMalloc(&p->d_wpack, pack.size()) != cudaSuccess;
-    fail = fail || cudaMalloc(&p->d_wrow, rowp.size() * 2) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_wf32, sizeof(float) * (size_t)(p->wf32_stride * n_agents)) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_status, 4) != cudaSuccess;
     if (fail) {
@@ -126,7 +109,6 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
     rc |= cudaMemcpy(p->d_wf32, h_params, sizeof(float) * (size_t)(p->wf32_stride * n_agents),
                      cudaMemcpyHostToDevice) == cudaSuccess ? 0 : 1;
     rc |= cudaMemset(p->d_status, 0, 4) == cudaSuccess ? 0 : 1;
-    rc |= cudaMemcpy(p->d_wrow, rowp.data(), rowp.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess ? 0 : 1;
     if (rc) {
         lob_policy_destroy(p);
         return LOB_ECUDA;
@@ -138,7 +120,7 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
 extern "C" int lob_policy_destroy(lob_policy *p) {
     if (!p) return LOB_EINVAL;
     cudaDeviceSynchronize();
-    void *bufs[] = {p->d_wpack, p->d_wf32, p->d_status, p->d_wrow, p->d_wpk, p->d_m, p->d_v, p->d_grad,
+    void *bufs[] = {p->d_wpack, p->d_wf32, p->d_status, p->d_wpk, p->d_m, p->d_v, p->d_grad,
                     p->d_adv, p->d_ret, p->d_stats, p->d_acc};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -162,7 +144,6 @@ static ppo::AdamParams adam_params(lob_policy *p) {
     a.sqnorm = p->d_acc + 2 * p->A;
     a.wpk = p->d_wpk; a.wpk_stride = p->wpk_stride;
     a.wfwd = p->d_wpack; a.wfwd_stride = p->wpack_stride;
-    a.wrow = p->d_wrow; a.wrow_stride = p->wrow_stride;
     return a;
 }
 
@@ -290,8 +271,8 @@ int policy_forward_internal(lob_policy *pol, const float *d_obs, int32_t n_envs,
 
 int policy_n_agents(const lob_policy *pol) { return pol ? pol->A : 0; }
 void policy_fused_params(const lob_policy *pol, lobk::FusedParams *f) {
-    f->wrow = pol->d_wrow;
-    f->wrow_stride = pol->wrow_stride;
+    f->wpack = pol->d_wpack;
+    f->wpack_stride = pol->wpack_stride;
     f->wf32 = pol->d_wf32;
     f->wf32_stride = pol->wf32_stride;
     f->D = pol->D;

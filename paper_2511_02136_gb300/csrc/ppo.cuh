@@ -502,8 +502,6 @@ struct AdamParams {
     long long wpk_stride;
     unsigned char *wfwd;             // the rollout forward's packed bf16 weights (W1 [128 x Dpf], W2, W3)
     long long wfwd_stride;
-    unsigned char *wrow;             // the fused rollout's row-major bf16 weights (W1 [128 x Dpf], W2, W3 [16 x 128])
-    long long wrow_stride;
 };
 
 // Weight i of an agent's block (a weight matrix entry; biases are skipped)
@@ -513,14 +511,12 @@ __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long
     const int D = p.D;
     unsigned char *u = p.wpk + (long long)a * p.wpk_stride;
     unsigned char *f = p.wfwd + (long long)a * p.wfwd_stride;
-    unsigned char *rw = p.wrow + (long long)a * p.wrow_stride;
     const unsigned n1 = (unsigned)(H * p.Dp * 2), n1f = (unsigned)(H * p.Dpf * 2), n2 = H * H * 2, n3 = 16 * H * 2;
     long long o = i;
     if (o < (long long)H * D) {
         const int r = (int)(o / D), c = (int)(o % D);
         st_bf16(u, cm_off(r, c, p.Dp), w);
         st_bf16(f, cm_off(r, c, p.Dpf), w);
-        st_bf16(rw, (unsigned)(2 * (r * p.Dpf + c)), w);
         return;
     }
     o -= (long long)H * D + H;
@@ -529,7 +525,6 @@ __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long
         st_bf16(u + n1, cm_off(r, c, H), w);                      // W2 [out x in]
         st_bf16(u + n1 + n2 + 2 * n3, cm_off(c, r, H), w);        // W2^T [in x out]
         st_bf16(f + n1f, cm_off(r, c, H), w);
-        st_bf16(rw + n1f, (unsigned)(2 * (r * H + c)), w);
         return;
     }
     o -= (long long)H * H + H;
@@ -538,7 +533,6 @@ __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long
         st_bf16(u + n1 + n2, cm_off(r, c, H), w);                 // W3 [16 x 128]
         st_bf16(u + n1 + n2 + n3, cm_off(c, r, 16), w);           // W3^T [128 x 16]
         st_bf16(f + n1f + n2, cm_off(r, c, H), w);
-        st_bf16(rw + n1f + n2, (unsigned)(2 * (r * H + c)), w);
     }
 }
 

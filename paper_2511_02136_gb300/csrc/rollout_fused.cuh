@@ -11,8 +11,10 @@
 
 namespace lobk {
 
+static_assert(sizeof(WarpSmem<LOB_K>) % 16 == 0, "the policy's tiles after the warps' areas stay 16-byte aligned");
+
 template <int K>
-__global__ void __launch_bounds__(FN * 32, 1) k_rollout_fused(const KParams p, const FusedParams f) {
+__global__ void __launch_bounds__(FWMAX * 32, 1) k_rollout_fused(const KParams p, const FusedParams f) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int nw = blockDim.x >> 5;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(FN * 32, 1) k_rollout_fused(const KParams p, c
     } else {
         for (int i = 0; i < p.n_steps; i++) fused_policy(fz, f, fc.phase, nw, tid);   // keep the CTA in step
     }
-    fused_teardown(fz, tid);
+    fused_teardown(fz, f, tid);
 }
 
 cudaError_t LOB_CAT(launch_fused_, LOB_K)(int blocks, int threads, size_t smem, cudaStream_t s, const KParams &p,

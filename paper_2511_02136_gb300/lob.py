@@ -59,7 +59,7 @@ EXPORTS = [
     "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
     "lob_live_orders", "lob_policy_get_params", "lob_ppo_update", "lob_set_multi_split",
 ]
-LOB_PREC_FP32, LOB_PREC_BF16 = 0, 1
+LOB_PREC_FP32, LOB_PREC_BF16, LOB_PREC_BF16_FUSED = 0, 1, 2
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
 LOB_MM_SPREAD_SKEW, LOB_MM_FIXED_QUANT, LOB_MM_DIRECTIONAL = 0, 1, 2
 LOB_PV_TOUCH, LOB_PV_MID = 0, 1

@@ -56,10 +56,11 @@ def test_forward_vs_fp64(prec, tol):
     lob.lob_policy_destroy(pol)
 
 
-def _policy_rollout(n, T, cap, prec, graph=False, seed=3, A=2):
+def _policy_rollout(n, T, cap, prec, graph=False, seed=3, A=2, exec_dir=-1):
     import torch
     st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(seed, n), T)
-    pr = Pair(n, st, n_agents=A, cap=cap, exec_target=512, action_mode=lob.LOB_ACT_HOST, n_threads=16)
+    pr = Pair(n, st, n_agents=A, cap=cap, exec_target=512, action_mode=lob.LOB_ACT_HOST, n_threads=16,
+              exec_dir=exec_dir)
     params = lob.init_policy_params(5, A, pr.env.D)
     pol = lob.lob_policy_create(A, pr.env.D, params)
     D = pr.env.D
@@ -96,11 +97,11 @@ def _policy_rollout(n, T, cap, prec, graph=False, seed=3, A=2):
     return float(np.mean(agree))
 
 
-@pytest.mark.parametrize("prec", [lob.LOB_PREC_BF16, lob.LOB_PREC_FP32])
+@pytest.mark.parametrize("prec", [lob.LOB_PREC_BF16, lob.LOB_PREC_FP32, lob.LOB_PREC_BF16_FUSED])
 def test_policy_rollout_replayed_into_oracle(prec):
     agree = _policy_rollout(300, 12, 100, prec)
     print(f"greedy agreement with FP64 along the rollout: {agree:.5f}")
-    assert agree >= (AGREE_BF16 if prec == lob.LOB_PREC_BF16 else 0.999)
+    assert agree >= (AGREE_BF16 if prec != lob.LOB_PREC_FP32 else 0.999)
 
 
 def test_policy_rollout_ten_agents_per_type():
@@ -114,9 +115,65 @@ def test_policy_rollout_under_cuda_graph():
     assert agree >= AGREE_BF16
 
 
-def test_fused_rollout_4096_envs_cap200_128_steps():
-    """The fused-policy configuration: 4,096 envs x capacity 200 x 100 msgs x
-    128 steps with the BF16 policy in the loop, replayed into the oracle."""
+def test_policy_rollout_4096_envs_cap200_128_steps():
+    """The policy-in-the-loop configuration: 4,096 envs x capacity 200 x 100
+    msgs x 128 steps with the batched BF16 policy between step launches,
+    replayed into the oracle."""
     agree = _policy_rollout(4096, 128, 200, lob.LOB_PREC_BF16)
     print(f"greedy agreement with FP64 along the 4096-env rollout: {agree:.5f}")
     assert agree >= AGREE_BF16
+
+
+def test_fused_rollout_4096_envs_cap200_128_steps_one_launch():
+    """The same configuration with the forward inside the step kernel: one
+    launch for the whole rollout, replayed into the oracle step by step."""
+    agree = _policy_rollout(4096, 128, 200, lob.LOB_PREC_BF16_FUSED)
+    print(f"fused: greedy agreement with FP64 along the 4096-env rollout: {agree:.5f}")
+    assert agree >= AGREE_BF16
+
+
+def test_fused_rollout_buy_task_ragged_ctas():
+    """A buy task and an env count that leaves the last CTA partly empty."""
+    agree = _policy_rollout(157, 20, 100, lob.LOB_PREC_BF16_FUSED, seed=9, exec_dir=1)
+    assert agree >= AGREE_BF16
+
+
+def test_fused_rollout_matches_two_launch_bf16():
+    """The fused forward and the batched BF16 forward take the same hidden-layer
+    products; their greedy actions agree except on near-ties."""
+    import torch
+    n, T = 512, 16
+    runs = []
+    for prec in (lob.LOB_PREC_BF16, lob.LOB_PREC_BF16_FUSED):
+        st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(21, n), T)
+        pr = Pair(n, st, cap=100, exec_target=512, action_mode=lob.LOB_ACT_HOST, n_threads=16)
+        params = lob.init_policy_params(5, 2, pr.env.D)
+        pol = lob.lob_policy_create(2, pr.env.D, params)
+        acts = torch.zeros((T, n, 2), dtype=torch.int32, device="cuda")
+        lob.lob_rollout_policy(pr.env.h, pol, T, prec, None, None, None, acts)
+        assert pr.env.sync() == 0 and lob.lob_policy_sync(pol) == 0
+        runs.append(acts[0].cpu().numpy())          # the first step: the same observation
+        lob.lob_policy_destroy(pol)
+        pr.close()
+    agree = np.mean(runs[0] == runs[1])
+    print(f"first-step action agreement fused vs two-launch: {agree:.5f}")
+    assert agree >= 0.99
+
+
+def test_fused_rollout_refuses_other_configurations():
+    """Capacity classes without a fused kernel are refused, not run another way."""
+    n, T = 64, 4
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=50), mbogen.env_seeds(22, n), T)
+    pr = Pair(n, st, cap=1000, exec_target=100, action_mode=lob.LOB_ACT_HOST)
+    pol = lob.lob_policy_create(2, pr.env.D, lob.init_policy_params(5, 2, pr.env.D))
+    with pytest.raises(lob.LobError):
+        lob.lob_rollout_policy(pr.env.h, pol, T, lob.LOB_PREC_BF16_FUSED, None, None, None, None)
+    lob.lob_policy_destroy(pol)
+    pr.close()
+    # a drawn task side runs on the extended step, which has no fused form
+    pr = Pair(n, st, cap=100, exec_target=100, exec_dir=0, action_mode=lob.LOB_ACT_HOST)
+    pol = lob.lob_policy_create(2, pr.env.D, lob.init_policy_params(5, 2, pr.env.D))
+    with pytest.raises(lob.LobError):
+        lob.lob_rollout_policy(pr.env.h, pol, T, lob.LOB_PREC_BF16_FUSED, None, None, None, None)
+    lob.lob_policy_destroy(pol)
+    pr.close()
