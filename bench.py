@@ -543,8 +543,9 @@ def run_workload(args):
             env.reset(sd)
             lob.lob_rollout(env.h, T_tune, None, obs[:T_tune], rew[:T_tune], None)
 
+        tried = []
         choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1,
-                               candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES)
+                               candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES, timed=tried)
         stream = torch.cuda.Stream()
         env.load_messages(md, od)
         env.reset(sd, stream)
@@ -567,7 +568,9 @@ def run_workload(args):
                 "config": {"workload": "8192 envs, caps uniform {50,100,200,500}, M_t ~ Poisson(lambda), "
                                        "lambda log-uniform [10,500], 500 steps, random policy, one graph-captured "
                                        "lob_rollout in the autotuned launch shape",
-                           "autotuned": choice.__dict__, "messages": msgs},
+                           "autotuned": choice.__dict__, "messages": msgs,
+                           "tuning_window_ms": [{"warps_per_block": c.warps_per_block, "persistent": c.persistent,
+                                                 "longest_first": c.longest_first, "ms": c.ms} for c in tried]},
                 "dtype": "int64", "data": "synthetic"}
         env.close()
     elif wl == "policy4096":
@@ -631,6 +634,62 @@ def run_workload(args):
                                        "tcgen05 forward between step launches; fp32: register-tiled CUDA-core "
                                        "forward between step launches"},
                 "dtype": "int64 book / bf16 policy", "data": "synthetic", "n_gpus": 1, "steps": T}
+    elif wl == "ppo4096":
+        # one IPPO epoch (4 minibatches per agent) on a policy-in-the-loop rollout
+        # of the 4,096-env, capacity-200, 128-step configuration
+        n, T, A, nmb = args.policy_envs, args.policy_steps, 2, 4
+        seeds = mbogen.env_seeds(31, n)
+        st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), seeds, T)
+        md, od, sd = upload(st, seeds)
+        env = lob.LobEnv(n, cap=200, episode_len=T, exec_target=512, action_mode=lob.LOB_ACT_HOST)
+        env.load_messages(md, od)
+        env.reset(sd)
+        D = env.D
+        params = lob.init_policy_params(5, A, D)
+        pol = lob.lob_policy_create(A, D, params)
+        obs0 = env.observe()[0].clone()
+        obs = torch.zeros((T, n, A, D), dtype=torch.float32, device=dev)
+        rew = torch.zeros((T, n, A), dtype=torch.int64, device=dev)
+        done = torch.zeros((T, n), dtype=torch.uint8, device=dev)
+        acts = torch.zeros((T, n, A), dtype=torch.int32, device=dev)
+        lob.lob_rollout_policy(env.h, pol, T, lob.LOB_PREC_BF16_FUSED, obs, rew, done, acts)
+        before = torch.cat([obs0[None], obs[:T - 1]], 0).contiguous()
+        logits = torch.zeros((T + 1, n, A, 12), dtype=torch.float32, device=dev)
+        values = torch.zeros((T + 1, n, A), dtype=torch.float32, device=dev)
+        for t in range(T + 1):
+            lob.lob_policy_forward(pol, (before[t] if t < T else obs[T - 1]).contiguous(), n, lob.LOB_PREC_BF16,
+                                   logits[t], values[t])
+        logp = torch.log_softmax(logits[:T], -1).gather(-1, acts.long()[..., None])[..., 0].contiguous()
+        perm = torch.stack([torch.randperm(T * n, generator=torch.Generator().manual_seed(32 + a))
+                            for a in range(A)]).to(torch.int32).to(dev)
+        hp = lob.ppo_hparams(n_minibatches=nmb)
+        upd = lambda: lob.lob_ppo_update(pol, T, n, before, acts, logp, values, rew, done, perm, hp)
+        upd()   # first call: optimiser state and packed weights (untimed)
+        torch.cuda.synchronize()
+        times = _flush_and_time(upd, args.reps + 2, dev)
+        if env.sync() != 0 or lob.lob_policy_sync(pol) != 0:
+            raise RuntimeError("device status after the update")
+        t = min(times)
+        lob.lob_policy_destroy(pol)
+        env.close()
+        samples = T * n * A
+        # per sample: the forward, 2 (D H + H H + H 13); the backward, the weight
+        # gradients of all three layers (as many products again) and the input
+        # gradients of layers 3 and 2, 2 (H 13 + H H)
+        H = 128
+        fwd = 2 * (D * H + H * H + H * 13)
+        flops = samples * (2 * fwd + 2 * (H * 13 + H * H))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        line = {"workload": "ppo4096" if (n, T) == (4096, 128) else f"ppo{n}x{T}",
+                "metric": "IPPO samples/sec (one epoch: GAE, 4 minibatches of clipped-PPO gradient, clip, Adam)",
+                "value": samples / t, "unit": "samples/s", "seconds_per_epoch": t, "samples": samples,
+                "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peaks["bf16_tflops"],
+                             "unit": "TFLOP/s", "frac": flops / t / 1e12 / peaks["bf16_tflops"],
+                             "flops_per_epoch": flops, "what": "whole update (all its kernels) against the bf16 burst peak"},
+                "config": {"workload": f"{n} envs x cap 200 x 100 msgs x {T} steps rollout (fused BF16 policy), "
+                                       "2 agents, 4 minibatches, BF16 operands with FP32 accumulation"},
+                "dtype": "bf16 / fp32", "data": "synthetic", "n_gpus": 1}
     elif wl == "episodes4096":
         # Table 2's training setup on one shared stream: 64-step episodes
         # starting every 64 data steps from book snapshots (top 10 levels),
@@ -830,8 +889,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="envs1024",
-                    choices=["envs1024", "envs16384", "uneven8192", "policy4096", "episodes4096", "table1",
-                             "compact1024", "stress65536"],
+                    choices=["envs1024", "envs16384", "uneven8192", "policy4096", "ppo4096", "episodes4096",
+                             "table1", "compact1024", "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stress-steps", type=int, default=256)

@@ -61,11 +61,11 @@ def _event_timer(run, repeats):
 
 
 def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=None, key=None,
-         timer=None, applier=None):
+         timer=None, applier=None, timed=None):
     """`run()` performs one timed unit of work on the current stream (it must
     reset/rebind whatever it consumes); returns the fastest Choice.  `timer`
     (run, repeats) -> ms and `applier` (h, choice, costs) default to CUDA
-    events and the C ABI."""
+    events and the C ABI; `timed`, a list, receives every candidate timed."""
     timer = timer or _event_timer
     applier = applier or apply
     if cache and key and os.path.exists(cache):
@@ -88,6 +88,8 @@ def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=Non
                 continue          # a shape this handle cannot take (e.g. more classes than warps)
             ch.ms = timer(run, repeats)
             results.append(ch)
+    if timed is not None:
+        timed.extend(results)
     win = min(results, key=lambda c: c.ms)
     applier(h, win, costs)
     if cache and key:

@@ -133,3 +133,80 @@ def test_ppo_update_rejects_bad_arguments():
         lob.lob_ppo_update(pol, 4, 4, x, x, x, x, x, x, x, lob.ppo_hparams(n_minibatches=4))
     assert ei.value.code == lob.LOB_ECAPACITY
     lob.lob_policy_destroy(pol)
+
+
+def test_ppo_epoch_on_the_fused_policy_rollout():
+    """One IPPO epoch on a real policy-in-the-loop rollout of the 4,096-env,
+    capacity-200, 128-step configuration (the fused BF16 rollout), against
+    the FP64 oracle's epoch on the same data, at the BF16 tolerances above.
+    The behaviour log-probabilities and values come from the batched BF16
+    forward on the observations each action was taken on (the reset
+    observation, then each step's output)."""
+    import torch
+    from paper_2511_02136_gb300 import mbogen
+    lob.build()
+    n, T, A, nmb = 4096, 128, 2, 4
+    seeds = mbogen.env_seeds(31, n)
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), seeds, T)
+    env = lob.LobEnv(n, cap=200, episode_len=T, exec_target=512, action_mode=lob.LOB_ACT_HOST)
+    env.load_messages(_dev(st.msgs.view(np.uint8)), _dev(st.offsets))
+    env.reset(_dev(seeds.view(np.int64)))
+    D = env.D
+    params = lob.init_policy_params(5, A, D)
+    pol = lob.lob_policy_create(A, D, params)
+    obs0, _, _ = env.observe()
+    obs = torch.zeros((T, n, A, D), dtype=torch.float32, device="cuda")
+    rew = torch.zeros((T, n, A), dtype=torch.int64, device="cuda")
+    done = torch.zeros((T, n), dtype=torch.uint8, device="cuda")
+    acts = torch.zeros((T, n, A), dtype=torch.int32, device="cuda")
+    lob.lob_rollout_policy(env.h, pol, T, lob.LOB_PREC_BF16_FUSED, obs, rew, done, acts)
+    assert env.sync() == 0 and lob.lob_policy_sync(pol) == 0
+    # the observation each action was taken on, and the behaviour policy's outputs on it
+    before = torch.cat([obs0.clone()[None], obs[:T - 1]], 0)
+    logits = torch.zeros((T + 1, n, A, 12), dtype=torch.float32, device="cuda")
+    values = torch.zeros((T + 1, n, A), dtype=torch.float32, device="cuda")
+    for t in range(T + 1):
+        src = before[t] if t < T else obs[T - 1]
+        lob.lob_policy_forward(pol, src.contiguous(), n, lob.LOB_PREC_BF16, logits[t], values[t])
+    assert lob.lob_policy_sync(pol) == 0
+    logp_old = torch.log_softmax(logits[:T].double(), -1).gather(-1, acts.long()[..., None])[..., 0].float()
+    perm = np.stack([np.random.default_rng(32 + a).permutation(T * n) for a in range(A)]).astype(np.int32)
+    P = params.shape[1]
+    grad_out = torch.zeros((nmb, A, P), dtype=torch.float32, device="cuda")
+    hp = lob.ppo_hparams(n_minibatches=nmb)
+    lob.lob_ppo_update(pol, T, n, before.contiguous(), acts, logp_old.contiguous(), values, rew, done, _dev(perm), hp,
+                       grad_out=grad_out)
+    new = torch.zeros((A, P), dtype=torch.float32, device="cuda")
+    lob.lob_policy_get_params(pol, new)
+    torch.cuda.synchronize()
+    assert lob.lob_policy_sync(pol) == 0
+    batch = dict(obs=before.cpu().numpy(), actions=acts.cpu().numpy(), logp_old=logp_old.cpu().numpy(),
+                 values=values.cpu().numpy(), rewards=rew.cpu().numpy(), dones=done.cpu().numpy())
+    assert batch["dones"][T - 1].all() and not batch["dones"][:T - 1].any()
+    hp64 = ppo.PPOHyper()
+    p64 = params.astype(np.float64)
+    new64, _, _ = ppo.ppo_epoch(p64, D, batch, perm, nmb, hp64)
+    g_gpu = grad_out.cpu().numpy().astype(np.float64)
+    new_gpu = new.cpu().numpy().astype(np.float64)
+    mb = T * n // nmb
+    for a in range(A):
+        r = hp64.reward_scale * batch["rewards"][:, :, a].astype(np.float64)
+        adv, ret = ppo.gae(r, batch["values"][:, :, a], np.broadcast_to(batch["dones"], (T, n)), hp64.gamma,
+                           hp64.gae_lambda)
+        idx = perm[a][:mb]
+        o = batch["obs"][:, :, a, :].reshape(T * n, D)
+        _, g64 = ppo.loss_and_grads(p64[a], D, o[idx], batch["actions"][:, :, a].reshape(-1)[idx],
+                                    batch["logp_old"][:, :, a].reshape(-1)[idx], adv.reshape(-1)[idx],
+                                    ret.reshape(-1)[idx], hp64)
+        g = g_gpu[0, a]
+        rel = np.linalg.norm(g - g64) / np.linalg.norm(g64)
+        cos = float(g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64)))
+        print(f"agent {a}: gradient rel err {rel:.3e}, cosine {cos:.6f}")
+        assert rel <= 3e-2 and cos >= 0.999, (a, rel, cos)
+        d_gpu, d64 = new_gpu[a] - p64[a], new64[a] - p64[a]
+        rel_d = np.linalg.norm(d_gpu - d64) / np.linalg.norm(d64)
+        print(f"agent {a}: weight change rel err {rel_d:.3e}")
+        assert rel_d <= 0.15, (a, rel_d)
+        assert np.max(np.abs(d_gpu - d64)) <= 2 * nmb * hp64.lr, (a, np.max(np.abs(d_gpu - d64)))
+    lob.lob_policy_destroy(pol)
+    env.close()
