@@ -278,6 +278,7 @@ def run_gpu(args):
     seeds_d = torch.from_numpy(seeds.view(np.int64).copy()).to(dev)
     env = lob.LobEnv(N_ENVS, cap=CAP, top_levels=L, episode_len=T, exec_target=EXEC_TARGET,
                      action_mode=lob.LOB_ACT_RANDOM, warps_per_block=args.wpb)
+    lob.lob_set_threads_per_env(env.h, args.threads_per_env)
     env.load_messages(msgs_d, off_d)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
@@ -368,8 +369,9 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                         "kernel": "k_env_steps<4> (plain; " + ("wide register budget, one wave)" if N_ENVS <= 1024
-                                                                     else "default register budget, several waves)"),
+                         "kernel": ("k_env_steps_split<4> (plain; one warp per book side)" if args.threads_per_env == 64
+                                    else "k_env_steps<4> (plain; " + ("wide register budget, one wave)" if N_ENVS <= 1024
+                                                                      else "default register budget, several waves)")),
                          "alg_bytes_per_launch": alg_bytes,
                          "mean_live_orders_per_env": live_ls / 2,
                          "live_orders_from": f"every timed step's load and store ({K} steps)"},
@@ -545,7 +547,8 @@ def run_workload(args):
 
         tried = []
         choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1,
-                               candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES, timed=tried)
+                               candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES +
+                               autotune.SPLIT_CANDIDATES, timed=tried)
         stream = torch.cuda.Stream()
         env.load_messages(md, od)
         env.reset(sd, stream)
@@ -570,7 +573,8 @@ def run_workload(args):
                                        "lob_rollout in the autotuned launch shape",
                            "autotuned": choice.__dict__, "messages": msgs,
                            "tuning_window_ms": [{"warps_per_block": c.warps_per_block, "persistent": c.persistent,
-                                                 "longest_first": c.longest_first, "ms": c.ms} for c in tried]},
+                                                 "longest_first": c.longest_first, "threads_per_env": c.threads_per_env,
+                                                 "ms": c.ms} for c in tried]},
                 "dtype": "int64", "data": "synthetic"}
         env.close()
     elif wl == "policy4096":
@@ -885,6 +889,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--wpb", type=int, default=0, help="warps per block (0 = library default)")
+    ap.add_argument("--threads-per-env", type=int, default=32, choices=[32, 64],
+                    help="64: one warp per book side (the plain step)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

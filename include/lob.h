@@ -449,6 +449,17 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent);
  * classes' env counts. */
 #define LOB_NCLASSES 6
 int lob_set_multi_split(lob_handle *h, const int32_t *warps_per_class);
+/* Threads per env: 32 (default, one warp runs both sides of an env's book) or
+ * 64: the plain step -- the benchmark pair or no agents, a fixed task side,
+ * the PV reward, no trace, capacity classes of 33..256 slots per side, no
+ * work queue (persistent 0) -- runs with one warp per book side.  Each warp
+ * handles the messages that change its side (its rests and cancels, and the
+ * takes of the other side's incoming orders); a limit add that may cross
+ * waits for the opposite warp's take to post its unfilled remainder; arrival
+ * stamps and the per-owner totals are merged at every staged chunk and every
+ * step's end.  Results are identical to 32; launches that do not qualify run
+ * one warp per env.  LOB_EINVAL for other values. */
+int lob_set_threads_per_env(lob_handle *h, int32_t threads);
 /* Failure-detection hook.  `cycles` bounds every wait of the step kernels on
  * a message tile, in SM cycles (0 = the default, about one second).  hold = 1
  * makes the next step or rollout launch leave each env's first message tile

@@ -7,9 +7,11 @@ envs (with the per-class warp split of each block); and env order (as
 created, or longest first from a per-env cost estimate) -- with CUDA events
 around a caller-supplied run, keeps the fastest, and caches the choice per
 workload signature in a JSON file.  The kernels themselves are unchanged: the
-shape is set through lob_set_launch / lob_set_multi_split / lob_set_env_costs
-before the timed runs.  Each env is one warp and messages are staged 32
-records at a time in every shape; the cache records both.
+shape is set through lob_set_launch / lob_set_multi_split / lob_set_env_costs /
+lob_set_threads_per_env before the timed runs.  Threads per env are 32 (one
+warp per env) or 64 (one warp per book side, for the plain step on a plain
+grid); messages are staged 32 records at a time in every shape.  The cache
+records the threads per env and the tile size with the shape.
 """
 from __future__ import annotations
 
@@ -23,6 +25,8 @@ DEFAULT_CANDIDATES = [(wpb, pers) for pers in (0, 1) for wpb in (1, 2, 4, 8)]
 # persistent = 2: one launch over every class (the split derived from the
 # classes' env counts for the given warps per block)
 MULTI_CANDIDATES = [(wpb, 2) for wpb in (4, 6, 8)]
+# two warps per env (one per book side): a plain grid, one env per block
+SPLIT_CANDIDATES = [(1, 0, 64)]
 
 
 @dataclass
@@ -41,6 +45,7 @@ def signature(n_envs, caps_hist, mean_msgs, steps, extra=""):
 
 def apply(h, choice: Choice, costs=None):
     lob.lob_set_launch(h, choice.warps_per_block, choice.persistent)
+    lob.lob_set_threads_per_env(h, choice.threads_per_env)
     lob.lob_set_env_costs(h, costs if (choice.longest_first and costs is not None) else None)
 
 
@@ -77,11 +82,13 @@ def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=Non
             return ch
     results = []
     orders = (False, True) if costs is not None else (False,)
-    for wpb, pers in candidates:
+    for cand in candidates:
+        wpb, pers = cand[0], cand[1]
+        tpe = cand[2] if len(cand) > 2 else 32
         for lf in orders:
             if lf and not pers:
                 continue          # the order only matters to the work queue
-            ch = Choice(wpb, pers, lf, 0.0)
+            ch = Choice(wpb, pers, lf, 0.0, threads_per_env=tpe)
             try:
                 applier(h, ch, costs)
             except lob.LobError:

@@ -219,6 +219,7 @@ struct lob_handle {
     // launch shape
     int wpb = 4;
     int persistent = 0;
+    int tpe = 32;                // threads per env: 64 runs the plain step with one warp per book side
     long long wait_budget = 0;   // 0: the default bound
     int hold_first = 0;          // failure-detection test hook (next launch only)
     int n_sm = 0;
@@ -777,9 +778,26 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
         p.n_list = cnt;
         p.queue = h->persistent ? h->d_queue + k : nullptr;
         h->launches++;
-        if (launch_k(CLASS_K[k], p.fills != nullptr || p.snaps != nullptr, cnt, wpb, h->persistent != 0, h->n_sm, ks, p) !=
-            cudaSuccess)
+        const int K = CLASS_K[k];
+        if (h->tpe == 64 && !h->persistent && p.fills == nullptr && p.snaps == nullptr && !kernel_ext(p) &&
+            (c.n_agents == 0 || c.n_agents == 2) && (K == 2 || K == 4 || K == 8) && !p.hold_first) {
+            // two warps per env, one block per env (lob_split.cuh)
+            static bool opted[3][64];
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LOB_ECUDA;
+            const int ki = K == 2 ? 0 : (K == 4 ? 1 : 2);
+            const size_t smem = split_pair_bytes(K);
+            if (!opted[ki][dev]) {
+                if (optin_steps_split(K, smem) != cudaSuccess) return LOB_ECUDA;
+                opted[ki][dev] = true;
+            }
+            KParams q = p;
+            q.book_prefetch = cnt <= 7 * h->n_sm ? 1 : 0;   // one wave: fetch the books early
+            if (launch_steps_split(K, cnt, 64, smem, ks, q) != cudaSuccess) return LOB_ECUDA;
+        } else if (launch_k(K, p.fills != nullptr || p.snaps != nullptr, cnt, wpb, h->persistent != 0, h->n_sm, ks,
+                            p) != cudaSuccess) {
             return LOB_ECUDA;
+        }
         if (fork && cudaEventRecord(h->cls_done[k], ks) != cudaSuccess) return LOB_ECUDA;
     }
     if (fork)
@@ -1243,6 +1261,12 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
             smem -= warp_smem_bytes(CLASS_K[best]);
         }
     }
+    return LOB_OK;
+}
+
+int lob_set_threads_per_env(lob_handle *h, int32_t threads) {
+    if (!h || (threads != 32 && threads != 64)) return LOB_EINVAL;
+    h->tpe = threads;
     return LOB_OK;
 }
 

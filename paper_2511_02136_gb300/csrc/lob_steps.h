@@ -27,6 +27,10 @@ cudaError_t launch_steps_multi(int blocks, int threads, size_t smem, cudaStream_
                                const MultiLayout &m);
 cudaError_t optin_steps_multi(size_t smem);
 int multi_blocks_per_sm(int threads, size_t smem);
+// two warps per env (lob_split.cuh; classes K = 2, 4, 8; the plain benchmark configuration)
+cudaError_t launch_steps_split(int K, int blocks, int threads, size_t smem, cudaStream_t s, const KParams &p);
+cudaError_t optin_steps_split(int K, size_t smem);
+size_t split_pair_bytes(int K);
 // fused BF16 rollout (classes K = 4 and 8)
 cudaError_t launch_fused_4(int blocks, int threads, size_t smem, cudaStream_t s, const KParams &p, const FusedParams &f);
 cudaError_t optin_fused_4(size_t smem);

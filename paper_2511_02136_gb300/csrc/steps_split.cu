@@ -1,0 +1,32 @@
+// steps_split.cu -- the two-warps-per-env step kernel (lob_split.cuh) of the
+// register-pool classes K = 2, 4 and 8, in a translation unit of its own.
+#include "lob_split.cuh"
+#include "lob_steps.h"
+
+namespace lobk {
+cudaError_t launch_steps_split(int K, int blocks, int threads, size_t smem, cudaStream_t s, const KParams &p) {
+    switch (K) {
+        case 2: k_env_steps_split<2><<<blocks, threads, smem, s>>>(p); break;
+        case 4: k_env_steps_split<4><<<blocks, threads, smem, s>>>(p); break;
+        case 8: k_env_steps_split<8><<<blocks, threads, smem, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+cudaError_t optin_steps_split(int K, size_t smem) {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    switch (K) {
+        case 2: return cudaFuncSetAttribute(k_env_steps_split<2>, A, (int)smem);
+        case 4: return cudaFuncSetAttribute(k_env_steps_split<4>, A, (int)smem);
+        case 8: return cudaFuncSetAttribute(k_env_steps_split<8>, A, (int)smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+size_t split_pair_bytes(int K) {
+    switch (K) {
+        case 2: return sizeof(WarpSmem<2>) + sizeof(SplitSmem);
+        case 4: return sizeof(WarpSmem<4>) + sizeof(SplitSmem);
+        default: return sizeof(WarpSmem<8>) + sizeof(SplitSmem);
+    }
+}
+}  // namespace lobk

@@ -25,11 +25,12 @@ _INC = os.path.join(_ROOT, "include")
 CHECKED = os.environ.get("LOB_CHECKED") == "1"
 LIB_PATH = os.path.join(_PKG, "liblob_checked.so" if CHECKED else "liblob.so")
 _SOURCES = [os.path.join(_CSRC, n) for n in
-            ["lob_api.cu", "policy_api.cu", "rollout_fused_k4.cu", "rollout_fused_k8.cu", "steps_multi.cu"] +
+            ["lob_api.cu", "policy_api.cu", "rollout_fused_k4.cu", "rollout_fused_k8.cu", "steps_multi.cu",
+             "steps_split.cu"] +
             [f"steps_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)] +
             [f"steps_ma_k{k}.cu" for k in (1, 2, 4, 8, 16, 32)]]
 _DEPS = _SOURCES + [os.path.join(_CSRC, n) for n in ("lob_device.cuh", "lob_ladder.cuh", "policy.cuh", "tc05.cuh", "ppo.cuh",
-                                                      "fused.cuh", "rollout_fused.cuh",
+                                                      "fused.cuh", "rollout_fused.cuh", "lob_split.cuh",
                                                       "policy_internal.h",
                                                       "lob_steps.h", "steps_inst.cuh", "steps_ma_inst.cuh")] + \
     [os.path.join(_INC, "lob.h")]
@@ -58,6 +59,7 @@ EXPORTS = [
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
     "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
     "lob_live_orders", "lob_policy_get_params", "lob_ppo_update", "lob_set_multi_split",
+    "lob_set_threads_per_env",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16, LOB_PREC_BF16_FUSED = 0, 1, 2
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
@@ -185,6 +187,7 @@ def _load():
         "lob_get_actions": (ctypes.c_int, [P, P, P]),
         "lob_live_orders": (ctypes.c_int, [P, P, P]),
         "lob_set_multi_split": (ctypes.c_int, [P, P]),
+        "lob_set_threads_per_env": (ctypes.c_int, [P, I32]),
         "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
         "lob_sync": (ctypes.c_int, [P, P]),
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
@@ -316,6 +319,11 @@ def lob_get_env_misc(h, out, stream=None):
 
 def lob_get_actions(h, out, stream=None):
     return _check(_load().lob_get_actions(h, _dp(out), _stream(stream)), "lob_get_actions")
+
+
+def lob_set_threads_per_env(h, threads):
+    """32: one warp per env; 64: one warp per book side for the plain step (see include/lob.h)."""
+    return _check(_load().lob_set_threads_per_env(h, threads), "lob_set_threads_per_env")
 
 
 def lob_set_multi_split(h, warps_per_class):

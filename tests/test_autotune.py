@@ -61,3 +61,23 @@ def test_signature_is_order_independent():
     a = autotune.signature(8, {100: 3, 50: 5}, 99.6, 500)
     b = autotune.signature(8, {50: 5, 100: 3}, 100.4, 500)
     assert a == b
+
+
+def test_threads_per_env_axis_is_timed_and_cached(tmp_path):
+    """A candidate with 64 threads per env (one warp per book side) is timed
+    like the others and, when fastest, is what the cache records."""
+    seen = []
+
+    def applier(h, ch, costs):
+        seen.append((ch.warps_per_block, ch.persistent, ch.longest_first, ch.threads_per_env))
+
+    def timer(run, repeats):
+        return 2.0 if seen[-1][3] == 64 else 5.0 + seen[-1][0]
+
+    cache = tmp_path / "tune.json"
+    win = autotune.tune(None, lambda: None, costs=[1.0], candidates=autotune.DEFAULT_CANDIDATES +
+                        autotune.SPLIT_CANDIDATES, timer=timer, applier=applier, cache=str(cache), key="k")
+    assert win.threads_per_env == 64 and win.persistent == 0
+    assert (1, 0, False, 64) in seen
+    assert json.loads(cache.read_text())["k"]["threads_per_env"] == 64
+    assert sum(1 for *_, t in seen if t == 64) == 2   # timed, then applied as the winner
