@@ -458,7 +458,9 @@ int lob_set_multi_split(lob_handle *h, const int32_t *warps_per_class);
  * waits for the opposite warp's take to post its unfilled remainder; arrival
  * stamps and the per-owner totals are merged at every staged chunk and every
  * step's end.  Results are identical to 32; launches that do not qualify run
- * one warp per env.  LOB_EINVAL for other values. */
+ * one warp per env.  On the 1,024-env benchmark workload it measured about
+ * twice the step time of 32 (more instructions in all and two code paths per
+ * SM), so 32 stays the default.  LOB_EINVAL for other values. */
 int lob_set_threads_per_env(lob_handle *h, int32_t threads);
 /* Failure-detection hook.  `cycles` bounds every wait of the step kernels on
  * a message tile, in SM cycles (0 = the default, about one second).  hold = 1

@@ -604,9 +604,11 @@ __device__ void run_env_split(const KParams &p, int e, WarpSmem<K> &sm, SplitSme
 
 
 // Two warps per env (even warp: bids, odd warp: asks), pairs of warps side by
-// side in the block; each pair has its own named barrier.
+// side in the block; each pair has its own named barrier.  128 registers: the
+// register file is split between the SM's four schedulers, and 1,024 envs
+// (2,048 warps) fit one wave only with four warps per scheduler.
 template <int K>
-__global__ void __maxnreg__(144) k_env_steps_split(const KParams p) {
+__global__ void __maxnreg__(128) k_env_steps_split(const KParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int pair = wib >> 1;

@@ -13,12 +13,22 @@ cudaError_t launch_steps_split(int K, int blocks, int threads, size_t smem, cuda
     }
     return cudaGetLastError();
 }
+// The shared memory a block may take, and the largest shared-memory carve-out
+// of the SM: a block is small (one env), so without it the default carve-out
+// bounds the resident blocks before the registers do.
+template <int KK>
+static cudaError_t optin_one(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_env_steps_split<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_steps_split<KK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
 cudaError_t optin_steps_split(int K, size_t smem) {
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     switch (K) {
-        case 2: return cudaFuncSetAttribute(k_env_steps_split<2>, A, (int)smem);
-        case 4: return cudaFuncSetAttribute(k_env_steps_split<4>, A, (int)smem);
-        case 8: return cudaFuncSetAttribute(k_env_steps_split<8>, A, (int)smem);
+        case 2: return optin_one<2>(smem);
+        case 4: return optin_one<4>(smem);
+        case 8: return optin_one<8>(smem);
         default: return cudaErrorInvalidValue;
     }
 }
