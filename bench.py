@@ -216,6 +216,22 @@ def parse_clock_rows(text):
             "samples": len(sm)}
 
 
+# the sources of the measured step kernel and of its launch (the traffic record
+# is void once any of them changes)
+TRAFFIC_SOURCES = ["include/lob.h"] + [f"paper_2511_02136_gb300/csrc/{n}" for n in (
+    "lob_api.cu", "lob_device.cuh", "lob_ladder.cuh", "fused.cuh", "tc05.cuh", "lob_steps.h", "steps_inst.cuh",
+    "steps_k4.cu")]
+
+
+def traffic_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for src in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, src), "rb") as g:
+            h.update(g.read())
+    return h.hexdigest()
+
+
 def _traffic_record():
     """ncu DRAM bytes per launch of the step kernel, if taken on the current source."""
     p = os.path.join(ROOT, "profiles", "k_env_steps_1024env_traffic.json")
@@ -223,13 +239,7 @@ def _traffic_record():
         return None
     with open(p) as f:
         rec = json.load(f)
-    from paper_2511_02136_gb300 import lob
-    import hashlib
-    h = hashlib.sha256()
-    for src in lob._DEPS:
-        with open(src, "rb") as g:
-            h.update(g.read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("source_sha256") != traffic_sources_sha256():
         return None
     return float(rec["dram_bytes_per_launch"])
 
@@ -577,6 +587,37 @@ def run_workload(args):
                                                  "ms": c.ms} for c in tried]},
                 "dtype": "int64", "data": "synthetic"}
         env.close()
+        if args.per_class:
+            # each capacity class alone on the whole GPU (its envs' streams, its best
+            # of a few shapes): the time each class needs by itself
+            per = {}
+            for cls in sorted(set(int(x) for x in caps)):
+                idx = np.nonzero(caps == cls)[0]
+                parts = [st.msgs[st.offsets[e, 0]:st.offsets[e, -1]] for e in idx]
+                base = np.concatenate([[0], np.cumsum([len(q) for q in parts])[:-1]]).astype(np.int64)
+                off2 = (st.offsets[idx] - st.offsets[idx, :1] + base[:, None]).astype(np.int64)
+                cmd, cod = (torch.from_numpy(np.concatenate(parts).view(np.uint8).copy()).to(dev),
+                            torch.from_numpy(off2).to(dev))
+                csd = torch.from_numpy(seeds[idx].view(np.int64).copy()).to(dev)
+                cenv = lob.LobEnv(len(idx), cap=cls, episode_len=T, exec_target=500, action_mode=lob.LOB_ACT_RANDOM)
+                best = None
+                for wpb, pers, lf in ((1, 1, True), (2, 1, True), (4, 1, True), (4, 0, False)):
+                    lob.lob_set_launch(cenv.h, wpb, pers)
+                    lob.lob_set_env_costs(cenv.h, costs[idx] if lf else None)
+                    cenv.load_messages(cmd, cod)
+                    cenv.reset(csd)
+                    torch.cuda.synchronize()
+                    tt = _flush_and_time(lambda: lob.lob_rollout(cenv.h, T, None, None, None, None), 1, dev)[0]
+                    cm = float(cenv.counters()[:, 0].sum().item())
+                    if best is None or tt < best[0]:
+                        best = (tt, wpb, pers, lf, cm)
+                per[cls] = {"envs": int(len(idx)), "seconds": best[0], "messages": best[4],
+                            "msgs_per_s": best[4] / best[0], "shape": {"warps_per_block": best[1],
+                                                                        "persistent": best[2],
+                                                                        "longest_first": best[3]},
+                            "max_lambda": float(st.lambdas[idx].max())}
+                cenv.close()
+            line["per_class_alone"] = per
     elif wl == "policy4096":
         n, T = args.policy_envs, args.policy_steps
         seeds = mbogen.env_seeds(3, n)
@@ -899,6 +940,7 @@ def main():
                              "table1", "compact1024", "stress65536"],
                     help="envs1024 is the benchmark line; the others print secondary lines")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--per-class", action="store_true", help="uneven8192: also time each capacity class alone")
     ap.add_argument("--stress-steps", type=int, default=256)
     ap.add_argument("--policy-envs", type=int, default=4096, help="policy4096: envs (a smaller case for profiling)")
     ap.add_argument("--policy-steps", type=int, default=128, help="policy4096: rollout steps")

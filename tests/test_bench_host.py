@@ -30,3 +30,13 @@ def test_peak_is_the_measured_copy_bandwidth():
         assert kind == "measured" and peak == float(json.load(open(p))["hbm_gbs"])
     else:
         assert kind == "fallback" and peak == 6800.0
+
+
+def test_traffic_record_sources_exist_and_hash_is_stable():
+    """The DRAM-traffic record is tied to the step kernel's own sources."""
+    import os
+    import bench
+    for src in bench.TRAFFIC_SOURCES:
+        assert os.path.exists(os.path.join(bench.ROOT, src)), src
+    h = bench.traffic_sources_sha256()
+    assert len(h) == 64 and h == bench.traffic_sources_sha256()
