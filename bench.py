@@ -18,6 +18,7 @@ on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -79,11 +80,11 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-class _NvmlPci(__import__("ctypes").Structure):
-    import ctypes as _c
-    _fields_ = [("busIdLegacy", _c.c_char * 16), ("domain", _c.c_uint), ("bus", _c.c_uint),
-                ("device", _c.c_uint), ("pciDeviceId", _c.c_uint), ("pciSubSystemId", _c.c_uint),
-                ("busId", _c.c_char * 32)]
+class _NvmlPci(ctypes.Structure):
+    """nvmlPciInfo_t (nvml.h)."""
+    _fields_ = [("busIdLegacy", ctypes.c_char * 16), ("domain", ctypes.c_uint), ("bus", ctypes.c_uint),
+                ("device", ctypes.c_uint), ("pciDeviceId", ctypes.c_uint), ("pciSubSystemId", ctypes.c_uint),
+                ("busId", ctypes.c_char * 32)]
 
 
 # NVML clock-event reason bits (nvml.h) reported by name
@@ -100,7 +101,6 @@ class Clocks:
     back to nvidia-smi at 200 ms (which sees nothing of a short region)."""
 
     def __init__(self, gpu_index):
-        import ctypes
         import threading
         self.rows, self.p, self.nv, self.t_in = [], None, None, None
         try:
@@ -145,7 +145,6 @@ class Clocks:
                 self.p = None
 
     def _poll(self):
-        import ctypes
         mhz, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
         while not self.stop_flag.is_set():
             ok = self.nv.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(mhz)) == 0

@@ -40,3 +40,30 @@ def test_traffic_record_sources_exist_and_hash_is_stable():
         assert os.path.exists(os.path.join(bench.ROOT, src)), src
     h = bench.traffic_sources_sha256()
     assert len(h) == 64 and h == bench.traffic_sources_sha256()
+
+
+def test_nvml_clock_samples_inside_or_bracketing_the_timed_region():
+    """The NVML poller keeps the samples taken inside the timed region; when the
+    region is shorter than one poll it keeps the polls on either side, and it
+    names the active slowdown reasons."""
+    import threading
+    import time
+    import bench
+
+    def fake(rows, t_in):
+        c = bench.Clocks.__new__(bench.Clocks)
+        c.nv, c.rows, c.t_in, c.max_mhz = object(), rows, t_in, 2070.0
+        c.stop_flag, c.th = threading.Event(), threading.Thread(target=lambda: None)
+        c.th.start()
+        return c
+
+    now = time.perf_counter()
+    c = fake([(now - 1.0, 1800.0, 0), (now - 0.4, 2070.0, 0x4), (now - 0.3, 2070.0, 0), (now + 10.0, 900.0, 0x40)],
+             now - 0.5)
+    r = c.stop()
+    assert r["sm_mhz"] == 2070.0 and r["samples"] == 2 and r["reasons"] == ["sw_power_cap"]
+    assert r["source"].endswith("inside the timed region")
+    c = fake([(now - 2.0, 2000.0, 0), (now + 5.0, 2060.0, 0x8)], time.perf_counter())
+    r = c.stop()
+    assert r["samples"] == 2 and r["sm_mhz"] == 2030.0 and r["reasons"] == ["hw_slowdown"]
+    assert "bracketing" in r["source"]
