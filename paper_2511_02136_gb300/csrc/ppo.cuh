@@ -83,9 +83,11 @@ struct __align__(1024) GradSmem {
     float db3[16];
     int act[128];
     float lpo[128], an[128], rt[128];
+    long long orow[128];                    // the tile's samples: observation row index, or -1 past the minibatch
     unsigned long long bar, wbar;
     unsigned tmem_base;
 };
+static_assert(sizeof(GradSmem) <= 227 * 1024, "one CTA's shared memory");
 
 // TMEM columns of the gradient kernel (512 allocated).
 constexpr unsigned TC_ACC = 0;      // 128: U1, U2, dH2, dH1 in turn
@@ -131,6 +133,49 @@ __device__ __forceinline__ void to_async() {
     pol::tc_fence_before();
     __syncthreads();
     pol::tc_fence_after();
+}
+
+// Sample smp's observation row index and per-row data (smp < 0: past the
+// minibatch): the action, the behaviour log-probability, the normalised
+// advantage and the value target.
+struct RowData {
+    long long ra;
+    int act;
+    float lpo, an, rt;
+};
+__device__ __forceinline__ RowData row_data(const GradParams &p, int a, const float *advp, const float *retp,
+                                            float mean, float istd, int smp) {
+    RowData d{-1, 0, 0.0f, 0.0f, 0.0f};
+    if (smp >= 0) {
+        const int t = smp / p.n_envs, e = smp - t * p.n_envs;
+        d.ra = ((long long)t * p.n_envs + e) * p.A + a;
+        d.act = p.actions[d.ra];
+        d.lpo = p.logp_old[d.ra];
+        d.an = (advp[smp] - mean) * istd;
+        d.rt = retp[smp];
+    }
+    return d;
+}
+__device__ __forceinline__ void put_row_data(GradSmem &sm, int i, const RowData &d) {
+    sm.orow[i] = d.ra;
+    sm.act[i] = d.act;
+    sm.lpo[i] = d.lpo;
+    sm.an[i] = d.an;
+    sm.rt[i] = d.rt;
+}
+constexpr int RPW = 128 / (PPT / 32);   // tile rows per warp
+// This warp's observation rows (w, w + 8, ...) of the tile sm.orow names,
+// features lane and lane + 32, all loads issued before any is used.
+__device__ __forceinline__ void load_rows(const GradParams &p, const GradSmem &sm, int warp, int lane,
+                                          float (&va)[RPW], float (&vb)[RPW]) {
+    const int D = p.D;
+#pragma unroll
+    for (int j = 0; j < RPW; j++) {
+        const long long ra = sm.orow[warp + (PPT / 32) * j];
+        const float *o = p.obs + (ra < 0 ? 0 : ra) * (long long)D;
+        va[j] = (ra >= 0 && lane < D) ? o[lane] : 0.0f;
+        vb[j] = (ra >= 0 && lane + 32 < D) ? o[lane + 32] : 0.0f;
+    }
 }
 
 __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
@@ -185,29 +230,32 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     const float *advp = p.adv + (long long)a * p.n_samples, *retp = p.ret + (long long)a * p.n_samples;
     const int *perm = p.perm + (long long)a * p.n_samples + p.mb_begin;
     bool first = true;
+    // The tiles' samples are gathered one tile ahead: while a tile's
+    // contractions run, the next tile's sample indices, per-row data and
+    // observation rows are loaded, so their latency stays off the tile's chain.
+    float va[RPW], vb[RPW];
+    int n_smp = -1;
+    RowData nd{-1, 0, 0.0f, 0.0f, 0.0f};
+    if (blockIdx.x < n_tiles) {
+        if (tid < 128)
+            put_row_data(sm, tid, row_data(p, a, advp, retp, mean, istd,
+                                           (int)blockIdx.x * 128 + tid < p.mb_size ? perm[blockIdx.x * 128 + tid] : -1));
+        __syncthreads();
+        load_rows(p, sm, warp, lane, va, vb);
+    }
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        // ---- stage the tile: X (scaled, bf16, ones column D), X^T, per-row data
-        {
-            const int r0 = tile * 128;
-            for (int i = tid; i < 128; i += PPT) {
-                const bool valid = r0 + i < p.mb_size;
-                const long long smp = valid ? perm[r0 + i] : 0;
-                const long long t = smp / p.n_envs, e = smp - t * p.n_envs;
-                const long long ra = (t * p.n_envs + e) * p.A + a;
-                sm.act[i] = valid ? p.actions[ra] : 0;
-                sm.lpo[i] = valid ? p.logp_old[ra] : 0.0f;
-                sm.an[i] = valid ? (advp[smp] - mean) * istd : 0.0f;
-                sm.rt[i] = valid ? retp[smp] : 0.0f;
-            }
-            // warp w stages rows w, w + 8, ...; lanes along the features
-            for (int i = warp; i < 128; i += PPT / 32) {
-                const bool valid = r0 + i < p.mb_size;
-                const long long smp = valid ? perm[r0 + i] : 0;
-                const long long t = smp / p.n_envs, e = smp - t * p.n_envs;
-                const float *o = p.obs + ((t * p.n_envs + e) * p.A + a) * (long long)D;
-                for (int k = lane; k < Dp; k += 32) {
+        const int next = tile + (int)gridDim.x;
+        // ---- X (scaled, bf16) and [X | 1]^T from the rows loaded ahead
+#pragma unroll
+        for (int j = 0; j < RPW; j++) {
+            const int i = warp + (PPT / 32) * j;
+            const bool valid = sm.orow[i] >= 0;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; h2++) {
+                const int k = lane + 32 * h2;
+                if (k < Dp) {
                     float v = 0.0f;
-                    if (valid) v = k < D ? o[k] * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
+                    if (valid) v = k < D ? (h2 ? vb[j] : va[j]) * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
                     st_bf16(sm.x, cm_off(i, k, Dp), k < D ? v : 0.0f);   // the forward's X has no ones column
                     st_bf16(sm.xt, cm_off(k, i, 128), v);
                 }
@@ -216,6 +264,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         to_async();
         // ---- U1 = X W1^T
         if (tid == 0) gemm(tmem + TC_ACC, sm.x, sm.w1, Dp, H, false);
+        if (tid < 128) n_smp = next < n_tiles && next * 128 + tid < p.mb_size ? perm[next * 128 + tid] : -1;
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         // h1 = tanh(U1 + b1) -> H1 (r1) and [H1 | 1]^T (r2)
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
@@ -243,6 +292,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         to_async();
         // ---- U2 = H1 W2^T
         if (tid == 0) gemm(tmem + TC_ACC, sm.r1, sm.w2, H, H, false);
+        if (tid < 128) nd = row_data(p, a, advp, retp, mean, istd, n_smp);   // the next tile's, in flight
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             float v[32];
@@ -327,7 +377,9 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         to_async();
-        // ---- dH2 = dY W3 and dW3^T += H2^T dY
+        // ---- dH2 = dY W3 and dW3^T += H2^T dY (this tile's per-row data is no
+        // longer read: the next tile's takes its place)
+        if (tid < 128) put_row_data(sm, tid, nd);
         if (tid == 0) {
             gemm(tmem + TC_ACC, sm.dy, sm.w3t, 16, H, false);
             gemm(tmem + TC_DW3, sm.r3, sm.dyt, 128, 16, !first);
@@ -356,7 +408,8 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         to_async();
-        // ---- dH1 = dU2 W2 and dW2 += dU2^T [H1 | 1]
+        // ---- dH1 = dU2 W2 and dW2 += dU2^T [H1 | 1]; the next tile's rows in flight
+        load_rows(p, sm, warp, lane, va, vb);
         if (tid == 0) {
             gemm(tmem + TC_ACC, sm.r1, sm.w2t, H, H, false);
             gemm(tmem + TC_DW2, sm.r3, sm.r2, 128, H1T_ROWS, !first);
