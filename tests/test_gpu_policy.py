@@ -177,3 +177,39 @@ def test_fused_rollout_refuses_other_configurations():
         lob.lob_rollout_policy(pr.env.h, pol, T, lob.LOB_PREC_BF16_FUSED, None, None, None, None)
     lob.lob_policy_destroy(pol)
     pr.close()
+
+
+def test_fused_rollout_without_step_outputs_keeps_the_handle_state():
+    """With no per-step output buffers the fused rollout writes each step's
+    outputs into the handle's own buffers; the last step's observation,
+    rewards and done flags, the books and the counters equal those of the
+    same rollout with every output kept."""
+    import torch
+    n, T = 97, 10
+    st = mbogen.generate(mbogen.MessageModel(msgs_per_step=100), mbogen.env_seeds(41, n), T)
+    res = []
+    for keep in (True, False):
+        pr = Pair(n, st, cap=100, exec_target=300, action_mode=lob.LOB_ACT_HOST)
+        pol = lob.lob_policy_create(2, pr.env.D, lob.init_policy_params(5, 2, pr.env.D))
+        D = pr.env.D
+        if keep:
+            outs = (torch.zeros((T, n, 2, D), dtype=torch.float32, device="cuda"),
+                    torch.zeros((T, n, 2), dtype=torch.int64, device="cuda"),
+                    torch.zeros((T, n), dtype=torch.uint8, device="cuda"),
+                    torch.zeros((T, n, 2), dtype=torch.int32, device="cuda"))
+        else:
+            outs = (None, None, None, None)
+        lob.lob_rollout_policy(pr.env.h, pol, T, lob.LOB_PREC_BF16_FUSED, *outs)
+        assert pr.env.sync() == 0 and lob.lob_policy_sync(pol) == 0
+        obs, rew, done = pr.env.observe()
+        res.append((obs.cpu().numpy(), rew.cpu().numpy(), done.cpu().numpy(), pr.env.counters().cpu().numpy(),
+                    pr.env.books(), None if outs[0] is None else outs[0][T - 1].cpu().numpy()))
+        lob.lob_policy_destroy(pol)
+        pr.close()
+    a, b = res
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a[0], a[5])          # the handle's observation is the last step's
+    for e in range(n):
+        for k in ("n", "px", "qty", "id", "ts"):
+            np.testing.assert_array_equal(a[4][e][k], b[4][e][k])
