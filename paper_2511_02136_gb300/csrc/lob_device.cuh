@@ -621,10 +621,11 @@ __device__ __forceinline__ void side_rest(Side<K> &S, PoolSmem<K> &P, int cap, i
     const int free_slot = __shfl_sync(FULL, slot_of<K>(lane, 31 - __clz(fr)), 31 - __clz(flanes));
     int pos;
     if constexpr (Side<K>::REG) {
-        pos = 0;
+        // one warp sum of the lanes' counts (fewer instructions than a ballot per register)
+        int cnt = 0;
 #pragma unroll
-        for (int r = 0; r < K; r++)
-            pos += __popc(__ballot_sync(FULL, ((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p)));
+        for (int r = 0; r < K; r++) cnt += (int)(((S.occ >> r) & 1u) && at_least<BID>(S.px[r], p));
+        pos = (int)__reduce_add_sync(FULL, (unsigned)cnt);
     } else {
         int cnt = 0;
 #pragma unroll (Side<K>::SU)
