@@ -28,7 +28,7 @@ struct lob_policy {
     long long launches = 0;
     // IPPO update (allocated by the first lob_ppo_update)
     int upd_Dp = 0;                       // padded (D + 1)
-    unsigned char *d_wpk = nullptr;       // the update's packed weights (with W3^T and W2^T)
+    unsigned char *d_wpk = nullptr;       // the update's packed weights (W1 with a zero bias column, W2, W3)
     long long wpk_stride = 0;
     float *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
     float *d_adv = nullptr, *d_ret = nullptr;
@@ -154,7 +154,7 @@ static int ppo_setup(lob_policy *p, cudaStream_t s) {
                              (int)sizeof(ppo::GradSmem)) != cudaSuccess)
         return LOB_ECUDA;
     p->upd_Dp = (p->D + 1 + 15) / 16 * 16;
-    p->wpk_stride = ((long long)H * p->upd_Dp + 2LL * H * H + 2 * 16LL * H) * 2;
+    p->wpk_stride = ((long long)H * p->upd_Dp + (long long)H * H + 16LL * H) * 2;
     const size_t P = (size_t)(p->wf32_stride * p->A);
     bool fail = cudaMalloc(&p->d_wpk, (size_t)(p->wpk_stride * p->A)) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_m, P * 4) != cudaSuccess;

@@ -19,14 +19,17 @@
 //                  both this update and the rollout's forward.
 //
 // The eight contractions of a tile (M = 128 everywhere; operands in the
-// no-swizzle K-major core-matrix layout of policy.cuh):
+// no-swizzle core-matrix layout of policy.cuh):
 //   U1 = X W1^T,  U2 = H1 W2^T,  Y = H2 W3^T                  (forward)
 //   dH2 = dY W3,  dH1 = dU2 W2                                (input gradients)
 //   dW3^T += H2^T dY,  dW2 += dU2^T [H1 | 1],  dW1 += dU1^T [X | 1]
-// where the weight-gradient products contract over the tile's samples (the
-// transposed tiles are written that way by the epilogues).  A column of ones
-// after the inputs (X's column D) and after H1 (row 128 of H1^T) gives db1 and
-// db2 as the last columns of dW1 and dW2; db3 is a 16-wide sum.
+// Every tile is stored once, row by row (samples by units, or outputs by
+// units for the weights), and read either K-major or MN-major: a transposed
+// operand (W2^T, W3^T, and the sample-contracted H2^T, dY^T, dU2^T, [H1 | 1]^T,
+// dU1^T, [X | 1]^T) is the same tile read MN-major, so no epilogue writes a
+// transposed copy.  A column of ones after the inputs (X's column D, whose W1
+// column is zero) and after H1 (column 128 of [H1 | 1]) gives db1 and db2 as
+// the last columns of dW1 and dW2; db3 is a 16-wide sum.
 #pragma once
 #include "tc05.cuh"
 
@@ -39,7 +42,7 @@ using pol::cm_off;
 
 constexpr int PPT = 256;        // threads per CTA of the gradient kernel
 constexpr int DPMAX = 48;       // widest padded input (obs dim + 1 <= 48: up to 10 levels)
-constexpr int H1T_ROWS = 144;   // H1^T with its ones row, padded to a multiple of 16
+constexpr int H1W = 144;        // row length of [H1 | 1]: 128 units, the ones column, padding to 16
 
 struct GradParams {
     int A, D, Dp;                // Dp = padded (D + 1)
@@ -55,7 +58,7 @@ struct GradParams {
     long long mb_begin;          // this minibatch: perm positions [mb_begin, mb_begin + mb_size)
     int mb_size;
     const float *stats;          // [A][2]: mean, 1 / (std + 1e-8) of the minibatch's advantages
-    const unsigned char *wpk;    // per agent: W1 [128 x Dp], W2, W3 [16 x 128], W3^T [128 x 16], W2^T, bf16 core layout
+    const unsigned char *wpk;    // per agent: W1 [128 x Dp], W2 [128 x 128], W3 [16 x 128], bf16 core layout
     long long wpk_stride;        // bytes per agent
     const float *wf32;           // per agent parameter block (biases read from here)
     long long wf32_stride;
@@ -67,18 +70,13 @@ struct GradParams {
 
 // Shared memory of the gradient kernel (one CTA per SM).
 struct __align__(1024) GradSmem {
-    unsigned char w1[H * DPMAX * 2];
-    unsigned char w2[H * H * 2];
-    unsigned char w3[16 * H * 2];
-    unsigned char w3t[H * 16 * 2];
-    unsigned char w2t[H * H * 2];
-    unsigned char x[128 * DPMAX * 2];       // X [128 samples x Dp]
-    unsigned char xt[DPMAX * 128 * 2];      // [X | 1]^T [Dp x 128 samples]
-    unsigned char r1[128 * H * 2];          // H1, then H2, then dU2, then dU1^T
-    unsigned char r2[H1T_ROWS * 128 * 2];   // [H1 | 1]^T [144 x 128 samples]
-    unsigned char r3[H * 128 * 2];          // H2^T, then dU2^T
+    unsigned char w1[H * DPMAX * 2];        // W1 [128 x Dp] (its column D zero)
+    unsigned char w2[H * H * 2];            // W2 [128 out x 128 in]; read MN-major as W2^T
+    unsigned char w3[16 * H * 2];           // W3 [16 x 128]; read MN-major as W3^T
+    unsigned char x[128 * DPMAX * 2];       // [X | 1] [128 samples x Dp]
+    unsigned char r1[128 * H * 2];          // H2, then dU2, then dU1 [128 samples x 128]
+    unsigned char r2[128 * H1W * 2];        // [H1 | 1] [128 samples x 144]
     unsigned char dy[128 * 16 * 2];         // dY [128 samples x 16]
-    unsigned char dyt[16 * 128 * 2];        // dY^T [16 x 128 samples]
     float b1[H], b2[H], b3[16];
     float db3[16];
     int act[128];
@@ -99,17 +97,26 @@ constexpr unsigned TC_DW2 = 224;    // 144: dW2 [128 u2 units x (128 + ones + pa
 __device__ __forceinline__ void st_bf16(unsigned char *tile, unsigned off, float v) {
     *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16_rn(v);
 }
-__device__ __forceinline__ float ld_bf16(const unsigned char *tile, unsigned off) {
-    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(tile + off));
-}
 
-// Issue C (+)= A B^T over K in steps of 16 (one thread); A [128 x K], B [N x K].
-__device__ __forceinline__ void gemm(unsigned tmem_d, const unsigned char *A_, const unsigned char *B_, int K, int N,
-                                     bool acc) {
-    const unsigned idesc = pol::idesc_bf16(128, N);
+// Descriptors of step kk (16 along K) of an operand held in a tile of rows
+// of length Kp (element (r, c) at cm_off(r, c, Kp)): K-major when the tile's
+// rows are the operand's rows (K along a row), MN-major when the tile's rows
+// run along K (the operand is the tile transposed: leading offset between
+// groups of 8 rows, stride offset between groups of 8 columns).
+__device__ __forceinline__ unsigned long long kdesc(const unsigned char *t, int Kp, int kk) {
+    return pol::sdesc(t + kk * 256, 128, (unsigned)Kp * 16);
+}
+__device__ __forceinline__ unsigned long long mdesc(const unsigned char *t, int Kp, int kk) {
+    return pol::sdesc(t + kk * 32 * Kp, (unsigned)Kp * 16, 128);
+}
+// Issue C (+)= A B^T over K in steps of 16 (one thread); A [128 x K] and B
+// [N x K], each from its tile (row length a_kp / b_kp) K-major or MN-major.
+__device__ __forceinline__ void gemm(unsigned tmem_d, const unsigned char *A_, int a_kp, bool a_mn,
+                                     const unsigned char *B_, int b_kp, bool b_mn, int K, int N, bool acc) {
+    const unsigned idesc = pol::idesc_bf16(128, N) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u);
     for (int kk = 0; kk < K / 16; kk++) {
-        const unsigned long long da = pol::sdesc(A_ + kk * 256, 128, (unsigned)(K / 8) * 128);
-        const unsigned long long db = pol::sdesc(B_ + kk * 256, 128, (unsigned)(K / 8) * 128);
+        const unsigned long long da = a_mn ? mdesc(A_, a_kp, kk) : kdesc(A_, a_kp, kk);
+        const unsigned long long db = b_mn ? mdesc(B_, b_kp, kk) : kdesc(B_, b_kp, kk);
         pol::mma_bf16(tmem_d, da, db, idesc, (acc || kk > 0) ? 1 : 0);
     }
 }
@@ -191,12 +198,10 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         pol::pbar_init(&sm.wbar);
         const unsigned char *src = p.wpk + (long long)a * p.wpk_stride;
         const unsigned n1 = (unsigned)(H * Dp * 2), n2 = H * H * 2, n3 = 16 * H * 2;
-        pol::pbar_expect(&sm.wbar, n1 + 2 * n2 + 2 * n3);
+        pol::pbar_expect(&sm.wbar, n1 + n2 + n3);
         pol::bulk_g2s(sm.w1, src, n1, &sm.wbar);
         pol::bulk_g2s(sm.w2, src + n1, n2, &sm.wbar);
         pol::bulk_g2s(sm.w3, src + n1 + n2, n3, &sm.wbar);
-        pol::bulk_g2s(sm.w3t, src + n1 + n2 + n3, n3, &sm.wbar);
-        pol::bulk_g2s(sm.w2t, src + n1 + n2 + 2 * n3, n2, &sm.wbar);
     }
     {
         const float *wf = p.wf32 + (long long)a * p.wf32_stride;
@@ -245,7 +250,8 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     }
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int next = tile + (int)gridDim.x;
-        // ---- X (scaled, bf16) and [X | 1]^T from the rows loaded ahead
+        // ---- [X | 1] (scaled, bf16) from the rows loaded ahead; W1's column D
+        // is zero, so the forward reads the same tile
 #pragma unroll
         for (int j = 0; j < RPW; j++) {
             const int i = warp + (PPT / 32) * j;
@@ -256,17 +262,16 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                 if (k < Dp) {
                     float v = 0.0f;
                     if (valid) v = k < D ? (h2 ? vb[j] : va[j]) * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
-                    st_bf16(sm.x, cm_off(i, k, Dp), k < D ? v : 0.0f);   // the forward's X has no ones column
-                    st_bf16(sm.xt, cm_off(k, i, 128), v);
+                    st_bf16(sm.x, cm_off(i, k, Dp), v);
                 }
             }
         }
         to_async();
         // ---- U1 = X W1^T
-        if (tid == 0) gemm(tmem + TC_ACC, sm.x, sm.w1, Dp, H, false);
+        if (tid == 0) gemm(tmem + TC_ACC, sm.x, Dp, false, sm.w1, Dp, false, Dp, H, false);
         if (tid < 128) n_smp = next < n_tiles && next * 128 + tid < p.mb_size ? perm[next * 128 + tid] : -1;
         if (!(ok = mma_round(sm, phase, p, tid))) break;
-        // h1 = tanh(U1 + b1) -> H1 (r1) and [H1 | 1]^T (r2)
+        // h1 = tanh(U1 + b1) -> [H1 | 1] (r2): this thread's row, 16-byte stores
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
@@ -279,19 +284,20 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const float h1 = pol::tanh_approx(v[j + 2 * q + 1] + sm.b1[c0 + j + 2 * q + 1]);
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
-                    st_bf16(sm.r2, cm_off(c0 + j + 2 * q, row, 128), h0);
-                    st_bf16(sm.r2, cm_off(c0 + j + 2 * q + 1, row, 128), h1);
                 }
-                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, c0 + j, H1W)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        {   // the ones row (valid samples) and the zero padding rows of [H1 | 1]^T
+        if (half == 1) {   // the ones column (valid samples) and the zero padding of [H1 | 1]
             const bool valid = tile * 128 + row < p.mb_size;
-            for (int k = H + half; k < H1T_ROWS; k += 2) st_bf16(sm.r2, cm_off(k, row, 128), (k == H && valid) ? 1.0f : 0.0f);
+            const __nv_bfloat162 one = __floats2bfloat162_rn(valid ? 1.0f : 0.0f, 0.0f);
+            const unsigned o = *reinterpret_cast<const unsigned *>(&one);
+            *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, H, H1W)) = make_uint4(o, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, H + 8, H1W)) = make_uint4(0u, 0u, 0u, 0u);
         }
         to_async();
         // ---- U2 = H1 W2^T
-        if (tid == 0) gemm(tmem + TC_ACC, sm.r1, sm.w2, H, H, false);
+        if (tid == 0) gemm(tmem + TC_ACC, sm.r2, H1W, false, sm.w2, H, false, H, H, false);
         if (tid < 128) nd = row_data(p, a, advp, retp, mean, istd, n_smp);   // the next tile's, in flight
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
@@ -306,15 +312,13 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const float h1 = pol::tanh_approx(v[j + 2 * q + 1] + sm.b2[c0 + j + 2 * q + 1]);
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
-                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q, row, 128), h0);
-                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q + 1, row, 128), h1);
                 }
                 *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         to_async();
         // ---- Y = H2 W3^T, then the loss gradient dY per sample
-        if (tid == 0) gemm(tmem + TC_Y, sm.r1, sm.w3, H, 16, false);
+        if (tid == 0) gemm(tmem + TC_Y, sm.r1, H, false, sm.w3, H, false, H, 16, false);
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         if (half == 0) {
             float v[32];
@@ -365,8 +369,6 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
             *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-#pragma unroll
-            for (int j = 0; j < 16; j++) st_bf16(sm.dyt, cm_off(j, row, 128), dy[j]);
             // db3: the bf16-rounded dY the other products use, summed over the tile
 #pragma unroll
             for (int j = 0; j < 16; j++) {
@@ -381,11 +383,11 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         // longer read: the next tile's takes its place)
         if (tid < 128) put_row_data(sm, tid, nd);
         if (tid == 0) {
-            gemm(tmem + TC_ACC, sm.dy, sm.w3t, 16, H, false);
-            gemm(tmem + TC_DW3, sm.r3, sm.dyt, 128, 16, !first);
+            gemm(tmem + TC_ACC, sm.dy, 16, false, sm.w3, H, true, 16, H, false);      // W3^T: W3 read MN-major
+            gemm(tmem + TC_DW3, sm.r1, H, true, sm.dy, 16, true, 128, 16, !first);    // H2^T, dY^T: both MN-major
         }
         if (!(ok = mma_round(sm, phase, p, tid))) break;
-        // dU2 = dH2 (1 - h2^2): dU2 into r1 in place of H2, dU2^T into r3
+        // dU2 = dH2 (1 - h2^2): dU2 into r1 in place of H2
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
@@ -401,8 +403,6 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const float d0 = v[j + 2 * q] * (1.0f - ha * ha), d1 = v[j + 2 * q + 1] * (1.0f - hb * hb);
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(d0, d1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
-                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q, row, 128), d0);
-                    st_bf16(sm.r3, cm_off(c0 + j + 2 * q + 1, row, 128), d1);
                 }
                 *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
@@ -411,23 +411,33 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         // ---- dH1 = dU2 W2 and dW2 += dU2^T [H1 | 1]; the next tile's rows in flight
         load_rows(p, sm, warp, lane, va, vb);
         if (tid == 0) {
-            gemm(tmem + TC_ACC, sm.r1, sm.w2t, H, H, false);
-            gemm(tmem + TC_DW2, sm.r3, sm.r2, 128, H1T_ROWS, !first);
+            gemm(tmem + TC_ACC, sm.r1, H, false, sm.w2, H, true, H, H, false);        // W2^T: W2 read MN-major
+            gemm(tmem + TC_DW2, sm.r1, H, true, sm.r2, H1W, true, 128, H1W, !first);  // dU2^T, [H1 | 1]^T
         }
         if (!(ok = mma_round(sm, phase, p, tid))) break;
-        // dU1 = dH1 (1 - h1^2), h1 from [H1 | 1]^T: dU1^T into r1
+        // dU1 = dH1 (1 - h1^2), h1 from [H1 | 1]: dU1 into r1 (this thread's row)
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const float h = ld_bf16(sm.r2, cm_off(c0 + j, row, 128));
-                st_bf16(sm.r1, cm_off(c0 + j, row, 128), v[j] * (1.0f - h * h));
+            for (int j = 0; j < 32; j += 8) {
+                const uint4 hv = *reinterpret_cast<const uint4 *>(sm.r2 + cm_off(row, c0 + j, H1W));
+                const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                unsigned w[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const __nv_bfloat162 h1 = *reinterpret_cast<const __nv_bfloat162 *>(&hw[q]);
+                    const float ha = __low2float(h1), hb = __high2float(h1);
+                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(v[j + 2 * q] * (1.0f - ha * ha),
+                                                                    v[j + 2 * q + 1] * (1.0f - hb * hb));
+                    w[q] = *reinterpret_cast<const unsigned *>(&t2);
+                }
+                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         to_async();
         // ---- dW1 += dU1^T [X | 1]
-        if (tid == 0) gemm(tmem + TC_DW1, sm.r1, sm.xt, 128, Dp, !first);
+        if (tid == 0) gemm(tmem + TC_DW1, sm.r1, H, true, sm.x, Dp, true, 128, Dp, !first);   // both MN-major
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         first = false;
     }
@@ -447,7 +457,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         // dW2 (row = u2 unit): columns < 128, column 128 = db2
-        for (int c0 = 32 * half; c0 < H1T_ROWS; c0 += 64) {
+        for (int c0 = 32 * half; c0 < H1W; c0 += 64) {
             float v[32];
             if (c0 + 32 <= 160) {
                 pol::tm_ld32(lrow + TC_DW2 + c0, v);
@@ -558,13 +568,13 @@ struct AdamParams {
 };
 
 // Weight i of an agent's block (a weight matrix entry; biases are skipped)
-// into both packed bf16 layouts: the update's (W1, W2, W3, W3^T, W2^T) and the
+// into both packed bf16 layouts: the update's (W1 with its zero bias column, W2, W3) and the
 // rollout forward's (W1, W2, W3).
 __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long i, float w) {
     const int D = p.D;
     unsigned char *u = p.wpk + (long long)a * p.wpk_stride;
     unsigned char *f = p.wfwd + (long long)a * p.wfwd_stride;
-    const unsigned n1 = (unsigned)(H * p.Dp * 2), n1f = (unsigned)(H * p.Dpf * 2), n2 = H * H * 2, n3 = 16 * H * 2;
+    const unsigned n1 = (unsigned)(H * p.Dp * 2), n1f = (unsigned)(H * p.Dpf * 2), n2 = H * H * 2;
     long long o = i;
     if (o < (long long)H * D) {
         const int r = (int)(o / D), c = (int)(o % D);
@@ -576,7 +586,6 @@ __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long
     if (o >= 0 && o < (long long)H * H) {
         const int r = (int)(o / H), c = (int)(o % H);
         st_bf16(u + n1, cm_off(r, c, H), w);                      // W2 [out x in]
-        st_bf16(u + n1 + n2 + 2 * n3, cm_off(c, r, H), w);        // W2^T [in x out]
         st_bf16(f + n1f, cm_off(r, c, H), w);
         return;
     }
@@ -584,7 +593,6 @@ __device__ __forceinline__ void repack_one(const AdamParams &p, int a, long long
     if (o >= 0 && o < (long long)NOUT * H) {
         const int r = (int)(o / H), c = (int)(o % H);
         st_bf16(u + n1 + n2, cm_off(r, c, H), w);                 // W3 [16 x 128]
-        st_bf16(u + n1 + n2 + n3, cm_off(c, r, 16), w);           // W3^T [128 x 16]
         st_bf16(f + n1f + n2, cm_off(r, c, H), w);
     }
 }
