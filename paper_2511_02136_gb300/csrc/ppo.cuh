@@ -40,7 +40,9 @@ using pol::NA;
 using pol::NOUT;
 using pol::cm_off;
 
-constexpr int PPT = 256;        // threads per CTA of the gradient kernel
+constexpr int PPT = 512;        // threads per CTA of the gradient kernel (a multiple of 128)
+constexpr int NQ = PPT / 128;   // warps per TMEM lane quarter: the column parts of an epilogue
+static_assert(PPT % 128 == 0 && (128 / NQ) % 32 == 0, "an epilogue's column parts are whole 32-column loads");
 constexpr int DPMAX = 48;       // widest padded input (obs dim + 1 <= 48: up to 10 levels)
 constexpr int H1W = 144;        // row length of [H1 | 1]: 128 units, the ones column, padding to 16
 
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         const float *wf = p.wf32 + (long long)a * p.wf32_stride;
         const float *b1 = wf + H * D, *b2 = b1 + H + H * H, *b3 = b2 + H + NOUT * H;
         if (tid < H) sm.b1[tid] = b1[tid];
-        else sm.b2[tid - H] = b2[tid - H];
+        else if (tid < 2 * H) sm.b2[tid - H] = b2[tid - H];
         if (tid < 16) {
             sm.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
             sm.db3[tid] = 0.0f;
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     pol::tc_fence_after();
     const unsigned tmem = sm.tmem_base;
     const int row = 32 * (warp & 3) + lane;         // TMEM lane = sample row (or unit row for dW)
-    const int half = warp >> 2;
+    const int part = warp >> 2;                     // this warp's column part of an epilogue
+    const int cb = part * (H / NQ), ce = cb + H / NQ;   // its columns of a 128-wide accumulator
     const unsigned lrow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
     bool ok = true;
     unsigned phase = 0;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         if (tid < 128) n_smp = next < n_tiles && next * 128 + tid < p.mb_size ? perm[next * 128 + tid] : -1;
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         // h1 = tanh(U1 + b1) -> [H1 | 1] (r2): this thread's row, 16-byte stores
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
 #pragma unroll
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                 *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, c0 + j, H1W)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        if (half == 1) {   // the ones column (valid samples) and the zero padding of [H1 | 1]
+        if (part == NQ - 1) {   // the ones column (valid samples) and the zero padding of [H1 | 1]
             const bool valid = tile * 128 + row < p.mb_size;
             const __nv_bfloat162 one = __floats2bfloat162_rn(valid ? 1.0f : 0.0f, 0.0f);
             const unsigned o = *reinterpret_cast<const unsigned *>(&one);
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         if (tid == 0) gemm(tmem + TC_ACC, sm.r2, H1W, false, sm.w2, H, false, H, H, false);
         if (tid < 128) nd = row_data(p, a, advp, retp, mean, istd, n_smp);   // the next tile's, in flight
         if (!(ok = mma_round(sm, phase, p, tid))) break;
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
 #pragma unroll
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         // ---- Y = H2 W3^T, then the loss gradient dY per sample
         if (tid == 0) gemm(tmem + TC_Y, sm.r1, H, false, sm.w3, H, false, H, 16, false);
         if (!(ok = mma_round(sm, phase, p, tid))) break;
-        if (half == 0) {
+        if (part == 0) {
             float v[32];
             pol::tm_ld32(lrow + TC_Y, v);   // columns 16..31 lie in dW3's accumulator: unused here
             const bool valid = tile * 128 + row < p.mb_size;
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         }
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         // dU2 = dH2 (1 - h2^2): dU2 into r1 in place of H2
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
 #pragma unroll
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         }
         if (!(ok = mma_round(sm, phase, p, tid))) break;
         // dU1 = dH1 (1 - h1^2), h1 from [H1 | 1]: dU1 into r1 (this thread's row)
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
             pol::tm_ld32(lrow + TC_ACC + c0, v);
 #pragma unroll
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         float *g = p.grad + (long long)a * p.wf32_stride;
         float *gW1 = g, *gb1 = g + H * D, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + NOUT * H;
         // dW1 (row = u1 unit): columns < D, column D = db1
-        for (int c0 = 32 * half; c0 < Dp; c0 += 64) {
+        for (int c0 = 32 * part; c0 < Dp; c0 += 32 * NQ) {
             float v[32];
             pol::tm_ld32(lrow + TC_DW1 + c0, v);
 #pragma unroll
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         // dW2 (row = u2 unit): columns < 128, column 128 = db2
-        for (int c0 = 32 * half; c0 < H1W; c0 += 64) {
+        for (int c0 = 32 * part; c0 < H1W; c0 += 32 * NQ) {
             float v[32];
             if (c0 + 32 <= 160) {
                 pol::tm_ld32(lrow + TC_DW2 + c0, v);
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         // dW3^T (row = h2 unit, column = output)
-        if (half == 0) {
+        if (part == 0) {
             float v[32];
             pol::tm_ld32(lrow + TC_DW3, v);
 #pragma unroll
