@@ -557,7 +557,7 @@ def run_workload(args):
         tried = []
         choice = autotune.tune(env.h, tune_run, costs=costs, repeats=1,
                                candidates=autotune.DEFAULT_CANDIDATES + autotune.MULTI_CANDIDATES +
-                               autotune.SPLIT_CANDIDATES, timed=tried)
+                               autotune.SPLIT_CANDIDATES, timed=tried, tiles=autotune.TILE_CANDIDATES)
         stream = torch.cuda.Stream()
         env.load_messages(md, od)
         env.reset(sd, stream)
@@ -583,7 +583,7 @@ def run_workload(args):
                            "autotuned": choice.__dict__, "messages": msgs,
                            "tuning_window_ms": [{"warps_per_block": c.warps_per_block, "persistent": c.persistent,
                                                  "longest_first": c.longest_first, "threads_per_env": c.threads_per_env,
-                                                 "ms": c.ms} for c in tried]},
+                                                 "tile_records": c.tile_records, "ms": c.ms} for c in tried]},
                 "dtype": "int64", "data": "synthetic"}
         env.close()
         if args.per_class:

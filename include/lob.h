@@ -462,6 +462,18 @@ int lob_set_multi_split(lob_handle *h, const int32_t *warps_per_class);
  * twice the step time of 32 (more instructions in all and two code paths per
  * SM), so 32 stays the default.  LOB_EINVAL for other values. */
 int lob_set_threads_per_env(lob_handle *h, int32_t threads);
+/* Message-tile size: each env's messages of a step are copied from device
+ * memory into shared memory `records` at a time (16, 32 -- the default -- or
+ * 64), double-buffered, and the step processes one staged tile while the next
+ * is in flight.  It applies to launches of the plain step (the benchmark pair
+ * or no agents, a fixed task side, the PV reward, device-resident 32-byte
+ * records, no trace), which has an instance per size; 64-record tiles take
+ * (2 x 64 + 1) x 32 bytes of shared memory per warp beyond its block, so
+ * fewer warps may fit a block of the larger capacity classes.  Every other
+ * launch (extended, traced, several agents per type, the one-kernel
+ * multi-class form, the fused policy rollout, 64 threads per env) stages 32.
+ * Results do not depend on it.  LOB_EINVAL for other values. */
+int lob_set_tile_records(lob_handle *h, int32_t records);
 /* Failure-detection hook.  `cycles` bounds every wait of the step kernels on
  * a message tile, in SM cycles (0 = the default, about one second).  hold = 1
  * makes the next step or rollout launch leave each env's first message tile

@@ -8,10 +8,12 @@ created, or longest first from a per-env cost estimate) -- with CUDA events
 around a caller-supplied run, keeps the fastest, and caches the choice per
 workload signature in a JSON file.  The kernels themselves are unchanged: the
 shape is set through lob_set_launch / lob_set_multi_split / lob_set_env_costs /
-lob_set_threads_per_env before the timed runs.  Threads per env are 32 (one
-warp per env) or 64 (one warp per book side, for the plain step on a plain
-grid); messages are staged 32 records at a time in every shape.  The cache
-records the threads per env and the tile size with the shape.
+lob_set_threads_per_env / lob_set_tile_records before the timed runs.
+Threads per env are 32 (one warp per env) or 64 (one warp per book side, for
+the plain step on a plain grid).  The message-tile size (records staged per
+copy: 16, 32 or 64) is tuned after the shape: the winning shape is timed
+again with each of the other sizes in `tiles`.  The cache records the
+threads per env and the tile size with the shape.
 """
 from __future__ import annotations
 
@@ -27,6 +29,8 @@ DEFAULT_CANDIDATES = [(wpb, pers) for pers in (0, 1) for wpb in (1, 2, 4, 8)]
 MULTI_CANDIDATES = [(wpb, 2) for wpb in (4, 6, 8)]
 # two warps per env (one per book side): a plain grid, one env per block
 SPLIT_CANDIDATES = [(1, 0, 64)]
+# records per staged message tile, timed on the winning shape
+TILE_CANDIDATES = (16, 32, 64)
 
 
 @dataclass
@@ -46,6 +50,7 @@ def signature(n_envs, caps_hist, mean_msgs, steps, extra=""):
 def apply(h, choice: Choice, costs=None):
     lob.lob_set_launch(h, choice.warps_per_block, choice.persistent)
     lob.lob_set_threads_per_env(h, choice.threads_per_env)
+    lob.lob_set_tile_records(h, choice.tile_records)
     lob.lob_set_env_costs(h, costs if (choice.longest_first and costs is not None) else None)
 
 
@@ -66,11 +71,13 @@ def _event_timer(run, repeats):
 
 
 def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=None, key=None,
-         timer=None, applier=None, timed=None):
+         timer=None, applier=None, timed=None, tiles=(32,)):
     """`run()` performs one timed unit of work on the current stream (it must
     reset/rebind whatever it consumes); returns the fastest Choice.  `timer`
     (run, repeats) -> ms and `applier` (h, choice, costs) default to CUDA
-    events and the C ABI; `timed`, a list, receives every candidate timed."""
+    events and the C ABI; `timed`, a list, receives every candidate timed;
+    `tiles` lists the message-tile sizes tried on the winning shape (the
+    shapes themselves are timed with 32-record tiles)."""
     timer = timer or _event_timer
     applier = applier or apply
     if cache and key and os.path.exists(cache):
@@ -95,6 +102,18 @@ def tune(h, run, costs=None, candidates=DEFAULT_CANDIDATES, repeats=2, cache=Non
                 continue          # a shape this handle cannot take (e.g. more classes than warps)
             ch.ms = timer(run, repeats)
             results.append(ch)
+    win = min(results, key=lambda c: c.ms)
+    for tr in tiles:
+        if tr == win.tile_records:
+            continue
+        ch = Choice(win.warps_per_block, win.persistent, win.longest_first, 0.0,
+                    threads_per_env=win.threads_per_env, tile_records=tr)
+        try:
+            applier(h, ch, costs)
+        except lob.LobError:
+            continue
+        ch.ms = timer(run, repeats)
+        results.append(ch)
     if timed is not None:
         timed.extend(results)
     win = min(results, key=lambda c: c.ms)

@@ -61,9 +61,13 @@ size_t warp_smem_bytes(int K) {
     }
 }
 
+// Per-warp buffers of staged tiles larger than the per-warp block's own
+// (two tiles and one record read past the second).
+size_t tile_ext_bytes(int T) { return T > TILE ? (size_t)(2 * T + 1) * sizeof(DevMsg) : 0; }
+
 // Most warps (envs) per block whose shared memory fits one block.
-int max_wpb(int K) {
-    const int m = (int)(SMEM_PER_BLOCK_MAX / warp_smem_bytes(K));
+int max_wpb(int K, int T = TILE) {
+    const int m = (int)(SMEM_PER_BLOCK_MAX / (warp_smem_bytes(K) + tile_ext_bytes(T)));
     return m < 8 ? m : 8;
 }
 // The same for the several-agents kernel (each warp also holds an agent block).
@@ -72,9 +76,11 @@ int max_wpb_ma(int K) {
     return m < 8 ? m : 8;
 }
 
+// Every launch shape's shared memory stays within SMEM_PER_BLOCK_MAX, which
+// the step kernels are opted into (the tile size changes a shape's bytes).
 cudaError_t optin_k(int K) {
-    const size_t smem = (size_t)max_wpb(K) * warp_smem_bytes(K);
-    const size_t smem_ma = (size_t)max_wpb_ma(K) * (warp_smem_bytes(K) + sizeof(AgentSmem));
+    const size_t smem = SMEM_PER_BLOCK_MAX;
+    const size_t smem_ma = SMEM_PER_BLOCK_MAX;
     cudaError_t e;
     switch (K) {
         case 1: e = optin_steps_1(smem); return e == cudaSuccess ? optin_steps_ma_1(smem_ma) : e;
@@ -104,10 +110,10 @@ cudaError_t ensure_optin() {
 
 // Resident blocks per SM of the wide step kernel, per (class, extended,
 // warps per block); queried once (the launch shape fixes the shared memory).
-int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem) {
-    static int cache[NCLASS][2][9];   // 0 = not queried yet
+int wide_blocks_per_sm(int K, bool ext, int wpb, size_t smem, int T) {
+    static int cache[NCLASS][2][9][3];   // 0 = not queried yet; last index: tile 16, 32, 64
     const int k = class_of(32 * K);
-    int &c = cache[k][ext ? 1 : 0][wpb];
+    int &c = cache[k][ext ? 1 : 0][wpb][T == 16 ? 0 : (T == 64 ? 2 : 1)];
     if (c == 0) {
         int nb = 0;
         switch (K) {
@@ -138,6 +144,7 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
                      const KParams &p) {
     if (p.n_agents > 2) {
         // several agents per type: the wide kernel with a per-warp agent block
+        // (messages staged TILE records at a time)
         wpb = wpb < max_wpb_ma(K) ? wpb : max_wpb_ma(K);
         int blocks = (n_list + wpb - 1) / wpb;
         if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
@@ -151,17 +158,22 @@ cudaError_t launch_k(int K, bool trace, int n_list, int wpb, bool persistent, in
             default: return launch_steps_ma_32(trace, blocks, 32 * wpb, smem, s, p);
         }
     }
-    wpb = wpb < max_wpb(K) ? wpb : max_wpb(K);
-    int blocks = (n_list + wpb - 1) / wpb;
-    if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
-    const size_t smem = (size_t)wpb * warp_smem_bytes(K);
     // the extended kernel when episode mode, a reward variant or another
     // action space is on
     const bool ext = kernel_ext(p);
+    // message tiles of 16 or 64 records: the plain kernel's own instances
+    // (wide register budget); every other launch stages TILE records
+    const int T = (!trace && !ext && p.tile != 0 && p.tile != TILE) ? p.tile : TILE;
+    wpb = wpb < max_wpb(K, T) ? wpb : max_wpb(K, T);
+    int blocks = (n_list + wpb - 1) / wpb;
+    if (persistent) blocks = std::min(blocks, n_sm * std::max(1, 32 / wpb));
+    const size_t smem = (size_t)wpb * (warp_smem_bytes(K) + tile_ext_bytes(T));
     // the wide register budget when every block is resident at once (one wave)
-    const bool wide = blocks <= wide_blocks_per_sm(K, ext, wpb, smem) * n_sm;
+    const bool one_wave = blocks <= wide_blocks_per_sm(K, ext, wpb, smem, T) * n_sm;
+    const bool wide = one_wave || T != TILE;
     KParams q = p;
-    q.book_prefetch = wide ? 1 : 0;   // every env starts at once: fetch the books early
+    q.tile = T;
+    q.book_prefetch = one_wave ? 1 : 0;   // every env starts at once: fetch the books early
     switch (K) {
         case 1: return launch_steps_1(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
         case 2: return launch_steps_2(trace, ext, wide, blocks, 32 * wpb, smem, s, q);
@@ -220,6 +232,7 @@ struct lob_handle {
     int wpb = 4;
     int persistent = 0;
     int tpe = 32;                // threads per env: 64 runs the plain step with one warp per book side
+    int tile = TILE;             // records per staged message tile (16, 32 or 64)
     long long wait_budget = 0;   // 0: the default bound
     int hold_first = 0;          // failure-detection test hook (next launch only)
     int n_sm = 0;
@@ -703,6 +716,7 @@ static KParams base_params(lob_handle *h, const lob_msg *msgs, const int64_t *of
     p.agents = h->d_agents;
     p.msgs_sysmem = msgs_sysmem ? 1 : 0;
     p.msg16 = msg16 ? 1 : 0;
+    p.tile = h->tile;
     if (h->ep_mode) {
         p.ep_mode = 1;
         p.n_starts = h->n_starts;
@@ -1267,6 +1281,12 @@ int lob_set_launch(lob_handle *h, int32_t warps_per_block, int32_t persistent) {
 int lob_set_threads_per_env(lob_handle *h, int32_t threads) {
     if (!h || (threads != 32 && threads != 64)) return LOB_EINVAL;
     h->tpe = threads;
+    return LOB_OK;
+}
+
+int lob_set_tile_records(lob_handle *h, int32_t records) {
+    if (!h || (records != 16 && records != 32 && records != TILE_MAX)) return LOB_EINVAL;
+    h->tile = records;
     return LOB_OK;
 }
 

@@ -31,7 +31,8 @@
 namespace lobk {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int TILE = 32;        // messages per staged tile
+constexpr int TILE = 32;        // messages per staged tile in the per-warp block (the default)
+constexpr int TILE_MAX = 64;    // the largest staged tile (its buffers then follow the per-warp blocks)
 constexpr int LMAX = 64;        // max observation levels per side
 constexpr int SMAX = 256;       // max pool slots per side (byte-wide index)
 constexpr int ST_BADMSG = 1, ST_BADACT = 2, ST_TIMEOUT = 4, ST_CHECK = 8;
@@ -140,6 +141,7 @@ struct KParams {
     AgentState *agents;              // several agents per type: [n_envs][n_agents]
     int msgs_sysmem;                 // messages (and offsets) in page-locked host memory
     int msg16;                       // background messages are 16-byte compact records
+    int tile;                        // records per staged tile the launch was sized for (0 = TILE)
     int ow_obs, ow_rew, ow_done;     // that output overwrites env e's slot every step (else one slot per step)
     int *act_steps;                  // fused rollout: the actions taken at each step [n_steps][n_envs][2], or NULL
     const float *obs_in;             // fused rollout: every env's current observation [n_envs][2][D]
@@ -255,8 +257,10 @@ static_assert(offsetof(WarpSmem<1>, tile) == 0 && offsetof(WarpSmem<32>, tile) =
 constexpr int AMSG_MA = 3 * LOB_MAX_PER_TYPE + 1;
 // the message loop keeps a chunk's dispatch indices in the carry-over flags'
 // space: a tile or the agents' orders, plus the one-ahead read
-static_assert(sizeof(WarpSmem<1>::cand) >= AMSG_MA + 1 && sizeof(WarpSmem<1>::cand) >= TILE + 1,
+static_assert(sizeof(WarpSmem<1>::cand) >= AMSG_MA + 1 && sizeof(WarpSmem<1>::cand) >= TILE_MAX,
               "dispatch indices fit the carry-over flags");
+static_assert(offsetof(WarpSmem<1>, rw) == offsetof(WarpSmem<1>, cand) + sizeof(WarpSmem<1>::cand),
+              "the dispatch index read one past a full tile stays in the warp's block");
 struct __align__(16) AgentSmem {
     DevMsg amsg[AMSG_MA];
     long long inv[AMAX], cash[AMAX], pv[AMAX], done[AMAX];
@@ -1205,12 +1209,12 @@ static __device__ __noinline__ int4 mm_other_quotes(int space, int act, int bb, 
     return make_int4(qb, qa, f, 0);
 }
 
-// One message tile (up to TILE records) copied by the warp's lanes, one
-// 32-byte record per lane, as one commit group.
+// One message tile (up to TILE_MAX records) copied by the warp's lanes, one
+// record per lane per pass, as one commit group.
 __device__ __forceinline__ void tile_copy_lanes(void *dst, const void *src, int count, int rec_bytes, int lane) {
-    if (lane < count) {
-        char *d = reinterpret_cast<char *>(dst) + (long long)lane * rec_bytes;
-        const char *g = reinterpret_cast<const char *>(src) + (long long)lane * rec_bytes;
+    for (int r = lane; r < count; r += 32) {
+        char *d = reinterpret_cast<char *>(dst) + (long long)r * rec_bytes;
+        const char *g = reinterpret_cast<const char *>(src) + (long long)r * rec_bytes;
         cp_async16(d, g);
         if (rec_bytes == 32) cp_async16(d + 16, g + 16);
     }
@@ -1220,23 +1224,27 @@ __device__ __forceinline__ void tile_copy_lanes(void *dst, const void *src, int 
 // A tile of compact records {px, qty, word = id << 4 | sell << 3 | type},
 // landed in the upper half of a tile buffer, rewritten in place as 32-byte
 // records (all lanes read before any lane writes).
-__device__ __forceinline__ void widen_tile(DevMsg *tile, int count, int lane) {
-    const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const char *>(tile) + 16 * TILE);
-    int4 w = make_int4(0, 0, 0, 0);
-    if (lane < count) w = src[lane];
+__device__ __forceinline__ DevMsg widen_record(int4 w) {
+    const long long word = ((long long)(unsigned)w.w << 32) | (unsigned)w.z;
+    DevMsg r;
+    r.ts = 0;
+    r.oid = word >> 4;
+    r.px = w.x;
+    r.qty = w.y;
+    r.type = (short)(word & 7);
+    r.side = (short)((word & 8) ? LOB_SELL : LOB_BUY);
+    r.pad = 0;
+    return r;
+}
+__device__ __forceinline__ void widen_tile(DevMsg *tile, int count, int T, int lane) {
+    const int4 *src = reinterpret_cast<const int4 *>(reinterpret_cast<const char *>(tile) + 16 * T);
+    // up to two records per lane (T <= 64), all read before any is written
+    int4 w0 = make_int4(0, 0, 0, 0), w1 = make_int4(0, 0, 0, 0);
+    if (lane < count) w0 = src[lane];
+    if (lane + 32 < count) w1 = src[lane + 32];
     __syncwarp();
-    if (lane < count) {
-        const long long word = ((long long)(unsigned)w.w << 32) | (unsigned)w.z;
-        DevMsg r;
-        r.ts = 0;
-        r.oid = word >> 4;
-        r.px = w.x;
-        r.qty = w.y;
-        r.type = (short)(word & 7);
-        r.side = (short)((word & 8) ? LOB_SELL : LOB_BUY);
-        r.pad = 0;
-        tile[lane] = r;
-    }
+    if (lane < count) tile[lane] = widen_record(w0);
+    if (lane + 32 < count) tile[lane + 32] = widen_record(w1);
     __syncwarp();
 }
 
@@ -1428,6 +1436,7 @@ __device__ __forceinline__ int msgs_ladder(WarpSmem<K> &sm, LadBlock<K> *lb, Sid
 // Message pipeline state of one warp (tiles issued so far).
 struct MsgPipe {
     unsigned tiles;
+    DevMsg *buf;   // tiles larger than TILE: this warp's two buffers (plus one record read ahead)
 };
 
 // Run n_steps env steps of env e with the book resident on chip.  EXT
@@ -1435,9 +1444,15 @@ struct MsgPipe {
 // without it those settings are ignored, so the host launches EXT whenever
 // one is set.  MA (which implies EXT) runs 2P agents with their state in the
 // warp's agent block agp; without it the agents are the benchmark pair.
-template <int K, bool TRACE, bool EXT, bool MA, bool FUSED = false>
+template <int K, bool TRACE, bool EXT, bool MA, bool FUSED = false, int TT = TILE>
 __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp, LadBlock<K> *lb, MsgPipe &pipe,
                         int lane, FusedCtx *fc = nullptr) {
+    // TT records per staged message tile: up to TILE in the per-warp block's
+    // buffers, more in the warp's own buffers after every per-warp block
+    static_assert(TT == 16 || TT == 32 || TT == 64, "staged tiles of 16, 32 or 64 records");
+    constexpr int T = TT;
+    constexpr int lgT = TT == 16 ? 4 : (TT == 64 ? 6 : 5);
+    DevMsg *const tb = TT > TILE ? pipe.buf : &sm.tile[0][0];
     constexpr bool XT = EXT || MA;
     // the price-ladder form for every untraced instance of the register-pool
     // classes (traces record the book after every message in the sorted form)
@@ -1524,7 +1539,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
             me = p.offsets[d + 1];
         }
         const int nmsg = (int)(me - mb);
-        const int ntiles = (nmsg + TILE - 1) / TILE;
+        const int ntiles = (nmsg + T - 1) >> lgT;
         const unsigned tile0 = pipe.tiles;
         // failure-detection test hook: the launch's first tile is not requested,
         // so the wait for it runs out (bulk-copy path only)
@@ -1532,12 +1547,12 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
         if (ntiles > 0) {
             __syncwarp();
             // compact tiles land in the upper half of the buffer and are widened on arrival
-            char *dst = reinterpret_cast<char *>(sm.tile[pipe.tiles & 1]) + (m16 ? 16 * TILE : 0);
+            char *dst = reinterpret_cast<char *>(tb + (pipe.tiles & 1) * T) + (m16 ? 16 * T : 0);
             if (sysm) {
-                tile_copy_lanes(dst, msg_base + mb * rec, min(TILE, nmsg), rec, lane);
+                tile_copy_lanes(dst, msg_base + mb * rec, min(T, nmsg), rec, lane);
             } else if (lane == 0 && !held) {
                 fence_proxy_async_smem();
-                tma_bulk_g2s(dst, msg_base + mb * rec, (unsigned)(min(TILE, nmsg) * rec), &sm.bar[pipe.tiles & 1]);
+                tma_bulk_g2s(dst, msg_base + mb * rec, (unsigned)(min(T, nmsg) * rec), &sm.bar[pipe.tiles & 1]);
             }
             pipe.tiles++;
         }
@@ -1764,20 +1779,20 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
                 }
                 if (ch + 1 < ntiles) {
                     __syncwarp();
-                    const char *src = msg_base + (mb + (long long)(ch + 1) * TILE) * rec;
-                    char *dst = reinterpret_cast<char *>(sm.tile[pipe.tiles & 1]) + (m16 ? 16 * TILE : 0);
+                    const char *src = msg_base + (mb + (long long)(ch + 1) * T) * rec;
+                    char *dst = reinterpret_cast<char *>(tb + (pipe.tiles & 1) * T) + (m16 ? 16 * T : 0);
                     if (sysm) {
-                        tile_copy_lanes(dst, src, min(TILE, nmsg - (ch + 1) * TILE), rec, lane);
+                        tile_copy_lanes(dst, src, min(T, nmsg - (ch + 1) * T), rec, lane);
                     } else if (lane == 0) {
                         fence_proxy_async_smem();
-                        tma_bulk_g2s(dst, src, (unsigned)(min(TILE, nmsg - (ch + 1) * TILE) * rec),
+                        tma_bulk_g2s(dst, src, (unsigned)(min(T, nmsg - (ch + 1) * T) * rec),
                                      &sm.bar[pipe.tiles & 1]);
                     }
                     pipe.tiles++;
                 }
-                base = sm.tile[buf];
-                cnt_ch = min(TILE, nmsg - ch * TILE);
-                if (m16) widen_tile(sm.tile[buf], cnt_ch, lane);
+                base = tb + buf * T;
+                cnt_ch = min(T, nmsg - ch * T);
+                if (m16) widen_tile(tb + buf * T, cnt_ch, T, lane);
             }
             const int4 *rp = reinterpret_cast<const int4 *>(base);
             c.c_msgs += cnt_ch;                 // a started chunk is always finished
@@ -2081,7 +2096,7 @@ __device__ void run_env(const KParams &p, int e, WarpSmem<K> &sm, AgentSmem *agp
 }
 
 // One warp per env; with a work queue (p.queue) warps take envs until none is left.
-template <int K, bool TRACE, bool EXT, bool MA>
+template <int K, bool TRACE, bool EXT, bool MA, int TT = TILE>
 __device__ __forceinline__ void env_steps_body(const KParams &p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -2094,23 +2109,28 @@ __device__ __forceinline__ void env_steps_body(const KParams &p) {
     LadBlock<K> *lb = ladder_class<K>() ? reinterpret_cast<LadBlock<K> *>(after) + wib : nullptr;
     after += nw * ladder_bytes<K>();
     AgentSmem *agp = MA ? reinterpret_cast<AgentSmem *>(after) + wib : nullptr;
+    after += MA ? nw * sizeof(AgentSmem) : 0;
+    // tiles of more than TILE records: the warps' buffers after every other
+    // per-warp block (two tiles and the record read one past the second)
+    DevMsg *tbuf = TT > TILE ? reinterpret_cast<DevMsg *>(after) + wib * (2 * TT + 1) : nullptr;
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
     }
     __syncwarp();
-    MsgPipe pipe{0u};
+    MsgPipe pipe{0u, tbuf};
     if (p.queue == nullptr) {
         const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-        if (w < p.n_list) run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
+        if (w < p.n_list)
+            run_env<K, TRACE, EXT, MA, false, TT>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
     } else {
         for (;;) {
             int w = 0;
             if (lane == 0) w = atomicAdd(p.queue, 1);
             w = __shfl_sync(FULL, w, 0);
             if (w >= p.n_list) break;
-            run_env<K, TRACE, EXT, MA>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
+            run_env<K, TRACE, EXT, MA, false, TT>(p, p.env_list ? p.env_list[w] : w, sm, agp, lb, pipe, lane);
         }
     }
 }
@@ -2125,9 +2145,9 @@ template <int K, bool TRACE, bool EXT, bool MA = false>
 __global__ void __launch_bounds__(256) k_env_steps(const KParams p) {
     env_steps_body<K, TRACE, EXT, MA>(p);
 }
-template <int K, bool TRACE, bool EXT, bool MA = false>
+template <int K, bool TRACE, bool EXT, bool MA = false, int TT = TILE>
 __global__ void __launch_bounds__(256, 1) k_env_steps_wide(const KParams p) {
-    env_steps_body<K, TRACE, EXT, MA>(p);
+    env_steps_body<K, TRACE, EXT, MA, TT>(p);
 }
 // A fixed register budget of NREG per thread, for launches of several waves
 // where resident warps per SM set the throughput: e.g. 168 keeps three 4-warp

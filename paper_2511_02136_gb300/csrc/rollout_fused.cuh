@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(FWMAX * 32, 1) k_rollout_fused(const KParams p
     __syncwarp();
     fused_policy(fz, f, fc.phase, nw, tid);
     if (active) {
-        MsgPipe pipe{0u};
+        MsgPipe pipe{0u, nullptr};
         run_env<K, false, false, false, true>(p, e, sm, nullptr, lb, pipe, lane, &fc);
     } else {
         for (int i = 0; i < p.n_steps; i++) fused_policy(fz, f, fc.phase, nw, tid);   // keep the CTA in step

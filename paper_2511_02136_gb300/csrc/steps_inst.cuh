@@ -18,7 +18,12 @@ template <int KK, bool ALWAYS_WIDE = (KK >= 8)>
 struct StepLaunch {
     static cudaError_t launch(bool trace, bool ext, bool wide, int blocks, int threads, size_t smem, cudaStream_t s,
                               const KParams &p) {
-        if (trace) k_env_steps_wide<KK, true, true><<<blocks, threads, smem, s>>>(p);
+        // other message-tile sizes: the plain kernel in the wide budget
+        // (p.tile is set only for launches that take it)
+        if (!trace && !ext && p.tile == 16) k_env_steps_wide<KK, false, false, false, 16><<<blocks, threads, smem, s>>>(p);
+        else if (!trace && !ext && p.tile == TILE_MAX)
+            k_env_steps_wide<KK, false, false, false, TILE_MAX><<<blocks, threads, smem, s>>>(p);
+        else if (trace) k_env_steps_wide<KK, true, true><<<blocks, threads, smem, s>>>(p);
         else if constexpr (ALWAYS_WIDE) {
             if (ext) k_env_steps_wide<KK, false, true><<<blocks, threads, smem, s>>>(p);
             else k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
@@ -39,6 +44,8 @@ struct StepLaunch {
         cudaError_t e = cudaFuncSetAttribute(k_env_steps_wide<KK, true, true>, A, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, true>, A, b);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, false>, A, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, false, false, 16>, A, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_wide<KK, false, false, false, TILE_MAX>, A, b);
         if constexpr (!ALWAYS_WIDE) {
             if constexpr (KK == 4) {
                 if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_nreg<KK, false, true, false, 168>, A, b);

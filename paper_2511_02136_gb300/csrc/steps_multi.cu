@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, 1) k_env_steps_multi(const KParams p, con
         fence_mbar_init();
     }
     __syncwarp();
-    MsgPipe pipe{0u};
+    MsgPipe pipe{0u, nullptr};
     for (;;) {
         int c = own, w = 0;
         bool got = false;

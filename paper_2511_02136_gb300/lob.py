@@ -59,7 +59,7 @@ EXPORTS = [
     "lob_checkpoint_bytes", "lob_save", "lob_load", "lob_set_episodes", "lob_get_episode_starts",
     "lob_step_host_async", "lob_load_messages16", "lob_set_episodes16", "lob_pack_messages16",
     "lob_live_orders", "lob_policy_get_params", "lob_ppo_update", "lob_set_multi_split",
-    "lob_set_threads_per_env",
+    "lob_set_threads_per_env", "lob_set_tile_records",
 ]
 LOB_PREC_FP32, LOB_PREC_BF16, LOB_PREC_BF16_FUSED = 0, 1, 2
 LOB_REWARD_PV, LOB_REWARD_BUYSELL, LOB_REWARD_SPOONER = 0, 1, 2
@@ -188,6 +188,7 @@ def _load():
         "lob_live_orders": (ctypes.c_int, [P, P, P]),
         "lob_set_multi_split": (ctypes.c_int, [P, P]),
         "lob_set_threads_per_env": (ctypes.c_int, [P, I32]),
+        "lob_set_tile_records": (ctypes.c_int, [P, I32]),
         "lob_set_trace": (ctypes.c_int, [P, P, I32, P, P, I64, P]),
         "lob_sync": (ctypes.c_int, [P, P]),
         "lob_set_launch": (ctypes.c_int, [P, I32, I32]),
@@ -324,6 +325,11 @@ def lob_get_actions(h, out, stream=None):
 def lob_set_threads_per_env(h, threads):
     """32: one warp per env; 64: one warp per book side for the plain step (see include/lob.h)."""
     return _check(_load().lob_set_threads_per_env(h, threads), "lob_set_threads_per_env")
+
+
+def lob_set_tile_records(h, records):
+    """Records per staged message tile: 16, 32 (default) or 64."""
+    return _check(_load().lob_set_tile_records(h, records), "lob_set_tile_records")
 
 
 def lob_set_multi_split(h, warps_per_class):

@@ -31,7 +31,7 @@ class Pair:
     def __init__(self, n_envs, st, *, n_agents=2, cap=100, caps=None, top_levels=10, episode_len=None,
                  mm_lot=1, exec_target=500, exec_dir=-1, action_mode=lob.LOB_ACT_RANDOM, start_px=10_000,
                  fill_cap=0, snap_cap=0, warps_per_block=0, persistent=0, n_threads=1, rewards=None,
-                 episodes=None, seeds=None, mm_space=0, compact=False, threads_per_env=32):
+                 episodes=None, seeds=None, mm_space=0, compact=False, threads_per_env=32, tile_records=32):
         """episodes: (starts, levels) puts both sides in episode mode over the
         single shared stream st (env 0 of st); seeds then gives the env seeds."""
         import torch
@@ -47,6 +47,8 @@ class Pair:
             lob.lob_set_launch(self.env.h, warps_per_block or 4, persistent)
         if threads_per_env != 32:
             lob.lob_set_threads_per_env(self.env.h, threads_per_env)
+        if tile_records != 32:
+            lob.lob_set_tile_records(self.env.h, tile_records)
         self.orc = oracle.Oracle(n_envs, n_agents=n_agents, cap=cap, top_levels=top_levels, episode_len=T,
                                  mm_lot=mm_lot, exec_target=exec_target, exec_dir=exec_dir,
                                  action_mode=action_mode, trace=(1 if fill_cap else 0) | (2 if snap_cap else 0),

@@ -81,3 +81,31 @@ def test_threads_per_env_axis_is_timed_and_cached(tmp_path):
     assert (1, 0, False, 64) in seen
     assert json.loads(cache.read_text())["k"]["threads_per_env"] == 64
     assert sum(1 for *_, t in seen if t == 64) == 2   # timed, then applied as the winner
+
+
+def test_tile_axis_timed_on_the_winning_shape(tmp_path):
+    """The message-tile sizes are timed on the winning shape only, and the
+    fastest (shape, tile) is applied and cached."""
+    seen = []
+
+    def applier(h, ch, costs):
+        seen.append((ch.warps_per_block, ch.persistent, ch.longest_first, ch.tile_records))
+
+    def timer(run, repeats):
+        wpb, pers, lf, tile = seen[-1]
+        base = 3.0 if (wpb, pers, lf) == (4, 1, True) else 10.0 + wpb
+        return base - (0.5 if tile == 64 else 0.0) + (0.5 if tile == 16 else 0.0)
+
+    cache = tmp_path / "tune.json"
+    timed = []
+    win = autotune.tune(None, lambda: None, costs=[1.0], timer=timer, applier=applier, cache=str(cache), key="k",
+                        timed=timed, tiles=autotune.TILE_CANDIDATES)
+    assert (win.warps_per_block, win.persistent, win.longest_first, win.tile_records) == (4, 1, True, 64)
+    assert win.ms == 2.5
+    # 12 shapes at 32 records, then the winner at 16 and 64
+    assert len(timed) == 14
+    assert sorted(c.tile_records for c in timed if (c.warps_per_block, c.persistent, c.longest_first) == (4, 1, True)) \
+        == [16, 32, 64]
+    assert all(c.tile_records == 32 for c in timed[:12])
+    assert seen[-1] == (4, 1, True, 64)
+    assert json.loads(cache.read_text())["k"]["tile_records"] == 64
