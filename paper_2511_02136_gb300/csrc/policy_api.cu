@@ -210,7 +210,8 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (mb + 127) / 128;
-    const int ctas = std::max(1, std::min(tiles, n_sm / A > 0 ? n_sm / A : 1));
+    // each CTA runs ppo::NS tile streams
+    const int ctas = std::max(1, std::min((tiles + ppo::NS - 1) / ppo::NS, n_sm / A > 0 ? n_sm / A : 1));
     ppo::GradParams g;
     std::memset(&g, 0, sizeof(g));
     g.A = A; g.D = p->D; g.Dp = p->upd_Dp; g.L = p->L; g.n_envs = b->n_envs; g.n_samples = N;

@@ -40,9 +40,16 @@ using pol::NA;
 using pol::NOUT;
 using pol::cm_off;
 
-constexpr int PPT = 512;        // threads per CTA of the gradient kernel (a multiple of 128)
-constexpr int NQ = PPT / 128;   // warps per TMEM lane quarter: the column parts of an epilogue
-static_assert(PPT % 128 == 0 && (128 / NQ) % 32 == 0, "an epilogue's column parts are whole 32-column loads");
+// Two tile streams per CTA: each stream of SPT threads (8 warps) takes every
+// other of the CTA's tiles and runs its contractions and epilogues on its own
+// operand tiles, TMEM accumulator, mbarrier and named barrier, so that one
+// stream's epilogues overlap the other's contractions; the weights and the
+// weight-gradient accumulators (TMEM, zeroed at the start) are shared.
+constexpr int NS = 2;            // tile streams per CTA
+constexpr int SPT = 256;         // threads per stream (a multiple of 128)
+constexpr int PPT = NS * SPT;    // threads per CTA of the gradient kernel
+constexpr int NQ = SPT / 128;    // warps of a stream per TMEM lane quarter: the column parts of an epilogue
+static_assert(SPT % 128 == 0 && (128 / NQ) % 32 == 0, "an epilogue's column parts are whole 32-column loads");
 constexpr int DPMAX = 48;       // widest padded input (obs dim + 1 <= 48: up to 10 levels)
 constexpr int H1W = 144;        // row length of [H1 | 1]: 128 units, the ones column, padding to 16
 
@@ -70,31 +77,41 @@ struct GradParams {
     long long wait_budget;
 };
 
+// One stream's operand tiles and per-row data.
+struct __align__(128) StreamSmem {
+    unsigned char x[128 * DPMAX * 2];       // [X | 1] [128 samples x Dp]
+    unsigned char r1[128 * H * 2];          // H2, then dU2, then dU1 [128 samples x 128]
+    unsigned char r2[128 * H1W * 2];        // [H1 | 1] [128 samples x 144]
+    unsigned char dy[128 * 16 * 2];         // dY [128 samples x 16]
+    int act[128];
+    float lpo[128], an[128], rt[128];
+    long long orow[128];                    // the tile's samples: observation row index, or -1 past the minibatch
+    unsigned long long bar;
+};
 // Shared memory of the gradient kernel (one CTA per SM).
 struct __align__(1024) GradSmem {
     unsigned char w1[H * DPMAX * 2];        // W1 [128 x Dp] (its column D zero)
     unsigned char w2[H * H * 2];            // W2 [128 out x 128 in]; read MN-major as W2^T
     unsigned char w3[16 * H * 2];           // W3 [16 x 128]; read MN-major as W3^T
-    unsigned char x[128 * DPMAX * 2];       // [X | 1] [128 samples x Dp]
-    unsigned char r1[128 * H * 2];          // H2, then dU2, then dU1 [128 samples x 128]
-    unsigned char r2[128 * H1W * 2];        // [H1 | 1] [128 samples x 144]
-    unsigned char dy[128 * 16 * 2];         // dY [128 samples x 16]
+    StreamSmem st[NS];
     float b1[H], b2[H], b3[16];
     float db3[16];
-    int act[128];
-    float lpo[128], an[128], rt[128];
-    long long orow[128];                    // the tile's samples: observation row index, or -1 past the minibatch
-    unsigned long long bar, wbar;
+    unsigned long long wbar;
     unsigned tmem_base;
 };
 static_assert(sizeof(GradSmem) <= 227 * 1024, "one CTA's shared memory");
 
-// TMEM columns of the gradient kernel (512 allocated).
-constexpr unsigned TC_ACC = 0;      // 128: U1, U2, dH2, dH1 in turn
-constexpr unsigned TC_Y = 128;      // 16: Y
-constexpr unsigned TC_DW3 = 144;    // 16: dW3^T [128 h2 units x 16 outputs]
-constexpr unsigned TC_DW1 = 160;    // Dp <= 48: dW1 [128 u1 units x Dp]
-constexpr unsigned TC_DW2 = 224;    // 144: dW2 [128 u2 units x (128 + ones + pad)]
+// TMEM columns of the gradient kernel (512 allocated): the shared
+// weight-gradient accumulators, then per stream the forward / input-gradient
+// accumulator and Y.
+constexpr unsigned TC_DW3 = 0;      // 16: dW3^T [128 h2 units x 16 outputs]
+constexpr unsigned TC_DW1 = 16;     // Dp <= 48: dW1 [128 u1 units x Dp]
+constexpr unsigned TC_DW2 = 64;     // 144: dW2 [128 u2 units x (128 + ones + pad)]
+constexpr unsigned TC_STREAMS = 208;
+__host__ __device__ constexpr unsigned tc_acc(int s) { return TC_STREAMS + 144u * (unsigned)s; }   // 128: U1, U2, dH2, dH1
+__host__ __device__ constexpr unsigned tc_y(int s) { return tc_acc(s) + 128u; }                   // 16: Y
+static_assert(TC_DW1 + DPMAX <= TC_DW2 && TC_DW2 + H1W <= TC_STREAMS && tc_y(NS - 1) + 16 <= 512,
+              "TMEM regions within the 512 columns");
 
 __device__ __forceinline__ void st_bf16(unsigned char *tile, unsigned off, float v) {
     *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16_rn(v);
@@ -123,24 +140,40 @@ __device__ __forceinline__ void gemm(unsigned tmem_d, const unsigned char *A_, i
     }
 }
 
-// Commit the issued MMAs and wait for them (all threads); false on timeout.
-__device__ __forceinline__ bool mma_round(GradSmem &sm, unsigned &phase, const GradParams &p, int tid) {
-    if (tid == 0) pol::mma_commit(&sm.bar);
-    const bool arrived = pol::pbar_wait(&sm.bar, phase, p.wait_budget);
-    if (__syncthreads_or(!arrived)) {
-        if (tid == 0) atomicOr(p.status, 4);
-        pol::pbar_wait(&sm.bar, phase, p.wait_budget);   // let the tensor core finish before TMEM is freed
+// Stream s's named barrier (ids 1 and 2; 0 is the whole CTA's): its SPT
+// threads only.  stream_sync_or also returns whether any of them passed true.
+__device__ __forceinline__ void stream_sync(int s) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + s), "r"(SPT) : "memory");
+}
+__device__ __forceinline__ bool stream_sync_or(int s, bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r) : "r"(v ? 1u : 0u), "r"(1 + s), "r"(SPT) : "memory");
+    return r != 0;
+}
+// Commit the MMAs the stream's issuing thread (ts == 0) issued and wait for
+// them (all the stream's threads); false on timeout.
+__device__ __forceinline__ bool mma_round(StreamSmem &S, int s, unsigned &phase, const GradParams &p, int ts) {
+    if (ts == 0) pol::mma_commit(&S.bar);
+    const bool arrived = pol::pbar_wait(&S.bar, phase, p.wait_budget);
+    if (stream_sync_or(s, !arrived)) {
+        if (ts == 0) atomicOr(p.status, 4);
+        pol::pbar_wait(&S.bar, phase, p.wait_budget);   // let the tensor core finish before TMEM is freed
         return false;
     }
     phase ^= 1u;
     pol::tc_fence_after();
     return true;
 }
-// Make the threads' shared-memory writes visible to the tensor core.
-__device__ __forceinline__ void to_async() {
+// Make the stream's shared-memory writes visible to the tensor core.
+__device__ __forceinline__ void to_async(int s) {
     pol::fence_async_smem();
     pol::tc_fence_before();
-    __syncthreads();
+    stream_sync(s);
     pol::tc_fence_after();
 }
 
@@ -165,22 +198,22 @@ __device__ __forceinline__ RowData row_data(const GradParams &p, int a, const fl
     }
     return d;
 }
-__device__ __forceinline__ void put_row_data(GradSmem &sm, int i, const RowData &d) {
+__device__ __forceinline__ void put_row_data(StreamSmem &sm, int i, const RowData &d) {
     sm.orow[i] = d.ra;
     sm.act[i] = d.act;
     sm.lpo[i] = d.lpo;
     sm.an[i] = d.an;
     sm.rt[i] = d.rt;
 }
-constexpr int RPW = 128 / (PPT / 32);   // tile rows per warp
-// This warp's observation rows (w, w + 8, ...) of the tile sm.orow names,
+constexpr int RPW = 128 / (SPT / 32);   // tile rows per warp of a stream
+// This warp's observation rows (sw, sw + 8, ...) of the tile sm.orow names,
 // features lane and lane + 32, all loads issued before any is used.
-__device__ __forceinline__ void load_rows(const GradParams &p, const GradSmem &sm, int warp, int lane,
+__device__ __forceinline__ void load_rows(const GradParams &p, const StreamSmem &sm, int sw, int lane,
                                           float (&va)[RPW], float (&vb)[RPW]) {
     const int D = p.D;
 #pragma unroll
     for (int j = 0; j < RPW; j++) {
-        const long long ra = sm.orow[warp + (PPT / 32) * j];
+        const long long ra = sm.orow[sw + (SPT / 32) * j];
         const float *o = p.obs + (ra < 0 ? 0 : ra) * (long long)D;
         va[j] = (ra >= 0 && lane < D) ? o[lane] : 0.0f;
         vb[j] = (ra >= 0 && lane + 32 < D) ? o[lane + 32] : 0.0f;
@@ -196,7 +229,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     const int n_tiles = (p.mb_size + 127) / 128;
     if (warp == 0) pol::tm_alloc(&sm.tmem_base, 512);
     if (tid == 0) {
-        pol::pbar_init(&sm.bar);
+        for (int s = 0; s < NS; s++) pol::pbar_init(&sm.st[s].bar);
         pol::pbar_init(&sm.wbar);
         const unsigned char *src = p.wpk + (long long)a * p.wpk_stride;
         const unsigned n1 = (unsigned)(H * Dp * 2), n2 = H * H * 2, n3 = 16 * H * 2;
@@ -219,8 +252,22 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     __syncthreads();
     pol::tc_fence_after();
     const unsigned tmem = sm.tmem_base;
+    // the weight-gradient accumulators start at zero (both streams accumulate
+    // into them from their first tile): 13 groups of 16 columns per lane
+    // quarter, spread over the four warps of each quarter
+    {
+        const unsigned qrow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+        for (int g = warp >> 2; g < (int)(TC_STREAMS / 16); g += PPT / 128) pol::tm_zero16(qrow + 16u * (unsigned)g);
+    }
+    pol::tc_fence_before();
+    __syncthreads();
+    pol::tc_fence_after();
+    // this thread's stream, its thread and warp within the stream
+    const int s = warp / (SPT / 32), ts = tid - s * SPT, sw = warp - s * (SPT / 32);
+    StreamSmem &S = sm.st[s];
+    const unsigned TA = tc_acc(s), TY = tc_y(s);
     const int row = 32 * (warp & 3) + lane;         // TMEM lane = sample row (or unit row for dW)
-    const int part = warp >> 2;                     // this warp's column part of an epilogue
+    const int part = sw >> 2;                       // this warp's column part of an epilogue
     const int cb = part * (H / NQ), ce = cb + H / NQ;   // its columns of a 128-wide accumulator
     const unsigned lrow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
     bool ok = true;
@@ -237,47 +284,50 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     const float inv_b = 1.0f / (float)p.mb_size;
     const float *advp = p.adv + (long long)a * p.n_samples, *retp = p.ret + (long long)a * p.n_samples;
     const int *perm = p.perm + (long long)a * p.n_samples + p.mb_begin;
-    bool first = true;
-    // The tiles' samples are gathered one tile ahead: while a tile's
-    // contractions run, the next tile's sample indices, per-row data and
-    // observation rows are loaded, so their latency stays off the tile's chain.
+    bool worked = false;
+    // Stream s takes tiles blockIdx.x + (s + NS k) gridDim.x.  Its samples are
+    // gathered one tile ahead: while a tile's contractions run, the next
+    // tile's sample indices, per-row data and observation rows are loaded, so
+    // their latency stays off the tile's chain.
+    const int tile0 = (int)blockIdx.x + s * (int)gridDim.x, tstep = NS * (int)gridDim.x;
     float va[RPW], vb[RPW];
     int n_smp = -1;
     RowData nd{-1, 0, 0.0f, 0.0f, 0.0f};
-    if (blockIdx.x < n_tiles) {
-        if (tid < 128)
-            put_row_data(sm, tid, row_data(p, a, advp, retp, mean, istd,
-                                           (int)blockIdx.x * 128 + tid < p.mb_size ? perm[blockIdx.x * 128 + tid] : -1));
-        __syncthreads();
-        load_rows(p, sm, warp, lane, va, vb);
+    if (ok && tile0 < n_tiles) {
+        if (ts < 128)
+            put_row_data(S, ts, row_data(p, a, advp, retp, mean, istd,
+                                         tile0 * 128 + ts < p.mb_size ? perm[tile0 * 128 + ts] : -1));
+        stream_sync(s);
+        load_rows(p, S, sw, lane, va, vb);
     }
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int next = tile + (int)gridDim.x;
+    for (int tile = tile0; tile < n_tiles && ok; tile += tstep) {
+        const int next = tile + tstep;
         // ---- [X | 1] (scaled, bf16) from the rows loaded ahead; W1's column D
         // is zero, so the forward reads the same tile
 #pragma unroll
         for (int j = 0; j < RPW; j++) {
-            const int i = warp + (PPT / 32) * j;
-            const bool valid = sm.orow[i] >= 0;
+            const int i = sw + (SPT / 32) * j;
+            const bool valid = S.orow[i] >= 0;
 #pragma unroll
             for (int h2 = 0; h2 < 2; h2++) {
                 const int k = lane + 32 * h2;
                 if (k < Dp) {
                     float v = 0.0f;
                     if (valid) v = k < D ? (h2 ? vb[j] : va[j]) * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
-                    st_bf16(sm.x, cm_off(i, k, Dp), v);
+                    st_bf16(S.x, cm_off(i, k, Dp), v);
                 }
             }
         }
-        to_async();
+        to_async(s);
         // ---- U1 = X W1^T
-        if (tid == 0) gemm(tmem + TC_ACC, sm.x, Dp, false, sm.w1, Dp, false, Dp, H, false);
-        if (tid < 128) n_smp = next < n_tiles && next * 128 + tid < p.mb_size ? perm[next * 128 + tid] : -1;
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (ts == 0) gemm(tmem + TA, S.x, Dp, false, sm.w1, Dp, false, Dp, H, false);
+        if (ts < 128) n_smp = next < n_tiles && next * 128 + ts < p.mb_size ? perm[next * 128 + ts] : -1;
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
+        worked = true;
         // h1 = tanh(U1 + b1) -> [H1 | 1] (r2): this thread's row, 16-byte stores
         for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
-            pol::tm_ld32(lrow + TC_ACC + c0, v);
+            pol::tm_ld32(lrow + TA + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
                 unsigned w[4];
@@ -288,24 +338,24 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
                 }
-                *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, c0 + j, H1W)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(S.r2 + cm_off(row, c0 + j, H1W)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         if (part == NQ - 1) {   // the ones column (valid samples) and the zero padding of [H1 | 1]
             const bool valid = tile * 128 + row < p.mb_size;
             const __nv_bfloat162 one = __floats2bfloat162_rn(valid ? 1.0f : 0.0f, 0.0f);
             const unsigned o = *reinterpret_cast<const unsigned *>(&one);
-            *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, H, H1W)) = make_uint4(o, 0u, 0u, 0u);
-            *reinterpret_cast<uint4 *>(sm.r2 + cm_off(row, H + 8, H1W)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(S.r2 + cm_off(row, H, H1W)) = make_uint4(o, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(S.r2 + cm_off(row, H + 8, H1W)) = make_uint4(0u, 0u, 0u, 0u);
         }
-        to_async();
+        to_async(s);
         // ---- U2 = H1 W2^T
-        if (tid == 0) gemm(tmem + TC_ACC, sm.r2, H1W, false, sm.w2, H, false, H, H, false);
-        if (tid < 128) nd = row_data(p, a, advp, retp, mean, istd, n_smp);   // the next tile's, in flight
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (ts == 0) gemm(tmem + TA, S.r2, H1W, false, sm.w2, H, false, H, H, false);
+        if (ts < 128) nd = row_data(p, a, advp, retp, mean, istd, n_smp);   // the next tile's, in flight
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
         for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
-            pol::tm_ld32(lrow + TC_ACC + c0, v);
+            pol::tm_ld32(lrow + TA + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
                 unsigned w[4];
@@ -316,16 +366,16 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(h0, h1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
                 }
-                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(S.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        to_async();
+        to_async(s);
         // ---- Y = H2 W3^T, then the loss gradient dY per sample
-        if (tid == 0) gemm(tmem + TC_Y, sm.r1, H, false, sm.w3, H, false, H, 16, false);
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (ts == 0) gemm(tmem + TY, S.r1, H, false, sm.w3, H, false, H, 16, false);
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
         if (part == 0) {
-            float v[32];
-            pol::tm_ld32(lrow + TC_Y, v);   // columns 16..31 lie in dW3's accumulator: unused here
+            float v[16];
+            pol::tm_ld16(lrow + TY, v);
             const bool valid = tile * 128 + row < p.mb_size;
             float z[NA];
             float m = -INFINITY;
@@ -339,29 +389,29 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
 #pragma unroll
             for (int j = 0; j < NA; j++) se += __expf(z[j] - m);
             const float lse = m + __logf(se);
-            float pj[NA], lp[NA], S = 0.0f;
+            float pj[NA], lp[NA], Sent = 0.0f;
 #pragma unroll
             for (int j = 0; j < NA; j++) {
                 lp[j] = z[j] - lse;
                 pj[j] = __expf(lp[j]);
-                S -= pj[j] * lp[j];
+                Sent -= pj[j] * lp[j];
             }
-            const int act = sm.act[row];
+            const int act = S.act[row];
             float lpa = lp[0];
 #pragma unroll
             for (int j = 1; j < NA; j++)
                 if (j == act) lpa = lp[j];
-            const float rho = __expf(lpa - sm.lpo[row]);
-            const float An = sm.an[row];
+            const float rho = __expf(lpa - S.lpo[row]);
+            const float An = S.an[row];
             const float rc = fminf(fmaxf(rho, 1.0f - p.clip_eps), 1.0f + p.clip_eps);
             const float g_rho = (rho * An <= rc * An) ? -An : 0.0f;
             float dy[16];
 #pragma unroll
             for (int j = 0; j < NA; j++) {
                 const float pg = g_rho * rho * ((j == act ? 1.0f : 0.0f) - pj[j]);
-                dy[j] = valid ? (pg + p.ent_coef * pj[j] * (lp[j] + S)) * inv_b : 0.0f;
+                dy[j] = valid ? (pg + p.ent_coef * pj[j] * (lp[j] + Sent)) * inv_b : 0.0f;
             }
-            dy[NA] = valid ? p.vf_coef * (V - sm.rt[row]) * inv_b : 0.0f;
+            dy[NA] = valid ? p.vf_coef * (V - S.rt[row]) * inv_b : 0.0f;
 #pragma unroll
             for (int j = NA + 1; j < 16; j++) dy[j] = 0.0f;
             unsigned w[8];
@@ -370,33 +420,33 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                 const __nv_bfloat162 t2 = __floats2bfloat162_rn(dy[2 * q], dy[2 * q + 1]);
                 w[q] = *reinterpret_cast<const unsigned *>(&t2);
             }
-            *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4 *>(sm.dy + cm_off(row, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<uint4 *>(S.dy + cm_off(row, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(S.dy + cm_off(row, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
             // db3: the bf16-rounded dY the other products use, summed over the tile
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                float s = __bfloat162float(__float2bfloat16_rn(dy[j]));
+                float t = __bfloat162float(__float2bfloat16_rn(dy[j]));
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) atomicAdd(&sm.db3[j], s);
+                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) atomicAdd(&sm.db3[j], t);
             }
         }
-        to_async();
+        to_async(s);
         // ---- dH2 = dY W3 and dW3^T += H2^T dY (this tile's per-row data is no
         // longer read: the next tile's takes its place)
-        if (tid < 128) put_row_data(sm, tid, nd);
-        if (tid == 0) {
-            gemm(tmem + TC_ACC, sm.dy, 16, false, sm.w3, H, true, 16, H, false);      // W3^T: W3 read MN-major
-            gemm(tmem + TC_DW3, sm.r1, H, true, sm.dy, 16, true, 128, 16, !first);    // H2^T, dY^T: both MN-major
+        if (ts < 128) put_row_data(S, ts, nd);
+        if (ts == 0) {
+            gemm(tmem + TA, S.dy, 16, false, sm.w3, H, true, 16, H, false);        // W3^T: W3 read MN-major
+            gemm(tmem + TC_DW3, S.r1, H, true, S.dy, 16, true, 128, 16, true);     // H2^T, dY^T: both MN-major
         }
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
         // dU2 = dH2 (1 - h2^2): dU2 into r1 in place of H2
         for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
-            pol::tm_ld32(lrow + TC_ACC + c0, v);
+            pol::tm_ld32(lrow + TA + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
-                const uint4 hv = *reinterpret_cast<const uint4 *>(sm.r1 + cm_off(row, c0 + j, H));
+                const uint4 hv = *reinterpret_cast<const uint4 *>(S.r1 + cm_off(row, c0 + j, H));
                 const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w};
                 unsigned w[4];
 #pragma unroll
@@ -407,24 +457,24 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                     const __nv_bfloat162 t2 = __floats2bfloat162_rn(d0, d1);
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
                 }
-                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(S.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        to_async();
+        to_async(s);
         // ---- dH1 = dU2 W2 and dW2 += dU2^T [H1 | 1]; the next tile's rows in flight
-        load_rows(p, sm, warp, lane, va, vb);
-        if (tid == 0) {
-            gemm(tmem + TC_ACC, sm.r1, H, false, sm.w2, H, true, H, H, false);        // W2^T: W2 read MN-major
-            gemm(tmem + TC_DW2, sm.r1, H, true, sm.r2, H1W, true, 128, H1W, !first);  // dU2^T, [H1 | 1]^T
+        load_rows(p, S, sw, lane, va, vb);
+        if (ts == 0) {
+            gemm(tmem + TA, S.r1, H, false, sm.w2, H, true, H, H, false);          // W2^T: W2 read MN-major
+            gemm(tmem + TC_DW2, S.r1, H, true, S.r2, H1W, true, 128, H1W, true);   // dU2^T, [H1 | 1]^T
         }
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
         // dU1 = dH1 (1 - h1^2), h1 from [H1 | 1]: dU1 into r1 (this thread's row)
         for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
-            pol::tm_ld32(lrow + TC_ACC + c0, v);
+            pol::tm_ld32(lrow + TA + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
-                const uint4 hv = *reinterpret_cast<const uint4 *>(sm.r2 + cm_off(row, c0 + j, H1W));
+                const uint4 hv = *reinterpret_cast<const uint4 *>(S.r2 + cm_off(row, c0 + j, H1W));
                 const unsigned hw[4] = {hv.x, hv.y, hv.z, hv.w};
                 unsigned w[4];
 #pragma unroll
@@ -435,21 +485,26 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
                                                                     v[j + 2 * q + 1] * (1.0f - hb * hb));
                     w[q] = *reinterpret_cast<const unsigned *>(&t2);
                 }
-                *reinterpret_cast<uint4 *>(sm.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(S.r1 + cm_off(row, c0 + j, H)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        to_async();
+        to_async(s);
         // ---- dW1 += dU1^T [X | 1]
-        if (tid == 0) gemm(tmem + TC_DW1, sm.r1, H, true, sm.x, Dp, true, 128, Dp, !first);   // both MN-major
-        if (!(ok = mma_round(sm, phase, p, tid))) break;
-        first = false;
+        if (ts == 0) gemm(tmem + TC_DW1, S.r1, H, true, S.x, Dp, true, 128, Dp, true);   // both MN-major
+        if (!(ok = mma_round(S, s, phase, p, ts))) break;
     }
-    // ---- the CTA's weight gradients into the FP32 buffer
-    if (ok && !first) {
+    // ---- both streams done: the CTA's weight gradients into the FP32 buffer
+    // (all 16 warps: four per TMEM lane quarter, 32-column parts)
+    pol::tc_fence_before();
+    const bool all_ok = !__syncthreads_or(!ok);
+    const bool any = __syncthreads_or(worked);
+    pol::tc_fence_after();
+    if (all_ok && any) {
+        const int fp = warp >> 2;                    // flush part 0..3
         float *g = p.grad + (long long)a * p.wf32_stride;
         float *gW1 = g, *gb1 = g + H * D, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + NOUT * H;
         // dW1 (row = u1 unit): columns < D, column D = db1
-        for (int c0 = 32 * part; c0 < Dp; c0 += 32 * NQ) {
+        for (int c0 = 32 * fp; c0 < Dp; c0 += PPT / 4) {
             float v[32];
             pol::tm_ld32(lrow + TC_DW1 + c0, v);
 #pragma unroll
@@ -460,22 +515,20 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
         }
         // dW2 (row = u2 unit): columns < 128, column 128 = db2
-        for (int c0 = 32 * part; c0 < H1W; c0 += 32 * NQ) {
+        for (int c0 = 32 * fp; c0 < H1W; c0 += PPT / 4) {
             float v[32];
-            if (c0 + 32 <= 160) {
-                pol::tm_ld32(lrow + TC_DW2 + c0, v);
+            pol::tm_ld32(lrow + TC_DW2 + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int k = c0 + j;
-                    if (k < H) atomicAdd(&gW2[row * H + k], v[j]);
-                    else if (k == H) atomicAdd(&gb2[row], v[j]);
-                }
+            for (int j = 0; j < 32; j++) {
+                const int k = c0 + j;
+                if (k < H) atomicAdd(&gW2[row * H + k], v[j]);
+                else if (k == H) atomicAdd(&gb2[row], v[j]);
             }
         }
         // dW3^T (row = h2 unit, column = output)
-        if (part == 0) {
-            float v[32];
-            pol::tm_ld32(lrow + TC_DW3, v);
+        if (fp == 0) {
+            float v[16];
+            pol::tm_ld16(lrow + TC_DW3, v);
 #pragma unroll
             for (int o = 0; o < NOUT; o++) atomicAdd(&gW3[o * H + row], v[o]);
         }
@@ -498,16 +551,33 @@ __global__ void k_ppo_gae(const long long *rewards, const float *values, const u
     const int e = i / A, a = i - e * A;
     const long long ns = (long long)T * n;
     float nxt = 0.0f;
-    for (int t = T - 1; t >= 0; t--) {
-        const long long ra = ((long long)t * n + e) * A + a;
-        const float live = done[(long long)t * n + e] ? 0.0f : 1.0f;
-        const float r = reward_scale * (float)rewards[ra];
-        const float v = values[ra];
-        const float vn = values[((long long)(t + 1) * n + e) * A + a];
-        const float delta = r + gamma * live * vn - v;
-        nxt = delta + gamma * lam * live * nxt;
-        adv[(long long)a * ns + (long long)t * n + e] = nxt;
-        ret[(long long)a * ns + (long long)t * n + e] = nxt + v;
+    float vn = values[((long long)T * n + e) * A + a];   // the bootstrap value
+    // the loads do not depend on the recurrence: GU steps' worth are issued
+    // together, then the recurrence runs over them
+    constexpr int GU = 16;
+    for (int t0 = T - 1; t0 >= 0; t0 -= GU) {
+        float rr[GU], vv[GU], lv[GU];
+#pragma unroll
+        for (int u = 0; u < GU; u++) {
+            const int t = t0 - u;
+            if (t >= 0) {
+                const long long ra = ((long long)t * n + e) * A + a;
+                lv[u] = done[(long long)t * n + e] ? 0.0f : 1.0f;
+                rr[u] = reward_scale * (float)rewards[ra];
+                vv[u] = values[ra];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; u++) {
+            const int t = t0 - u;
+            if (t >= 0) {
+                const float delta = rr[u] + gamma * lv[u] * vn - vv[u];
+                nxt = delta + gamma * lam * lv[u] * nxt;
+                adv[(long long)a * ns + (long long)t * n + e] = nxt;
+                ret[(long long)a * ns + (long long)t * n + e] = nxt + vv[u];
+                vn = vv[u];
+            }
+        }
     }
 }
 
