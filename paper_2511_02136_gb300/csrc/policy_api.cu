@@ -34,7 +34,7 @@ struct lob_policy {
     float *d_adv = nullptr, *d_ret = nullptr;
     long long adv_cap = 0;                // samples per agent the advantage buffers hold
     float *d_stats = nullptr;             // [A][2]
-    double *d_acc = nullptr;              // [A][2] sums, then [A] squared norms after them
+    double *d_acc = nullptr;              // [A][2] sums, then [A] squared norms, then a block counter (zeroed between uses)
     long long adam_t = 0;
 };
 
@@ -161,7 +161,7 @@ static int ppo_setup(lob_policy *p, cudaStream_t s) {
     fail = fail || cudaMalloc(&p->d_v, P * 4) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_grad, P * 4) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_stats, (size_t)p->A * 2 * 4) != cudaSuccess;
-    fail = fail || cudaMalloc(&p->d_acc, (size_t)p->A * 3 * 8) != cudaSuccess;
+    fail = fail || cudaMalloc(&p->d_acc, ((size_t)p->A * 3 + 1) * 8) != cudaSuccess;
     if (fail) {
         cudaGetLastError();
         return LOB_ENOMEM;
@@ -201,9 +201,9 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     const int A = p->A;
     const long long P = p->wf32_stride;
     const int nenv_a = b->n_envs * A;
-    ppo::k_ppo_gae<<<(nenv_a + 127) / 128, 128, 0, s>>>(reinterpret_cast<const long long *>(b->d_rewards),
-                                                          b->d_values, b->d_done, b->T, b->n_envs, A, hp->gamma,
-                                                          hp->gae_lambda, hp->reward_scale, p->d_adv, p->d_ret);
+    ppo::k_ppo_gae<<<(nenv_a + ppo::GAE_PAIRS - 1) / ppo::GAE_PAIRS, ppo::GAE_PAIRS * ppo::GAE_CH, 0, s>>>(
+        reinterpret_cast<const long long *>(b->d_rewards), b->d_values, b->d_done, b->T, b->n_envs, A, hp->gamma,
+        hp->gae_lambda, hp->reward_scale, p->d_adv, p->d_ret);
     p->launches++;
     const int mb = (int)(N / hp->n_minibatches);
     int n_sm = 0, dev = 0;
@@ -222,14 +222,18 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     g.status = p->d_status; g.wait_budget = 2000000000LL;
     ppo::AdamParams ad = adam_params(p);
     ad.lr = hp->lr; ad.beta1 = hp->beta1; ad.beta2 = hp->beta2; ad.eps = hp->adam_eps; ad.max_norm = hp->max_grad_norm;
+    // the accumulators, their block counter and the gradient start at zero;
+    // from then on the kernels that read them zero them for the next minibatch
+    // (k_ppo_stats's last block the sums, squared norms and counter; k_ppo_adam
+    // the gradient)
+    unsigned *d_ctr = reinterpret_cast<unsigned *>(p->d_acc + 3 * A);
+    if (cudaMemsetAsync(p->d_acc, 0, ((size_t)A * 3 + 1) * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(p->d_grad, 0, (size_t)(P * A) * 4, s) != cudaSuccess)
+        return LOB_ECUDA;
     for (int k = 0; k < hp->n_minibatches; k++) {
         g.mb_begin = (long long)k * mb;
-        if (cudaMemsetAsync(p->d_acc, 0, (size_t)A * 3 * 8, s) != cudaSuccess ||
-            cudaMemsetAsync(p->d_grad, 0, (size_t)(P * A) * 4, s) != cudaSuccess)
-            return LOB_ECUDA;
-        ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A), 256, 0, s>>>(p->d_adv, b->d_perm, N,
-                                                                                               g.mb_begin, mb, p->d_acc);
-        ppo::k_ppo_stats_fin<<<1, 64, 0, s>>>(p->d_acc, A, mb, p->d_stats);
+        ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A), 256, 0, s>>>(
+            p->d_adv, b->d_perm, N, g.mb_begin, mb, A, p->d_acc, d_ctr, p->d_stats);
         ppo::k_ppo_grad<<<dim3(ctas, A), ppo::PPT, sizeof(ppo::GradSmem), s>>>(g);
         if (b->d_grad_out &&
             cudaMemcpyAsync(b->d_grad_out + (size_t)k * A * P, p->d_grad, (size_t)(P * A) * 4, cudaMemcpyDeviceToDevice,
@@ -240,7 +244,7 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
         ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)p->adam_t));
         ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)p->adam_t));
         ppo::k_ppo_adam<<<dim3(64, A), 256, 0, s>>>(ad);
-        p->launches += 5;
+        p->launches += 4;
     }
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }

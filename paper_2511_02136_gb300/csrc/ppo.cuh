@@ -542,48 +542,92 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     }
 }
 
-// Advantages and value targets (GAE), one thread per (agent, env), backwards
-// over the rollout: delta = r + gamma (1 - d) V' - V, A = delta + gamma lambda (1 - d) A'.
-__global__ void k_ppo_gae(const long long *rewards, const float *values, const unsigned char *done, int T, int n,
-                          int A, float gamma, float lam, float reward_scale, float *adv, float *ret) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * A) return;
-    const int e = i / A, a = i - e * A;
+// Advantages and value targets (GAE) over the rollout, backwards in t:
+// delta = r + gamma (1 - d) V' - V, A = delta + gamma lambda (1 - d) A'.  A
+// block takes GAE_PAIRS (agent, env) pairs, each split into GAE_CH chunks of
+// steps, one warp per chunk (lane = pair): every chunk composes its steps
+// into one affine map A_lo = P + Q A_hi, one warp chains the maps from
+// A_T = 0 to get each chunk's boundary value, and every chunk then runs the
+// recurrence over its own steps from that value (the rollout reads hit L2 the
+// second time).  Launch: ceil(n A / GAE_PAIRS) blocks of GAE_PAIRS * GAE_CH threads.
+constexpr int GAE_PAIRS = 32, GAE_CH = 8;
+__global__ void __launch_bounds__(GAE_PAIRS * GAE_CH) k_ppo_gae(const long long *rewards, const float *values,
+                                                                const unsigned char *done, int T, int n, int A,
+                                                                float gamma, float lam, float reward_scale,
+                                                                float *adv, float *ret) {
+    __shared__ float sP[GAE_CH][GAE_PAIRS], sQ[GAE_CH][GAE_PAIRS], sE[GAE_CH][GAE_PAIRS];
+    const int li = threadIdx.x % GAE_PAIRS, c = threadIdx.x / GAE_PAIRS;
+    const int i = blockIdx.x * GAE_PAIRS + li;
+    const bool on = i < n * A;
+    const int e = on ? i / A : 0, a = on ? i - e * A : 0;
     const long long ns = (long long)T * n;
-    float nxt = 0.0f;
-    float vn = values[((long long)T * n + e) * A + a];   // the bootstrap value
-    // the loads do not depend on the recurrence: GU steps' worth are issued
-    // together, then the recurrence runs over them
-    constexpr int GU = 16;
-    for (int t0 = T - 1; t0 >= 0; t0 -= GU) {
-        float rr[GU], vv[GU], lv[GU];
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            const int t = t0 - u;
-            if (t >= 0) {
-                const long long ra = ((long long)t * n + e) * A + a;
-                lv[u] = done[(long long)t * n + e] ? 0.0f : 1.0f;
-                rr[u] = reward_scale * (float)rewards[ra];
-                vv[u] = values[ra];
-            }
+    const int CH = (T + GAE_CH - 1) / GAE_CH;
+    const int t_lo = min(T, c * CH), t_hi = min(T, t_lo + CH);
+    float P = 0.0f, Q = 1.0f;
+    if (on) {
+        float vn = values[((long long)t_hi * n + e) * A + a];
+#pragma unroll 4
+        for (int t = t_hi - 1; t >= t_lo; t--) {
+            const long long ra = ((long long)t * n + e) * A + a;
+            const float live = done[(long long)t * n + e] ? 0.0f : 1.0f;
+            const float v = values[ra];
+            const float delta = reward_scale * (float)rewards[ra] + gamma * live * vn - v;
+            const float ct = gamma * lam * live;
+            P = delta + ct * P;
+            Q = ct * Q;
+            vn = v;
         }
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            const int t = t0 - u;
-            if (t >= 0) {
-                const float delta = rr[u] + gamma * lv[u] * vn - vv[u];
-                nxt = delta + gamma * lam * lv[u] * nxt;
-                adv[(long long)a * ns + (long long)t * n + e] = nxt;
-                ret[(long long)a * ns + (long long)t * n + e] = nxt + vv[u];
-                vn = vv[u];
-            }
+    }
+    sP[c][li] = P;
+    sQ[c][li] = Q;
+    __syncthreads();
+    if (c == 0) {
+        float A_end = 0.0f;   // A_T
+        for (int k = GAE_CH - 1; k >= 0; k--) {
+            sE[k][li] = A_end;
+            A_end = sP[k][li] + sQ[k][li] * A_end;
+        }
+    }
+    __syncthreads();
+    if (on) {
+        float nxt = sE[c][li];
+        float vn = values[((long long)t_hi * n + e) * A + a];
+#pragma unroll 4
+        for (int t = t_hi - 1; t >= t_lo; t--) {
+            const long long ra = ((long long)t * n + e) * A + a;
+            const float live = done[(long long)t * n + e] ? 0.0f : 1.0f;
+            const float v = values[ra];
+            const float delta = reward_scale * (float)rewards[ra] + gamma * live * vn - v;
+            nxt = delta + gamma * lam * live * nxt;
+            adv[(long long)a * ns + (long long)t * n + e] = nxt;
+            ret[(long long)a * ns + (long long)t * n + e] = nxt + v;
+            vn = v;
         }
     }
 }
 
-// Sum and sum of squares (FP64) of the minibatch's advantages per agent.
-__global__ void k_ppo_stats(const float *adv, const int *perm, long long ns, long long mb_begin, int mb_size,
-                            double *acc) {
+// Sum over a block of 256 threads (FP64), valid in thread 0.
+__device__ __forceinline__ double block_sum256(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; w++) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Sum and sum of squares (FP64) of the minibatch's advantages per agent (one
+// atomic pair per block), then, in the last block to finish, their mean and
+// 1 / (std + 1e-8) (population std) per agent; that block also zeroes the
+// sums and the squared-norm accumulators after them (acc[3A] doubles) and the
+// block counter for their next use.  Launch: blocks of 256 threads, grid (x, A).
+__global__ void __launch_bounds__(256) k_ppo_stats(const float *adv, const int *perm, long long ns, long long mb_begin,
+                                                   int mb_size, int A, double *acc, unsigned *ctr, float *stats) {
+    __shared__ double red[8];
+    __shared__ bool last;
     const int a = blockIdx.y;
     double s = 0.0, s2 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < mb_size; i += (long long)gridDim.x * blockDim.x) {
@@ -591,38 +635,43 @@ __global__ void k_ppo_stats(const float *adv, const int *perm, long long ns, lon
         s += v;
         s2 += v * v;
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
+    s = block_sum256(s, red);
+    s2 = block_sum256(s2, red);
+    if (threadIdx.x == 0) {
         atomicAdd(&acc[2 * a], s);
         atomicAdd(&acc[2 * a + 1], s2);
+        __threadfence();
+        last = atomicAdd(ctr, 1u) == gridDim.x * gridDim.y - 1;
     }
-}
-// mean and 1 / (std + 1e-8) (population std) from the sums.
-__global__ void k_ppo_stats_fin(const double *acc, int A, int mb_size, float *stats) {
-    const int a = threadIdx.x;
-    if (a >= A) return;
-    const double mean = acc[2 * a] / mb_size;
-    double var = acc[2 * a + 1] / mb_size - mean * mean;
-    var = var > 0.0 ? var : 0.0;
-    stats[2 * a] = (float)mean;
-    stats[2 * a + 1] = (float)(1.0 / (sqrt(var) + 1e-8));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < A) {
+        const int b = threadIdx.x;
+        const volatile double *va = acc;
+        const double mean = va[2 * b] / mb_size;
+        double var = va[2 * b + 1] / mb_size - mean * mean;
+        var = var > 0.0 ? var : 0.0;
+        stats[2 * b] = (float)mean;
+        stats[2 * b + 1] = (float)(1.0 / (sqrt(var) + 1e-8));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * A; k += blockDim.x) acc[k] = 0.0;
+    if (threadIdx.x == 0) *ctr = 0u;
 }
 
-// Squared L2 norm of each agent's gradient (FP64 sums).
-__global__ void k_ppo_sqnorm(const float *grad, long long P, double *out) {
+// Squared L2 norm of each agent's gradient (FP64 sums, one atomic per block).
+// Launch: blocks of 256 threads, grid (x, A).
+__global__ void __launch_bounds__(256) k_ppo_sqnorm(const float *grad, long long P, double *out) {
+    __shared__ double red[8];
     const int a = blockIdx.y;
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
         const double g = grad[(long long)a * P + i];
         s += g * g;
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&out[a], s);
+    s = block_sum256(s, red);
+    if (threadIdx.x == 0) atomicAdd(&out[a], s);
 }
 
 struct AdamParams {
@@ -630,7 +679,7 @@ struct AdamParams {
     long long P;
     float *w;                        // [A][P] master FP32 parameters
     float *m, *v;                    // [A][P] Adam moments
-    const float *grad;               // [A][P]
+    float *grad;                     // [A][P], zeroed here once read (the next minibatch accumulates into it)
     const double *sqnorm;            // [A]
     float lr, beta1, beta2, eps, max_norm;
     float bc1, bc2;                  // 1 - beta^t for this step
@@ -688,6 +737,7 @@ __global__ void k_ppo_adam(const AdamParams p) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += (long long)gridDim.x * blockDim.x) {
         const long long k = (long long)a * p.P + i;
         const float g = p.grad[k] * sc;
+        p.grad[k] = 0.0f;
         const float m = p.beta1 * p.m[k] + (1.0f - p.beta1) * g;
         const float v = p.beta2 * p.v[k] + (1.0f - p.beta2) * g * g;
         p.m[k] = m;
