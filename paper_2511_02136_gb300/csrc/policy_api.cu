@@ -31,6 +31,8 @@ struct lob_policy {
     unsigned char *d_wpk = nullptr;       // the update's packed weights (W1 with a zero bias column, W2, W3)
     long long wpk_stride = 0;
     float *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
+    float *d_gpart = nullptr;             // [A][gpart_ctas][P]: each gradient CTA's own weight gradients
+    int gpart_ctas = 0;
     float *d_adv = nullptr, *d_ret = nullptr;
     long long adv_cap = 0;                // samples per agent the advantage buffers hold
     float *d_stats = nullptr;             // [A][2]
@@ -120,7 +122,7 @@ extern "C" int lob_policy_create(int32_t n_agents, int32_t obs_dim, const float 
 extern "C" int lob_policy_destroy(lob_policy *p) {
     if (!p) return LOB_EINVAL;
     cudaDeviceSynchronize();
-    void *bufs[] = {p->d_wpack, p->d_wf32, p->d_status, p->d_wpk, p->d_m, p->d_v, p->d_grad,
+    void *bufs[] = {p->d_wpack, p->d_wf32, p->d_status, p->d_wpk, p->d_m, p->d_v, p->d_grad, p->d_gpart,
                     p->d_adv, p->d_ret, p->d_stats, p->d_acc};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -160,6 +162,13 @@ static int ppo_setup(lob_policy *p, cudaStream_t s) {
     fail = fail || cudaMalloc(&p->d_m, P * 4) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_v, P * 4) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_grad, P * 4) != cudaSuccess;
+    {
+        int n_sm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        p->gpart_ctas = std::max(1, n_sm / p->A);
+        fail = fail || cudaMalloc(&p->d_gpart, P * (size_t)p->gpart_ctas * 4) != cudaSuccess;
+    }
     fail = fail || cudaMalloc(&p->d_stats, (size_t)p->A * 2 * 4) != cudaSuccess;
     fail = fail || cudaMalloc(&p->d_acc, ((size_t)p->A * 3 + 1) * 8) != cudaSuccess;
     if (fail) {
@@ -210,36 +219,35 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (mb + 127) / 128;
-    // each CTA runs ppo::NS tile streams
-    const int ctas = std::max(1, std::min((tiles + ppo::NS - 1) / ppo::NS, n_sm / A > 0 ? n_sm / A : 1));
+    // each CTA runs ppo::NS tile streams and owns one slice of the partial-gradient buffer
+    const int ctas = std::max(1, std::min((tiles + ppo::NS - 1) / ppo::NS, std::min(p->gpart_ctas, n_sm / A > 0 ? n_sm / A : 1)));
     ppo::GradParams g;
     std::memset(&g, 0, sizeof(g));
     g.A = A; g.D = p->D; g.Dp = p->upd_Dp; g.L = p->L; g.n_envs = b->n_envs; g.n_samples = N;
     g.obs = b->d_obs; g.actions = b->d_actions; g.logp_old = b->d_logp_old; g.adv = p->d_adv; g.ret = p->d_ret;
     g.perm = b->d_perm; g.mb_size = mb; g.stats = p->d_stats;
     g.wpk = p->d_wpk; g.wpk_stride = p->wpk_stride; g.wf32 = p->d_wf32; g.wf32_stride = P;
-    g.grad = p->d_grad; g.clip_eps = hp->clip_eps; g.vf_coef = hp->vf_coef; g.ent_coef = hp->ent_coef;
+    g.gpart = p->d_gpart; g.gpart_ct = p->gpart_ctas; g.clip_eps = hp->clip_eps; g.vf_coef = hp->vf_coef; g.ent_coef = hp->ent_coef;
     g.status = p->d_status; g.wait_budget = 2000000000LL;
     ppo::AdamParams ad = adam_params(p);
     ad.lr = hp->lr; ad.beta1 = hp->beta1; ad.beta2 = hp->beta2; ad.eps = hp->adam_eps; ad.max_norm = hp->max_grad_norm;
-    // the accumulators, their block counter and the gradient start at zero;
-    // from then on the kernels that read them zero them for the next minibatch
-    // (k_ppo_stats's last block the sums, squared norms and counter; k_ppo_adam
-    // the gradient)
+    // the accumulators and their block counter start at zero; from then on
+    // k_ppo_stats's last block zeroes them (sums, squared norms, counter) for
+    // the next minibatch
     unsigned *d_ctr = reinterpret_cast<unsigned *>(p->d_acc + 3 * A);
-    if (cudaMemsetAsync(p->d_acc, 0, ((size_t)A * 3 + 1) * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(p->d_grad, 0, (size_t)(P * A) * 4, s) != cudaSuccess)
-        return LOB_ECUDA;
+    if (cudaMemsetAsync(p->d_acc, 0, ((size_t)A * 3 + 1) * 8, s) != cudaSuccess) return LOB_ECUDA;
+    const int red_blocks = (int)std::min<long long>(128, (P + 255) / 256);
     for (int k = 0; k < hp->n_minibatches; k++) {
         g.mb_begin = (long long)k * mb;
         ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A), 256, 0, s>>>(
             p->d_adv, b->d_perm, N, g.mb_begin, mb, A, p->d_acc, d_ctr, p->d_stats);
         ppo::k_ppo_grad<<<dim3(ctas, A), ppo::PPT, sizeof(ppo::GradSmem), s>>>(g);
+        ppo::k_ppo_reduce<<<dim3(red_blocks, A), 256, 0, s>>>(p->d_gpart, ctas, p->gpart_ctas, P, p->d_grad,
+                                                               p->d_acc + 2 * A);
         if (b->d_grad_out &&
             cudaMemcpyAsync(b->d_grad_out + (size_t)k * A * P, p->d_grad, (size_t)(P * A) * 4, cudaMemcpyDeviceToDevice,
                             s) != cudaSuccess)
             return LOB_ECUDA;
-        ppo::k_ppo_sqnorm<<<dim3(32, A), 256, 0, s>>>(p->d_grad, P, p->d_acc + 2 * A);
         p->adam_t++;
         ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)p->adam_t));
         ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)p->adam_t));

@@ -71,7 +71,8 @@ struct GradParams {
     long long wpk_stride;        // bytes per agent
     const float *wf32;           // per agent parameter block (biases read from here)
     long long wf32_stride;
-    float *grad;                 // [A][P] FP32, zeroed by the host before the launch
+    float *gpart;                // [A][gpart_ct][P] FP32: CTA x writes all of its agent's weight gradients to slice x
+    int gpart_ct;                // slices per agent (>= gridDim.x)
     float clip_eps, vf_coef, ent_coef;
     int *status;
     long long wait_budget;
@@ -284,7 +285,6 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
     const float inv_b = 1.0f / (float)p.mb_size;
     const float *advp = p.adv + (long long)a * p.n_samples, *retp = p.ret + (long long)a * p.n_samples;
     const int *perm = p.perm + (long long)a * p.n_samples + p.mb_begin;
-    bool worked = false;
     // Stream s takes tiles blockIdx.x + (s + NS k) gridDim.x.  Its samples are
     // gathered one tile ahead: while a tile's contractions run, the next
     // tile's sample indices, per-row data and observation rows are loaded, so
@@ -323,7 +323,6 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         if (ts == 0) gemm(tmem + TA, S.x, Dp, false, sm.w1, Dp, false, Dp, H, false);
         if (ts < 128) n_smp = next < n_tiles && next * 128 + ts < p.mb_size ? perm[next * 128 + ts] : -1;
         if (!(ok = mma_round(S, s, phase, p, ts))) break;
-        worked = true;
         // h1 = tanh(U1 + b1) -> [H1 | 1] (r2): this thread's row, 16-byte stores
         for (int c0 = cb; c0 < ce; c0 += 32) {
             float v[32];
@@ -493,15 +492,15 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         if (ts == 0) gemm(tmem + TC_DW1, S.r1, H, true, S.x, Dp, true, 128, Dp, true);   // both MN-major
         if (!(ok = mma_round(S, s, phase, p, ts))) break;
     }
-    // ---- both streams done: the CTA's weight gradients into the FP32 buffer
-    // (all 16 warps: four per TMEM lane quarter, 32-column parts)
+    // ---- both streams done: the CTA's weight gradients, plain stores into its
+    // own slice of the partial buffer (k_ppo_reduce sums the slices); all 16
+    // warps, four per TMEM lane quarter, 32-column parts
     pol::tc_fence_before();
-    const bool all_ok = !__syncthreads_or(!ok);
-    const bool any = __syncthreads_or(worked);
+    __syncthreads();
     pol::tc_fence_after();
-    if (all_ok && any) {
+    {
         const int fp = warp >> 2;                    // flush part 0..3
-        float *g = p.grad + (long long)a * p.wf32_stride;
+        float *g = p.gpart + ((long long)a * p.gpart_ct + blockIdx.x) * p.wf32_stride;
         float *gW1 = g, *gb1 = g + H * D, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H, *gb3 = gW3 + NOUT * H;
         // dW1 (row = u1 unit): columns < D, column D = db1
         for (int c0 = 32 * fp; c0 < Dp; c0 += PPT / 4) {
@@ -510,8 +509,8 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
 #pragma unroll
             for (int j = 0; j < 32; j++) {
                 const int k = c0 + j;
-                if (k < D) atomicAdd(&gW1[row * D + k], v[j]);
-                else if (k == D) atomicAdd(&gb1[row], v[j]);
+                if (k < D) gW1[row * D + k] = v[j];
+                else if (k == D) gb1[row] = v[j];
             }
         }
         // dW2 (row = u2 unit): columns < 128, column 128 = db2
@@ -521,8 +520,8 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
 #pragma unroll
             for (int j = 0; j < 32; j++) {
                 const int k = c0 + j;
-                if (k < H) atomicAdd(&gW2[row * H + k], v[j]);
-                else if (k == H) atomicAdd(&gb2[row], v[j]);
+                if (k < H) gW2[row * H + k] = v[j];
+                else if (k == H) gb2[row] = v[j];
             }
         }
         // dW3^T (row = h2 unit, column = output)
@@ -530,9 +529,9 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             float v[16];
             pol::tm_ld16(lrow + TC_DW3, v);
 #pragma unroll
-            for (int o = 0; o < NOUT; o++) atomicAdd(&gW3[o * H + row], v[o]);
+            for (int o = 0; o < NOUT; o++) gW3[o * H + row] = v[o];
         }
-        if (tid < NOUT) atomicAdd(&gb3[tid], sm.db3[tid]);
+        if (tid < NOUT) gb3[tid] = sm.db3[tid];
     }
     pol::tc_fence_before();
     __syncthreads();
@@ -660,18 +659,29 @@ __global__ void __launch_bounds__(256) k_ppo_stats(const float *adv, const int *
     if (threadIdx.x == 0) *ctr = 0u;
 }
 
-// Squared L2 norm of each agent's gradient (FP64 sums, one atomic per block).
-// Launch: blocks of 256 threads, grid (x, A).
-__global__ void __launch_bounds__(256) k_ppo_sqnorm(const float *grad, long long P, double *out) {
+// Each agent's gradient: the sum over the n_ct gradient CTAs' slices of the
+// partial buffer ([A][stride_ct][P]), and its squared L2 norm (FP64 sums, one
+// atomic per block into sqnorm[a]).  Launch: blocks of 256 threads, grid (x, A).
+__global__ void __launch_bounds__(256) k_ppo_reduce(const float *gpart, int n_ct, int stride_ct, long long P,
+                                                    float *grad, double *sqnorm) {
     __shared__ double red[8];
     const int a = blockIdx.y;
-    double s = 0.0;
+    const float *src = gpart + (long long)a * stride_ct * P;
+    double sq = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
-        const double g = grad[(long long)a * P + i];
-        s += g * g;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int c = 0;
+        for (; c + 4 <= n_ct; c += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc[u] += src[(long long)(c + u) * P + i];
+        }
+        for (; c < n_ct; c++) acc[0] += src[(long long)c * P + i];
+        const float gsum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        grad[(long long)a * P + i] = gsum;
+        sq += (double)gsum * gsum;
     }
-    s = block_sum256(s, red);
-    if (threadIdx.x == 0) atomicAdd(&out[a], s);
+    sq = block_sum256(sq, red);
+    if (threadIdx.x == 0) atomicAdd(&sqnorm[a], sq);
 }
 
 struct AdamParams {
@@ -679,7 +689,7 @@ struct AdamParams {
     long long P;
     float *w;                        // [A][P] master FP32 parameters
     float *m, *v;                    // [A][P] Adam moments
-    float *grad;                     // [A][P], zeroed here once read (the next minibatch accumulates into it)
+    const float *grad;               // [A][P]
     const double *sqnorm;            // [A]
     float lr, beta1, beta2, eps, max_norm;
     float bc1, bc2;                  // 1 - beta^t for this step
@@ -737,7 +747,6 @@ __global__ void k_ppo_adam(const AdamParams p) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.P; i += (long long)gridDim.x * blockDim.x) {
         const long long k = (long long)a * p.P + i;
         const float g = p.grad[k] * sc;
-        p.grad[k] = 0.0f;
         const float m = p.beta1 * p.m[k] + (1.0f - p.beta1) * g;
         const float v = p.beta2 * p.v[k] + (1.0f - p.beta2) * g * g;
         p.m[k] = m;
