@@ -669,11 +669,15 @@ __global__ void __launch_bounds__(256) k_ppo_reduce(const float *gpart, int n_ct
     const float *src = gpart + (long long)a * stride_ct * P;
     double sq = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        // 16 slices' loads in flight at a time
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         int c = 0;
-        for (; c + 4 <= n_ct; c += 4) {
+        for (; c + 16 <= n_ct; c += 16) {
+            float t[16];
 #pragma unroll
-            for (int u = 0; u < 4; u++) acc[u] += src[(long long)(c + u) * P + i];
+            for (int u = 0; u < 16; u++) t[u] = src[(long long)(c + u) * P + i];
+#pragma unroll
+            for (int u = 0; u < 16; u++) acc[u & 3] += t[u];
         }
         for (; c < n_ct; c++) acc[0] += src[(long long)c * P + i];
         const float gsum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
