@@ -7,14 +7,15 @@
 // clipping to a global L2 norm and Adam (Kingma & Ba 2015).  Per minibatch:
 //
 //   k_ppo_gae      (once per update) advantages and value targets per
-//                  (agent, env), backwards over the rollout;
+//                  (agent, env), backwards over the rollout as a chunked scan;
 //   k_ppo_stats    mean and 1 / (std + 1e-8) of the minibatch's advantages;
 //   k_ppo_grad     forward, loss gradient and backward of 128-sample tiles on
 //                  the tensor cores (tcgen05, BF16 operands, FP32 TMEM
-//                  accumulators), the weight gradients accumulated in TMEM
-//                  over all tiles a CTA takes, then added to the FP32
-//                  gradient buffer;
-//   k_ppo_sqnorm   the squared global gradient norm per agent;
+//                  accumulators) in two tile streams per CTA, the weight
+//                  gradients accumulated in TMEM over all tiles a CTA takes,
+//                  then stored into the CTA's slice of a partial buffer;
+//   k_ppo_reduce   the slices summed into the gradient, and its squared
+//                  global norm per agent;
 //   k_ppo_adam     clip, Adam, and the BF16 repack of the new weights for
 //                  both this update and the rollout's forward.
 //
