@@ -414,9 +414,14 @@ int lob_create(const lob_config *cfg, const int32_t *h_caps, lob_handle **out) {
     for (int k = 0; k < NCLASS; k++) h->n_active_classes += h->class_count[k] > 0;
     if (h->n_active_classes > 1) {
         rc |= cuda_ok(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        // larger classes (longer per-message chains) on higher-priority streams:
+        // the block scheduler places their blocks first
+        int prio_least = 0, prio_greatest = 0;
+        rc |= cuda_ok(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
         for (int k = 0; k < NCLASS; k++) {
             if (h->class_count[k] == 0) continue;
-            rc |= cuda_ok(cudaStreamCreateWithFlags(&h->cls_stream[k], cudaStreamNonBlocking));
+            const int prio = std::max(prio_greatest, prio_least - k);
+            rc |= cuda_ok(cudaStreamCreateWithPriority(&h->cls_stream[k], cudaStreamNonBlocking, prio));
             rc |= cuda_ok(cudaEventCreateWithFlags(&h->cls_done[k], cudaEventDisableTiming));
         }
     }
@@ -777,7 +782,8 @@ static int launch_steps(lob_handle *h, const lob_msg *msgs, const int64_t *offse
     }
     const bool fork = h->n_active_classes > 1;
     if (fork && cudaEventRecord(h->ev_fork, s) != cudaSuccess) return LOB_ECUDA;
-    for (int k = 0; k < NCLASS; k++) {
+    // the largest class first: its envs have the longest per-message chains
+    for (int k = NCLASS - 1; k >= 0; k--) {
         const int cnt = h->class_count[k];
         if (cnt == 0) continue;
         cudaStream_t ks = s;
