@@ -12,7 +12,10 @@
 namespace lobk {
 // K >= 8: every instance in the wide register budget; K <= 4: the plain and
 // extended kernels in both budgets (the host picks by batch size), the traced
-// one wide.  The dispatch is a template so that the branches of the other
+// one wide.  For launches of several waves K = 4 takes a fixed budget: 168
+// registers for the extended kernel (three 4-warp blocks per SM), 128 for the
+// plain one (16 warps per SM instead of the 12 its own 158 registers leave;
+// it spills a few hundred bytes and still measured 2.7 % faster at 16,384 envs).  The dispatch is a template so that the branches of the other
 // case are never instantiated.
 template <int KK, bool ALWAYS_WIDE = (KK >= 8)>
 struct StepLaunch {
@@ -34,6 +37,7 @@ struct StepLaunch {
                 else k_env_steps<KK, false, true><<<blocks, threads, smem, s>>>(p);
             }
             else if (wide) k_env_steps_wide<KK, false, false><<<blocks, threads, smem, s>>>(p);
+            else if constexpr (KK == 4) k_env_steps_nreg<KK, false, false, false, 128><<<blocks, threads, smem, s>>>(p);
             else k_env_steps<KK, false, false><<<blocks, threads, smem, s>>>(p);
         }
         return cudaGetLastError();
@@ -53,6 +57,8 @@ struct StepLaunch {
                 if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, true>, A, b);
             }
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps<KK, false, false>, A, b);
+            if constexpr (KK == 4)
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_env_steps_nreg<KK, false, false, false, 128>, A, b);
         }
         return e;
     }
