@@ -422,13 +422,29 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
             }
             *reinterpret_cast<uint4 *>(S.dy + cm_off(row, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4 *>(S.dy + cm_off(row, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-            // db3: the bf16-rounded dY the other products use, summed over the tile
+            // db3: the bf16-rounded dY the other products use, summed over the
+            // tile by a reduce-scatter butterfly (each step halves the columns a
+            // lane carries: 16 shuffles for the 16 columns), then one atomic
+            // per column from the even lanes
+            {
+                float r16[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                float t = __bfloat162float(__float2bfloat16_rn(dy[j]));
+                for (int j = 0; j < 16; j++) r16[j] = __bfloat162float(__float2bfloat16_rn(dy[j]));
+                float r8[8], r4[4], r2[2];
+                const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == 0) atomicAdd(&sm.db3[j], t);
+                for (int j = 0; j < 8; j++)
+                    r8[j] = (b4 ? r16[j + 8] : r16[j]) + __shfl_xor_sync(0xffffffffu, b4 ? r16[j] : r16[j + 8], 16);
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    r4[j] = (b3 ? r8[j + 4] : r8[j]) + __shfl_xor_sync(0xffffffffu, b3 ? r8[j] : r8[j + 4], 8);
+#pragma unroll
+                for (int j = 0; j < 2; j++)
+                    r2[j] = (b2 ? r4[j + 2] : r4[j]) + __shfl_xor_sync(0xffffffffu, b2 ? r4[j] : r4[j + 2], 4);
+                float r1 = (b1 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? r2[0] : r2[1], 2);
+                r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+                const int col = (b4 ? 8 : 0) + (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+                if ((lane & 1) == 0) atomicAdd(&sm.db3[col], r1);
             }
         }
         to_async(s);
