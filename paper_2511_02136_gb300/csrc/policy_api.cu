@@ -35,8 +35,9 @@ struct lob_policy {
     int gpart_ctas = 0;
     float *d_adv = nullptr, *d_ret = nullptr;
     long long adv_cap = 0;                // samples per agent the advantage buffers hold
-    float *d_stats = nullptr;             // [A][2]
-    double *d_acc = nullptr;              // [A][2] sums, then [A] squared norms, then a block counter (zeroed between uses)
+    int mb_cap = 0;                       // minibatches the statistics buffers hold
+    float *d_stats = nullptr;             // [mb][A][2]: mean, 1 / (std + 1e-8) of each minibatch's advantages
+    double *d_acc = nullptr;              // [mb][A][2] sums, [mb][A] squared norms, [mb] block counters; zeroed per update
     long long adam_t = 0;
 };
 
@@ -143,7 +144,7 @@ static ppo::AdamParams adam_params(lob_policy *p) {
     a.A = p->A; a.D = p->D; a.Dp = p->upd_Dp; a.Dpf = p->Dp;
     a.P = p->wf32_stride;
     a.w = p->d_wf32; a.m = p->d_m; a.v = p->d_v; a.grad = p->d_grad;
-    a.sqnorm = p->d_acc + 2 * p->A;
+    a.sqnorm = nullptr;   // per minibatch, set by the update
     a.wpk = p->d_wpk; a.wpk_stride = p->wpk_stride;
     a.wfwd = p->d_wpack; a.wfwd_stride = p->wpack_stride;
     return a;
@@ -169,8 +170,7 @@ static int ppo_setup(lob_policy *p, cudaStream_t s) {
         p->gpart_ctas = std::max(1, n_sm / p->A);
         fail = fail || cudaMalloc(&p->d_gpart, P * (size_t)p->gpart_ctas * 4) != cudaSuccess;
     }
-    fail = fail || cudaMalloc(&p->d_stats, (size_t)p->A * 2 * 4) != cudaSuccess;
-    fail = fail || cudaMalloc(&p->d_acc, ((size_t)p->A * 3 + 1) * 8) != cudaSuccess;
+
     if (fail) {
         cudaGetLastError();
         return LOB_ENOMEM;
@@ -195,6 +195,20 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ppo_setup(p, s);
     if (rc != LOB_OK) return rc;
+    const int nmb = hp->n_minibatches;
+    if (p->mb_cap < nmb) {
+        if (p->d_stats) cudaFree(p->d_stats);
+        if (p->d_acc) cudaFree(p->d_acc);
+        p->d_stats = nullptr;
+        p->d_acc = nullptr;
+        p->mb_cap = 0;
+        if (cudaMalloc(&p->d_stats, (size_t)nmb * p->A * 2 * 4) != cudaSuccess ||
+            cudaMalloc(&p->d_acc, (size_t)nmb * (p->A * 3 + 1) * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return LOB_ENOMEM;
+        }
+        p->mb_cap = nmb;
+    }
     if (p->adv_cap < N) {
         if (p->d_adv) cudaFree(p->d_adv);
         if (p->d_ret) cudaFree(p->d_ret);
@@ -231,19 +245,21 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
     g.status = p->d_status; g.wait_budget = 2000000000LL;
     ppo::AdamParams ad = adam_params(p);
     ad.lr = hp->lr; ad.beta1 = hp->beta1; ad.beta2 = hp->beta2; ad.eps = hp->adam_eps; ad.max_norm = hp->max_grad_norm;
-    // the accumulators and their block counter start at zero; from then on
-    // k_ppo_stats's last block zeroes them (sums, squared norms, counter) for
-    // the next minibatch
-    unsigned *d_ctr = reinterpret_cast<unsigned *>(p->d_acc + 3 * A);
-    if (cudaMemsetAsync(p->d_acc, 0, ((size_t)A * 3 + 1) * 8, s) != cudaSuccess) return LOB_ECUDA;
+    // every minibatch's statistics in one launch after GAE; the sums, squared
+    // norms and block counters of all minibatches start at zero
+    double *d_sums = p->d_acc, *d_sq = p->d_acc + (size_t)nmb * 2 * A;
+    unsigned *d_ctr = reinterpret_cast<unsigned *>(p->d_acc + (size_t)nmb * 3 * A);
+    if (cudaMemsetAsync(p->d_acc, 0, (size_t)nmb * (A * 3 + 1) * 8, s) != cudaSuccess) return LOB_ECUDA;
+    ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A, nmb), 256, 0, s>>>(
+        p->d_adv, b->d_perm, N, mb, A, d_sums, d_ctr, p->d_stats);
+    p->launches++;
     const int red_blocks = (int)std::min<long long>(128, (P + 255) / 256);
-    for (int k = 0; k < hp->n_minibatches; k++) {
+    for (int k = 0; k < nmb; k++) {
         g.mb_begin = (long long)k * mb;
-        ppo::k_ppo_stats<<<dim3(std::max(1, std::min(64, (mb + 255) / 256)), A), 256, 0, s>>>(
-            p->d_adv, b->d_perm, N, g.mb_begin, mb, A, p->d_acc, d_ctr, p->d_stats);
+        g.stats = p->d_stats + (size_t)k * 2 * A;
         ppo::k_ppo_grad<<<dim3(ctas, A), ppo::PPT, sizeof(ppo::GradSmem), s>>>(g);
         ppo::k_ppo_reduce<<<dim3(red_blocks, A), 256, 0, s>>>(p->d_gpart, ctas, p->gpart_ctas, P, p->d_grad,
-                                                               p->d_acc + 2 * A);
+                                                               d_sq + (size_t)k * A);
         if (b->d_grad_out &&
             cudaMemcpyAsync(b->d_grad_out + (size_t)k * A * P, p->d_grad, (size_t)(P * A) * 4, cudaMemcpyDeviceToDevice,
                             s) != cudaSuccess)
@@ -251,8 +267,9 @@ extern "C" int lob_ppo_update(lob_policy *p, const lob_ppo_batch *b, const lob_p
         p->adam_t++;
         ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)p->adam_t));
         ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)p->adam_t));
+        ad.sqnorm = d_sq + (size_t)k * A;
         ppo::k_ppo_adam<<<dim3(64, A), 256, 0, s>>>(ad);
-        p->launches += 4;
+        p->launches += 3;
     }
     return cudaGetLastError() == cudaSuccess ? LOB_OK : LOB_ECUDA;
 }

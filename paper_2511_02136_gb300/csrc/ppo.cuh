@@ -8,7 +8,8 @@
 //
 //   k_ppo_gae      (once per update) advantages and value targets per
 //                  (agent, env), backwards over the rollout as a chunked scan;
-//   k_ppo_stats    mean and 1 / (std + 1e-8) of the minibatch's advantages;
+//   k_ppo_stats    (once per update) mean and 1 / (std + 1e-8) of every
+//                  minibatch's advantages;
 //   k_ppo_grad     forward, loss gradient and backward of 128-sample tiles on
 //                  the tensor cores (tcgen05, BF16 operands, FP32 TMEM
 //                  accumulators) in two tile streams per CTA, the weight
@@ -635,16 +636,20 @@ __device__ __forceinline__ double block_sum256(double v, double *red) {
     return t;
 }
 
-// Sum and sum of squares (FP64) of the minibatch's advantages per agent (one
-// atomic pair per block), then, in the last block to finish, their mean and
-// 1 / (std + 1e-8) (population std) per agent; that block also zeroes the
-// sums and the squared-norm accumulators after them (acc[3A] doubles) and the
-// block counter for their next use.  Launch: blocks of 256 threads, grid (x, A).
-__global__ void __launch_bounds__(256) k_ppo_stats(const float *adv, const int *perm, long long ns, long long mb_begin,
-                                                   int mb_size, int A, double *acc, unsigned *ctr, float *stats) {
+// Sum and sum of squares (FP64) of every minibatch's advantages per agent
+// (blockIdx.z = minibatch, of mb_size consecutive positions of the sample
+// order; one atomic pair per block), then, in the last block of a minibatch
+// to finish, their mean and 1 / (std + 1e-8) (population std) per agent.
+// acc: [n_mb][A][2] sums, zeroed before the launch; ctr: [n_mb] block counters,
+// zeroed before the launch; stats: [n_mb][A][2].  Launch: blocks of 256
+// threads, grid (x, A, n_mb), once per epoch after GAE.
+__global__ void __launch_bounds__(256) k_ppo_stats(const float *adv, const int *perm, long long ns, int mb_size, int A,
+                                                   double *acc, unsigned *ctr, float *stats) {
     __shared__ double red[8];
     __shared__ bool last;
-    const int a = blockIdx.y;
+    const int a = blockIdx.y, k = blockIdx.z;
+    const long long mb_begin = (long long)k * mb_size;
+    double *acc_k = acc + (long long)k * 2 * A;
     double s = 0.0, s2 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < mb_size; i += (long long)gridDim.x * blockDim.x) {
         const double v = adv[(long long)a * ns + perm[(long long)a * ns + mb_begin + i]];
@@ -654,26 +659,23 @@ __global__ void __launch_bounds__(256) k_ppo_stats(const float *adv, const int *
     s = block_sum256(s, red);
     s2 = block_sum256(s2, red);
     if (threadIdx.x == 0) {
-        atomicAdd(&acc[2 * a], s);
-        atomicAdd(&acc[2 * a + 1], s2);
+        atomicAdd(&acc_k[2 * a], s);
+        atomicAdd(&acc_k[2 * a + 1], s2);
         __threadfence();
-        last = atomicAdd(ctr, 1u) == gridDim.x * gridDim.y - 1;
+        last = atomicAdd(ctr + k, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     if (threadIdx.x < A) {
         const int b = threadIdx.x;
-        const volatile double *va = acc;
+        const volatile double *va = acc_k;
         const double mean = va[2 * b] / mb_size;
         double var = va[2 * b + 1] / mb_size - mean * mean;
         var = var > 0.0 ? var : 0.0;
-        stats[2 * b] = (float)mean;
-        stats[2 * b + 1] = (float)(1.0 / (sqrt(var) + 1e-8));
+        stats[((long long)k * A + b) * 2] = (float)mean;
+        stats[((long long)k * A + b) * 2 + 1] = (float)(1.0 / (sqrt(var) + 1e-8));
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 3 * A; k += blockDim.x) acc[k] = 0.0;
-    if (threadIdx.x == 0) *ctr = 0u;
 }
 
 // Each agent's gradient: the sum over the n_ct gradient CTAs' slices of the
