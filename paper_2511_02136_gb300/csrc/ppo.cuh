@@ -210,7 +210,7 @@ __device__ __forceinline__ void put_row_data(StreamSmem &sm, int i, const RowDat
 }
 constexpr int RPW = 128 / (SPT / 32);   // tile rows per warp of a stream
 // This warp's observation rows (sw, sw + 8, ...) of the tile sm.orow names,
-// features lane and lane + 32, all loads issued before any is used.
+// features 2 lane and 2 lane + 1, all loads issued before any is used.
 __device__ __forceinline__ void load_rows(const GradParams &p, const StreamSmem &sm, int sw, int lane,
                                           float (&va)[RPW], float (&vb)[RPW]) {
     const int D = p.D;
@@ -218,8 +218,8 @@ __device__ __forceinline__ void load_rows(const GradParams &p, const StreamSmem 
     for (int j = 0; j < RPW; j++) {
         const long long ra = sm.orow[sw + (SPT / 32) * j];
         const float *o = p.obs + (ra < 0 ? 0 : ra) * (long long)D;
-        va[j] = (ra >= 0 && lane < D) ? o[lane] : 0.0f;
-        vb[j] = (ra >= 0 && lane + 32 < D) ? o[lane + 32] : 0.0f;
+        va[j] = (ra >= 0 && 2 * lane < D) ? o[2 * lane] : 0.0f;
+        vb[j] = (ra >= 0 && 2 * lane + 1 < D) ? o[2 * lane + 1] : 0.0f;
     }
 }
 
@@ -306,17 +306,21 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
         const int next = tile + tstep;
         // ---- [X | 1] (scaled, bf16) from the rows loaded ahead; W1's column D
         // is zero, so the forward reads the same tile
+        // features 2 lane and 2 lane + 1 of each of this warp's rows: one
+        // 4-byte store of the bf16 pair (adjacent in the core-matrix row)
+        {
+            const int k0 = 2 * lane, k1 = 2 * lane + 1;
+            const float s0 = k0 < D ? pol::obs_scale(k0, p.L) : 0.0f, s1 = k1 < D ? pol::obs_scale(k1, p.L) : 0.0f;
+            const float c0 = k0 == D ? 1.0f : 0.0f, c1 = k1 == D ? 1.0f : 0.0f;   // the ones column
 #pragma unroll
-        for (int j = 0; j < RPW; j++) {
-            const int i = sw + (SPT / 32) * j;
-            const bool valid = S.orow[i] >= 0;
-#pragma unroll
-            for (int h2 = 0; h2 < 2; h2++) {
-                const int k = lane + 32 * h2;
-                if (k < Dp) {
-                    float v = 0.0f;
-                    if (valid) v = k < D ? (h2 ? vb[j] : va[j]) * pol::obs_scale(k, p.L) : (k == D ? 1.0f : 0.0f);
-                    st_bf16(S.x, cm_off(i, k, Dp), v);
+            for (int j = 0; j < RPW; j++) {
+                const int i = sw + (SPT / 32) * j;
+                if (k0 < Dp) {
+                    const bool valid = S.orow[i] >= 0;
+                    const float v0 = valid ? (k0 < D ? va[j] * s0 : c0) : 0.0f;
+                    const float v1 = valid ? (k1 < D ? vb[j] * s1 : c1) : 0.0f;
+                    const __nv_bfloat162 t2 = __floats2bfloat162_rn(v0, v1);
+                    *reinterpret_cast<__nv_bfloat162 *>(S.x + cm_off(i, k0, Dp)) = t2;
                 }
             }
         }
