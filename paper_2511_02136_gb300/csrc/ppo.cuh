@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(PPT, 1) k_ppo_grad(const GradParams p) {
 // A_T = 0 to get each chunk's boundary value, and every chunk then runs the
 // recurrence over its own steps from that value (the rollout reads hit L2 the
 // second time).  Launch: ceil(n A / GAE_PAIRS) blocks of GAE_PAIRS * GAE_CH threads.
-constexpr int GAE_PAIRS = 32, GAE_CH = 8;
+constexpr int GAE_PAIRS = 32, GAE_CH = 16;
 __global__ void __launch_bounds__(GAE_PAIRS * GAE_CH) k_ppo_gae(const long long *rewards, const float *values,
                                                                 const unsigned char *done, int T, int n, int A,
                                                                 float gamma, float lam, float reward_scale,
